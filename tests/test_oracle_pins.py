@@ -1,0 +1,505 @@
+"""Pins of the CPU oracle against what the scheme and the mathematics fix.
+
+None of these re-type the oracle's formulas.  Each compares the oracle with a
+closed form, an invariant, a limit that reduces to a textbook routine, or the
+Navier-Stokes transport coefficients the scheme is built to reproduce
+(arXiv:2208.09132 Sec. 2: tau_g = mu/p, Pr = tau_g/tau_b):
+
+  quadrature / equilibria   closed-form moments of the Maxwellian
+  van Leer (eq. VanLeer)    the harmonic-mean form 2ab/(a+b)
+  fixed point               a uniform Maxwellian never changes
+  conservation              periodic domains conserve rho, rho u, rho E
+  specular walls            mirror-image method on a doubled periodic domain
+  free streaming (tau->inf) textbook MUSCL-Hancock advection per velocity;
+                            2nd-order convergence to the exact shift
+  Euler limit (Sec. 3.1)    exact Riemann solution of the Sod tube
+  NS limit                  shear-wave decay exp(-nu k^2 t) (eq. NSshear),
+                            sound damping (k^2/2)[(4/3)nu + zeta/rho + (gamma-1)chi],
+                            isobaric entropy-mode decay chi k^2, chi = mu/(rho Pr),
+                            and the same sound damping seen from a moving frame
+  dimensional reduction     a y-uniform 2D run equals the 1D run; transposed
+                            data give transposed results; mirrored data give
+                            mirrored results
+"""
+import math
+
+import numpy as np
+import pytest
+
+import refs
+from paper_2208_09132_gb300 import workloads as wl
+
+R = 0.5
+
+
+def cplx_amp(f, x, k):
+    return 2.0 * np.sum((f - f.mean()) * np.exp(-1j * k * x)) / f.size
+
+
+# ------------------------------------------------------------------ quadrature
+
+def test_trapezoid_weights_closed_forms(oracle_mod):
+    x, w = oracle_mod.vgrid_1d(33, -4.0, 4.0, oracle_mod.RULE_TRAPEZOID)
+    assert x[0] == -4.0 and x[-1] == 4.0
+    assert abs(w.sum() - 8.0) < 1e-14
+    assert abs((w * x).sum()) < 1e-14
+    # trapezoid on a Gaussian over +-8 sigma: spectrally accurate
+    x, w = oracle_mod.vgrid_1d(64, -8.0, 8.0, oracle_mod.RULE_TRAPEZOID)
+    gauss = np.exp(-x * x / 2)
+    assert abs((w * gauss).sum() - math.sqrt(2 * math.pi)) < 1e-12
+    assert abs((w * x * x * gauss).sum() - math.sqrt(2 * math.pi)) < 1e-12
+    assert abs((w * x ** 4 * gauss).sum() - 3 * math.sqrt(2 * math.pi)) < 5e-11   # tail beyond 8 sigma ~ 1.3e-11
+
+
+def test_boole_weights_closed_forms(oracle_mod):
+    x, w = oracle_mod.vgrid_1d(17, -2.0, 2.0, oracle_mod.RULE_BOOLE)
+    for p in range(6):    # exact for polynomials of degree <= 5
+        exact = (2.0 ** (p + 1) - (-2.0) ** (p + 1)) / (p + 1)
+        assert abs((w * x ** p).sum() - exact) < 1e-12
+    # degree 6 is not exact on coarse panels
+    assert abs((w * x ** 6).sum() - 2 * 2.0 ** 7 / 7) > 1e-6
+    with pytest.raises(ValueError):
+        oracle_mod.vgrid_1d(16, -2.0, 2.0, oracle_mod.RULE_BOOLE)
+
+
+# ------------------------------------------------------------------- van Leer
+
+def test_vanleer_is_harmonic_mean(oracle_mod):
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=400) * np.exp(rng.uniform(-5, 5, 400))
+    b = rng.normal(size=400) * np.exp(rng.uniform(-5, 5, 400))
+    a[:20] = 0.0
+    b[10:30] = 0.0
+    got = np.array([oracle_mod.vanleer(x, y) for x, y in zip(a, b)])
+    ref = refs.harmonic_slope(a, b)
+    assert np.allclose(got, ref, rtol=1e-14, atol=0)
+    assert oracle_mod.vanleer(1.0, 1.0) == 1.0
+    assert oracle_mod.vanleer(-2.0, -2.0) == -2.0
+    assert oracle_mod.vanleer(3.0, -1.0) == 0.0
+
+
+# ---------------------------------------------------------------- equilibria
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+@pytest.mark.parametrize("K", [0.0, 2.0])
+def test_equilibrium_moments(oracle_mod, D, K):
+    nv = {1: 96, 2: 48, 3: 28}[D]
+    cfg, f = wl.uniform(dim=D, n=(2, 2, 2), nv=(nv, nv, nv), vmax=9.0, K=K)
+    o = oracle_mod.Oracle(cfg)
+    xi, w = o.velocities()
+    rho, T = 1.3, 1.7
+    u = np.array([0.4, -0.3, 0.2])[:D]
+    ge, be = o.equilibrium(rho, u, T)
+    RT = R * T
+    assert abs((w * ge).sum() - rho) < 1e-12 * rho
+    for a in range(D):
+        assert abs((w * xi[:, a] * ge).sum() - rho * u[a]) < 1e-12
+        # pressure: sum w (xi_a - u_a)^2 g_eq = rho R T
+        assert abs((w * (xi[:, a] - u[a]) ** 2 * ge).sum() - rho * RT) < 1e-12
+    cv = (3.0 + K) * R / 2.0
+    rhoE = rho * (0.5 * (u ** 2).sum() + cv * T)
+    assert abs((w * be).sum() - rhoE) < 1e-12 * rhoE
+
+
+# ----------------------------------------------------------------- fixed point
+
+@pytest.mark.parametrize("D,nsteps,nv", [(1, 1000, 24), (2, 100, 12), (3, 10, 8)])
+def test_uniform_maxwellian_is_fixed_point(oracle_mod, D, nsteps, nv):
+    cfg, f = wl.uniform(dim=D, n=(6, 5, 4), nv=(nv, nv, nv), u=(0.3, -0.2, 0.1), T=1.2,
+                        Pr=2.0 / 3.0, kn=1e-2)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    g0, b0 = o.distributions()
+    W0 = o.conserved()
+    o.step(nsteps)
+    g1, b1 = o.distributions()
+    assert np.abs(g1 - g0).max() <= 1e-14 * np.abs(g0).max()
+    assert np.abs(b1 - b0).max() <= 1e-14 * np.abs(b0).max()
+    assert np.abs(o.conserved() - W0).max() <= 1e-14 * np.abs(W0).max()
+
+
+def test_fixed_point_boole_odd_grid(oracle_mod):
+    # odd node count puts a node at xi = 0 (reading: mean of both reconstructions)
+    cfg, f = wl.uniform(dim=1, n=(7,), nv=(17,), u=(0.2,), T=1.0)
+    cfg["rule"] = 1
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    g0, _ = o.distributions()
+    o.step(200)
+    g1, _ = o.distributions()
+    assert np.abs(g1 - g0).max() <= 1e-14 * g0.max()
+
+
+# ---------------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("D,nsteps,nv", [(1, 400, 32), (2, 40, 12), (3, 6, 8)])
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.5])
+def test_conservation_periodic(oracle_mod, D, nsteps, nv, Pr):
+    cfg, f = wl.random_smooth(dim=D, n=(16, 10, 6), nv=(nv, nv, nv), seed=D, amp=0.3, Pr=Pr, kn=3e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    S0 = o.conserved().sum(0)
+    o.step(nsteps)
+    S1 = o.conserved().sum(0)
+    scale = np.array([S0[0]] + [S0[0]] * D + [S0[-1]])
+    assert np.all(np.abs(S1 - S0) <= 1e-13 * scale)
+    # the state changed
+    assert np.abs(o.moments()[:, 0] - f[:, 0]).max() > 1e-6
+
+
+def test_specular_walls_conserve_mass_and_energy(oracle_mod):
+    cfg, f = wl.sod(nx=64, nv=32, kn=1e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    S0 = o.conserved().sum(0)
+    o.step(300)
+    S1 = o.conserved().sum(0)
+    assert abs(S1[0] - S0[0]) <= 1e-13 * S0[0]
+    assert abs(S1[2] - S0[2]) <= 1e-13 * S0[2]
+    # the momentum change equals the net wall impulse, which is positive (p_L > p_R)
+    assert S1[1] > 0
+
+
+def test_specular_equals_mirror_image_on_doubled_periodic_domain(oracle_mod):
+    nx, nv = 24, 16
+    cfg, f = wl.random_smooth(dim=1, n=(nx,), nv=(nv,), seed=11, amp=0.3, bc=wl.BC_SPECULAR, kn=5e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    # doubled periodic domain [0,2]: cells nx..2nx-1 mirror cells nx-1..0, u -> -u
+    cfg2 = dict(cfg)
+    cfg2["n"] = [2 * nx, 1, 1]
+    cfg2["hi"] = [2.0, 1.0, 1.0]
+    cfg2["bc"] = [[wl.BC_PERIODIC] * 2] * 3
+    f2 = np.concatenate([f, f[::-1] * np.array([1.0, -1.0, 1.0])], axis=0)
+    o2 = oracle_mod.Oracle(cfg2)
+    assert o2.dt == o.dt
+    o2.init(f2)
+    o.step(150)
+    o2.step(150)
+    m1 = o.moments()
+    m2 = o2.moments()
+    assert np.abs(m1 - m2[:nx]).max() <= 1e-12
+    assert np.abs(m1 * np.array([1, -1, 1]) - m2[nx:][::-1]).max() <= 1e-12
+
+
+# -------------------------------------------------------------- free streaming
+
+def test_free_streaming_is_muscl_hancock_advection(oracle_mod):
+    nx, nv = 40, 12
+    cfg, f = wl.random_smooth(dim=1, n=(nx,), nv=(nv,), seed=5, amp=0.4, mu_ref=1e250, omega=0.0)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    g0, b0 = o.distributions()
+    xi, w = o.velocities()
+    nsteps = 60
+    o.step(nsteps)
+    g1, b1 = o.distributions()
+    dx = 1.0 / nx
+    for i in range(nv):
+        ref_g = refs.muscl_hancock_advection(g0[:, i], xi[i, 0], dx, o.dt, nsteps)
+        ref_b = refs.muscl_hancock_advection(b0[:, i], xi[i, 0], dx, o.dt, nsteps)
+        assert np.abs(g1[:, i] - ref_g).max() <= 1e-13 * np.abs(g0).max()
+        assert np.abs(b1[:, i] - ref_b).max() <= 1e-13 * np.abs(b0).max()
+
+
+def test_free_streaming_converges_second_order_to_exact_shift(oracle_mod):
+    errs = []
+    t_end = 0.05
+    for nx in (32, 64, 128):
+        cfg = wl._base(1, [nx], [0.0], [1.0], [[0, 0]], [8], [-2.0], [2.0], K=2.0, mu_ref=1e250,
+                       T_ref=1.0, omega=0.0, cfl=0.4)
+        _, (x,) = wl.cell_centres(cfg)
+        f = wl._fields(1.0 + 0.2 * np.sin(2 * math.pi * x), [np.zeros_like(x)], np.ones_like(x))
+        o = oracle_mod.Oracle(cfg)
+        n = int(round(t_end / o.dt))
+        cfg["dt"] = t_end / n
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        g0, _ = o.distributions()
+        xi, _ = o.velocities()
+        o.step(n)
+        g1, _ = o.distributions()
+        # exact: every velocity's profile shifted by xi t.  The initial state
+        # holds point values, so compare with the shifted point values.
+        err = 0.0
+        for i in range(8):
+            c0 = g0[:, i].mean()   # equilibrium prefactor of velocity i (rho averages to 1)
+            pt = 1.0 + 0.2 * np.sin(2 * math.pi * (x - xi[i, 0] * t_end))
+            err = max(err, np.abs(g1[:, i] / c0 - pt).mean())
+        errs.append(err)
+    order1 = math.log2(errs[0] / errs[1])
+    order2 = math.log2(errs[1] / errs[2])
+    assert order1 > 1.7 and order2 > 1.7, errs
+
+
+def test_free_streaming_2d_diagonal_second_order(oracle_mod):
+    """A profile advected along oblique characteristics converges at 2nd order only
+    when the reconstruction uses the full slope vector, tangential parts included."""
+    def err(nx, t_end=0.05, nv=4, vmax=2.0):
+        cfg = wl._base(2, [nx, nx], [0, 0], [1, 1], [[0, 0], [0, 0]], [nv, nv], [-vmax] * 2, [vmax] * 2,
+                       K=2.0, mu_ref=1e250, T_ref=1.0, omega=0.0, cfl=0.4)
+        _, (x, y) = wl.cell_centres(cfg)
+        f = wl._fields(1 + 0.2 * np.sin(2 * math.pi * (x + 2 * y)), [0 * x, 0 * x], np.ones_like(x))
+        n = int(round(t_end / oracle_mod.Oracle(cfg).dt))
+        cfg["dt"] = t_end / n
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        g0, _ = o.distributions()
+        xi, _ = o.velocities()
+        o.step(n)
+        g1, _ = o.distributions()
+        e = 0.0
+        for i in range(nv * nv):
+            pt = 1 + 0.2 * np.sin(2 * math.pi * ((x - xi[i, 0] * t_end) + 2 * (y - xi[i, 1] * t_end)))
+            e = max(e, np.abs(g1[:, i] / g0[:, i].mean() - pt).mean())
+        return e
+
+    e = [err(nx) for nx in (32, 64, 128)]
+    assert math.log2(e[1] / e[2]) > 1.8, e
+    assert e[2] < 6e-4, e
+
+
+# ------------------------------------------------------------------ Euler limit
+
+def test_euler_limit_sod_against_exact_riemann(oracle_mod):
+    res = []
+    for nx in (128, 256):
+        cfg, f = wl.sod(nx=nx, nv=64, kn=1e-5, cfl=0.5)
+        o = oracle_mod.Oracle(cfg)
+        n = int(math.ceil(0.15 / o.dt))
+        cfg["dt"] = 0.15 / n
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        o.step(n)
+        m = o.moments()
+        _, (x,) = wl.cell_centres(cfg)
+        gamma = (cfg["K"] + 5) / (cfg["K"] + 3)
+        rho, u, p = refs.exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, gamma, x, 0.15)
+        l1 = np.abs(m[:, 0] - rho).mean()
+        l1u = np.abs(m[:, 1] - u).mean()
+        l1p = np.abs(m[:, 0] * R * m[:, 2] - p).mean()
+        res.append((l1, l1u, l1p))
+    (a128, u128, p128), (a256, u256, p256) = res
+    assert a256 < 6e-3 and u256 < 1e-2 and p256 < 6e-3, res
+    assert a256 < 0.75 * a128 and p256 < 0.75 * p128, res
+
+
+# --------------------------------------------------------- Navier-Stokes rates
+
+def _shear_rate(oracle_mod, mu, Pr, nx=32, nv=24, vmax=6.0):
+    cfg = wl._base(2, [nx, 1], [0, 0], [1, 1], [[0, 0], [0, 0]], [nv, nv], [-vmax] * 2, [vmax] * 2,
+                   K=0.0, mu_ref=mu, T_ref=2.0, omega=0.0, Pr=Pr, cfl=0.5)
+    _, (x, y) = wl.cell_centres(cfg)
+    f = wl._fields(np.ones_like(x), [np.zeros_like(x), 1e-3 * np.sin(2 * math.pi * x)],
+                   np.full_like(x, 2.0))
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    k = 2 * math.pi
+    n1 = int(round(0.1 / o.dt))
+    n2 = int(round(0.4 / o.dt))
+    o.step(n1)
+    a1 = abs(cplx_amp(o.moments()[:, 2], x, k))
+    o.step(n2 - n1)
+    a2 = abs(cplx_amp(o.moments()[:, 2], x, k))
+    return math.log(a1 / a2) / ((n2 - n1) * o.dt), k * k * mu
+
+
+@pytest.mark.slow
+def test_ns_shear_wave_decay(oracle_mod):
+    """eq. NSshear: u_y decays as exp(-4 pi^2 nu t), nu = mu/rho."""
+    rate, pred = _shear_rate(oracle_mod, mu=0.005, Pr=2.0 / 3.0, nx=48)
+    assert abs(rate / pred - 1.0) < 0.02, (rate, pred)
+
+
+def _sound_rate(oracle_mod, mu, Pr, K, U=0.0, nx=128, nv=64, vmax=8.0):
+    gam = (K + 5) / (K + 3)
+    cs = math.sqrt(gam)      # rho = 1, p = 1
+    cfg = wl._base(1, [nx], [0], [1], [[0, 0]], [nv], [-vmax], [vmax], K=K, mu_ref=mu, T_ref=2.0,
+                   omega=0.0, Pr=Pr, cfl=0.5)
+    _, (x,) = wl.cell_centres(cfg)
+    d = 1e-4
+    s = np.sin(2 * math.pi * x)
+    rho = 1 + d * s
+    u = U + d * cs * s
+    p = 1 + gam * d * s
+    o = oracle_mod.Oracle(cfg)
+    o.init(wl._fields(rho, [u], p / (rho * R)))
+    k = 2 * math.pi
+
+    def amp():   # right-going Riemann invariant: excludes the entropy and left-going modes
+        m = o.moments()
+        pp = m[:, 0] * R * m[:, 2]
+        return abs(cplx_amp(pp, x, k) / cs + cplx_amp(m[:, 1], x, k)) / 2
+
+    n1 = int(round(0.1 / o.dt))
+    n2 = n1 + int(round(0.5 / o.dt))
+    o.step(n1)
+    a1 = amp()
+    o.step(n2 - n1)
+    a2 = amp()
+    zeta = 2 * K / (3 * (3 + K)) * mu            # bulk viscosity with K internal DoF
+    pred = k * k / 2 * ((4.0 / 3.0) * mu + zeta + (gam - 1) * mu / Pr)
+    return math.log(a1 / a2) / ((n2 - n1) * o.dt), pred
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Pr,K", [(2.0 / 3.0, 0.0), (1.5, 0.0), (2.0 / 3.0, 2.0)])
+def test_ns_sound_damping(oracle_mod, Pr, K):
+    rate, pred = _sound_rate(oracle_mod, 0.005, Pr, K)
+    assert abs(rate / pred - 1.0) < 0.01, (rate, pred)
+
+
+@pytest.mark.slow
+def test_ns_sound_damping_in_moving_frame(oracle_mod):
+    """Galilean invariance at Pr != 1 holds only with the Z/tau_bg source (eq. bsource)."""
+    rate, pred = _sound_rate(oracle_mod, 0.005, 2.0 / 3.0, 0.0, U=0.5, vmax=9.0)
+    assert abs(rate / pred - 1.0) < 0.015, (rate, pred)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.0, 1.5])
+def test_ns_entropy_mode_conduction(oracle_mod, Pr):
+    """Isobaric density/temperature mode decays at chi k^2, chi = mu/(rho Pr) (Pr = tau_g/tau_b)."""
+    mu, nx = 0.005, 64
+    cfg = wl._base(1, [nx], [0], [1], [[0, 0]], [64], [-8.0], [8.0], K=0.0, mu_ref=mu, T_ref=2.0,
+                   omega=0.0, Pr=Pr, cfl=0.5)
+    _, (x,) = wl.cell_centres(cfg)
+    rho = 1 + 1e-4 * np.sin(2 * math.pi * x)
+    o = oracle_mod.Oracle(cfg)
+    o.init(wl._fields(rho, [np.zeros_like(x)], 1.0 / (rho * R)))
+    k = 2 * math.pi
+
+    def amp():   # isobaric part: density minus its acoustic share
+        m = o.moments()
+        pp = m[:, 0] * R * m[:, 2]
+        return abs(cplx_amp(m[:, 0], x, k) - cplx_amp(pp, x, k) / (5.0 / 3.0))
+
+    n1 = int(round(0.2 / o.dt))
+    n2 = int(round(1.0 / o.dt))
+    o.step(n1)
+    a1 = amp()
+    o.step(n2 - n1)
+    a2 = amp()
+    rate = math.log(a1 / a2) / ((n2 - n1) * o.dt)
+    pred = mu / Pr * k * k
+    assert abs(rate / pred - 1.0) < 0.03, (rate, pred)
+
+
+# ------------------------------------------------------------------ symmetries
+
+def _one_d_and_two_d(oracle_mod, nx, nv, f1, mu_ref, omega, steps):
+    cfg1 = wl._base(1, [nx], [0], [1], [[0, 0]], [nv], [-8.0], [8.0], K=2.0, mu_ref=mu_ref,
+                    T_ref=1.0, omega=omega, Pr=2.0 / 3.0, cfl=0.5)
+    o1 = oracle_mod.Oracle(cfg1)
+    o1.init(f1)
+    cfg2 = wl._base(2, [nx, 2], [0, 0], [1, 1], [[0, 0], [0, 0]], [nv, nv], [-8.0, -8.0], [8.0, 8.0],
+                    K=2.0, mu_ref=mu_ref, T_ref=1.0, omega=omega, Pr=2.0 / 3.0, dt=o1.dt)
+    f2 = np.zeros((2 * nx, 4))
+    for j in range(2):
+        f2[j * nx:(j + 1) * nx, [0, 1, 3]] = f1
+    o2 = oracle_mod.Oracle(cfg2)
+    o2.init(f2)
+    o1.step(steps)
+    o2.step(steps)
+    return o1.moments(), o2.moments()
+
+
+def test_two_d_y_uniform_free_streaming_equals_one_d(oracle_mod):
+    """The reduced 1D model integrates the frozen velocity component analytically
+    ((3 - D + K) R T in eq. beq); the 2D model resolves it on the grid.  In free
+    streaming with uniform T every (xi_x, xi_y) profile is a positive multiple of
+    the xi_y = 0 profile, and the van Leer limiter is homogeneous of degree one,
+    so the xi_y-marginal of the 2D run is the 1D run up to quadrature roundoff."""
+    nx, nv = 20, 32
+    _, (x,) = wl.cell_centres(wl._base(1, [nx], [0], [1], [[0, 0]], [nv], [-8.0], [8.0]))
+    f1 = wl._fields(1.0 + 0.3 * np.sin(2 * math.pi * x), [0.4 * np.cos(2 * math.pi * x)],
+                    np.ones_like(x))
+    m1, m2 = _one_d_and_two_d(oracle_mod, nx, nv, f1, mu_ref=1e250, omega=0.0, steps=40)
+    for c1, c2 in ((0, 0), (1, 1), (2, 3)):
+        assert np.abs(m2[:nx, c2] - m1[:, c1]).max() < 1e-13
+    assert np.abs(m2[:, 2]).max() < 1e-14
+    assert np.abs(m1[:, 0] - f1[:, 0]).max() > 1e-2      # it moved
+
+
+def test_two_d_y_uniform_collisional_close_to_one_d(oracle_mod):
+    """With collisions the limiter acts on non-separable profiles, so 2D and 1D
+    agree only to the scheme's own error (a loose consistency check)."""
+    nx, nv = 20, 32
+    cfg1, f1 = wl.random_smooth(dim=1, n=(nx,), nv=(nv,), seed=7, amp=0.3, vmax=8.0)
+    m1, m2 = _one_d_and_two_d(oracle_mod, nx, nv, f1, mu_ref=cfg1["mu_ref"], omega=0.5, steps=40)
+    for c1, c2 in ((0, 0), (1, 1), (2, 3)):
+        assert np.abs(m2[:nx, c2] - m1[:, c1]).max() < 2e-3
+    assert np.abs(m2[:, 2]).max() < 1e-12
+
+
+def test_two_d_transpose_gives_transposed_result(oracle_mod):
+    nx, ny, nv = 9, 7, 10
+    cfg, f = wl.random_smooth(dim=2, n=(nx, ny), nv=(nv, nv), seed=2, amp=0.3, kn=5e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    cfgT = dict(cfg)
+    cfgT["n"] = [ny, nx, 1]
+    ff = f.reshape(ny, nx, 4)
+    fT = np.ascontiguousarray(ff.transpose(1, 0, 2)[:, :, [0, 2, 1, 3]]).reshape(-1, 4)
+    oT = oracle_mod.Oracle(cfgT)
+    oT.init(fT)
+    o.step(25)
+    oT.step(25)
+    m = o.moments().reshape(ny, nx, 4)
+    mT = oT.moments().reshape(nx, ny, 4).transpose(1, 0, 2)[:, :, [0, 2, 1, 3]]
+    assert np.abs(m - mT).max() < 1e-13
+
+
+def test_three_d_axis_permutation(oracle_mod):
+    n, nv = (6, 5, 4), 6
+    cfg, f = wl.random_smooth(dim=3, n=n, nv=(nv, nv, nv), seed=4, amp=0.3, kn=5e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    # cyclic permutation (x, y, z) -> (y, z, x)
+    cfgP = dict(cfg)
+    cfgP["n"] = [n[1], n[2], n[0]]
+    ff = f.reshape(n[2], n[1], n[0], 5)                    # [z][y][x]
+    fP = ff.transpose(2, 0, 1, 3)                          # new [z'=x][y'=z][x'=y]
+    fP = np.ascontiguousarray(fP[..., [0, 2, 3, 1, 4]]).reshape(-1, 5)
+    oP = oracle_mod.Oracle(cfgP)
+    oP.init(fP)
+    o.step(8)
+    oP.step(8)
+    m = o.moments().reshape(n[2], n[1], n[0], 5)
+    mP = oP.moments().reshape(n[0], n[2], n[1], 5).transpose(1, 2, 0, 3)[..., [0, 3, 1, 2, 4]]
+    assert np.abs(m - mP).max() < 1e-13
+
+
+def test_mirror_symmetry_one_d(oracle_mod):
+    cfg, f = wl.random_smooth(dim=1, n=(30,), nv=(16,), seed=9, amp=0.3, kn=5e-3)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    fm = np.ascontiguousarray(f[::-1] * np.array([1.0, -1.0, 1.0]))
+    om = oracle_mod.Oracle(cfg)
+    om.init(fm)
+    o.step(60)
+    om.step(60)
+    m = o.moments()
+    mm = om.moments()[::-1] * np.array([1.0, -1.0, 1.0])
+    assert np.abs(m - mm).max() < 1e-13
+
+
+def test_dirichlet_far_boundaries_do_not_matter_early(oracle_mod):
+    """Before any signal reaches x = 0 or 1 the Sod solution does not depend on the BC."""
+    cfg_s, f = wl.sod(nx=64, nv=32, kn=1e-4, bc=wl.BC_SPECULAR)
+    cfg_d, _ = wl.sod(nx=64, nv=32, kn=1e-4, bc=wl.BC_DIRICHLET)
+    a = oracle_mod.Oracle(cfg_s)
+    b = oracle_mod.Oracle(cfg_d)
+    a.init(f)
+    b.init(f)
+    a.step(30)
+    b.step(30)
+    assert np.abs(a.moments() - b.moments()).max() < 1e-12
+    # a uniform state under Dirichlet ghosts stays fixed
+    cfg_u, fu = wl.uniform(dim=1, n=(10,), nv=(16,), u=(0.3,), bc=wl.BC_DIRICHLET)
+    c = oracle_mod.Oracle(cfg_u)
+    c.init(fu)
+    g0, _ = c.distributions()
+    c.step(100)
+    g1, _ = c.distributions()
+    assert np.abs(g1 - g0).max() <= 1e-14 * g0.max()
