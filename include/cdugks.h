@@ -1,0 +1,187 @@
+/*
+ * cdugks.h -- C ABI of the GB300 (sm_103a) implementation of one time step of
+ * the Coupled Discrete Unified Gas Kinetic Scheme (CDUGKS) of Zamora,
+ * Slaughter & Abel, arXiv:2208.09132.
+ *
+ * The state of a problem instance is the pair of reduced distributions g
+ * (velocity distribution, eq. g) and b (total-energy distribution, eq. b) on
+ * every (spatial cell, discrete velocity) point, plus the conserved variables
+ * W = (rho, rho u, rho E) of every cell, which the scheme tracks explicitly
+ * (Sec. 2: "The rule is made explicit by updating the conserved variables W").
+ * One call of cdugks_step advances all of it by the update of Sec. 2.1
+ * ("The Algorithm"): the quarter-step shift of eq. phibarplus, van Leer
+ * limited upwind reconstruction (eq. VanLeer) along the characteristics
+ * (eq. relation), the face moments of eqs. rhobar-rhoEbar, the face
+ * equilibrium (eqs. geq, beq) and inversion of eq. phibar, the microflux of
+ * eq. flux, the conserved-variable update of eqs. rhoupdate-rhoEupdate and the
+ * distribution update of eq. phiupdate.  External acceleration is zero.
+ *
+ * Conventions
+ *   - Every call returns int: CDUGKS_OK (0) or a negative CDUGKS_ERR_*.
+ *     No exception crosses the ABI.  cdugks_strerror() names a code;
+ *     cdugks_last_error() gives the message of the last failure on this thread.
+ *   - Device memory is owned by the caller: cdugks_workspace_bytes() says how
+ *     much, cdugks_bind() hands it over (256-byte aligned base).  The library
+ *     allocates no device memory of its own and never frees caller memory.
+ *   - All device work is enqueued on the stream given to cdugks_bind().
+ *     cdugks_step() is asynchronous; cdugks_moments(), cdugks_conserved(),
+ *     cdugks_distributions(), cdugks_get_state() and cdugks_sync_status()
+ *     synchronise that stream.
+ *   - Host pointers are borrowed for the duration of the call only.
+ *   - Cell order is x fastest, then y, then z.  Velocity order is the tensor
+ *     product of the 1D grids with the first component fastest.
+ *   - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef CDUGKS_H
+#define CDUGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CDUGKS_API __attribute__((visibility("default")))
+#else
+#define CDUGKS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define CDUGKS_OK 0
+#define CDUGKS_ERR_INVALID (-1)     /* bad argument or problem description */
+#define CDUGKS_ERR_OOM (-2)         /* bound workspace too small */
+#define CDUGKS_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define CDUGKS_ERR_NONFINITE (-4)   /* a conserved variable became NaN/Inf */
+#define CDUGKS_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define CDUGKS_ERR_UNBOUND (-6)     /* no workspace bound / state not initialised */
+#define CDUGKS_ERR_NEGATIVE (-7)    /* density or temperature became <= 0 */
+
+/* -------------------------------------------------------- problem setup */
+#define CDUGKS_BC_PERIODIC 0        /* wrap-around */
+#define CDUGKS_BC_SPECULAR 1        /* mirror wall: normal velocity reversed */
+#define CDUGKS_BC_DIRICHLET 2       /* ghosts hold the equilibrium of the initial edge state */
+
+#define CDUGKS_RULE_TRAPEZOID 0     /* composite trapezoid weights */
+#define CDUGKS_RULE_BOOLE 1         /* composite Boole (4th-order Newton-Cotes), n = 4m+1 */
+
+#define CDUGKS_FP64 0               /* g, b stored and computed in double */
+#define CDUGKS_FP32 1               /* g, b stored and computed in float; W, T and all
+                                       velocity-space sums accumulated in double */
+
+/* Spatial grid: dim = D in {1,2,3}; n[a] cells on [lo[a], hi[a]] along axis
+ * a < D (entries a >= D ignored); bc[a][0] / bc[a][1] the low / high side.
+ * Periodic must be set on both sides of an axis or on neither; specular
+ * needs n[a] >= 2 and a velocity range symmetric about 0 on that axis. */
+typedef struct {
+    int dim;
+    int n[3];
+    double lo[3], hi[3];
+    int bc[3][2];
+} cdugks_grid;
+
+/* Velocity grid (Sec. 2, discrete velocity method): n[a] >= 2 nodes on
+ * [lo[a], hi[a]] including both ends, tensor product over a < dim. */
+typedef struct {
+    int n[3];
+    double lo[3], hi[3];
+    int rule;
+} cdugks_vgrid;
+
+/* Physics (Sec. 2): K internal degrees of freedom (gamma = (K+5)/(K+3));
+ * gas constant R (0.5 in the paper); viscosity mu = mu_ref (T/T_ref)^omega
+ * (eq. visc); Prandtl number Pr = tau_g / tau_b; dt > 0 fixes the time step,
+ * dt <= 0 takes the CFL rule of Sec. 4, dt = cfl dx_min / (2 |xi|_max). */
+typedef struct {
+    double K, R;
+    double mu_ref, T_ref, omega;
+    double Pr;
+    double cfl, dt;
+    int precision;                  /* CDUGKS_FP64 or CDUGKS_FP32 */
+} cdugks_phys;
+
+typedef struct cdugks cdugks_t;     /* opaque handle; host metadata only */
+
+/* Validate the description and create a handle (no device work).
+ * Errors: INVALID.  *out is NULL on failure. */
+CDUGKS_API int cdugks_create(const cdugks_grid *grid, const cdugks_vgrid *vgrid, const cdugks_phys *phys,
+                  cdugks_t **out);
+
+/* Device bytes the caller must provide to cdugks_bind (phase-space state in
+ * two buffers, conserved variables, face-moment partial sums, velocity tables,
+ * status word). */
+CDUGKS_API int cdugks_workspace_bytes(const cdugks_t *h, size_t *bytes);
+
+/* Hand over caller-owned device memory (>= cdugks_workspace_bytes, 256-byte
+ * aligned) and the cudaStream_t (as void*; NULL = legacy default stream) all
+ * later device work is ordered on.  Uploads the velocity tables.
+ * Errors: INVALID (null/misaligned), OOM (too small), CUDA. */
+CDUGKS_API int cdugks_bind(cdugks_t *h, void *device_ptr, size_t bytes, void *cuda_stream);
+
+/* Maxwell-Boltzmann initialisation (Sec. 3.4: all problems start from
+ * eqs. geq/beq for the given moments).  rho_u_T: host array [Nc][2+D] of
+ * cell-centre density, velocity components and temperature.  W^0 is
+ * (rho, rho u, rho (u^2/2 + c_v T)) with c_v = (3+K)R/2.  Synchronous.
+ * Errors: INVALID (non-positive rho/T), UNBOUND, CUDA. */
+CDUGKS_API int cdugks_init(cdugks_t *h, const double *rho_u_T);
+
+/* Enqueue nsteps time steps of Sec. 2.1 on the bound stream (asynchronous).
+ * Errors: UNBOUND, INVALID (nsteps < 0), CUDA (launch failure). */
+CDUGKS_API int cdugks_step(cdugks_t *h, int nsteps);
+
+/* Synchronise the stream and report the device status word: OK, or
+ * NONFINITE / NEGATIVE if any step since the last check produced a
+ * non-finite conserved variable or rho <= 0 or T <= 0.  Clears the word. */
+CDUGKS_API int cdugks_sync_status(cdugks_t *h);
+
+/* Macroscopic fields from the tracked W: host out[Nc][2+D] = rho, u[D], T.
+ * Synchronous (device-to-host copy of Nc*(2+D) doubles). */
+CDUGKS_API int cdugks_moments(cdugks_t *h, double *out);
+
+/* The tracked conserved variables W: host out[Nc][2+D]. Synchronous. */
+CDUGKS_API int cdugks_conserved(cdugks_t *h, double *out);
+
+/* The distributions g, b at the current time level, host [Nc][Nv] each, as
+ * double (converted from the storage precision).  Uses the idle state buffer
+ * on the device as scratch.  Synchronous. */
+CDUGKS_API int cdugks_distributions(cdugks_t *h, double *g, double *b);
+
+/* Checkpoint: opaque host image of the device state (distributions in their
+ * storage form, W, step count).  cdugks_set_state restores it bitwise, so a
+ * restarted run reproduces an uninterrupted one exactly. */
+CDUGKS_API int cdugks_state_bytes(const cdugks_t *h, size_t *bytes);
+CDUGKS_API int cdugks_get_state(cdugks_t *h, void *host, size_t bytes);
+CDUGKS_API int cdugks_set_state(cdugks_t *h, const void *host, size_t bytes);
+
+/* Introspection. */
+typedef struct {
+    int dim;
+    long long ncells;               /* Nc */
+    int nvel;                       /* Nv (unpadded) */
+    int nvel_padded;                /* Nv rounded up to the 32-velocity tile */
+    double dt;                      /* time step in use */
+    long long steps;                /* steps taken since cdugks_init */
+    int precision;
+    int velocity_groups;            /* velocity-space split of the sweeps */
+    double state_bytes;             /* bytes of one copy of (g, b) on the device */
+} cdugks_info_t;
+CDUGKS_API int cdugks_info(const cdugks_t *h, cdugks_info_t *info);
+
+/* Tuning: split velocity space into groups of tiles for the two sweeps
+ * (0 = automatic).  Results are independent of the split up to the order of
+ * the final sums over groups (a fixed order, so runs are reproducible). */
+CDUGKS_API int cdugks_set_velocity_groups(cdugks_t *h, int groups);
+
+CDUGKS_API void cdugks_destroy(cdugks_t *h);
+CDUGKS_API const char *cdugks_strerror(int code);
+CDUGKS_API const char *cdugks_last_error(void);
+
+/* Hard-sphere convention for a Knudsen number (an input convention, not part
+ * of the scheme): mu_ref = (5/16) Kn L rho_ref sqrt(2 pi R T_ref). */
+CDUGKS_API double cdugks_mu_from_kn(double kn, double rho_ref, double T_ref, double R, double length);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,237 @@
+"""Thin Python binding of the C ABI in ``include/cdugks.h`` (ctypes).
+
+Argument marshalling only: every step of the scheme runs in the CUDA library.
+PyTorch provides the device workspace and the stream.  There is no CPU
+fallback; loading fails loudly when the library is missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNBOUND, ERR_NEGATIVE = -1, -2, -3, -4, -5, -6, -7
+BC_PERIODIC, BC_SPECULAR, BC_DIRICHLET = 0, 1, 2
+RULE_TRAPEZOID, RULE_BOOLE = 0, 1
+FP64, FP32 = 0, 1
+
+EXPORTS = [
+    "cdugks_create", "cdugks_workspace_bytes", "cdugks_bind", "cdugks_init", "cdugks_step",
+    "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
+    "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
+    "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
+    "cdugks_mu_from_kn",
+]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", (ctypes.c_int * 2) * 3)]
+
+
+class VGrid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("rule", ctypes.c_int)]
+
+
+class Phys(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double), ("R", ctypes.c_double), ("mu_ref", ctypes.c_double),
+                ("T_ref", ctypes.c_double), ("omega", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ncells", ctypes.c_longlong), ("nvel", ctypes.c_int),
+                ("nvel_padded", ctypes.c_int), ("dt", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("precision", ctypes.c_int), ("velocity_groups", ctypes.c_int),
+                ("state_bytes", ctypes.c_double)]
+
+
+class CdugksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load (building first if needed) the CUDA library and declare its ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_needed else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run paper_2208_09132_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = P(ctypes.c_double)
+    sig = {
+        "cdugks_create": (i, [P(Grid), P(VGrid), P(Phys), P(vp)]),
+        "cdugks_workspace_bytes": (i, [vp, P(sz)]),
+        "cdugks_bind": (i, [vp, vp, sz, vp]),
+        "cdugks_init": (i, [vp, dp]),
+        "cdugks_step": (i, [vp, i]),
+        "cdugks_sync_status": (i, [vp]),
+        "cdugks_moments": (i, [vp, dp]),
+        "cdugks_conserved": (i, [vp, dp]),
+        "cdugks_distributions": (i, [vp, dp, dp]),
+        "cdugks_state_bytes": (i, [vp, P(sz)]),
+        "cdugks_get_state": (i, [vp, vp, sz]),
+        "cdugks_set_state": (i, [vp, vp, sz]),
+        "cdugks_info": (i, [vp, P(Info)]),
+        "cdugks_set_velocity_groups": (i, [vp, i]),
+        "cdugks_destroy": (None, [vp]),
+        "cdugks_strerror": (ctypes.c_char_p, [i]),
+        "cdugks_last_error": (ctypes.c_char_p, []),
+        "cdugks_mu_from_kn": (d, [d, d, d, d, d]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        lib = load()
+        raise CdugksError(rc, lib.cdugks_last_error().decode() or lib.cdugks_strerror(rc).decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def describe(cfg: dict, precision: int | None = None):
+    """C structs for a problem description dict (see ``workloads``)."""
+    D = int(cfg["dim"])
+    g, v, p = Grid(), VGrid(), Phys()
+    g.dim = D
+    for a in range(3):
+        g.n[a] = int(cfg["n"][a]) if a < D else 1
+        g.lo[a] = float(cfg["lo"][a]) if a < D else 0.0
+        g.hi[a] = float(cfg["hi"][a]) if a < D else 1.0
+        for s in range(2):
+            g.bc[a][s] = int(cfg["bc"][a][s]) if a < D else 0
+        v.n[a] = int(cfg["nv"][a]) if a < D else 1
+        v.lo[a] = float(cfg["vlo"][a]) if a < D else 0.0
+        v.hi[a] = float(cfg["vhi"][a]) if a < D else 0.0
+    v.rule = int(cfg.get("rule", 0))
+    p.K = float(cfg["K"])
+    p.R = float(cfg.get("R", 0.5))
+    p.mu_ref = float(cfg["mu_ref"])
+    p.T_ref = float(cfg["T_ref"])
+    p.omega = float(cfg.get("omega", 0.5))
+    p.Pr = float(cfg["Pr"])
+    p.cfl = float(cfg.get("cfl", 0.5))
+    p.dt = float(cfg.get("dt", 0.0) or 0.0)
+    if precision is None:
+        precision = FP64 if cfg.get("precision", "fp64") == "fp64" else FP32
+    p.precision = int(precision)
+    return g, v, p
+
+
+class Solver:
+    """One CDUGKS problem instance on the GPU.
+
+    The device workspace is a torch uint8 tensor on ``device``; all work runs
+    on ``stream`` (default: torch's current stream for the device).
+    """
+
+    def __init__(self, cfg: dict, precision: int | None = None, device: str = "cuda:0", stream=None,
+                 velocity_groups: int = 0, workspace=None):
+        import torch
+
+        self._lib = load()
+        g, v, p = describe(cfg, precision)
+        h = ctypes.c_void_p()
+        _check(self._lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        if velocity_groups:
+            _check(self._lib.cdugks_set_velocity_groups(h, int(velocity_groups)))
+        nbytes = ctypes.c_size_t()
+        _check(self._lib.cdugks_workspace_bytes(h, ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=dev)
+        self._ws = workspace
+        base = workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        avail = workspace.numel() - (aligned - base)
+        _check(self._lib.cdugks_bind(h, ctypes.c_void_p(aligned), ctypes.c_size_t(avail),
+                                     ctypes.c_void_p(self.stream.cuda_stream)))
+        self.D = int(cfg["dim"])
+        inf = self.info()
+        self.Nc = int(inf.ncells)
+        self.Nv = int(inf.nvel)
+        self.dt = float(inf.dt)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.cdugks_destroy(h)
+            self._h = None
+
+    def info(self) -> Info:
+        inf = Info()
+        _check(self._lib.cdugks_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def set_velocity_groups(self, groups: int):
+        _check(self._lib.cdugks_set_velocity_groups(self._h, int(groups)))
+
+    def init(self, rho_u_T: np.ndarray):
+        a = np.ascontiguousarray(rho_u_T, dtype=np.float64).reshape(self.Nc, 2 + self.D)
+        _check(self._lib.cdugks_init(self._h, _dptr(a)))
+
+    def step(self, nsteps: int = 1):
+        _check(self._lib.cdugks_step(self._h, int(nsteps)))
+
+    def sync_status(self) -> int:
+        return int(self._lib.cdugks_sync_status(self._h))
+
+    def moments(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.Nc, 2 + self.D))
+        _check(self._lib.cdugks_moments(self._h, _dptr(out)))
+        return out
+
+    def conserved(self) -> np.ndarray:
+        out = np.empty((self.Nc, 2 + self.D))
+        _check(self._lib.cdugks_conserved(self._h, _dptr(out)))
+        return out
+
+    def distributions(self):
+        g = np.empty((self.Nc, self.Nv))
+        b = np.empty((self.Nc, self.Nv))
+        _check(self._lib.cdugks_distributions(self._h, _dptr(g), _dptr(b)))
+        return g, b
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(self._lib.cdugks_state_bytes(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.cdugks_get_state(self._h, buf, n))
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.cdugks_set_state(self._h, buf, ctypes.c_size_t(len(blob))))
+
+
+def mu_from_kn(kn, rho_ref, T_ref, R=0.5, length=1.0) -> float:
+    return float(load().cdugks_mu_from_kn(kn, rho_ref, T_ref, R, length))

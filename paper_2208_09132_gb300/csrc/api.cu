@@ -1,0 +1,600 @@
+// api.cu -- the C ABI of include/cdugks.h: problem validation, workspace layout
+// in caller-owned device memory, velocity tables, and the per-step launch
+// sequence of the CDUGKS update (arXiv:2208.09132, Sec. 2.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cdugks.h"
+#include "launch.cuh"
+
+using cdg::Bufs;
+using cdg::CellC;
+using cdg::FaceC;
+using cdg::Geo;
+using cdg::VI;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CDUGKS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t phi[2], W, cellc, cellc0, facec[3], wf[3], mf[3], xi, w, hxi2, refl, io, status, total;
+};
+
+}  // namespace
+
+struct cdugks {
+    cdugks_grid grid;
+    cdugks_vgrid vgrid;
+    cdugks_phys phys;
+    Geo g;
+    int prec;              // CDUGKS_FP64 / CDUGKS_FP32
+    size_t elt;            // bytes of one stored value
+    size_t cellc_bytes, facec_bytes;
+    int Nv;
+    int gcap;              // velocity groups the workspace is laid out for
+    int gsel;              // requested groups (0 = auto)
+    Layout lay;
+    unsigned char* base;
+    size_t bound_bytes;
+    cudaStream_t stream;
+    bool bound, initialised;
+    int cur;               // state buffer holding phi* of the current time level
+    long long steps;
+    std::vector<double> xi;   // [3][Nvp]
+    std::vector<double> w, hxi2;
+    std::vector<int> refl;    // [8][Nvp]
+};
+
+namespace {
+
+// 1D nodes (both ends included) and weights, Sec. 2 quadrature sum_k w_k.
+bool vgrid_1d(int n, double lo, double hi, int rule, std::vector<double>& x, std::vector<double>& w) {
+    if (n < 2 || !(hi > lo)) return false;
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double d = (hi - lo) / (n - 1);
+    for (int k = 0; k < n; ++k) x[k] = lo + (hi - lo) * (double)k / (double)(n - 1);
+    if (rule == CDUGKS_RULE_TRAPEZOID) {
+        for (int k = 0; k < n; ++k) w[k] = (k == 0 || k == n - 1) ? 0.5 * d : d;
+    } else if (rule == CDUGKS_RULE_BOOLE) {
+        if ((n - 1) % 4 != 0) return false;
+        const double c[5] = {14.0, 64.0, 24.0, 64.0, 14.0};
+        for (int p = 0; p + 4 < n; p += 4)
+            for (int j = 0; j < 5; ++j) w[p + j] += c[j] * d / 45.0;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+int groups_for(const cdugks* h, int requested) {
+    const Geo& g = h->g;
+    if (requested > 0) return std::min(requested, g.NVT);
+    // enough CTAs for a few full waves over 152 SMs (at least 2 resident per SM)
+    const long long tiles = (long long)g.tiles[0] * g.tiles[1] * g.tiles[2];
+    const long long want = 152LL * 2 * 4;
+    long long G = (want + tiles - 1) / tiles;
+    G = std::max(1LL, std::min<long long>(G, g.NVT));
+    G = std::min<long long>(G, 64);
+    return (int)G;
+}
+
+void set_groups(cdugks* h, int G) {
+    Geo& g = h->g;
+    g.ntpg = (g.NVT + G - 1) / G;
+    g.G = (g.NVT + g.ntpg - 1) / g.ntpg;
+}
+
+void make_layout(cdugks* h) {
+    const Geo& g = h->g;
+    const int NM = 2 + g.D;
+    Layout& L = h->lay;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t state = (size_t)g.Nvp * (size_t)g.Nc * 2 * h->elt;
+    L.phi[0] = take(state);
+    L.phi[1] = take(state);
+    L.W = take(sizeof(double) * NM * g.Nc);
+    L.cellc = take(h->cellc_bytes * g.Nc);
+    L.cellc0 = take(h->cellc_bytes * g.Nc);
+    for (int a = 0; a < 3; ++a) {
+        const long long nf = a < g.D ? g.nf[a] : 0;
+        L.facec[a] = take(h->facec_bytes * nf);
+        L.wf[a] = take(sizeof(double) * (size_t)h->gcap * NM * nf);
+        L.mf[a] = take(sizeof(double) * (size_t)h->gcap * NM * nf);
+    }
+    L.xi = take(h->elt * 3 * g.Nvp);
+    L.w = take(h->elt * g.Nvp);
+    L.hxi2 = take(h->elt * g.Nvp);
+    L.refl = take(sizeof(int) * 8 * g.Nvp);
+    L.io = take(sizeof(double) * NM * g.Nc);
+    L.status = take(256);
+    L.total = off;
+}
+
+template <typename T>
+Bufs<T> bufs(const cdugks* h, int in) {
+    Bufs<T> b;
+    unsigned char* p = h->base;
+    const Layout& L = h->lay;
+    b.phi_in = reinterpret_cast<const T*>(p + L.phi[in]);
+    b.phi_out = reinterpret_cast<T*>(p + L.phi[1 - in]);
+    b.W = reinterpret_cast<double*>(p + L.W);
+    b.cellc = reinterpret_cast<CellC<T>*>(p + L.cellc);
+    b.cellc0 = reinterpret_cast<CellC<T>*>(p + L.cellc0);
+    for (int a = 0; a < 3; ++a) {
+        b.facec[a] = reinterpret_cast<FaceC<T>*>(p + L.facec[a]);
+        b.wf[a] = reinterpret_cast<double*>(p + L.wf[a]);
+        b.mf[a] = reinterpret_cast<double*>(p + L.mf[a]);
+    }
+    b.xi = reinterpret_cast<const T*>(p + L.xi);
+    b.w = reinterpret_cast<const T*>(p + L.w);
+    b.hxi2 = reinterpret_cast<const T*>(p + L.hxi2);
+    b.refl = reinterpret_cast<const int*>(p + L.refl);
+    b.status = reinterpret_cast<int*>(p + L.status);
+    return b;
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double>& v) {
+    std::vector<T> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+    return o;
+}
+
+int check_ready(const cdugks* h, bool need_init) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    if (!h->bound) return fail(CDUGKS_ERR_UNBOUND, "no workspace bound (cdugks_bind)");
+    if (need_init && !h->initialised) return fail(CDUGKS_ERR_UNBOUND, "state not initialised (cdugks_init)");
+    return CDUGKS_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    int dim, prec, Nvp, pad;
+    long long Nc, steps;
+    double dt;
+};
+
+}  // namespace
+
+extern "C" {
+
+int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdugks_phys* phys, cdugks_t** out) {
+    if (!out) return fail(CDUGKS_ERR_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!grid || !vgrid || !phys) return fail(CDUGKS_ERR_INVALID, "null description");
+    const int D = grid->dim;
+    if (D < 1 || D > 3) return fail(CDUGKS_ERR_INVALID, "dim must be 1, 2 or 3");
+    if (phys->precision != CDUGKS_FP64 && phys->precision != CDUGKS_FP32)
+        return fail(CDUGKS_ERR_INVALID, "precision must be CDUGKS_FP64 or CDUGKS_FP32");
+    if (!(phys->R > 0) || !(phys->mu_ref > 0) || !(phys->T_ref > 0) || !(phys->Pr > 0) || !(phys->K >= 0) ||
+        !std::isfinite(phys->omega))
+        return fail(CDUGKS_ERR_INVALID, "physics parameters must be positive (K >= 0)");
+    cdugks* h = new (std::nothrow) cdugks();
+    if (!h) return fail(CDUGKS_ERR_OOM, "host allocation failed");
+    h->grid = *grid;
+    h->vgrid = *vgrid;
+    h->phys = *phys;
+    h->prec = phys->precision;
+    h->elt = h->prec == CDUGKS_FP32 ? sizeof(float) : sizeof(double);
+    h->cellc_bytes = h->prec == CDUGKS_FP32 ? sizeof(CellC<float>) : sizeof(CellC<double>);
+    h->facec_bytes = h->prec == CDUGKS_FP32 ? sizeof(FaceC<float>) : sizeof(FaceC<double>);
+    Geo& g = h->g;
+    std::memset(&g, 0, sizeof(g));
+    g.D = D;
+    g.Nc = 1;
+    const cdg::TileShape ts = cdg::tile_shape(h->prec == CDUGKS_FP32 ? 1 : 0, D);
+    std::vector<double> nodes[3], wts[3];
+    int nv[3] = {1, 1, 1};
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            if (grid->n[a] < 1 || !(grid->hi[a] > grid->lo[a])) {
+                delete h;
+                return fail(CDUGKS_ERR_INVALID, "each active axis needs n >= 1 and hi > lo");
+            }
+            for (int s = 0; s < 2; ++s) {
+                const int bc = grid->bc[a][s];
+                if (bc < 0 || bc > 2) {
+                    delete h;
+                    return fail(CDUGKS_ERR_INVALID, "unknown boundary condition");
+                }
+                if (bc == CDUGKS_BC_SPECULAR && (grid->n[a] < 2 || vgrid->lo[a] != -vgrid->hi[a])) {
+                    delete h;
+                    return fail(CDUGKS_ERR_INVALID, "specular walls need n >= 2 and a symmetric velocity range");
+                }
+            }
+            if ((grid->bc[a][0] == CDUGKS_BC_PERIODIC) != (grid->bc[a][1] == CDUGKS_BC_PERIODIC)) {
+                delete h;
+                return fail(CDUGKS_ERR_INVALID, "periodic must be set on both sides of an axis");
+            }
+            if (!vgrid_1d(vgrid->n[a], vgrid->lo[a], vgrid->hi[a], vgrid->rule, nodes[a], wts[a])) {
+                delete h;
+                return fail(CDUGKS_ERR_INVALID, "bad velocity grid (n >= 2, hi > lo, Boole needs n = 4m+1)");
+            }
+            nv[a] = vgrid->n[a];
+            g.n[a] = grid->n[a];
+            g.bc[a][0] = grid->bc[a][0];
+            g.bc[a][1] = grid->bc[a][1];
+            g.dx[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
+            g.tiles[a] = (g.n[a] + ts.t[a] - 1) / ts.t[a];
+        } else {
+            nodes[a].assign(1, 0.0);
+            wts[a].assign(1, 1.0);
+            g.n[a] = 1;
+            g.dx[a] = 1.0;
+            g.tiles[a] = 1;
+        }
+        g.Nc *= g.n[a];
+    }
+    const long long Nv = (long long)nv[0] * nv[1] * nv[2];
+    if (Nv > (1LL << 26) || g.Nc > (1LL << 31)) {
+        delete h;
+        return fail(CDUGKS_ERR_INVALID, "problem too large");
+    }
+    h->Nv = (int)Nv;
+    g.NVT = (int)((Nv + VI - 1) / VI);
+    g.Nvp = g.NVT * VI;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) g.fn[a][b] = g.n[b] + (a == b && a < D ? 1 : 0);
+        g.nf[a] = (long long)g.fn[a][0] * g.fn[a][1] * g.fn[a][2];
+    }
+    // velocity tables (padding: xi = 0, w = 0)
+    h->xi.assign(3 * (size_t)g.Nvp, 0.0);
+    h->w.assign(g.Nvp, 0.0);
+    h->hxi2.assign(g.Nvp, 0.0);
+    h->refl.assign(8 * (size_t)g.Nvp, 0);
+    double vmax = 0.0;
+    for (int k2 = 0; k2 < nv[2]; ++k2)
+        for (int k1 = 0; k1 < nv[1]; ++k1)
+            for (int k0 = 0; k0 < nv[0]; ++k0) {
+                const long long i = k0 + (long long)nv[0] * (k1 + (long long)nv[1] * k2);
+                const double x[3] = {nodes[0][k0], nodes[1][k1], nodes[2][k2]};
+                double s = 0.0;
+                for (int a = 0; a < D; ++a) {
+                    h->xi[(size_t)a * g.Nvp + i] = x[a];
+                    s += x[a] * x[a];
+                }
+                h->w[i] = wts[0][k0] * wts[1][k1] * wts[2][k2];
+                h->hxi2[i] = 0.5 * s;
+                vmax = std::max(vmax, std::sqrt(s));
+                for (int m = 0; m < 8; ++m) {
+                    const int r0 = (m & 1) ? nv[0] - 1 - k0 : k0;
+                    const int r1 = (m & 2) ? nv[1] - 1 - k1 : k1;
+                    const int r2 = (m & 4) ? nv[2] - 1 - k2 : k2;
+                    h->refl[(size_t)m * g.Nvp + i] = (int)(r0 + (long long)nv[0] * (r1 + (long long)nv[1] * r2));
+                }
+            }
+    for (long long i = Nv; i < g.Nvp; ++i)
+        for (int m = 0; m < 8; ++m) h->refl[(size_t)m * g.Nvp + i] = (int)i;
+    // time step: fixed CFL rule of Sec. 4 unless given
+    double dt = phys->dt;
+    if (!(dt > 0)) {
+        double dxmin = g.dx[0];
+        for (int a = 1; a < D; ++a) dxmin = std::min(dxmin, g.dx[a]);
+        if (!(phys->cfl > 0) || !(vmax > 0)) {
+            delete h;
+            return fail(CDUGKS_ERR_INVALID, "need dt > 0 or cfl > 0 with a nonzero velocity grid");
+        }
+        dt = phys->cfl * dxmin / (2.0 * vmax);
+    }
+    g.dt = dt;
+    g.h = 0.5 * dt;
+    for (int a = 0; a < 3; ++a) {
+        g.hdx[a] = g.h / g.dx[a];
+        g.idx[a] = 1.0 / g.dx[a];
+    }
+    g.K = phys->K;
+    g.R = phys->R;
+    g.mu_ref = phys->mu_ref;
+    g.T_ref = phys->T_ref;
+    g.omega = phys->omega;
+    g.Pr = phys->Pr;
+    h->gsel = 0;
+    h->gcap = groups_for(h, 0);
+    set_groups(h, h->gcap);
+    make_layout(h);
+    h->stream = nullptr;
+    h->cur = 0;
+    *out = h;
+    return CDUGKS_OK;
+}
+
+int cdugks_set_velocity_groups(cdugks_t* h, int groups) {
+    if (!h || groups < 0) return fail(CDUGKS_ERR_INVALID, "bad velocity group count");
+    const int G = groups_for(h, groups);
+    if (h->bound && G > h->gcap)
+        return fail(CDUGKS_ERR_INVALID, "more velocity groups than the bound workspace was laid out for");
+    if (!h->bound && G > h->gcap) {
+        h->gcap = G;
+        make_layout(h);
+    }
+    h->gsel = groups;
+    set_groups(h, G);
+    return CDUGKS_OK;
+}
+
+int cdugks_workspace_bytes(const cdugks_t* h, size_t* bytes) {
+    if (!h || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
+    *bytes = h->lay.total;
+    return CDUGKS_OK;
+}
+
+int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) {
+    if (!h || !device_ptr) return fail(CDUGKS_ERR_INVALID, "null argument");
+    if (((uintptr_t)device_ptr) % kAlign) return fail(CDUGKS_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (bytes < h->lay.total) return fail(CDUGKS_ERR_OOM, "workspace smaller than cdugks_workspace_bytes");
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, device_ptr);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(CDUGKS_ERR_INVALID, "workspace is not device memory");
+    h->base = static_cast<unsigned char*>(device_ptr);
+    h->bound_bytes = bytes;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    const Geo& g = h->g;
+    // velocity tables in the storage precision
+    if (h->prec == CDUGKS_FP32) {
+        auto xi = cast_vec<float>(h->xi), w = cast_vec<float>(h->w), hx = cast_vec<float>(h->hxi2);
+        if ((e = cudaMemcpyAsync(h->base + h->lay.xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice, h->stream)) ||
+            (e = cudaMemcpyAsync(h->base + h->lay.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, h->stream)) ||
+            (e = cudaMemcpyAsync(h->base + h->lay.hxi2, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice, h->stream)))
+            return cuda_fail(e, "upload velocity tables");
+        if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
+    } else {
+        if ((e = cudaMemcpyAsync(h->base + h->lay.xi, h->xi.data(), h->xi.size() * 8, cudaMemcpyHostToDevice,
+                                 h->stream)) ||
+            (e = cudaMemcpyAsync(h->base + h->lay.w, h->w.data(), h->w.size() * 8, cudaMemcpyHostToDevice, h->stream)) ||
+            (e = cudaMemcpyAsync(h->base + h->lay.hxi2, h->hxi2.data(), h->hxi2.size() * 8, cudaMemcpyHostToDevice,
+                                 h->stream)))
+            return cuda_fail(e, "upload velocity tables");
+    }
+    if ((e = cudaMemcpyAsync(h->base + h->lay.refl, h->refl.data(), h->refl.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, h->stream)))
+        return cuda_fail(e, "upload reflection table");
+    if ((e = cudaMemsetAsync(h->base + h->lay.status, 0, 256, h->stream))) return cuda_fail(e, "clear status");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
+    (void)g;
+    h->bound = true;
+    h->initialised = false;
+    return CDUGKS_OK;
+}
+
+int cdugks_init(cdugks_t* h, const double* rho_u_T) {
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    if (!rho_u_T) return fail(CDUGKS_ERR_INVALID, "null fields");
+    const Geo& g = h->g;
+    const int NM = 2 + g.D;
+    for (long long c = 0; c < g.Nc; ++c) {
+        const double rho = rho_u_T[c * NM], T = rho_u_T[c * NM + 1 + g.D];
+        if (!(rho > 0) || !(T > 0)) return fail(CDUGKS_ERR_INVALID, "density and temperature must be positive");
+        for (int m = 0; m < NM; ++m)
+            if (!std::isfinite(rho_u_T[c * NM + m])) return fail(CDUGKS_ERR_INVALID, "non-finite field");
+    }
+    cudaError_t e;
+    double* io = reinterpret_cast<double*>(h->base + h->lay.io);
+    if ((e = cudaMemcpyAsync(io, rho_u_T, sizeof(double) * NM * g.Nc, cudaMemcpyHostToDevice, h->stream)))
+        return cuda_fail(e, "upload fields");
+    // initial state goes to buffer 0: launch with phi_in = buffer 1, phi_out = buffer 0
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_init_f32(g, bufs<float>(h, 1), io, h->stream);
+    else e = cdg::launch_init_f64(g, bufs<double>(h, 1), io, h->stream);
+    if (e) return cuda_fail(e, "init kernel");
+    if ((e = cudaMemsetAsync(h->base + h->lay.status, 0, 256, h->stream))) return cuda_fail(e, "clear status");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "init");
+    h->cur = 0;
+    h->steps = 0;
+    h->initialised = true;
+    return CDUGKS_OK;
+}
+
+int cdugks_step(cdugks_t* h, int nsteps) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(CDUGKS_ERR_INVALID, "nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e;
+        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, bufs<float>(h, h->cur), h->stream);
+        else e = cdg::launch_step_f64(h->g, bufs<double>(h, h->cur), h->stream);
+        if (e) return cuda_fail(e, "step launch");
+        h->cur = 1 - h->cur;
+        h->steps += 1;
+    }
+    return CDUGKS_OK;
+}
+
+int cdugks_sync_status(cdugks_t* h) {
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    int st = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&st, h->base + h->lay.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream)))
+        return cuda_fail(e, "read status");
+    if ((e = cudaMemsetAsync(h->base + h->lay.status, 0, 256, h->stream))) return cuda_fail(e, "clear status");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
+    if (st & cdg::ST_NONFINITE) return fail(CDUGKS_ERR_NONFINITE, "a conserved variable became non-finite");
+    if (st & cdg::ST_NEGATIVE) return fail(CDUGKS_ERR_NEGATIVE, "density or internal energy became <= 0");
+    return CDUGKS_OK;
+}
+
+static int fetch_cells(cdugks_t* h, double* out, int conserved) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!out) return fail(CDUGKS_ERR_INVALID, "null output");
+    const Geo& g = h->g;
+    double* io = reinterpret_cast<double*>(h->base + h->lay.io);
+    cudaError_t e = cdg::launch_moments(g, reinterpret_cast<double*>(h->base + h->lay.W), io, conserved, h->stream);
+    if (e) return cuda_fail(e, "moments kernel");
+    if ((e = cudaMemcpyAsync(out, io, sizeof(double) * (2 + g.D) * g.Nc, cudaMemcpyDeviceToHost, h->stream)))
+        return cuda_fail(e, "download moments");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "moments");
+    return CDUGKS_OK;
+}
+
+int cdugks_moments(cdugks_t* h, double* out) { return fetch_cells(h, out, 0); }
+int cdugks_conserved(cdugks_t* h, double* out) { return fetch_cells(h, out, 1); }
+
+int cdugks_distributions(cdugks_t* h, double* gout, double* bout) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!gout || !bout) return fail(CDUGKS_ERR_INVALID, "null output");
+    const Geo& g = h->g;
+    cudaError_t e;
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_finalise_f32(g, bufs<float>(h, h->cur), h->stream);
+    else e = cdg::launch_finalise_f64(g, bufs<double>(h, h->cur), h->stream);
+    if (e) return cuda_fail(e, "finalise kernel");
+    const size_t n = (size_t)g.Nvp * g.Nc * 2;
+    std::vector<unsigned char> host(n * h->elt);
+    if ((e = cudaMemcpyAsync(host.data(), h->base + h->lay.phi[1 - h->cur], host.size(), cudaMemcpyDeviceToHost,
+                             h->stream)))
+        return cuda_fail(e, "download distributions");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "distributions");
+    // layout marshalling only: [tile][cell][field][lane] -> [cell][velocity]
+    for (long long c = 0; c < g.Nc; ++c)
+        for (int i = 0; i < h->Nv; ++i) {
+            const size_t ad = ((size_t)(i / VI) * g.Nc + c) * (2 * VI) + (i % VI);
+            double gv, bv;
+            if (h->prec == CDUGKS_FP32) {
+                gv = reinterpret_cast<const float*>(host.data())[ad];
+                bv = reinterpret_cast<const float*>(host.data())[ad + VI];
+            } else {
+                gv = reinterpret_cast<const double*>(host.data())[ad];
+                bv = reinterpret_cast<const double*>(host.data())[ad + VI];
+            }
+            gout[(size_t)c * h->Nv + i] = gv;
+            bout[(size_t)c * h->Nv + i] = bv;
+        }
+    return CDUGKS_OK;
+}
+
+int cdugks_state_bytes(const cdugks_t* h, size_t* bytes) {
+    if (!h || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
+    const Geo& g = h->g;
+    *bytes = sizeof(StateHeader) + (size_t)g.Nvp * g.Nc * 2 * h->elt + sizeof(double) * (2 + g.D) * g.Nc;
+    return CDUGKS_OK;
+}
+
+int cdugks_get_state(cdugks_t* h, void* host, size_t bytes) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    size_t need;
+    cdugks_state_bytes(h, &need);
+    if (!host || bytes < need) return fail(CDUGKS_ERR_INVALID, "state buffer too small");
+    const Geo& g = h->g;
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "CDUGKS1", 8);
+    hd.dim = g.D;
+    hd.prec = h->prec;
+    hd.Nvp = g.Nvp;
+    hd.Nc = g.Nc;
+    hd.steps = h->steps;
+    hd.dt = g.dt;
+    unsigned char* p = static_cast<unsigned char*>(host);
+    std::memcpy(p, &hd, sizeof(hd));
+    const size_t sb = (size_t)g.Nvp * g.Nc * 2 * h->elt;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(p + sizeof(hd), h->base + h->lay.phi[h->cur], sb, cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaMemcpyAsync(p + sizeof(hd) + sb, h->base + h->lay.W, sizeof(double) * (2 + g.D) * g.Nc,
+                             cudaMemcpyDeviceToHost, h->stream)))
+        return cuda_fail(e, "download state");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "get_state");
+    return CDUGKS_OK;
+}
+
+int cdugks_set_state(cdugks_t* h, const void* host, size_t bytes) {
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    size_t need;
+    cdugks_state_bytes(h, &need);
+    if (!host || bytes < need) return fail(CDUGKS_ERR_INVALID, "state buffer too small");
+    const Geo& g = h->g;
+    StateHeader hd;
+    std::memcpy(&hd, host, sizeof(hd));
+    if (std::memcmp(hd.magic, "CDUGKS1", 8) || hd.dim != g.D || hd.prec != h->prec || hd.Nvp != g.Nvp ||
+        hd.Nc != g.Nc || hd.dt != g.dt)
+        return fail(CDUGKS_ERR_INVALID, "state image does not match this problem");
+    const unsigned char* p = static_cast<const unsigned char*>(host);
+    const size_t sb = (size_t)g.Nvp * g.Nc * 2 * h->elt;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->base + h->lay.phi[0], p + sizeof(hd), sb, cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyAsync(h->base + h->lay.W, p + sizeof(hd) + sb, sizeof(double) * (2 + g.D) * g.Nc,
+                             cudaMemcpyHostToDevice, h->stream)))
+        return cuda_fail(e, "upload state");
+    h->cur = 0;
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_cellc_f32(g, bufs<float>(h, 0), h->stream);
+    else e = cdg::launch_cellc_f64(g, bufs<double>(h, 0), h->stream);
+    if (e) return cuda_fail(e, "cell constants");
+    if (!h->initialised) {
+        // Dirichlet ghost constants: the restored state stands in for the initial one
+        if ((e = cudaMemcpyAsync(h->base + h->lay.cellc0, h->base + h->lay.cellc, h->cellc_bytes * g.Nc,
+                                 cudaMemcpyDeviceToDevice, h->stream)))
+            return cuda_fail(e, "copy constants");
+    }
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "set_state");
+    h->steps = hd.steps;
+    h->initialised = true;
+    return CDUGKS_OK;
+}
+
+int cdugks_info(const cdugks_t* h, cdugks_info_t* info) {
+    if (!h || !info) return fail(CDUGKS_ERR_INVALID, "null argument");
+    info->dim = h->g.D;
+    info->ncells = h->g.Nc;
+    info->nvel = h->Nv;
+    info->nvel_padded = h->g.Nvp;
+    info->dt = h->g.dt;
+    info->steps = h->steps;
+    info->precision = h->prec;
+    info->velocity_groups = h->g.G;
+    info->state_bytes = (double)h->g.Nvp * (double)h->g.Nc * 2.0 * (double)h->elt;
+    return CDUGKS_OK;
+}
+
+void cdugks_destroy(cdugks_t* h) { delete h; }
+
+const char* cdugks_strerror(int code) {
+    switch (code) {
+        case CDUGKS_OK: return "ok";
+        case CDUGKS_ERR_INVALID: return "invalid argument";
+        case CDUGKS_ERR_OOM: return "workspace too small";
+        case CDUGKS_ERR_CUDA: return "CUDA error";
+        case CDUGKS_ERR_NONFINITE: return "non-finite conserved variable";
+        case CDUGKS_ERR_TIMEOUT: return "device wait timed out";
+        case CDUGKS_ERR_UNBOUND: return "workspace not bound or state not initialised";
+        case CDUGKS_ERR_NEGATIVE: return "non-positive density or temperature";
+        default: return "unknown error";
+    }
+}
+
+const char* cdugks_last_error(void) { return g_last_error.c_str(); }
+
+double cdugks_mu_from_kn(double kn, double rho_ref, double T_ref, double R, double length) {
+    return 5.0 / 16.0 * kn * length * rho_ref * std::sqrt(2.0 * 3.14159265358979323846 * R * T_ref);
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, exports every
+symbol include/cdugks.h declares, and validates problem descriptions.  No
+compute call here needs a GPU (cdugks_create does no device work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2208_09132_gb300 import cdugks, workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "cdugks.h")).read()
+    return sorted(set(re.findall(r"CDUGKS_API\s+[\w\s\*]*?\b(cdugks_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_symbols() == sorted(cdugks.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cdugks.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def _create(cfg, precision=cdugks.FP64):
+    lib = cdugks.load()
+    g, v, p = cdugks.describe(cfg, precision)
+    h = ctypes.c_void_p()
+    rc = lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h))
+    return rc, h
+
+
+def test_create_and_workspace_size():
+    lib = cdugks.load()
+    cfg, _ = wl.workload_c1()
+    rc, h = _create(cfg)
+    assert rc == 0 and h.value
+    n = ctypes.c_size_t()
+    assert lib.cdugks_workspace_bytes(h, ctypes.byref(n)) == 0
+    state = 256 * 64 * 2 * 8
+    assert n.value >= 2 * state
+    info = cdugks.Info()
+    assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+    assert info.ncells == 256 and info.nvel == 64 and info.nvel_padded == 64
+    # unbound handle refuses device work with UNBOUND
+    assert lib.cdugks_step(h, 1) == cdugks.ERR_UNBOUND
+    lib.cdugks_destroy(h)
+
+
+def test_time_step_matches_the_cfl_rule_of_the_oracle(oracle_mod):
+    for cfg in (wl.workload_c1()[0], wl.workload_c2(scale=8)[0], wl.workload_c3(scale=8)[0]):
+        rc, h = _create(cfg)
+        assert rc == 0
+        info = cdugks.Info()
+        cdugks.load().cdugks_info(h, ctypes.byref(info))
+        assert info.dt == oracle_mod.Oracle(cfg).dt
+        cdugks.load().cdugks_destroy(h)
+
+
+@pytest.mark.parametrize("mutate,err", [
+    (lambda c: c.update(dim=4), cdugks.ERR_INVALID),
+    (lambda c: c["n"].__setitem__(0, 0), cdugks.ERR_INVALID),
+    (lambda c: c.update(rule=1), cdugks.ERR_INVALID),            # 64 nodes is not 4m+1
+    (lambda c: c["vlo"].__setitem__(0, -7.0), cdugks.ERR_INVALID),  # specular needs symmetric range
+    (lambda c: c.update(Pr=0.0), cdugks.ERR_INVALID),
+    (lambda c: c["bc"].__setitem__(0, [0, 1]), cdugks.ERR_INVALID),
+])
+def test_create_rejects_bad_descriptions(mutate, err):
+    cfg, _ = wl.workload_c1()
+    cfg = {k: (list(map(list, v)) if k == "bc" else (list(v) if isinstance(v, list) else v)) for k, v in cfg.items()}
+    mutate(cfg)
+    rc, h = _create(cfg)
+    assert rc == err
+    assert not h.value
+    assert cdugks.load().cdugks_last_error()
+
+
+def test_strerror_and_mu_convention():
+    lib = cdugks.load()
+    assert lib.cdugks_strerror(cdugks.ERR_NEGATIVE).decode()
+    mu = cdugks.mu_from_kn(1e-3, 1.5, (2.5 / 1.5) / 0.5, 0.5, 1.0)
+    assert abs(mu - wl.mu_from_kn(1e-3, 1.5, 2.5 / 1.5)) < 1e-15

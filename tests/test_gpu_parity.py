@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs, element by element on the macroscopic fields (rho, u,
+T from the tracked W) and on the distributions.
+
+Tolerances: the FP64 path must match to relative L-infinity <= 1e-12 (per
+field, max|gpu - oracle| / max|oracle|); the FP32-storage path to <= 1e-5 on
+rho, u, T with conservation drift <= 1e-6 relative.  Cases span several
+spatial tiles with ragged tails, padded velocity tiles, every boundary kind
+(and their corners), D = 1, 2, 3, the xi = 0 node of odd grids, the
+collisionless limit and the near-Euler limit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2208_09132_gb300 import cdugks, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+P, S, DI = wl.BC_PERIODIC, wl.BC_SPECULAR, wl.BC_DIRICHLET
+
+
+def rel_linf(a, b):
+    """Per-field relative L-infinity over cells: max|a-b| / max|b| for rho and T;
+    the velocity components share one scale, the largest |u| component of the
+    reference field (a component that is identically zero has no scale of its own)."""
+    den = np.abs(b).max(axis=0)
+    if b.shape[1] > 3:
+        den[1:-1] = den[1:-1].max()
+    return np.abs(a - b).max(axis=0) / np.maximum(den, 1e-300)
+
+
+def _bc(cfg, bcs):
+    for a, pair in enumerate(bcs):
+        cfg["bc"][a] = list(pair)
+    return cfg
+
+
+def case(name):
+    """Seeded problem descriptions for the parity cases."""
+    if name == "1d_periodic_ragged_padded":
+        return wl.random_smooth(dim=1, n=(100,), nv=(24,), seed=1, amp=0.3, kn=3e-3), 60
+    if name == "1d_sod_dirichlet":
+        return wl.sod(nx=70, nv=32, kn=1e-4, bc=DI), 60
+    if name == "1d_sod_specular":
+        return wl.sod(nx=130, nv=40, kn=1e-3, bc=S), 60
+    if name == "1d_boole_odd_grid":
+        cfg, f = wl.random_smooth(dim=1, n=(50,), nv=(17,), seed=2, amp=0.3, kn=1e-2)
+        cfg["rule"] = 1
+        return (cfg, f), 40
+    if name == "1d_free_streaming":
+        return wl.random_smooth(dim=1, n=(64,), nv=(32,), seed=3, amp=0.3, mu_ref=1e250, omega=0.0), 40
+    if name == "1d_near_euler":
+        return wl.random_smooth(dim=1, n=(64,), nv=(32,), seed=4, amp=0.3, kn=1e-6), 40
+    if name == "2d_periodic_ragged":
+        return wl.random_smooth(dim=2, n=(19, 13), nv=(8, 6), seed=5, amp=0.3, kn=5e-3), 15
+    if name == "2d_specular_x_periodic_y":
+        cfg, f = wl.random_smooth(dim=2, n=(12, 10), nv=(8, 8), seed=6, amp=0.3, kn=5e-3)
+        return (_bc(cfg, [(S, S), (P, P)]), f), 15
+    if name == "2d_dirichlet_x_specular_y":
+        cfg, f = wl.random_smooth(dim=2, n=(11, 9), nv=(8, 8), seed=7, amp=0.3, kn=5e-3)
+        return (_bc(cfg, [(DI, DI), (S, S)]), f), 12
+    if name == "2d_kh_small":
+        return wl.kelvin_helmholtz(n=24, nv=8, kn=1e-3), 10
+    if name == "3d_periodic_ragged":
+        return wl.random_smooth(dim=3, n=(6, 5, 7), nv=(6, 4, 4), seed=8, amp=0.3, kn=5e-3), 5
+    if name == "3d_specular_corners":
+        cfg, f = wl.random_smooth(dim=3, n=(5, 6, 4), nv=(4, 4, 4), seed=9, amp=0.3, kn=5e-3)
+        return (_bc(cfg, [(S, S), (S, S), (S, S)]), f), 5
+    if name == "3d_mixed_bc":
+        cfg, f = wl.random_smooth(dim=3, n=(6, 5, 5), nv=(4, 4, 6), seed=10, amp=0.3, kn=5e-3)
+        return (_bc(cfg, [(DI, DI), (P, P), (S, S)]), f), 5
+    if name == "3d_shear_small":
+        return wl.shear3d(n=8, nv=6, kn=1e-2), 5
+    raise KeyError(name)
+
+
+CASES = ["1d_periodic_ragged_padded", "1d_sod_dirichlet", "1d_sod_specular", "1d_boole_odd_grid",
+         "1d_free_streaming", "1d_near_euler", "2d_periodic_ragged", "2d_specular_x_periodic_y",
+         "2d_dirichlet_x_specular_y", "2d_kh_small", "3d_periodic_ragged", "3d_specular_corners",
+         "3d_mixed_bc", "3d_shear_small"]
+
+
+def run_both(oracle_mod, cfg, f, steps, precision, groups=0):
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    s = cdugks.Solver(cfg, precision=precision, velocity_groups=groups)
+    assert s.dt == o.dt
+    s.init(f)
+    s.step(steps)
+    assert s.sync_status() == 0
+    return o, s
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp64_matches_oracle(oracle_mod, name):
+    (cfg, f), steps = case(name)
+    o, s = run_both(oracle_mod, cfg, f, steps, cdugks.FP64)
+    err = rel_linf(s.moments(), o.moments())
+    assert np.all(err <= 1e-12), (name, err)
+    go, bo = o.distributions()
+    gs, bs = s.distributions()
+    assert np.abs(gs - go).max() <= 1e-12 * np.abs(go).max()
+    assert np.abs(bs - bo).max() <= 1e-12 * np.abs(bo).max()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp32_matches_oracle(oracle_mod, name):
+    (cfg, f), steps = case(name)
+    o, s = run_both(oracle_mod, cfg, f, steps, cdugks.FP32)
+    err = rel_linf(s.moments(), o.moments())
+    assert np.all(err <= 1e-5), (name, err)
+
+
+def test_c1_sod_fp64_full_workload(oracle_mod):
+    """The 1D Sod workload exactly as benchmarked: 256 cells, 64 velocities, 200 steps."""
+    cfg, f = wl.workload_c1()
+    o, s = run_both(oracle_mod, cfg, f, cfg["steps"], cdugks.FP64)
+    err = rel_linf(s.moments(), o.moments())
+    assert np.all(err <= 1e-12), err
+
+
+def test_velocity_groups_do_not_change_results(oracle_mod):
+    (cfg, f), steps = case("2d_periodic_ragged")
+    a = cdugks.Solver(cfg, precision=cdugks.FP64, velocity_groups=1)
+    b = cdugks.Solver(cfg, precision=cdugks.FP64, velocity_groups=2)
+    for s in (a, b):
+        s.init(f)
+        s.step(steps)
+    assert np.all(rel_linf(a.moments(), b.moments()) <= 1e-14)
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-13), (cdugks.FP32, 1e-6)])
+def test_conservation_periodic(precision, tol):
+    cfg, f = wl.random_smooth(dim=2, n=(40, 24), nv=(12, 12), seed=12, amp=0.3, kn=3e-3)
+    s = cdugks.Solver(cfg, precision=precision)
+    s.init(f)
+    S0 = s.conserved().sum(0)
+    s.step(200)
+    S1 = s.conserved().sum(0)
+    scale = np.array([S0[0], S0[0], S0[0], S0[3]])
+    assert np.all(np.abs(S1 - S0) <= tol * scale), (S1 - S0) / scale
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_uniform_maxwellian_fixed_point(D):
+    cfg, f = wl.uniform(dim=D, n=(9, 7, 5), nv=(12, 8, 6), u=(0.3, -0.2, 0.1), T=1.1)
+    s = cdugks.Solver(cfg, precision=cdugks.FP64)
+    s.init(f)
+    g0, b0 = s.distributions()
+    s.step(50)
+    g1, b1 = s.distributions()
+    assert np.abs(g1 - g0).max() <= 1e-14 * g0.max()
+    assert np.abs(b1 - b0).max() <= 1e-14 * b0.max()
+
+
+@pytest.mark.parametrize("precision", [cdugks.FP64, cdugks.FP32])
+def test_checkpoint_restart_is_bitwise(precision):
+    cfg, f = wl.random_smooth(dim=2, n=(20, 12), nv=(8, 8), seed=13, amp=0.3, kn=3e-3)
+    a = cdugks.Solver(cfg, precision=precision)
+    a.init(f)
+    a.step(7)
+    blob = a.get_state()
+    a.step(9)
+    b = cdugks.Solver(cfg, precision=precision)
+    b.set_state(blob)
+    b.step(9)
+    assert b.info().steps == 16
+    assert np.array_equal(a.moments(), b.moments())
+    assert a.get_state() == b.get_state()
+
+
+def test_status_flags_report_a_broken_state():
+    cfg, f = wl.random_smooth(dim=1, n=(32,), nv=(16,), seed=14, amp=0.2, kn=3e-3)
+    s = cdugks.Solver(cfg, precision=cdugks.FP64)
+    s.init(f)
+    blob = bytearray(s.get_state())
+    # negate the energy of every cell in the W block at the end of the image
+    Nc, NM = 32, 3
+    W = np.frombuffer(bytes(blob[-Nc * NM * 8:]), dtype=np.float64).reshape(NM, Nc).copy()
+    W[2] = -W[2]
+    blob[-Nc * NM * 8:] = W.tobytes()
+    s.set_state(bytes(blob))
+    s.step(1)
+    assert s.sync_status() in (cdugks.ERR_NEGATIVE, cdugks.ERR_NONFINITE)
