@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the CDUGKS phase-space step on GB300.
+
+Metric: phase-space point-updates per second (one point-update = g and b
+advanced one time step at one (cell, discrete velocity) point, the "phase space
+cell update" of the paper's scaling study).
+
+Default workload: the 2D Kelvin-Helmholtz problem with FP32 storage, 256^2
+periodic cells x 32^2 velocities on [-6,6]^2, Kn = 1e-3, Pr = 1 (synthetic
+initial fields).  One bench step = one full time step of the scheme.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c1|c2|c3|c3s]
+
+N > 1 runs independent replicas (the path does not shard across GPUs on this
+build), one per rank under torch.distributed.run; value = all points / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2208_09132_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "phase-space point-updates/s"
+UNIT = "point-updates/s"
+ALGO_BYTES = {  # algorithmic bytes per phase-space point per launch (state read/write only)
+    "sweep_a": {"fp32": 8, "fp64": 16},     # read g*, b*
+    "sweep_b": {"fp32": 16, "fp64": 32},    # read g*, b*; write g*, b*
+}
+
+
+def pick_workload(name):
+    if name == "c1":
+        return wl.workload_c1()
+    if name == "c2":
+        return wl.workload_c2()
+    if name == "c3":
+        return wl.workload_c3(kn=1e-4)
+    if name == "c3s":        # 3D shear at half resolution in space and velocity
+        return wl.workload_c3(kn=1e-4, scale=2, nv=12)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def points(cfg):
+    return wl.ncells(cfg) * wl.nvel(cfg)
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "sweeps_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_2208_09132_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, kernel, precision):
+    """DRAM bytes per point for a kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    e = d.get("entries", {}).get(f"{workload}:{precision}:{kernel}")
+    return None if e is None else float(e["dram_bytes_per_point"])
+
+
+def cpu_baseline(cfg, budget_s=12.0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the same
+    velocity grid and physics on a reduced spatial grid."""
+    import oracle
+    oracle.build()
+    sample = dict(cfg)
+    D = cfg["dim"]
+    side = {1: 256, 2: 32, 3: 8}[D]
+    sample["n"] = [min(cfg["n"][a], side) if a < D else 1 for a in range(3)]
+    if D == 3 and wl.nvel(cfg) > 4096:
+        sample["n"] = [4, 4, 4]
+    sample["dt"] = 0.0
+    _, X = wl.cell_centres(sample)
+    nc = wl.ncells(sample)
+    rng_fields = np.column_stack([np.ones(nc)] + [0.1 * np.sin(2 * math.pi * X[0])] * D + [np.full(nc, cfg["T_ref"])])
+    o = oracle.Oracle(sample)
+    o.init(rng_fields)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    el = time.perf_counter() - t0
+    pts = wl.ncells(sample) * wl.nvel(sample)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": pts * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{'x'.join(str(v) for v in sample['n'][:D])} cells x {wl.nvel(sample)} velocities, "
+                      f"{n} steps, {el:.1f} s (same velocity grid and physics as the workload)"}
+
+
+# ------------------------------------------------------------------- ranks
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2208_09132_gb300 import cdugks
+
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    cfg, fields = pick_workload(args.workload)
+    prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
+    pname = "fp64" if prec == cdugks.FP64 else "fp32"
+    P = points(cfg)
+    s = cdugks.Solver(cfg, precision=prec, device=dev)
+    stream = s.stream
+    s.init(fields)
+    for _ in range(args.warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    if s.sync_status() != 0:
+        raise RuntimeError("device status flagged a broken state during warm-up")
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        s.step(1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    total_ms = max_over_ranks(total_ms, ws)
+    status = s.sync_status()
+    value = ws * P * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel durations of the same launches (CUDA events on the bound stream)
+    nprof = max(3, min(args.steps, 50))
+    ph = s.profile_step(nprof)
+    names = ["sweep_a", "face_constants", "sweep_b", "w_update"]
+    dom = max(("sweep_a", "sweep_b"), key=lambda k: ph[names.index(k)])
+    t_dom = ph[names.index(dom)] / 1e3
+    abytes = ALGO_BYTES[dom][pname] * P
+    peak, peak_kind = measured_peak_hbm()
+    achieved = abytes / t_dom / 1e9
+    traffic_pp = ncu_traffic(args.workload, dom, pname)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "algorithmic_bytes_per_point": ALGO_BYTES[dom][pname],
+                "traffic": None if traffic_pp is None else traffic_pp * P,
+                "phase_ms": {n: round(float(v), 4) for n, v in zip(names, ph)},
+                "step_bytes_per_point": ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname],
+                "step_hbm_frac": round((ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname]) * P
+                                       / (total_ms / args.steps / 1e3) / 1e9 / peak, 4)}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    NM = 2 + cfg["dim"]
+    host_in = torch.empty((wl.ncells(cfg), NM), dtype=torch.float64, pin_memory=True)
+    host_in.numpy()[:] = fields
+    host_out = torch.empty((wl.ncells(cfg), NM), dtype=torch.float64, pin_memory=True)
+    e2e_steps = args.steps
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init(host_in.numpy())
+    s.step(e2e_steps)
+    s.moments(host_out.numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e = {"value": ws * P * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": host_in.numel() * 8 / e2e_steps,
+           "d2h_bytes_per_step": host_out.numel() * 8 / e2e_steps,
+           "what": "cdugks_init from pinned host fields + cdugks_step(K) + cdugks_moments to pinned host"}
+
+    # ---- the plain FP64 path on the same workload (the one-instance comparison)
+    fp64 = None
+    if prec == cdugks.FP32 and not args.skip_fp64:
+        s64 = cdugks.Solver(cfg, precision=cdugks.FP64, device=dev)
+        s64.init(fields)
+        s64.step(2)
+        n64 = max(3, min(20, args.steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s64.stream)
+        s64.step(n64)
+        e1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fp64 = {"value": P * n64 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n64, "steps": n64}
+        del s64
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(cfg) if (ws == 1 and not args.skip_cpu) else None
+        launches_per_step = 3 + cfg["dim"]
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if pname == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "precision": pname, "cells": wl.ncells(cfg),
+                       "velocities": wl.nvel(cfg), "points": P, "dt": s.dt,
+                       "state_bytes": s.info().state_bytes,
+                       "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
+                             else "state fits in L2",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "fp64_plain": fp64,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "status_ok": status == 0,
+        }
+    return result
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args, ws, rank):
+    """The CPU oracle as it stands, each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    cfg, _ = pick_workload(args.workload)
+    D = cfg["dim"]
+    sample = dict(cfg)
+    side = {1: 256, 2: 32, 3: 4}[D]
+    sample["n"] = [min(cfg["n"][a], side) if a < D else 1 for a in range(3)]
+    sample["dt"] = 0.0
+    nc = wl.ncells(sample)
+    _, X = wl.cell_centres(sample)
+    f = np.column_stack([np.ones(nc)] + [0.1 * np.sin(2 * math.pi * X[0])] * D + [np.full(nc, cfg["T_ref"])])
+    o = oracle.Oracle(sample)
+    o.init(f)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    pts = wl.ncells(sample) * wl.nvel(sample)
+    v = pts * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    samp = f"{'x'.join(str(v) for v in sample['n'][:D])} cells x {wl.nvel(sample)} velocities per step"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "precision": "fp64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": samp, "value": v, "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 plain comparison")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        res = run_ours(args, ws, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,13 @@ CDUGKS_API int cdugks_init(cdugks_t *h, const double *rho_u_T);
  * Errors: UNBOUND, INVALID (nsteps < 0), CUDA (launch failure). */
 CDUGKS_API int cdugks_step(cdugks_t *h, int nsteps);
 
+/* Advance nsteps steps exactly as cdugks_step does, timing each phase with
+ * CUDA events on the bound stream: ms_out[0..3] = mean milliseconds per step
+ * of sweep A (face moments), the face constants, sweep B (fluxes and
+ * distribution update) and the W update.  Synchronises once at the end.
+ * Errors: UNBOUND, INVALID (nsteps outside [1, 1e5] or null ms_out), CUDA. */
+CDUGKS_API int cdugks_profile_step(cdugks_t *h, int nsteps, double *ms_out);
+
 /* Synchronise the stream and report the device status word: OK, or
  * NONFINITE / NEGATIVE if any step since the last check produced a
  * non-finite conserved variable or rho <= 0 or T <= 0.  Clears the word. */

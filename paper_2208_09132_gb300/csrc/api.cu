@@ -427,6 +427,38 @@ int cdugks_step(cdugks_t* h, int nsteps) {
     return CDUGKS_OK;
 }
 
+int cdugks_profile_step(cdugks_t* h, int nsteps, double* ms_out) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (nsteps < 1 || nsteps > 100000 || !ms_out) return fail(CDUGKS_ERR_INVALID, "need 1 <= nsteps <= 1e5 and ms_out");
+    // all events exist before the first launch, so the device never waits on the host
+    std::vector<cudaEvent_t> ev((size_t)nsteps * 5);
+    cudaError_t e = cudaSuccess;
+    size_t made = 0;
+    for (; made < ev.size(); ++made)
+        if ((e = cudaEventCreate(&ev[made]))) break;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+        cudaEvent_t* es = &ev[(size_t)s * 5];
+        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, bufs<float>(h, h->cur), h->stream, es);
+        else e = cdg::launch_step_f64(h->g, bufs<double>(h, h->cur), h->stream, es);
+        if (e) break;
+        h->cur = 1 - h->cur;
+        h->steps += 1;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[(size_t)s * 5 + k], ev[(size_t)s * 5 + k + 1]);
+            acc[k] += ms;
+        }
+    for (size_t k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    if (e) return cuda_fail(e, "profile_step");
+    for (int k = 0; k < 4; ++k) ms_out[k] = acc[k] / nsteps;
+    return CDUGKS_OK;
+}
+
 int cdugks_sync_status(cdugks_t* h) {
     int rc = check_ready(h, false);
     if (rc) return rc;

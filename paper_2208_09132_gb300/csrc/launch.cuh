@@ -17,8 +17,9 @@ TileShape tile_shape(int precision, int D);
 size_t sweep_smem_bytes(int precision, int D);
 
 // One time step: sweep A, face constants, sweep B, W update (+ cell constants of W^{n+1}).
-cudaError_t launch_step_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s);
-cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s);
+// ev: null, or five events recorded before, between and after the four phases.
+cudaError_t launch_step_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s, cudaEvent_t* ev = nullptr);
+cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // Maxwellian initial state from device fields [Nc][2+D] (rho, u, T).
 cudaError_t launch_init_f32(const Geo& g, const Bufs<float>& b, const double* fields, cudaStream_t s);
 cudaError_t launch_init_f64(const Geo& g, const Bufs<double>& b, const double* fields, cudaStream_t s);

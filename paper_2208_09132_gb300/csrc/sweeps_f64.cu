@@ -26,11 +26,11 @@ size_t sweep_smem_bytes(int precision, int D) {
     return SweepSmem<double, 3, 4, 2, 2>::bytes;
 }
 
-cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s) {
+cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s, cudaEvent_t* ev) {
     switch (g.D) {
-        case 1: return run_step<double, 1, 64, 1, 1>(g, b, s);
-        case 2: return run_step<double, 2, 8, 8, 1>(g, b, s);
-        default: return run_step<double, 3, 4, 2, 2>(g, b, s);
+        case 1: return run_step<double, 1, 64, 1, 1>(g, b, s, ev);
+        case 2: return run_step<double, 2, 8, 8, 1>(g, b, s, ev);
+        default: return run_step<double, 3, 4, 2, 2>(g, b, s, ev);
     }
 }
 cudaError_t launch_init_f64(const Geo& g, const Bufs<double>& b, const double* f, cudaStream_t s) {

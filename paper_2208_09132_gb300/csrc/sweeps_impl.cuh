@@ -6,7 +6,7 @@
 namespace cdg {
 
 template <typename T, int D, int TX, int TY, int TZ>
-cudaError_t run_step(const Geo& g, const Bufs<T>& b, cudaStream_t s) {
+cudaError_t run_step(const Geo& g, const Bufs<T>& b, cudaStream_t s, cudaEvent_t* ev) {
     using SM = SweepSmem<T, D, TX, TY, TZ>;
     static bool configured = false;
     cudaError_t e;
@@ -20,13 +20,18 @@ cudaError_t run_step(const Geo& g, const Bufs<T>& b, cudaStream_t s) {
         configured = true;
     }
     const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
+    if (ev) cudaEventRecord(ev[0], s);
     k_sweep<T, D, TX, TY, TZ, false><<<grid, NTHREADS, SM::bytes, s>>>(g, b);
+    if (ev) cudaEventRecord(ev[1], s);
     for (int a = 0; a < D; ++a) {
         const unsigned blocks = (unsigned)((g.nf[a] + 127) / 128);
         k_facec<T, D><<<blocks, 128, 0, s>>>(g, b, a);
     }
+    if (ev) cudaEventRecord(ev[2], s);
     k_sweep<T, D, TX, TY, TZ, true><<<grid, NTHREADS, SM::bytes, s>>>(g, b);
+    if (ev) cudaEventRecord(ev[3], s);
     k_wupdate<T, D><<<(unsigned)((g.Nc + 127) / 128), 128, 0, s>>>(g, b);
+    if (ev) cudaEventRecord(ev[4], s);
     return cudaGetLastError();
 }
 
