@@ -18,7 +18,7 @@ using cdg::Bufs;
 using cdg::CellC;
 using cdg::FaceC;
 using cdg::Geo;
-using cdg::VI;
+using cdg::VC;
 
 namespace {
 
@@ -37,7 +37,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t phi[2], W, cellc, cellc0, facec[3], wf[3], mf[3], xi, w, hxi2, refl, io, status, total;
+    size_t phi[2], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, total;
 };
 
 }  // namespace
@@ -60,8 +60,7 @@ struct cdugks {
     bool bound, initialised;
     int cur;               // state buffer holding phi* of the current time level
     long long steps;
-    std::vector<double> xi;   // [3][Nvp]
-    std::vector<double> w, hxi2;
+    std::vector<double> vel;  // [Nvp][8]: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0
     std::vector<int> refl;    // [8][Nvp]
 };
 
@@ -127,9 +126,7 @@ void make_layout(cdugks* h) {
         L.wf[a] = take(sizeof(double) * (size_t)h->gcap * NM * nf);
         L.mf[a] = take(sizeof(double) * (size_t)h->gcap * NM * nf);
     }
-    L.xi = take(h->elt * 3 * g.Nvp);
-    L.w = take(h->elt * g.Nvp);
-    L.hxi2 = take(h->elt * g.Nvp);
+    L.vel = take(h->elt * 8 * g.Nvp);
     L.refl = take(sizeof(int) * 8 * g.Nvp);
     L.io = take(sizeof(double) * NM * g.Nc);
     L.status = take(256);
@@ -151,9 +148,7 @@ Bufs<T> bufs(const cdugks* h, int in) {
         b.wf[a] = reinterpret_cast<double*>(p + L.wf[a]);
         b.mf[a] = reinterpret_cast<double*>(p + L.mf[a]);
     }
-    b.xi = reinterpret_cast<const T*>(p + L.xi);
-    b.w = reinterpret_cast<const T*>(p + L.w);
-    b.hxi2 = reinterpret_cast<const T*>(p + L.hxi2);
+    b.vel = reinterpret_cast<const T*>(p + L.vel);
     b.refl = reinterpret_cast<const int*>(p + L.refl);
     b.status = reinterpret_cast<int*>(p + L.status);
     return b;
@@ -257,16 +252,14 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
         return fail(CDUGKS_ERR_INVALID, "problem too large");
     }
     h->Nv = (int)Nv;
-    g.NVT = (int)((Nv + VI - 1) / VI);
-    g.Nvp = g.NVT * VI;
+    g.NVT = (int)((Nv + VC - 1) / VC);
+    g.Nvp = g.NVT * VC;
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) g.fn[a][b] = g.n[b] + (a == b && a < D ? 1 : 0);
         g.nf[a] = (long long)g.fn[a][0] * g.fn[a][1] * g.fn[a][2];
     }
     // velocity tables (padding: xi = 0, w = 0)
-    h->xi.assign(3 * (size_t)g.Nvp, 0.0);
-    h->w.assign(g.Nvp, 0.0);
-    h->hxi2.assign(g.Nvp, 0.0);
+    h->vel.assign(8 * (size_t)g.Nvp, 0.0);
     h->refl.assign(8 * (size_t)g.Nvp, 0);
     double vmax = 0.0;
     for (int k2 = 0; k2 < nv[2]; ++k2)
@@ -276,11 +269,11 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
                 const double x[3] = {nodes[0][k0], nodes[1][k1], nodes[2][k2]};
                 double s = 0.0;
                 for (int a = 0; a < D; ++a) {
-                    h->xi[(size_t)a * g.Nvp + i] = x[a];
+                    h->vel[(size_t)i * 8 + a] = x[a];
                     s += x[a] * x[a];
                 }
-                h->w[i] = wts[0][k0] * wts[1][k1] * wts[2][k2];
-                h->hxi2[i] = 0.5 * s;
+                h->vel[(size_t)i * 8 + 3] = wts[0][k0] * wts[1][k1] * wts[2][k2];
+                h->vel[(size_t)i * 8 + 4] = 0.5 * s;
                 vmax = std::max(vmax, std::sqrt(s));
                 for (int m = 0; m < 8; ++m) {
                     const int r0 = (m & 1) ? nv[0] - 1 - k0 : k0;
@@ -357,21 +350,16 @@ int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) 
     h->bound_bytes = bytes;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     const Geo& g = h->g;
-    // velocity tables in the storage precision
+    // velocity table in the storage precision
     if (h->prec == CDUGKS_FP32) {
-        auto xi = cast_vec<float>(h->xi), w = cast_vec<float>(h->w), hx = cast_vec<float>(h->hxi2);
-        if ((e = cudaMemcpyAsync(h->base + h->lay.xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice, h->stream)) ||
-            (e = cudaMemcpyAsync(h->base + h->lay.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, h->stream)) ||
-            (e = cudaMemcpyAsync(h->base + h->lay.hxi2, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice, h->stream)))
-            return cuda_fail(e, "upload velocity tables");
+        auto v = cast_vec<float>(h->vel);
+        if ((e = cudaMemcpyAsync(h->base + h->lay.vel, v.data(), v.size() * 4, cudaMemcpyHostToDevice, h->stream)))
+            return cuda_fail(e, "upload velocity table");
         if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
     } else {
-        if ((e = cudaMemcpyAsync(h->base + h->lay.xi, h->xi.data(), h->xi.size() * 8, cudaMemcpyHostToDevice,
-                                 h->stream)) ||
-            (e = cudaMemcpyAsync(h->base + h->lay.w, h->w.data(), h->w.size() * 8, cudaMemcpyHostToDevice, h->stream)) ||
-            (e = cudaMemcpyAsync(h->base + h->lay.hxi2, h->hxi2.data(), h->hxi2.size() * 8, cudaMemcpyHostToDevice,
+        if ((e = cudaMemcpyAsync(h->base + h->lay.vel, h->vel.data(), h->vel.size() * 8, cudaMemcpyHostToDevice,
                                  h->stream)))
-            return cuda_fail(e, "upload velocity tables");
+            return cuda_fail(e, "upload velocity table");
     }
     if ((e = cudaMemcpyAsync(h->base + h->lay.refl, h->refl.data(), h->refl.size() * sizeof(int),
                              cudaMemcpyHostToDevice, h->stream)))
@@ -508,14 +496,14 @@ int cdugks_distributions(cdugks_t* h, double* gout, double* bout) {
     // layout marshalling only: [tile][cell][field][lane] -> [cell][velocity]
     for (long long c = 0; c < g.Nc; ++c)
         for (int i = 0; i < h->Nv; ++i) {
-            const size_t ad = ((size_t)(i / VI) * g.Nc + c) * (2 * VI) + (i % VI);
+            const size_t ad = ((size_t)(i / VC) * g.Nc + c) * (2 * VC) + (i % VC);
             double gv, bv;
             if (h->prec == CDUGKS_FP32) {
                 gv = reinterpret_cast<const float*>(host.data())[ad];
-                bv = reinterpret_cast<const float*>(host.data())[ad + VI];
+                bv = reinterpret_cast<const float*>(host.data())[ad + VC];
             } else {
                 gv = reinterpret_cast<const double*>(host.data())[ad];
-                bv = reinterpret_cast<const double*>(host.data())[ad + VI];
+                bv = reinterpret_cast<const double*>(host.data())[ad + VC];
             }
             gout[(size_t)c * h->Nv + i] = gv;
             bout[(size_t)c * h->Nv + i] = bv;

@@ -1,28 +1,28 @@
 // kernels.cuh -- sm_103a device code of the CDUGKS step (arXiv:2208.09132, Sec. 2.1).
 //
-// One time step is three launches on the caller's stream:
+// One time step is four kinds of launch on the caller's stream:
 //
-//   sweep A  per (spatial tile, velocity group): finalise phi^n from the stored
-//            pre-update value phi* (the last factor of eq. phiupdate, deferred
-//            until W^n is known), form phibar+ (eq. phibarplus) on the tile and
-//            a two-cell halo in shared memory, reconstruct phibar at every
-//            owned face along the characteristic (eqs. VanLeer, relation) and
-//            reduce the face conserved variables (eqs. rhobar-rhoEbar) over the
-//            group's velocities: warp butterfly per 32-velocity tile, then a
-//            compensated accumulator per face in shared memory.
-//   sweep B  the same reconstruction, then the face equilibrium (eqs. geq,
-//            beq) from the face W, inversion of eq. phibar, the microflux
-//            xi.n phi (eq. flux), the face moments of the flux (for W) and the
-//            per-velocity net flux, which feeds phi* of eq. phiupdate, written
-//            to the other state buffer.
-//   W update W^{n+1} = W^n - dt sum_faces (M_right - M_left)/dx (eqs.
-//            rhoupdate-rhoEupdate, outward normals), with the status check.
+//   sweep A   per (tile of cells, group of velocity chunks): finalise phi^n from
+//             the stored pre-update value phi* (the last factor of eq. phiupdate,
+//             deferred until W^n is known), form phibar+ (eq. phibarplus) on the
+//             tile and its two-cell halo in shared memory, van Leer slopes
+//             (eq. VanLeer), reconstruct phibar at the owned faces along the
+//             characteristic (eq. relation) and sum the face conserved variables
+//             (eqs. rhobar-rhoEbar) over the group's velocities.
+//   face      sum the groups' partial face W; face constants (u, T, tau).
+//   sweep B   the same reconstruction, then the face equilibrium (eqs. geq,
+//             beq), the inverse of eq. phibar, the microflux xi.n phi (eq. flux),
+//             its moments (for W) and the per-velocity net flux that gives phi*
+//             of eq. phiupdate, written to the other state buffer.
+//   W update  W^{n+1} = W^n - dt sum_faces (M_right - M_left)/dx (eqs.
+//             rhoupdate-rhoEupdate, outward normals), the status check and the
+//             cell constants of W^{n+1}.
 //
-// Layout in HBM: phi*[velocity tile][cell][field g|b][32 lanes], so a warp
-// reads 2 x 128 contiguous bytes (FP32) per cell and a tile of cells of one
-// velocity tile is a dense slab.  Boundaries are applied by index mapping
-// while the halo is loaded (periodic wrap, mirror with reflected velocity,
-// fixed equilibrium), not by ghost copies.
+// Layout in HBM: phi*[velocity chunk][cell][field g|b][VC], VC = 4 velocities,
+// so one cell's chunk of g and b is one 32-byte sector (FP32) read with two
+// 16-byte vector loads.  Boundaries are applied by index mapping while the
+// halo is loaded (periodic wrap, mirror with reflected velocity, fixed
+// equilibrium), not by ghost copies.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,9 +31,7 @@
 
 namespace cdg {
 
-constexpr int VI = 32;            // velocities per tile = lanes of a warp
-constexpr int NWARPS = 8;
-constexpr int NTHREADS = VI * NWARPS;
+constexpr int VC = 4;             // velocities per chunk: the innermost run of the state layout
 
 enum { BC_PERIODIC = 0, BC_SPECULAR = 1, BC_DIRICHLET = 2 };
 enum { ST_NONFINITE = 1, ST_NEGATIVE = 2 };
@@ -44,9 +42,9 @@ struct Geo {
     int n[3];
     int bc[3][2];
     long long Nc;
-    int Nvp;          // padded velocity count (multiple of VI)
-    int NVT;          // velocity tiles
-    int ntpg;         // velocity tiles per group
+    int Nvp;          // padded velocity count (multiple of VC)
+    int NVT;          // velocity chunks (Nvp / VC)
+    int ntpg;         // velocity chunks per group
     int G;            // velocity groups
     int tiles[3];     // spatial tiles per axis
     int fn[3][3];     // face-array extents per axis a: fn[a][b] = n[b] + (a == b)
@@ -71,9 +69,7 @@ struct Bufs {
     FaceC<T>* facec[3];   // [nf_a] constants of the face W (between the sweeps)
     double* wf[3];        // [G][2+D][nf_a] face W partial sums (sweep A)
     double* mf[3];        // [G][2+D][nf_a] face flux-moment partial sums (sweep B)
-    const T* xi;          // [3][Nvp]
-    const T* w;           // [Nvp] quadrature weights (0 on padding)
-    const T* hxi2;        // [Nvp] |xi|^2 / 2
+    const T* vel;         // [Nvp][8] per velocity: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0 (w = 0 on padding)
     const int* refl;      // [8][Nvp] velocity index with the components of mask reversed
     int* status;
 };
@@ -194,13 +190,14 @@ struct Vel {
 template <typename T, int D>
 __device__ __forceinline__ Vel<T, D> load_vel(const Geo& g, const Bufs<T>& bf, int i) {
     Vel<T, D> v;
+    const T* rec = bf.vel + (size_t)i * 8;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        v.xi[a] = bf.xi[a * g.Nvp + i];
+        v.xi[a] = rec[a];
         v.nu[a] = (T)g.hdx[a] * v.xi[a];
     }
-    v.w = bf.w[i];
-    v.hxi2 = bf.hxi2[i];
+    v.w = rec[3];
+    v.hxi2 = rec[4];
     return v;
 }
 
@@ -224,66 +221,22 @@ __device__ __forceinline__ T zeta(const C& c, const Vel<T, D>& v) {
     return z;
 }
 
-// ------------------------------------------------------- warp reductions
+// ------------------------------------------------------------- accumulation
 
-// Sum NM values over the 32 lanes.  Returns, in every lane, the total of one
-// moment; moment_of_lane() says which.  Recursive halving: at each of the
-// first log2(NP) steps a lane keeps half of its values and receives the
-// partner's half of the other values.
-template <typename T, int NM>
-struct WarpSum {
-    static constexpr int NP = NM <= 2 ? 2 : (NM <= 4 ? 4 : 8);
-    static constexpr int LG = NP == 2 ? 1 : (NP == 4 ? 2 : 3);
-    static __device__ __forceinline__ T run(const T (&vin)[NM], int lane) {
-        T v[NP];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) v[k] = k < NM ? vin[k] : T(0);
-        int cnt = NP;
-#pragma unroll
-        for (int s = 0; s < LG; ++s) {
-            const int mask = 16 >> s;
-            const bool hi = (lane & mask) != 0;
-            cnt >>= 1;
-#pragma unroll
-            for (int k = 0; k < NP / 2; ++k) {
-                if (k < cnt) {
-                    T keep = hi ? v[k + cnt] : v[k];
-                    T send = hi ? v[k] : v[k + cnt];
-                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
-                }
-            }
-        }
-        T r = v[0];
-#pragma unroll
-        for (int s = LG; s < 5; ++s) r += __shfl_xor_sync(0xffffffffu, r, 16 >> s);
-        return r;
-    }
-    // lane bits 4, 3, 2 (most significant first) select the value index
-    static __device__ __forceinline__ int moment_of_lane(int lane) {
-        int m = 0;
-#pragma unroll
-        for (int s = 0; s < LG; ++s) m = (m << 1) | ((lane >> (4 - s)) & 1);
-        return m;
-    }
-    static __device__ __forceinline__ bool writer(int lane) {
-        return (lane & ((1 << (5 - LG)) - 1)) == 0;
-    }
-};
-
-// Compensated accumulation of per-tile sums (FP32: Kahan pair; FP64: plain).
-template <typename T> struct Acc;
-template <> struct Acc<float> {
+// Running sum of per-chunk partial sums: a Kahan pair in FP32, plain in FP64.
+template <typename T> struct Kahan;
+template <> struct Kahan<float> {
     float s, c;
     __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
     __device__ __forceinline__ void add(float x) {
-        float y = x - c;
-        float t = s + y;
+        const float y = x - c;
+        const float t = s + y;
         c = (t - s) - y;
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
-template <> struct Acc<double> {
+template <> struct Kahan<double> {
     double s;
     __device__ __forceinline__ void zero() { s = 0.0; }
     __device__ __forceinline__ void add(double x) { s += x; }
@@ -325,269 +278,452 @@ __device__ __forceinline__ long long face_index(const Geo& g, int a, const int q
     return (long long)q[0] + (long long)g.fn[a][0] * ((long long)q[1] + (long long)g.fn[a][1] * q[2]);
 }
 
-template <typename T>
+// Offset of (cell, velocity i, field) in the state layout [i/VC][cell][field][i%VC].
 __device__ __forceinline__ size_t phi_addr(const Geo& g, long long cell, int i, int field) {
-    return ((size_t)(i / VI) * (size_t)g.Nc + (size_t)cell) * (2 * VI) + (size_t)field * VI + (i % VI);
+    return ((size_t)(i / VC) * (size_t)g.Nc + (size_t)cell) * (2 * VC) + (size_t)field * VC + (i % VC);
 }
 
-// --------------------------------------------------------------- the sweep
+// VC consecutive values as vector loads / stores (16-byte aligned by layout).
+template <typename T> struct Chunk;
+template <> struct Chunk<float> {
+    static __device__ __forceinline__ void load(const float* p, float (&v)[VC]) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float (&v)[VC]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Chunk<double> {
+    static __device__ __forceinline__ void load(const double* p, double (&v)[VC]) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double* p, const double (&v)[VC]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
 
-template <int D, int TX, int TY, int TZ>
+// --------------------------------------------------------------- the sweep
+//
+// One CTA owns a tile of cells (one thread per cell) for the velocity tiles
+// of its group and walks them VC velocities at a time.  Per chunk:
+//   phase 1  phibar+ for the tile and its two-cell halo -> shared memory
+//   phase 2  van Leer slopes (eq. VanLeer) of the cells one layer around
+//            the tile -> shared memory
+//   phase 3  per owned cell, its left faces (and right faces where no other
+//            thread has them): upwind reconstruction (eq. relation).
+//            Sweep A sums the face moments (eqs. rhobar-rhoEbar) in
+//            registers; sweep B forms the face phi (eq. phibar inverted), the
+//            flux xi_a phi and its moments, and stages the flux in shared memory
+//   phase 4  (sweep B) per owned cell and velocity: net flux, phi* (eq. phiupdate).
+// All threads of a warp hold the same velocity, so the upwind choice never
+// diverges.
+
+template <int D, int T0_, int T1_, int T2_>
 struct Tile {
-    static constexpr int T0 = TX, T1 = D >= 2 ? TY : 1, T2 = D >= 3 ? TZ : 1;
-    // tile + halo: local cells [-2, T+1] per active axis (the right face of the
-    // last cell reads the slope at local T, which needs local T+1)
+    static constexpr int T0 = T0_, T1 = D >= 2 ? T1_ : 1, T2 = D >= 3 ? T2_ : 1;
+    static constexpr int NT = T0 * T1 * T2;                                   // threads = owned cells
+    // halo box: local cells [-2, T+1] per active axis
     static constexpr int E0 = T0 + 4, E1 = D >= 2 ? T1 + 4 : 1, E2 = D >= 3 ? T2 + 4 : 1;
     static constexpr int BOX = E0 * E1 * E2;
-    static constexpr int OWN = T0 * T1 * T2;
-    static constexpr int NM = 2 + D;
+    static constexpr int NH = BOX - NT;
+    // slope box: local cells [-1, T] per active axis
+    static constexpr int F0 = T0 + 2, F1 = D >= 2 ? T1 + 2 : 1, F2 = D >= 3 ? T2 + 2 : 1;
+    static constexpr int SB = F0 * F1 * F2;
     static constexpr int NF0 = (T0 + 1) * T1 * T2;
     static constexpr int NF1 = D >= 2 ? T0 * (T1 + 1) * T2 : 0;
     static constexpr int NF2 = D >= 3 ? T0 * T1 * (T2 + 1) : 0;
-    static constexpr int NFT = NF0 + NF1 + NF2;         // local face table
-    static __host__ __device__ constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? E0 : E0 * E1); }
-    static __host__ __device__ constexpr int tdim(int a) { return a == 0 ? T0 : (a == 1 ? T1 : T2); }
-    static __host__ __device__ constexpr int foff(int a) { return a == 0 ? 0 : (a == 1 ? NF0 : NF0 + NF1); }
-    // local face (axis a) with right cell at local coords l (l_a in [0, T_a])
-    static __device__ __forceinline__ int face_local(int a, int l0, int l1, int l2) {
+    static constexpr int NFT = NF0 + NF1 + NF2;
+    __host__ __device__ static constexpr int bstride(int a) { return a == 0 ? 1 : (a == 1 ? E0 : E0 * E1); }
+    __host__ __device__ static constexpr int sstride(int a) { return a == 0 ? 1 : (a == 1 ? F0 : F0 * F1); }
+    __host__ __device__ static constexpr int tdim(int a) { return a == 0 ? T0 : (a == 1 ? T1 : T2); }
+    __host__ __device__ static constexpr int foff(int a) { return a == 0 ? 0 : (a == 1 ? NF0 : NF0 + NF1); }
+    __device__ static __forceinline__ int box_of(int l0, int l1, int l2) {
+        return (l0 + 2) + E0 * ((D >= 2 ? l1 + 2 : 0) + E1 * (D >= 3 ? l2 + 2 : 0));
+    }
+    __device__ static __forceinline__ int sbox_of(int l0, int l1, int l2) {
+        return (l0 + 1) + F0 * ((D >= 2 ? l1 + 1 : 0) + F1 * (D >= 3 ? l2 + 1 : 0));
+    }
+    // local face of axis a whose right cell has local coordinates l (l_a in [0, T_a])
+    __device__ static __forceinline__ int face_local(int a, int l0, int l1, int l2) {
         const int d0 = T0 + (a == 0), d1 = T1 + (a == 1);
         return foff(a) + l0 + d0 * (l1 + d1 * l2);
     }
-    static __device__ __forceinline__ int box_of(int l0, int l1, int l2) {
-        return (l0 + 2) + E0 * ((D >= 2 ? l1 + 2 : 0) + E1 * (D >= 3 ? l2 + 2 : 0));
-    }
 };
 
-template <typename T, int D, int TX, int TY, int TZ>
-struct SweepSmem {
-    using TL = Tile<D, TX, TY, TZ>;
-    static constexpr size_t off_P = 0;                                              // [BOX][2][VI] T
-    static constexpr size_t off_cc = off_P + sizeof(T) * TL::BOX * 2 * VI;          // [BOX] CellC
-    static constexpr size_t off_src = off_cc + sizeof(CellC<T>) * TL::BOX;          // [BOX] long long
-    static constexpr size_t off_fl = off_src + sizeof(long long) * TL::BOX;         // [BOX] int flags
-    static constexpr size_t off_fc = ((off_fl + sizeof(int) * TL::BOX + 15) / 16) * 16;  // [NFT] FaceC
-    static constexpr size_t off_acc = ((off_fc + sizeof(FaceC<T>) * TL::NFT + 15) / 16) * 16;  // [NFT][NM] Acc
-    static constexpr size_t bytes = off_acc + sizeof(Acc<T>) * TL::NFT * TL::NM;
+template <typename T, int D, int T0, int T1, int T2>
+struct Smem {
+    using TL = Tile<D, T0, T1, T2>;
+    static constexpr int NCC = D + 11;   // phase-1 constants per box cell
+    static constexpr int NFC = D + 7;    // face constants
+    static constexpr size_t nP = (size_t)2 * VC * TL::BOX;
+    static constexpr size_t nS = (size_t)D * 2 * VC * TL::SB;
+    static constexpr size_t nCC = (size_t)NCC * TL::BOX;
+    static constexpr size_t nFF = (size_t)2 * VC * TL::NFT;
+    static constexpr size_t nFC = (size_t)NFC * TL::NFT;
+    __host__ __device__ static constexpr size_t tcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
+    __host__ __device__ static constexpr size_t bytes(bool B) { return tcount(B) * sizeof(T) + sizeof(int) * (2 * TL::BOX + TL::NH + 1); }
 };
 
-// Reconstruct phibar at the face between box cells L = R - e_a and R along
-// axis a for this lane's velocity: the upwind cell by the sign of xi_a,
-// value phibar+_up + (x_f - h xi - x_up) . sigma_up with the van Leer slope
-// vector of phibar+ at the upwind cell (eq. relation; eq. VanLeer).
-template <typename T, int D, typename TL>
-__device__ __forceinline__ void reconstruct(const T* __restrict__ P, int L, int R, int a, const Vel<T, D>& v,
-                                            int lane, T& gb, T& bb) {
-    auto one = [&](int up, T ka, T& og, T& ob) {
-        const T* pg = P + (size_t)up * 2 * VI + lane;
-        T cg = pg[0], cb = pg[VI];
-        T rg = cg, rb = cb;
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-            const int s = TL::stride(b) * 2 * VI;
-            T lg = pg[-s], lb = pg[VI - s], hg = pg[s], hb = pg[VI + s];
-            T k = (b == a) ? ka : -v.nu[b];
-            rg = fma(k, Num<T>::vanleer(cg - lg, hg - cg), rg);
-            rb = fma(k, Num<T>::vanleer(cb - lb, hb - cb), rb);
-        }
-        og = rg;
-        ob = rb;
-    };
-    const T xa = v.xi[a];
-    const bool left = xa > T(0);
-    const int up = left ? L : R;
-    const T ka = (left ? T(0.5) : T(-0.5)) - v.nu[a];
-    one(up, ka, gb, bb);
-    if (__any_sync(0xffffffffu, xa == T(0))) {   // xi . n = 0: mean of both one-sided values
-        if (xa == T(0)) {
-            T g2, b2;
-            one(L, T(0.5), gb, bb);
-            one(R, T(-0.5), g2, b2);
-            gb = T(0.5) * (gb + g2);
-            bb = T(0.5) * (bb + b2);
-        }
-    }
-}
-
-template <typename T, int D, int TX, int TY, int TZ, bool SWEEP_B>
-__global__ void __launch_bounds__(NTHREADS) k_sweep(Geo g, Bufs<T> bf) {
-    using TL = Tile<D, TX, TY, TZ>;
-    using SM = SweepSmem<T, D, TX, TY, TZ>;
-    constexpr int NM = TL::NM;
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Bufs<T> bf) {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    using SM = Smem<T, D, T0_, T1_, T2_>;
+    constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* P = reinterpret_cast<T*>(smem + SM::off_P);
-    CellC<T>* cc = reinterpret_cast<CellC<T>*>(smem + SM::off_cc);
-    long long* csrc = reinterpret_cast<long long*>(smem + SM::off_src);
-    int* cfl = reinterpret_cast<int*>(smem + SM::off_fl);
-    FaceC<T>* fc = reinterpret_cast<FaceC<T>*>(smem + SM::off_fc);
-    Acc<T>* acc = reinterpret_cast<Acc<T>*>(smem + SM::off_acc);
+    T* const P = reinterpret_cast<T*>(smem);      // [2][VC][BOX] phibar+
+    T* const S = P + SM::nP;                      // [D][2][VC][SB] raw van Leer slopes (times dx)
+    T* const CC = S + SM::nS;                     // [NCC][BOX] cell constants
+    T* const FF = CC + SM::nCC;                   // [2][VC][NFT] face fluxes (sweep B)
+    T* const FC = FF + SM::nFF;                   // [NFC][NFT] face constants (sweep B)
+    int* const csrc = reinterpret_cast<int*>(smem + sizeof(T) * SM::tcount(SWEEP_B));
+    int* const cfl = csrc + BOX;
+    int* const halo = cfl + BOX;
+    int* const nhalo = halo + TL::NH;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = threadIdx.x;
     int tb = blockIdx.x;
     int org[3] = {0, 0, 0};
     org[0] = (tb % g.tiles[0]) * TL::T0;
     tb /= g.tiles[0];
     if (D >= 2) { org[1] = (tb % g.tiles[1]) * TL::T1; tb /= g.tiles[1]; }
-    if (D >= 3) { org[2] = tb * TL::T2; }
+    if (D >= 3) org[2] = tb * TL::T2;
     const int grp = blockIdx.y;
     const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
 
-    // ---- prologue: box cells (BC mapping, cell constants), face constants, accumulators
-    for (int k = tid; k < TL::BOX; k += NTHREADS) {
-        int l[3] = {k % TL::E0 - 2, D >= 2 ? (k / TL::E0) % TL::E1 - 2 : 0, D >= 3 ? k / (TL::E0 * TL::E1) - 2 : 0};
+    // this thread's cell
+    const int la[3] = {t % TL::T0, D >= 2 ? (t / TL::T0) % TL::T1 : 0, D >= 3 ? t / (TL::T0 * TL::T1) : 0};
+    const int qa[3] = {org[0] + la[0], org[1] + la[1], org[2] + la[2]};
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
+    const int kc = TL::box_of(la[0], la[1], la[2]);
+    const int sc = TL::sbox_of(la[0], la[1], la[2]);
+
+    // ---- prologue: halo box (boundary mapping, constants), halo list, face constants
+    if (t == 0) *nhalo = 0;
+    __syncthreads();
+    for (int k = t; k < BOX; k += TL::NT) {
+        const int l[3] = {k % TL::E0 - 2, D >= 2 ? (k / TL::E0) % TL::E1 - 2 : 0,
+                          D >= 3 ? k / (TL::E0 * TL::E1) - 2 : 0};
         int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
         int refl;
         bool dir;
         resolve(g, q, refl, dir);
         const long long c = cell_index(g, q);
-        CellC<T> cst = dir ? bf.cellc0[c] : bf.cellc[c];
-        for (int a = 0; a < D; ++a)
-            if (refl & (1 << a)) cst.u[a] = -cst.u[a];
-        cc[k] = cst;
-        csrc[k] = c;
+        const CellC<T>& cs = dir ? bf.cellc0[c] : bf.cellc[c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) CC[a * BOX + k] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
+        CC[(D + 0) * BOX + k] = cs.cexp;
+        CC[(D + 1) * BOX + k] = cs.pref;
+        CC[(D + 2) * BOX + k] = cs.eb;
+        CC[(D + 3) * BOX + k] = cs.hu2;
+        CC[(D + 4) * BOX + k] = cs.fa_g;
+        CC[(D + 5) * BOX + k] = cs.fb_g;
+        CC[(D + 6) * BOX + k] = cs.fa_b;
+        CC[(D + 7) * BOX + k] = cs.fb_b;
+        CC[(D + 8) * BOX + k] = cs.sa_g;
+        CC[(D + 9) * BOX + k] = cs.sa_b;
+        CC[(D + 10) * BOX + k] = cs.ssrc;
+        csrc[k] = (int)c;
         cfl[k] = refl | (dir ? 8 : 0);
+        bool inner = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) inner = inner && l[a] >= 0 && l[a] < TL::tdim(a);
+        if (!inner) halo[atomicAdd(nhalo, 1)] = k;
     }
-    for (int k = tid; k < TL::NFT * NM; k += NTHREADS) acc[k].zero();
     if (SWEEP_B) {
-        for (int f = tid; f < TL::NFT; f += NTHREADS) {
-            int a = f < TL::NF0 ? 0 : (f < TL::NF0 + TL::NF1 ? 1 : 2);
-            int r = f - TL::foff(a);
+        for (int f = t; f < NFT; f += TL::NT) {
+            const int a = f < TL::NF0 ? 0 : (f < TL::NF0 + TL::NF1 ? 1 : 2);
+            const int r = f - TL::foff(a);
             const int d0 = TL::T0 + (a == 0), d1 = TL::T1 + (a == 1);
             int q[3] = {org[0] + r % d0, org[1] + (D >= 2 ? (r / d0) % d1 : 0), org[2] + (D >= 3 ? r / (d0 * d1) : 0)};
             bool ok = true;
             for (int b = 0; b < D; ++b) ok = ok && q[b] <= g.n[b] - (b == a ? 0 : 1);
-            if (ok) fc[f] = bf.facec[a][face_index(g, a, q)];
+            if (!ok) continue;
+            const FaceC<T>& fs = bf.facec[a][face_index(g, a, q)];
+#pragma unroll
+            for (int b = 0; b < D; ++b) FC[b * NFT + f] = fs.u[b];
+            FC[(D + 0) * NFT + f] = fs.cexp;
+            FC[(D + 1) * NFT + f] = fs.pref;
+            FC[(D + 2) * NFT + f] = fs.eb;
+            FC[(D + 3) * NFT + f] = fs.hu2;
+            FC[(D + 4) * NFT + f] = fs.al_g;
+            FC[(D + 5) * NFT + f] = fs.al_b;
+            FC[(D + 6) * NFT + f] = fs.gam_b;
         }
     }
+    // constants of the owned cell for the distribution update
+    T um_g = T(0), um_b = T(0), usrc = T(0);
+    if (SWEEP_B && valid) {
+        const CellC<T>& cs = bf.cellc[cell_index(g, qa)];
+        um_g = cs.um_g;
+        um_b = cs.um_b;
+        usrc = cs.usrc;
+    }
+    // which faces this thread computes: left faces; right faces where no other thread does
+    bool right[3] = {false, false, false};
+    bool own_right[3] = {false, false, false};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        own_right[a] = valid && qa[a] == g.n[a] - 1;
+        right[a] = valid && (SWEEP_B ? (la[a] == TL::tdim(a) - 1 || own_right[a]) : own_right[a]);
+    }
+    Kahan<T> acc[D][2][NM];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) acc[a][s2][m].zero();
     __syncthreads();
+    const int nh = *nhalo;
 
     for (int vt = vt0; vt < vt1; ++vt) {
-        const int i = vt * VI + lane;
-        const Vel<T, D> v = load_vel<T, D>(g, bf, i);
-
-        // ---- phase 1: phibar+ on the box (eq. phibarplus) from the finalised phi
-        for (int k = warp; k < TL::BOX; k += NWARPS) {
-            const CellC<T>& c = cc[k];
-            const int fl = cfl[k];
-            T ge, be;
-            equilibrium<T, D>(c, v, ge, be);
-            T pg, pb;
-            if (fl & 8) {
-                pg = ge;
-                pb = be;
-            } else {
-                const int is = (fl & 7) ? bf.refl[(fl & 7) * g.Nvp + i] : i;
-                const size_t ad = phi_addr<T>(g, csrc[k], is, 0);
-                const T sg = bf.phi_in[ad], sb = bf.phi_in[ad + VI];
-                const T gg = fma(c.fa_g, sg, c.fb_g * ge);
-                const T bb = fma(c.fa_b, sb, c.fb_b * be);
-                const T dg = gg - ge;
-                pg = fma(c.sa_g, dg, ge);
-                pb = fma(c.ssrc * zeta<T, D>(c, v), dg, fma(c.sa_b, bb - be, be));
+        // velocity records of the chunk (same for every thread)
+        T xi[VC][D], nu[VC][D], w[VC], hx[VC];
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const T* rec = bf.vel + (size_t)(vt * VC + v) * 8;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                xi[v][a] = rec[a];
+                nu[v][a] = (T)g.hdx[a] * xi[v][a];
             }
-            P[(size_t)k * 2 * VI + lane] = pg;
-            P[(size_t)k * 2 * VI + VI + lane] = pb;
+            w[v] = rec[3];
+            hx[v] = rec[4];
+        }
+
+        // ---- phase 1: phibar+ = eq + sa (phi - eq) [+ ssrc Z (g - g_eq)] on the box (eq. phibarplus)
+        T og[VC], ob[VC], oge[VC], obe[VC];   // the owned cell's phi and phi_eq (sweep B)
+        auto cell = [&](int k, bool keep) {
+            const int fl = cfl[k];
+            const long long c = csrc[k];
+            T u[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = CC[a * BOX + k];
+            const T cexp = CC[(D + 0) * BOX + k], pref = CC[(D + 1) * BOX + k], eb = CC[(D + 2) * BOX + k];
+            const T hu2 = CC[(D + 3) * BOX + k];
+            T gs[VC], bs[VC];
+            if (fl & 8) {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) gs[v] = bs[v] = T(0);
+            } else if (fl & 7) {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    const int is = bf.refl[(fl & 7) * g.Nvp + vt * VC + v];
+                    gs[v] = bf.phi_in[phi_addr(g, c, is, 0)];
+                    bs[v] = bf.phi_in[phi_addr(g, c, is, 1)];
+                }
+            } else {
+                const size_t ad = phi_addr(g, c, vt * VC, 0);
+                Chunk<T>::load(bf.phi_in + ad, gs);
+                Chunk<T>::load(bf.phi_in + ad + VC, bs);
+            }
+            const T fa_g = CC[(D + 4) * BOX + k], fb_g = CC[(D + 5) * BOX + k];
+            const T fa_b = CC[(D + 6) * BOX + k], fb_b = CC[(D + 7) * BOX + k];
+            const T sa_g = CC[(D + 8) * BOX + k], sa_b = CC[(D + 9) * BOX + k], ssrc = CC[(D + 10) * BOX + k];
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                T c2 = T(0), z = -hu2;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const T d = xi[v][a] - u[a];
+                    c2 = fma(d, d, c2);
+                    z = fma(xi[v][a], u[a], z);
+                }
+                const T ge = pref * Num<T>::expo(cexp * c2);
+                const T be = (hx[v] + eb) * ge;
+                T pg, pb;
+                if (fl & 8) {
+                    pg = ge;
+                    pb = be;
+                } else {
+                    const T gg = fma(fa_g, gs[v], fb_g * ge);
+                    const T bb = fma(fa_b, bs[v], fb_b * be);
+                    const T dg = gg - ge;
+                    pg = fma(sa_g, dg, ge);
+                    pb = fma(ssrc * z, dg, fma(sa_b, bb - be, be));
+                    if (SWEEP_B && keep) {
+                        og[v] = gg;
+                        ob[v] = bb;
+                        oge[v] = ge;
+                        obe[v] = be;
+                    }
+                }
+                P[(0 * VC + v) * BOX + k] = pg;
+                P[(1 * VC + v) * BOX + k] = pb;
+            }
+        };
+        cell(kc, valid);
+        for (int h = t; h < nh; h += TL::NT) cell(halo[h], false);
+        __syncthreads();
+
+        // ---- phase 2: van Leer slopes (times dx) of the cells [-1, T] around the tile
+        for (int s = t; s < SB; s += TL::NT) {
+            const int sl0 = s % TL::F0 - 1, sl1 = D >= 2 ? (s / TL::F0) % TL::F1 - 1 : 0;
+            const int sl2 = D >= 3 ? s / (TL::F0 * TL::F1) - 1 : 0;
+            const int k = TL::box_of(sl0, sl1, sl2);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int st = TL::bstride(a);
+#pragma unroll
+                for (int f = 0; f < 2; ++f)
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        const T* pp = P + (f * VC + v) * BOX + k;
+                        const T c = pp[0];
+                        S[((a * 2 + f) * VC + v) * SB + s] = Num<T>::vanleer(c - pp[-st], pp[st] - c);
+                    }
+            }
         }
         __syncthreads();
 
-        // ---- phase 2: owned cells
-        for (int o = warp; o < TL::OWN; o += NWARPS) {
-            const int l0 = o % TL::T0, l1 = D >= 2 ? (o / TL::T0) % TL::T1 : 0, l2 = D >= 3 ? o / (TL::T0 * TL::T1) : 0;
-            const int q0 = org[0] + l0, q1 = org[1] + l1, q2 = org[2] + l2;
-            if (q0 >= g.n[0] || (D >= 2 && q1 >= g.n[1]) || (D >= 3 && q2 >= g.n[2])) continue;
-            const int kc = TL::box_of(l0, l1, l2);
-            const int qa[3] = {q0, q1, q2};
-            const int la[3] = {l0, l1, l2};
-            T dFg = T(0), dFb = T(0);
+        // ---- phase 3: faces of the owned cell
+        if (valid) {
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const int s = TL::stride(a);
-                const bool last = qa[a] == g.n[a] - 1;
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {     // 0: left face of the cell, 1: right face
-                    if (!SWEEP_B && side == 1 && !last) continue;
-                    const int R = kc + side * s, L = R - s;
-                    T gb, bb;
-                    reconstruct<T, D, TL>(P, L, R, a, v, lane, gb, bb);
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 1 && !right[a]) continue;
+                    const int Lb = kc + (side - 1) * TL::bstride(a), Rb = Lb + TL::bstride(a);
+                    const int Ls = sc + (side - 1) * TL::sstride(a), Rs = Ls + TL::sstride(a);
                     int lf[3] = {la[0], la[1], la[2]};
                     lf[a] += side;
                     const int fl = TL::face_local(a, lf[0], lf[1], lf[2]);
-                    const bool own = side == 0 || last;
-                    T mom[NM];
-                    if (!SWEEP_B) {
-                        // face conserved variables (eqs. rhobar-rhoEbar with a = 0)
-                        const T wg = v.w * gb;
-                        mom[0] = wg;
+                    const bool own = side == 0 || own_right[a];
+                    T fu[D], fcexp = T(0), fpref = T(0), feb = T(0), fhu2 = T(0), alg = T(0), alb = T(0), gmb = T(0);
+                    if (SWEEP_B) {
 #pragma unroll
-                        for (int b = 0; b < D; ++b) mom[1 + b] = v.xi[b] * wg;
-                        mom[1 + D] = v.w * bb;
-                    } else {
-                        // face equilibrium and inversion of eq. phibar, then the microflux
-                        const FaceC<T>& f = fc[fl];
-                        T ge, be;
-                        equilibrium<T, D>(f, v, ge, be);
-                        const T gf = fma(f.al_g, gb - ge, ge);
-                        const T bf_ = fma(f.gam_b * zeta<T, D>(f, v), gf - ge, fma(f.al_b, bb - be, be));
-                        const T Fg = v.xi[a] * gf, Fb = v.xi[a] * bf_;
-                        const T idx = (T)g.idx[a];
-                        if (side == 0) {
-                            dFg = fma(-idx, Fg, dFg);
-                            dFb = fma(-idx, Fb, dFb);
-                        } else {
-                            dFg = fma(idx, Fg, dFg);
-                            dFb = fma(idx, Fb, dFb);
+                        for (int b = 0; b < D; ++b) fu[b] = FC[b * NFT + fl];
+                        fcexp = FC[(D + 0) * NFT + fl];
+                        fpref = FC[(D + 1) * NFT + fl];
+                        feb = FC[(D + 2) * NFT + fl];
+                        fhu2 = FC[(D + 3) * NFT + fl];
+                        alg = FC[(D + 4) * NFT + fl];
+                        alb = FC[(D + 5) * NFT + fl];
+                        gmb = FC[(D + 6) * NFT + fl];
+                    }
+                    T sm[NM];
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) sm[m] = T(0);
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        // phibar at the face, t + h: upwind value + (x_f - h xi - x_up) . sigma_up
+                        auto recon = [&](int up, int ups, T ka, T& gb, T& bb) {
+                            T rg = P[(0 * VC + v) * BOX + up], rb = P[(1 * VC + v) * BOX + up];
+#pragma unroll
+                            for (int b = 0; b < D; ++b) {
+                                const T k = (b == a) ? ka : -nu[v][b];
+                                rg = fma(k, S[((b * 2 + 0) * VC + v) * SB + ups], rg);
+                                rb = fma(k, S[((b * 2 + 1) * VC + v) * SB + ups], rb);
+                            }
+                            gb = rg;
+                            bb = rb;
+                        };
+                        const T x = xi[v][a];
+                        T gb, bb;
+                        if (x != T(0)) {
+                            const bool lft = x > T(0);
+                            recon(lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(0.5) : T(-0.5)) - nu[v][a], gb, bb);
+                        } else {   // xi . n = 0: mean of both one-sided values
+                            T g2, b2;
+                            recon(Lb, Ls, T(0.5), gb, bb);
+                            recon(Rb, Rs, T(-0.5), g2, b2);
+                            gb = T(0.5) * (gb + g2);
+                            bb = T(0.5) * (bb + b2);
                         }
-                        const T wg = v.w * Fg;
-                        mom[0] = wg;
+                        if (!SWEEP_B) {
+                            // face conserved variables (eqs. rhobar-rhoEbar, a = 0)
+                            const T wg = w[v] * gb;
+                            sm[0] += wg;
 #pragma unroll
-                        for (int b = 0; b < D; ++b) mom[1 + b] = v.xi[b] * wg;
-                        mom[1 + D] = v.w * Fb;
+                            for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
+                            sm[1 + D] = fma(w[v], bb, sm[1 + D]);
+                        } else {
+                            // face equilibrium, inverse of eq. phibar, microflux xi_a phi
+                            T c2 = T(0), z = -fhu2;
+#pragma unroll
+                            for (int b = 0; b < D; ++b) {
+                                const T d = xi[v][b] - fu[b];
+                                c2 = fma(d, d, c2);
+                                z = fma(xi[v][b], fu[b], z);
+                            }
+                            const T ge = fpref * Num<T>::expo(fcexp * c2);
+                            const T be = (hx[v] + feb) * ge;
+                            const T gf = fma(alg, gb - ge, ge);
+                            const T bfv = fma(gmb * z, gf - ge, fma(alb, bb - be, be));
+                            const T Fg = x * gf, Fb = x * bfv;
+                            FF[(0 * VC + v) * NFT + fl] = Fg;
+                            FF[(1 * VC + v) * NFT + fl] = Fb;
+                            const T wg = w[v] * Fg;
+                            sm[0] += wg;
+#pragma unroll
+                            for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
+                            sm[1 + D] = fma(w[v], Fb, sm[1 + D]);
+                        }
                     }
                     if (own) {
-                        const T r = WarpSum<T, NM>::run(mom, lane);
-                        const int m = WarpSum<T, NM>::moment_of_lane(lane);
-                        if (WarpSum<T, NM>::writer(lane) && m < NM) acc[fl * NM + m].add(r);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) acc[a][side][m].add(sm[m]);
                     }
                 }
             }
-            if (SWEEP_B) {
-                // distribution update (eq. phiupdate) up to its last factor:
-                // phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) + dt S - dt dF
-                const CellC<T>& c = cc[kc];
-                T ge, be;
-                equilibrium<T, D>(c, v, ge, be);
-                const long long cell = csrc[kc];
-                const size_t ad = phi_addr<T>(g, cell, i, 0);
-                const T sg = bf.phi_in[ad], sb = bf.phi_in[ad + VI];
-                const T gg = fma(c.fa_g, sg, c.fb_g * ge);
-                const T bb = fma(c.fa_b, sb, c.fb_b * be);
-                const T dg = gg - ge;
+        }
+
+        if (SWEEP_B) {
+            __syncthreads();
+            // ---- phase 4: phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
+            if (valid) {
+                T u[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) u[a] = CC[a * BOX + kc];
+                const T hu2 = CC[(D + 3) * BOX + kc];
+                T ng[VC], nb[VC];
                 const T dt = (T)g.dt;
-                const T ng = fma(-dt, dFg, fma(c.um_g, dg, ge));
-                const T nb = fma(-dt, dFb, fma(c.usrc * zeta<T, D>(c, v), dg, fma(c.um_b, bb - be, be)));
-                bf.phi_out[ad] = ng;
-                bf.phi_out[ad + VI] = nb;
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    T dFg = T(0), dFb = T(0), z = -hu2;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const int fl0 = TL::face_local(a, la[0], la[1], la[2]);
+                        const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
+                        const T idx = (T)g.idx[a];
+                        dFg = fma(idx, FF[(0 * VC + v) * NFT + fl1] - FF[(0 * VC + v) * NFT + fl0], dFg);
+                        dFb = fma(idx, FF[(1 * VC + v) * NFT + fl1] - FF[(1 * VC + v) * NFT + fl0], dFb);
+                        z = fma(xi[v][a], u[a], z);
+                    }
+                    const T dg = og[v] - oge[v];
+                    ng[v] = fma(-dt, dFg, fma(um_g, dg, oge[v]));
+                    nb[v] = fma(-dt, dFb, fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
+                }
+                const size_t ad = phi_addr(g, cell_index(g, qa), vt * VC, 0);
+                Chunk<T>::store(bf.phi_out + ad, ng);
+                Chunk<T>::store(bf.phi_out + ad + VC, nb);
             }
         }
         __syncthreads();
     }
 
-    // ---- epilogue: write this group's partial face sums
-    double* const* dst = SWEEP_B ? bf.mf : bf.wf;
-    for (int k = tid; k < TL::NFT * NM; k += NTHREADS) {
-        const int f = k / NM, m = k % NM;
-        int a = f < TL::NF0 ? 0 : (f < TL::NF0 + TL::NF1 ? 1 : 2);
-        if (a >= D) continue;
-        int r = f - TL::foff(a);
-        const int d0 = TL::T0 + (a == 0), d1 = TL::T1 + (a == 1);
-        int l[3] = {r % d0, D >= 2 ? (r / d0) % d1 : 0, D >= 3 ? r / (d0 * d1) : 0};
-        int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
-        bool own = true;
-        for (int b = 0; b < D; ++b) {
-            if (b == a) own = own && q[b] <= g.n[b] && (l[b] < TL::tdim(b) || q[b] == g.n[b]);
-            else own = own && q[b] < g.n[b];
+    // ---- epilogue: this group's partial face sums
+    if (valid) {
+        double* const* dst = SWEEP_B ? bf.mf : bf.wf;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const long long f0 = face_index(g, a, qa);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][0][m].value();
+            if (own_right[a]) {
+                int qr[3] = {qa[0], qa[1], qa[2]};
+                qr[a] += 1;
+                const long long f1 = face_index(g, a, qr);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f1] = acc[a][1][m].value();
+            }
         }
-        if (!own) continue;
-        dst[a][((size_t)grp * NM + m) * g.nf[a] + face_index(g, a, q)] = acc[k].value();
     }
 }
 
@@ -685,9 +821,9 @@ __global__ void k_init(Geo g, Bufs<T> bf, const double* __restrict__ fields) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
         equilibrium<T, D>(cc, v, ge, be);
-        const size_t ad = phi_addr<T>(g, c, i, 0);
+        const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = ge;
-        bf.phi_out[ad + VI] = be;
+        bf.phi_out[ad + VC] = be;
     }
 }
 
@@ -719,9 +855,9 @@ __global__ void k_finalise(Geo g, Bufs<T> bf) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
         equilibrium<T, D>(cc, v, ge, be);
-        const size_t ad = phi_addr<T>(g, c, i, 0);
+        const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
-        bf.phi_out[ad + VI] = fma(cc.fa_b, bf.phi_in[ad + VI], cc.fb_b * be);
+        bf.phi_out[ad + VC] = fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);
     }
 }
 

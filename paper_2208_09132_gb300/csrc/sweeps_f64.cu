@@ -6,31 +6,31 @@ namespace cdg {
 
 TileShape tile_shape(int precision, int D) {
     if (precision == 1) {
-        if (D == 1) return {{64, 1, 1}};
-        if (D == 2) return {{16, 8, 1}};
-        return {{4, 4, 4}};
+        if (D == 1) return {{256, 1, 1}};
+        if (D == 2) return {{32, 8, 1}};
+        return {{8, 4, 4}};
     }
-    if (D == 1) return {{64, 1, 1}};
-    if (D == 2) return {{8, 8, 1}};
-    return {{4, 2, 2}};
+    if (D == 1) return {{256, 1, 1}};
+    if (D == 2) return {{16, 8, 1}};
+    return {{4, 4, 4}};
 }
 
 size_t sweep_smem_bytes(int precision, int D) {
     if (precision == 1) {
-        if (D == 1) return SweepSmem<float, 1, 64, 1, 1>::bytes;
-        if (D == 2) return SweepSmem<float, 2, 16, 8, 1>::bytes;
-        return SweepSmem<float, 3, 4, 4, 4>::bytes;
+        if (D == 1) return Smem<float, 1, 256, 1, 1>::bytes(true);
+        if (D == 2) return Smem<float, 2, 32, 8, 1>::bytes(true);
+        return Smem<float, 3, 8, 4, 4>::bytes(true);
     }
-    if (D == 1) return SweepSmem<double, 1, 64, 1, 1>::bytes;
-    if (D == 2) return SweepSmem<double, 2, 8, 8, 1>::bytes;
-    return SweepSmem<double, 3, 4, 2, 2>::bytes;
+    if (D == 1) return Smem<double, 1, 256, 1, 1>::bytes(true);
+    if (D == 2) return Smem<double, 2, 16, 8, 1>::bytes(true);
+    return Smem<double, 3, 4, 4, 4>::bytes(true);
 }
 
 cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s, cudaEvent_t* ev) {
     switch (g.D) {
-        case 1: return run_step<double, 1, 64, 1, 1>(g, b, s, ev);
-        case 2: return run_step<double, 2, 8, 8, 1>(g, b, s, ev);
-        default: return run_step<double, 3, 4, 2, 2>(g, b, s, ev);
+        case 1: return run_step<double, 1, 256, 1, 1>(g, b, s, ev);
+        case 2: return run_step<double, 2, 16, 8, 1>(g, b, s, ev);
+        default: return run_step<double, 3, 4, 4, 4>(g, b, s, ev);
     }
 }
 cudaError_t launch_init_f64(const Geo& g, const Bufs<double>& b, const double* f, cudaStream_t s) {
