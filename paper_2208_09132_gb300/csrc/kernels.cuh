@@ -79,7 +79,11 @@ struct Bufs {
 template <typename T> struct Num;
 template <> struct Num<float> {
     // equilibrium exponent on base 2: exp(-c^2/(2RT)) = exp2(c^2 * cexp)
-    static __device__ __forceinline__ float expo(float x) { return exp2f(x); }
+    static __device__ __forceinline__ float expo(float x) {
+        float y;   // hardware base-2 exponential (relative error ~2^-22, subnormal results flushed)
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     static __host__ __device__ __forceinline__ double cexp_scale() { return 1.4426950408889634; }
     static __device__ __forceinline__ float vanleer(float s1, float s2) {
         float p = s1 * s2;
@@ -354,37 +358,53 @@ struct Tile {
     }
 };
 
+// Four values of the working precision: one velocity chunk of one cell, or
+// four packed constants.  Aligned so that shared-memory traffic is 128-bit.
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+    T v[4];
+};
+
 template <typename T, int D, int T0, int T1, int T2>
 struct Smem {
     using TL = Tile<D, T0, T1, T2>;
-    static constexpr int NCC = D + 11;   // phase-1 constants per box cell
-    static constexpr int NFC = D + 7;    // face constants
-    static constexpr size_t nP = (size_t)2 * VC * TL::BOX;
-    static constexpr size_t nS = (size_t)D * 2 * VC * TL::SB;
-    static constexpr size_t nCC = (size_t)NCC * TL::BOX;
-    static constexpr size_t nFF = (size_t)2 * VC * TL::NFT;
-    static constexpr size_t nFC = (size_t)NFC * TL::NFT;
-    __host__ __device__ static constexpr size_t tcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
-    __host__ __device__ static constexpr size_t bytes(bool B) { return tcount(B) * sizeof(T) + sizeof(int) * (2 * TL::BOX + TL::NH + 1); }
+    static constexpr int NCC = D + 11;           // phase-1 constants per box cell
+    static constexpr int NCCV = (NCC + 3) / 4;   // ... packed in V4
+    static constexpr int NFC = D + 7;            // face constants
+    static constexpr int NFCV = (NFC + 3) / 4;
+    static constexpr size_t nP = (size_t)2 * TL::BOX;          // V4 units
+    static constexpr size_t nS = (size_t)D * 2 * TL::SB;
+    static constexpr size_t nCC = (size_t)NCCV * TL::BOX;
+    static constexpr size_t nFF = (size_t)2 * TL::NFT;
+    static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
+    __host__ __device__ static constexpr size_t vcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
+    __host__ __device__ static constexpr size_t bytes(bool B) {
+        return vcount(B) * sizeof(V4<T>) + sizeof(int) * (2 * TL::BOX + TL::NH + 32);
+    }
 };
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Bufs<T> bf) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using SM = Smem<T, D, T0_, T1_, T2_>;
+    using Q = V4<T>;
     constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* const P = reinterpret_cast<T*>(smem);      // [2][VC][BOX] phibar+
-    T* const S = P + SM::nP;                      // [D][2][VC][SB] raw van Leer slopes (times dx)
-    T* const CC = S + SM::nS;                     // [NCC][BOX] cell constants
-    T* const FF = CC + SM::nCC;                   // [2][VC][NFT] face fluxes (sweep B)
-    T* const FC = FF + SM::nFF;                   // [NFC][NFT] face constants (sweep B)
-    int* const csrc = reinterpret_cast<int*>(smem + sizeof(T) * SM::tcount(SWEEP_B));
+    constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
+    static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
+    static_assert(TL::NT % 32 == 0, "whole warps");
+    extern __shared__ __align__(32) unsigned char smem[];
+    Q* const P = reinterpret_cast<Q*>(smem);      // [2][BOX] phibar+ chunk per cell
+    Q* const S = P + SM::nP;                      // [D][2][SB] raw van Leer slopes (times dx)
+    Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
+    Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
+    Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
+    int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
     int* const cfl = csrc + BOX;
     int* const halo = cfl + BOX;
-    int* const nhalo = halo + TL::NH;
+    int* const wcount = halo + TL::NH;            // [32] per-warp halo counts
 
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = TL::NT / 32;
     int tb = blockIdx.x;
     int org[3] = {0, 0, 0};
     org[0] = (tb % g.tiles[0]) * TL::T0;
@@ -403,37 +423,75 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
     const int kc = TL::box_of(la[0], la[1], la[2]);
     const int sc = TL::sbox_of(la[0], la[1], la[2]);
 
-    // ---- prologue: halo box (boundary mapping, constants), halo list, face constants
-    if (t == 0) *nhalo = 0;
-    __syncthreads();
+    auto box_local = [&](int k, int l[3]) {
+        l[0] = k % TL::E0 - 2;
+        l[1] = D >= 2 ? (k / TL::E0) % TL::E1 - 2 : 0;
+        l[2] = D >= 3 ? k / (TL::E0 * TL::E1) - 2 : 0;
+    };
+    auto is_halo = [&](int k) {
+        int l[3];
+        box_local(k, l);
+        bool inner = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) inner = inner && l[a] >= 0 && l[a] < TL::tdim(a);
+        return !inner;
+    };
+
+    // ---- prologue: halo box (boundary mapping, packed constants), ordered halo list, face constants
     for (int k = t; k < BOX; k += TL::NT) {
-        const int l[3] = {k % TL::E0 - 2, D >= 2 ? (k / TL::E0) % TL::E1 - 2 : 0,
-                          D >= 3 ? k / (TL::E0 * TL::E1) - 2 : 0};
+        int l[3];
+        box_local(k, l);
         int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
         int refl;
         bool dir;
         resolve(g, q, refl, dir);
         const long long c = cell_index(g, q);
         const CellC<T>& cs = dir ? bf.cellc0[c] : bf.cellc[c];
+        T cst[4 * NCCV];
 #pragma unroll
-        for (int a = 0; a < D; ++a) CC[a * BOX + k] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
-        CC[(D + 0) * BOX + k] = cs.cexp;
-        CC[(D + 1) * BOX + k] = cs.pref;
-        CC[(D + 2) * BOX + k] = cs.eb;
-        CC[(D + 3) * BOX + k] = cs.hu2;
-        CC[(D + 4) * BOX + k] = cs.fa_g;
-        CC[(D + 5) * BOX + k] = cs.fb_g;
-        CC[(D + 6) * BOX + k] = cs.fa_b;
-        CC[(D + 7) * BOX + k] = cs.fb_b;
-        CC[(D + 8) * BOX + k] = cs.sa_g;
-        CC[(D + 9) * BOX + k] = cs.sa_b;
-        CC[(D + 10) * BOX + k] = cs.ssrc;
+        for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
+        cst[D + 0] = cs.cexp;
+        cst[D + 1] = cs.pref;
+        cst[D + 2] = cs.eb;
+        cst[D + 3] = cs.hu2;
+        cst[D + 4] = cs.fa_g;
+        cst[D + 5] = cs.fb_g;
+        cst[D + 6] = cs.fa_b;
+        cst[D + 7] = cs.fb_b;
+        cst[D + 8] = cs.sa_g;
+        cst[D + 9] = cs.sa_b;
+        cst[D + 10] = cs.ssrc;
+#pragma unroll
+        for (int j = D + 11; j < 4 * NCCV; ++j) cst[j] = T(0);
+#pragma unroll
+        for (int j = 0; j < NCCV; ++j) {
+            Q qv;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
+            CC[j * BOX + k] = qv;
+        }
         csrc[k] = (int)c;
         cfl[k] = refl | (dir ? 8 : 0);
-        bool inner = true;
-#pragma unroll
-        for (int a = 0; a < D; ++a) inner = inner && l[a] >= 0 && l[a] < TL::tdim(a);
-        if (!inner) halo[atomicAdd(nhalo, 1)] = k;
+    }
+    {   // halo list in box order (warp ballots), so neighbouring threads touch neighbouring cells
+        constexpr int PER = ((BOX + NW - 1) / NW + 31) / 32 * 32;
+        const int k0 = warp * PER, k1 = min(BOX, k0 + PER);
+        int cnt = 0;
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int k = kb + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, k < k1 && is_halo(k)));
+        }
+        if (lane == 0) wcount[warp] = cnt;
+        __syncthreads();
+        int base = 0;
+        for (int w2 = 0; w2 < warp; ++w2) base += wcount[w2];
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int k = kb + lane;
+            const bool hk = k < k1 && is_halo(k);
+            const unsigned m = __ballot_sync(0xffffffffu, hk);
+            if (hk) halo[base + __popc(m & ((1u << lane) - 1u))] = k;
+            base += __popc(m);
+        }
     }
     if (SWEEP_B) {
         for (int f = t; f < NFT; f += TL::NT) {
@@ -445,15 +503,25 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
             for (int b = 0; b < D; ++b) ok = ok && q[b] <= g.n[b] - (b == a ? 0 : 1);
             if (!ok) continue;
             const FaceC<T>& fs = bf.facec[a][face_index(g, a, q)];
+            T cst[4 * NFCV];
 #pragma unroll
-            for (int b = 0; b < D; ++b) FC[b * NFT + f] = fs.u[b];
-            FC[(D + 0) * NFT + f] = fs.cexp;
-            FC[(D + 1) * NFT + f] = fs.pref;
-            FC[(D + 2) * NFT + f] = fs.eb;
-            FC[(D + 3) * NFT + f] = fs.hu2;
-            FC[(D + 4) * NFT + f] = fs.al_g;
-            FC[(D + 5) * NFT + f] = fs.al_b;
-            FC[(D + 6) * NFT + f] = fs.gam_b;
+            for (int b = 0; b < D; ++b) cst[b] = fs.u[b];
+            cst[D + 0] = fs.cexp;
+            cst[D + 1] = fs.pref;
+            cst[D + 2] = fs.eb;
+            cst[D + 3] = fs.hu2;
+            cst[D + 4] = fs.al_g;
+            cst[D + 5] = fs.al_b;
+            cst[D + 6] = fs.gam_b;
+#pragma unroll
+            for (int j = D + 7; j < 4 * NFCV; ++j) cst[j] = T(0);
+#pragma unroll
+            for (int j = 0; j < NFCV; ++j) {
+                Q qv;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
+                FC[j * NFT + f] = qv;
+            }
         }
     }
     // constants of the owned cell for the distribution update
@@ -480,7 +548,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
 #pragma unroll
             for (int m = 0; m < NM; ++m) acc[a][s2][m].zero();
     __syncthreads();
-    const int nh = *nhalo;
+    constexpr int NH = TL::NH;
 
     for (int vt = vt0; vt < vt1; ++vt) {
         // velocity records of the chunk (same for every thread)
@@ -496,17 +564,31 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
             w[v] = rec[3];
             hx[v] = rec[4];
         }
+        // per axis: +1 / -1 when the chunk's four xi_a share a strict sign, else 0
+        int sgn[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            bool pos = true, neg = true;
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                pos = pos && xi[v][a] > T(0);
+                neg = neg && xi[v][a] < T(0);
+            }
+            sgn[a] = pos ? 1 : (neg ? -1 : 0);
+        }
 
         // ---- phase 1: phibar+ = eq + sa (phi - eq) [+ ssrc Z (g - g_eq)] on the box (eq. phibarplus)
         T og[VC], ob[VC], oge[VC], obe[VC];   // the owned cell's phi and phi_eq (sweep B)
         auto cell = [&](int k, bool keep) {
             const int fl = cfl[k];
             const long long c = csrc[k];
-            T u[D];
+            T cst[4 * NCCV];
 #pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = CC[a * BOX + k];
-            const T cexp = CC[(D + 0) * BOX + k], pref = CC[(D + 1) * BOX + k], eb = CC[(D + 2) * BOX + k];
-            const T hu2 = CC[(D + 3) * BOX + k];
+            for (int j = 0; j < NCCV; ++j) {
+                const Q qv = CC[j * BOX + k];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cst[4 * j + e] = qv.v[e];
+            }
             T gs[VC], bs[VC];
             if (fl & 8) {
 #pragma unroll
@@ -523,30 +605,30 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
                 Chunk<T>::load(bf.phi_in + ad, gs);
                 Chunk<T>::load(bf.phi_in + ad + VC, bs);
             }
-            const T fa_g = CC[(D + 4) * BOX + k], fb_g = CC[(D + 5) * BOX + k];
-            const T fa_b = CC[(D + 6) * BOX + k], fb_b = CC[(D + 7) * BOX + k];
-            const T sa_g = CC[(D + 8) * BOX + k], sa_b = CC[(D + 9) * BOX + k], ssrc = CC[(D + 10) * BOX + k];
+            const T cexp = cst[D + 0], pref = cst[D + 1], eb = cst[D + 2], hu2 = cst[D + 3];
+            const T fa_g = cst[D + 4], fb_g = cst[D + 5], fa_b = cst[D + 6], fb_b = cst[D + 7];
+            const T sa_g = cst[D + 8], sa_b = cst[D + 9], ssrc = cst[D + 10];
+            Q qg, qb;
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
                 T c2 = T(0), z = -hu2;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const T d = xi[v][a] - u[a];
+                    const T d = xi[v][a] - cst[a];
                     c2 = fma(d, d, c2);
-                    z = fma(xi[v][a], u[a], z);
+                    z = fma(xi[v][a], cst[a], z);
                 }
                 const T ge = pref * Num<T>::expo(cexp * c2);
                 const T be = (hx[v] + eb) * ge;
-                T pg, pb;
                 if (fl & 8) {
-                    pg = ge;
-                    pb = be;
+                    qg.v[v] = ge;
+                    qb.v[v] = be;
                 } else {
                     const T gg = fma(fa_g, gs[v], fb_g * ge);
                     const T bb = fma(fa_b, bs[v], fb_b * be);
                     const T dg = gg - ge;
-                    pg = fma(sa_g, dg, ge);
-                    pb = fma(ssrc * z, dg, fma(sa_b, bb - be, be));
+                    qg.v[v] = fma(sa_g, dg, ge);
+                    qb.v[v] = fma(ssrc * z, dg, fma(sa_b, bb - be, be));
                     if (SWEEP_B && keep) {
                         og[v] = gg;
                         ob[v] = bb;
@@ -554,12 +636,12 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
                         obe[v] = be;
                     }
                 }
-                P[(0 * VC + v) * BOX + k] = pg;
-                P[(1 * VC + v) * BOX + k] = pb;
             }
+            P[0 * BOX + k] = qg;
+            P[1 * BOX + k] = qb;
         };
         cell(kc, valid);
-        for (int h = t; h < nh; h += TL::NT) cell(halo[h], false);
+        for (int h = t; h < NH; h += TL::NT) cell(halo[h], false);
         __syncthreads();
 
         // ---- phase 2: van Leer slopes (times dx) of the cells [-1, T] around the tile
@@ -568,16 +650,17 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
             const int sl2 = D >= 3 ? s / (TL::F0 * TL::F1) - 1 : 0;
             const int k = TL::box_of(sl0, sl1, sl2);
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const int st = TL::bstride(a);
+            for (int f = 0; f < 2; ++f) {
+                const Q c = P[f * BOX + k];
 #pragma unroll
-                for (int f = 0; f < 2; ++f)
+                for (int a = 0; a < D; ++a) {
+                    const int st = TL::bstride(a);
+                    const Q l = P[f * BOX + k - st], r = P[f * BOX + k + st];
+                    Q o;
 #pragma unroll
-                    for (int v = 0; v < VC; ++v) {
-                        const T* pp = P + (f * VC + v) * BOX + k;
-                        const T c = pp[0];
-                        S[((a * 2 + f) * VC + v) * SB + s] = Num<T>::vanleer(c - pp[-st], pp[st] - c);
-                    }
+                    for (int v = 0; v < VC; ++v) o.v[v] = Num<T>::vanleer(c.v[v] - l.v[v], r.v[v] - c.v[v]);
+                    S[(a * 2 + f) * SB + s] = o;
+                }
             }
         }
         __syncthreads();
@@ -595,76 +678,108 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
                     lf[a] += side;
                     const int fl = TL::face_local(a, lf[0], lf[1], lf[2]);
                     const bool own = side == 0 || own_right[a];
-                    T fu[D], fcexp = T(0), fpref = T(0), feb = T(0), fhu2 = T(0), alg = T(0), alb = T(0), gmb = T(0);
-                    if (SWEEP_B) {
+                    // phibar at the face, t + h: upwind value + (x_f - h xi - x_up) . sigma_up
+                    T gb[VC], bb[VC];
+                    if (sgn[a] != 0) {
+                        const bool lft = sgn[a] > 0;
+                        const int up = lft ? Lb : Rb, ups = lft ? Ls : Rs;
+                        const Q pg = P[0 * BOX + up], pb = P[1 * BOX + up];
+                        Q sg[D], sb[D];
 #pragma unroll
-                        for (int b = 0; b < D; ++b) fu[b] = FC[b * NFT + fl];
-                        fcexp = FC[(D + 0) * NFT + fl];
-                        fpref = FC[(D + 1) * NFT + fl];
-                        feb = FC[(D + 2) * NFT + fl];
-                        fhu2 = FC[(D + 3) * NFT + fl];
-                        alg = FC[(D + 4) * NFT + fl];
-                        alb = FC[(D + 5) * NFT + fl];
-                        gmb = FC[(D + 6) * NFT + fl];
+                        for (int b = 0; b < D; ++b) {
+                            sg[b] = S[(b * 2 + 0) * SB + ups];
+                            sb[b] = S[(b * 2 + 1) * SB + ups];
+                        }
+                        const T half = lft ? T(0.5) : T(-0.5);
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            T rg = pg.v[v], rb = pb.v[v];
+#pragma unroll
+                            for (int b = 0; b < D; ++b) {
+                                const T k = (b == a) ? half - nu[v][a] : -nu[v][b];
+                                rg = fma(k, sg[b].v[v], rg);
+                                rb = fma(k, sb[b].v[v], rb);
+                            }
+                            gb[v] = rg;
+                            bb[v] = rb;
+                        }
+                    } else {
+                        const T* Ps = reinterpret_cast<const T*>(P);
+                        const T* Ss = reinterpret_cast<const T*>(S);
+                        auto recon = [&](int v, int up, int ups, T ka, T& rg, T& rb) {
+                            rg = Ps[(0 * BOX + up) * VC + v];
+                            rb = Ps[(1 * BOX + up) * VC + v];
+#pragma unroll
+                            for (int b = 0; b < D; ++b) {
+                                const T k = (b == a) ? ka : -nu[v][b];
+                                rg = fma(k, Ss[((b * 2 + 0) * SB + ups) * VC + v], rg);
+                                rb = fma(k, Ss[((b * 2 + 1) * SB + ups) * VC + v], rb);
+                            }
+                        };
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            const T x = xi[v][a];
+                            if (x != T(0)) {
+                                const bool lft = x > T(0);
+                                recon(v, lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(0.5) : T(-0.5)) - nu[v][a], gb[v], bb[v]);
+                            } else {   // xi . n = 0: mean of both one-sided values
+                                T g1, b1, g2, b2;
+                                recon(v, Lb, Ls, T(0.5), g1, b1);
+                                recon(v, Rb, Rs, T(-0.5), g2, b2);
+                                gb[v] = T(0.5) * (g1 + g2);
+                                bb[v] = T(0.5) * (b1 + b2);
+                            }
+                        }
                     }
                     T sm[NM];
 #pragma unroll
                     for (int m = 0; m < NM; ++m) sm[m] = T(0);
+                    if (!SWEEP_B) {
+                        // face conserved variables (eqs. rhobar-rhoEbar, a = 0)
 #pragma unroll
-                    for (int v = 0; v < VC; ++v) {
-                        // phibar at the face, t + h: upwind value + (x_f - h xi - x_up) . sigma_up
-                        auto recon = [&](int up, int ups, T ka, T& gb, T& bb) {
-                            T rg = P[(0 * VC + v) * BOX + up], rb = P[(1 * VC + v) * BOX + up];
-#pragma unroll
-                            for (int b = 0; b < D; ++b) {
-                                const T k = (b == a) ? ka : -nu[v][b];
-                                rg = fma(k, S[((b * 2 + 0) * VC + v) * SB + ups], rg);
-                                rb = fma(k, S[((b * 2 + 1) * VC + v) * SB + ups], rb);
-                            }
-                            gb = rg;
-                            bb = rb;
-                        };
-                        const T x = xi[v][a];
-                        T gb, bb;
-                        if (x != T(0)) {
-                            const bool lft = x > T(0);
-                            recon(lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(0.5) : T(-0.5)) - nu[v][a], gb, bb);
-                        } else {   // xi . n = 0: mean of both one-sided values
-                            T g2, b2;
-                            recon(Lb, Ls, T(0.5), gb, bb);
-                            recon(Rb, Rs, T(-0.5), g2, b2);
-                            gb = T(0.5) * (gb + g2);
-                            bb = T(0.5) * (bb + b2);
-                        }
-                        if (!SWEEP_B) {
-                            // face conserved variables (eqs. rhobar-rhoEbar, a = 0)
-                            const T wg = w[v] * gb;
+                        for (int v = 0; v < VC; ++v) {
+                            const T wg = w[v] * gb[v];
                             sm[0] += wg;
 #pragma unroll
                             for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
-                            sm[1 + D] = fma(w[v], bb, sm[1 + D]);
-                        } else {
-                            // face equilibrium, inverse of eq. phibar, microflux xi_a phi
+                            sm[1 + D] = fma(w[v], bb[v], sm[1 + D]);
+                        }
+                    } else {
+                        // face equilibrium, inverse of eq. phibar, microflux xi_a phi
+                        T fcst[4 * NFCV];
+#pragma unroll
+                        for (int j = 0; j < NFCV; ++j) {
+                            const Q qv = FC[j * NFT + fl];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
+                        }
+                        const T fcexp = fcst[D + 0], fpref = fcst[D + 1], feb = fcst[D + 2], fhu2 = fcst[D + 3];
+                        const T alg = fcst[D + 4], alb = fcst[D + 5], gmb = fcst[D + 6];
+                        Q fg, fb;
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
                             T c2 = T(0), z = -fhu2;
 #pragma unroll
                             for (int b = 0; b < D; ++b) {
-                                const T d = xi[v][b] - fu[b];
+                                const T d = xi[v][b] - fcst[b];
                                 c2 = fma(d, d, c2);
-                                z = fma(xi[v][b], fu[b], z);
+                                z = fma(xi[v][b], fcst[b], z);
                             }
                             const T ge = fpref * Num<T>::expo(fcexp * c2);
                             const T be = (hx[v] + feb) * ge;
-                            const T gf = fma(alg, gb - ge, ge);
-                            const T bfv = fma(gmb * z, gf - ge, fma(alb, bb - be, be));
-                            const T Fg = x * gf, Fb = x * bfv;
-                            FF[(0 * VC + v) * NFT + fl] = Fg;
-                            FF[(1 * VC + v) * NFT + fl] = Fb;
+                            const T gf = fma(alg, gb[v] - ge, ge);
+                            const T bfv = fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+                            const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
+                            fg.v[v] = Fg;
+                            fb.v[v] = Fb;
                             const T wg = w[v] * Fg;
                             sm[0] += wg;
 #pragma unroll
                             for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
                             sm[1 + D] = fma(w[v], Fb, sm[1 + D]);
                         }
+                        FF[0 * NFT + fl] = fg;
+                        FF[1 * NFT + fl] = fb;
                     }
                     if (own) {
 #pragma unroll
@@ -678,27 +793,38 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
             __syncthreads();
             // ---- phase 4: phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
             if (valid) {
+                T dFg[VC], dFb[VC];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int fl0 = TL::face_local(a, la[0], la[1], la[2]);
+                    const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
+                    const Q g0 = FF[0 * NFT + fl0], g1 = FF[0 * NFT + fl1];
+                    const Q b0 = FF[1 * NFT + fl0], b1 = FF[1 * NFT + fl1];
+                    const T idx = (T)g.idx[a];
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        dFg[v] = fma(idx, g1.v[v] - g0.v[v], dFg[v]);
+                        dFb[v] = fma(idx, b1.v[v] - b0.v[v], dFb[v]);
+                    }
+                }
+                const Q c0 = CC[0 * BOX + kc];
                 T u[D];
 #pragma unroll
-                for (int a = 0; a < D; ++a) u[a] = CC[a * BOX + kc];
-                const T hu2 = CC[(D + 3) * BOX + kc];
+                for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
+                const T hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
+                (void)c0;
                 T ng[VC], nb[VC];
                 const T dt = (T)g.dt;
 #pragma unroll
                 for (int v = 0; v < VC; ++v) {
-                    T dFg = T(0), dFb = T(0), z = -hu2;
+                    T z = -hu2;
 #pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        const int fl0 = TL::face_local(a, la[0], la[1], la[2]);
-                        const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
-                        const T idx = (T)g.idx[a];
-                        dFg = fma(idx, FF[(0 * VC + v) * NFT + fl1] - FF[(0 * VC + v) * NFT + fl0], dFg);
-                        dFb = fma(idx, FF[(1 * VC + v) * NFT + fl1] - FF[(1 * VC + v) * NFT + fl0], dFb);
-                        z = fma(xi[v][a], u[a], z);
-                    }
+                    for (int a = 0; a < D; ++a) z = fma(xi[v][a], u[a], z);
                     const T dg = og[v] - oge[v];
-                    ng[v] = fma(-dt, dFg, fma(um_g, dg, oge[v]));
-                    nb[v] = fma(-dt, dFb, fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
+                    ng[v] = fma(-dt, dFg[v], fma(um_g, dg, oge[v]));
+                    nb[v] = fma(-dt, dFb[v], fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
                 }
                 const size_t ad = phi_addr(g, cell_index(g, qa), vt * VC, 0);
                 Chunk<T>::store(bf.phi_out + ad, ng);
