@@ -184,6 +184,32 @@ CDUGKS_API void cdugks_destroy(cdugks_t *h);
 CDUGKS_API const char *cdugks_strerror(int code);
 CDUGKS_API const char *cdugks_last_error(void);
 
+/* Allocation-free time step (the paper has no counterpart: this is a
+ * convenience of this library).  For callers that cannot allocate device
+ * memory themselves -- code inside a framework whose memory pool owns the GPU
+ * and only lends out existing buffers, or a latency-critical loop where a
+ * device allocation could synchronise the device or fail -- this advances the
+ * state by exactly one step without cdugks_bind and without any allocation.
+ *   h        a handle from cdugks_create (binding it is not required)
+ *   phi_in   device state at t_n in the layout of the distribution block of
+ *            cdugks_get_state: [Nvp/4][Nc][g|b][4] values of the handle's
+ *            precision (32-byte aligned)
+ *   phi_out  device buffer of the same size for t_{n+1} (not phi_in)
+ *   W        device conserved variables [2+D][Nc] doubles, updated in place
+ *   stream   cudaStream_t as void* (NULL = legacy default stream)
+ * Asynchronous; no device status word is reported (inspect W).  Every other
+ * piece of device scratch lives in one fixed 32 MiB array in this library
+ * (held by every GPU that loads it until the process exits): problems whose
+ * cell/face tables and face-moment sums exceed it are rejected with
+ * CDUGKS_ERR_INVALID and a message giving the size needed.  Periodic and
+ * specular boundaries only.  All calls share that array, and it keeps what
+ * the last call left in it: calls whose work may overlap on one GPU (for
+ * instance calls on two streams) race on it, so serialise them.  The first
+ * call on each device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  Errors: INVALID, CUDA. */
+CDUGKS_API int cdugks_step_noalloc(cdugks_t *h, const void *phi_in, void *phi_out, double *W, void *cuda_stream);
+
 /* Hard-sphere convention for a Knudsen number (an input convention, not part
  * of the scheme): mu_ref = (5/16) Kn L rho_ref sqrt(2 pi R T_ref). */
 CDUGKS_API double cdugks_mu_from_kn(double kn, double rho_ref, double T_ref, double R, double length);

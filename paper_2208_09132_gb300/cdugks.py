@@ -24,7 +24,7 @@ EXPORTS = [
     "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
-    "cdugks_mu_from_kn",
+    "cdugks_mu_from_kn", "cdugks_step_noalloc",
 ]
 
 
@@ -96,6 +96,7 @@ def load(build_if_needed: bool = True):
         "cdugks_strerror": (ctypes.c_char_p, [i]),
         "cdugks_last_error": (ctypes.c_char_p, []),
         "cdugks_mu_from_kn": (d, [d, d, d, d, d]),
+        "cdugks_step_noalloc": (i, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/cdugks.h"
@@ -61,6 +63,7 @@ struct cdugks {
     int cur;               // state buffer holding phi* of the current time level
     long long steps;
     std::vector<double> vel;  // [Nvp][8]: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0
+    std::vector<float> vel32; // the same table rounded to float (FP32 storage)
     std::vector<int> refl;    // [8][Nvp]
 };
 
@@ -284,6 +287,7 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
             }
     for (long long i = Nv; i < g.Nvp; ++i)
         for (int m = 0; m < 8; ++m) h->refl[(size_t)m * g.Nvp + i] = (int)i;
+    h->vel32 = cast_vec<float>(h->vel);
     // time step: fixed CFL rule of Sec. 4 unless given
     double dt = phys->dt;
     if (!(dt > 0)) {
@@ -352,10 +356,9 @@ int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) 
     const Geo& g = h->g;
     // velocity table in the storage precision
     if (h->prec == CDUGKS_FP32) {
-        auto v = cast_vec<float>(h->vel);
-        if ((e = cudaMemcpyAsync(h->base + h->lay.vel, v.data(), v.size() * 4, cudaMemcpyHostToDevice, h->stream)))
+        if ((e = cudaMemcpyAsync(h->base + h->lay.vel, h->vel32.data(), h->vel32.size() * 4, cudaMemcpyHostToDevice,
+                                 h->stream)))
             return cuda_fail(e, "upload velocity table");
-        if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
     } else {
         if ((e = cudaMemcpyAsync(h->base + h->lay.vel, h->vel.data(), h->vel.size() * 8, cudaMemcpyHostToDevice,
                                  h->stream)))
@@ -612,6 +615,137 @@ const char* cdugks_strerror(int code) {
 }
 
 const char* cdugks_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free step.  Some callers cannot allocate device memory: code that
+// runs inside a host framework whose memory pool owns all of the GPU and only
+// lends out buffers it already holds, or a latency-critical loop in which a
+// device allocation (which may synchronise the whole device, or fail once the
+// pool is fragmented) is not acceptable.  For them cdugks_step_noalloc takes
+// the state buffers from the caller and keeps every other piece of device
+// scratch (cell and face constants, face-moment partial sums, velocity
+// tables, status word) in the fixed array below.  The array lives in every
+// process that loads this library, on every GPU it touches, until exit.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;   // 32 MiB
+constexpr int kNoallocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices];
+
+// Device address of the scratch array on the current device.  In host code the
+// symbol is only a stand-in; its device address is looked up once per device,
+// with that device current, and cached.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(CDUGKS_ERR_INVALID, "device index too large");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CDUGKS_OK;
+}
+
+template <typename T>
+int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStream_t st) {
+    Geo g = h->g;
+    const int NM = 2 + g.D;
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(reinterpret_cast<void**>(&base));
+    if (rc) return rc;
+    // scratch layout; fewer velocity groups when the partial sums would not fit
+    size_t need = 0, off_cellc = 0, off_facec[3] = {0, 0, 0}, off_wf[3] = {0, 0, 0}, off_mf[3] = {0, 0, 0};
+    size_t off_vel = 0, off_refl = 0, off_status = 0;
+    for (int G = std::max(1, g.G);; G = std::max(1, G / 2)) {
+        g.ntpg = (g.NVT + G - 1) / G;
+        g.G = (g.NVT + g.ntpg - 1) / g.ntpg;
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            const size_t o = off;
+            off = align_up(off + bytes);
+            return o;
+        };
+        off_cellc = take(h->cellc_bytes * (size_t)g.Nc);
+        for (int a = 0; a < 3; ++a) {
+            const size_t nf = a < g.D ? (size_t)g.nf[a] : 0;
+            off_facec[a] = take(h->facec_bytes * nf);
+            off_wf[a] = take(sizeof(double) * (size_t)g.G * NM * nf);
+            off_mf[a] = take(sizeof(double) * (size_t)g.G * NM * nf);
+        }
+        off_vel = take(sizeof(T) * 8 * (size_t)g.Nvp);
+        off_refl = take(sizeof(int) * 8 * (size_t)g.Nvp);
+        off_status = take(256);
+        need = off;
+        if (need <= kNoallocScratchBytes || G == 1) break;
+    }
+    if (need > kNoallocScratchBytes) {
+        char msg[200];
+        std::snprintf(msg, sizeof msg,
+                      "problem needs %zu bytes of scratch; the allocation-free step has %zu (use cdugks_step)", need,
+                      kNoallocScratchBytes);
+        return fail(CDUGKS_ERR_INVALID, msg);
+    }
+    Bufs<T> b;
+    b.phi_in = static_cast<const T*>(phi_in);
+    b.phi_out = static_cast<T*>(phi_out);
+    b.W = W;
+    b.cellc = reinterpret_cast<CellC<T>*>(base + off_cellc);
+    b.cellc0 = b.cellc;   // no Dirichlet ghosts on this path
+    for (int a = 0; a < 3; ++a) {
+        b.facec[a] = reinterpret_cast<FaceC<T>*>(base + off_facec[a]);
+        b.wf[a] = reinterpret_cast<double*>(base + off_wf[a]);
+        b.mf[a] = reinterpret_cast<double*>(base + off_mf[a]);
+    }
+    b.vel = reinterpret_cast<const T*>(base + off_vel);
+    b.refl = reinterpret_cast<const int*>(base + off_refl);
+    b.status = reinterpret_cast<int*>(base + off_status);
+    // the array keeps whatever the last call left: reload the tables, clear the status word
+    cudaError_t e;
+    const void* vel = h->prec == CDUGKS_FP32 ? static_cast<const void*>(h->vel32.data())
+                                             : static_cast<const void*>(h->vel.data());
+    if ((e = cudaMemcpyAsync(base + off_vel, vel, sizeof(T) * 8 * (size_t)g.Nvp, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(base + off_refl, h->refl.data(), sizeof(int) * h->refl.size(), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = cudaMemsetAsync(base + off_status, 0, 256, st)))
+        return cuda_fail(e, "prepare scratch");
+    if constexpr (std::is_same<T, float>::value) {
+        e = cdg::launch_cellc_f32(g, b, st);
+        if (!e) e = cdg::launch_step_f32(g, b, st);
+    } else {
+        e = cdg::launch_cellc_f64(g, b, st);
+        if (!e) e = cdg::launch_step_f64(g, b, st);
+    }
+    if (e) return cuda_fail(e, "allocation-free step launch");
+    return CDUGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdugks_step_noalloc(cdugks_t* h, const void* phi_in, void* phi_out, double* W, void* cuda_stream) {
+    if (!h || !phi_in || !phi_out || !W) return fail(CDUGKS_ERR_INVALID, "null argument");
+    if (phi_in == phi_out) return fail(CDUGKS_ERR_INVALID, "phi_in and phi_out must be different buffers");
+    for (int a = 0; a < h->g.D; ++a)
+        if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
+            return fail(CDUGKS_ERR_INVALID, "the allocation-free step supports periodic and specular boundaries only");
+    if ((((uintptr_t)phi_in) | ((uintptr_t)phi_out)) % 32 || ((uintptr_t)W) % 8)
+        return fail(CDUGKS_ERR_INVALID, "state buffers must be 32-byte aligned and W 8-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (h->prec == CDUGKS_FP32) return noalloc_run<float>(h, phi_in, phi_out, W, st);
+    return noalloc_run<double>(h, phi_in, phi_out, W, st);
+}
 
 double cdugks_mu_from_kn(double kn, double rho_ref, double T_ref, double R, double length) {
     return 5.0 / 16.0 * kn * length * rho_ref * std::sqrt(2.0 * 3.14159265358979323846 * R * T_ref);
