@@ -10,7 +10,7 @@ periodic cells x 32^2 velocities on [-6,6]^2, Kn = 1e-3, Pr = 1 (synthetic
 initial fields).  One bench step = one full time step of the scheme.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c3|c3s]
+                  [--workload c1|c2|c3|c3s|c4|c5] [--no-tune]
 
 N > 1 runs independent replicas (the path does not shard across GPUs on this
 build), one per rank under torch.distributed.run; value = all points / max time.
@@ -57,6 +57,11 @@ def pick_workload(name):
 
 def points(cfg):
     return wl.ncells(cfg) * wl.nvel(cfg)
+
+
+def default_tile_1d(nx):
+    """Tile shape for a 1D instance: fewer, fuller CTAs for long grids."""
+    return 0 if nx > 1536 else (1 if nx > 384 else 2)
 
 
 # --------------------------------------------------------------------- clocks
@@ -212,6 +217,139 @@ def max_over_ranks(x, ws):
 
 # ---------------------------------------------------------------- our arm
 
+def run_batched(args, ws, rank, local):
+    """Many uneven 1D instances (the batched thermoacoustic workload) stepped
+    together: one launch per kernel for all members, replayed from a CUDA graph."""
+    import torch
+
+    from paper_2208_09132_gb300 import cdugks
+
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    probs = wl.workload_c4()
+    P = sum(points(c) for c, _ in probs)
+    members = []
+    choices = {}
+    for cfg, f in probs:
+        if args.tune:
+            from paper_2208_09132_gb300 import tune
+            tile, groups = tune.tune(cfg, cdugks.FP32, context="batch", device=dev)
+        else:
+            tile, groups = default_tile_1d(cfg["n"][0]), 1
+        choices[(tile, groups)] = choices.get((tile, groups), 0) + 1
+        s = cdugks.Solver(cfg, precision=cdugks.FP32, device=dev, tile_id=tile, velocity_groups=groups)
+        s.init(f)
+        members.append(s)
+    batch = cdugks.Batch(members, device=dev)
+    gsteps = 10
+    batch.capture(gsteps)
+    stream = batch.stream
+    batch.step(max(args.warmup, 3))
+    if batch.sync() != 0:
+        raise RuntimeError("a member's status flagged a broken state during warm-up")
+    K = max(gsteps, args.steps // gsteps * gsteps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K // gsteps + 1)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(K // gsteps):
+        batch.step(gsteps)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) / gsteps for k in range(K // gsteps)]
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), ws)
+    status = batch.sync()
+    value = ws * P * K / (total_ms / 1e3)
+    peak, peak_kind = measured_peak_hbm()
+    step_bytes = 24 * P
+    achieved = step_bytes / (total_ms / K / 1e3) / 1e9
+
+    # the plain FP64 path, one instance at a time, on the same instances
+    fp64 = None
+    if not args.skip_fp64:
+        plain = []
+        for cfg, f in probs:
+            s = cdugks.Solver(cfg, precision=cdugks.FP64, device=dev)
+            s.init(f)
+            plain.append(s)
+        n64 = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n64):
+            for s in plain:
+                s.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fp64 = {"value": P * n64 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n64, "steps": n64,
+                "what": "each instance stepped alone in FP64, one after another"}
+        del plain
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_thermoacoustic_1d_256_instances", "instances": len(probs), "points": P,
+                   "launch": f"one launch per kernel for all members, CUDA graph of {gsteps} steps",
+                   "tile_groups_counts": {f"tile{t}_g{g}": n for (t, g), n in sorted(choices.items())},
+                   "l2": "inputs larger than L2" if P * 8 > 129e6 else "state fits in L2"},
+        "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
+        "roofline": {"bound": "hbm", "kernel": "batched step (all kernels)", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_point": 24, "traffic": None},
+        "cpu_baseline": None, "e2e": None, "fp64_plain": fp64,
+        "gpu_launches": K * 6, "clocks": clk, "status_ok": status == 0,
+    }
+
+
+def run_served(args, ws, rank, local):
+    """The served stream: Poisson arrivals of 2D Gresho / Kelvin-Helmholtz
+    solves admitted by device-memory footprint and stepped together."""
+    import torch
+
+    from paper_2208_09132_gb300 import serving
+
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    reqs = serving.stream_c5(count=args.requests, t_end=args.t_end)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serving.Server(budget_bytes=int(0.6 * free), max_slots=64, max_round=32, device=dev)
+    # warm-up: one tiny request compiles/loads everything
+    warm = serving.stream_c5(count=1, t_end=0.002)
+    serving.Server(budget_bytes=int(0.6 * free), device=dev).run(warm)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = max_over_ranks(time.perf_counter() - t0, ws)
+    clk = clocks.stop()
+    rep = srv.report(wall)
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": ws * rep["point_updates"] / wall, "unit": UNIT, "n_gpus": ws,
+        "steps": rep["rounds"], "warmup": 1, "ms_per_step": wall * 1e3 / max(rep["rounds"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"served_stream_{len(reqs)}_requests", "arrivals": "Poisson 50/s, seed 1",
+                   "requests": len(reqs), "t_end": args.t_end,
+                   "sizes": "cells 32^2-128^2, velocities 8^2-24^2, Gresho or Kelvin-Helmholtz, Kn 1e-4..1",
+                   "admission": "device-memory footprint within 60% of free memory, <= 64 slots"},
+        "latency_ms": {"p50": rep["p50_time_to_solution_s"] * 1e3, "p99": rep["p99_time_to_solution_s"] * 1e3,
+                       "what": "time to solution from arrival"},
+        "served": rep, "cpu_baseline": None, "e2e": None, "roofline": None,
+        "gpu_launches": None, "clocks": clk,
+    }
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -223,7 +361,11 @@ def run_ours(args, ws, rank, local):
     prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
-    s = cdugks.Solver(cfg, precision=prec, device=dev)
+    tile, groups = 0, 0
+    if args.tune:
+        from paper_2208_09132_gb300 import tune
+        tile, groups = tune.tune(cfg, prec, context="alone", device=dev)
+    s = cdugks.Solver(cfg, precision=prec, device=dev, tile_id=tile, velocity_groups=groups)
     stream = s.stream
     s.init(fields)
     for _ in range(args.warmup):
@@ -318,6 +460,7 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": cfg["name"], "precision": pname, "cells": wl.ncells(cfg),
                        "velocities": wl.nvel(cfg), "points": P, "dt": s.dt,
                        "state_bytes": s.info().state_bytes,
+                       "tile": list(s.info().tile)[:cfg["dim"]], "velocity_groups": s.info().velocity_groups,
                        "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
                              else "state fits in L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -378,12 +521,19 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 plain comparison")
+    ap.add_argument("--no-tune", dest="tune", action="store_false", help="default tile / group choice")
+    ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
+    ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, ws, rank)
+    elif args.workload == "c4":
+        res = run_batched(args, ws, rank, local)
+    elif args.workload == "c5":
+        res = run_served(args, ws, rank, local)
     else:
         res = run_ours(args, ws, rank, local)
     if rank == 0 and res is not None:

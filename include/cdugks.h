@@ -172,6 +172,8 @@ typedef struct {
     int precision;
     int velocity_groups;            /* velocity-space split of the sweeps */
     double state_bytes;             /* bytes of one copy of (g, b) on the device */
+    int tile_id;                    /* tile shape of the sweeps (cdugks_set_tile) */
+    int tile[3];                    /* its cells per axis */
 } cdugks_info_t;
 CDUGKS_API int cdugks_info(const cdugks_t *h, cdugks_info_t *info);
 
@@ -179,6 +181,36 @@ CDUGKS_API int cdugks_info(const cdugks_t *h, cdugks_info_t *info);
  * (0 = automatic).  Results are independent of the split up to the order of
  * the final sums over groups (a fixed order, so runs are reproducible). */
 CDUGKS_API int cdugks_set_velocity_groups(cdugks_t *h, int groups);
+
+/* Tuning: the spatial tile shape of the sweeps, one of cdugks_tile_count()
+ * instantiated shapes per (precision, dim) (0 = default).  Results do not
+ * depend on the shape. */
+CDUGKS_API int cdugks_tile_count(int precision, int dim);
+CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent instances stepped together: every kernel of a time step
+ * is one launch over a device work list of all members' (tile, velocity
+ * group) items, so uneven instances fill the GPU together.  Members must be
+ * bound and initialised, of one precision and dim; each keeps its own
+ * workspace.  The batch needs a small caller-owned workspace for its tables
+ * and runs on its own stream; do not touch the members on other streams
+ * between cdugks_batch_bind and cdugks_batch_sync.  Results of a member are
+ * the same as stepping it alone with the same tile shape and groups. */
+typedef struct cdugks_batch cdugks_batch_t;
+CDUGKS_API int cdugks_batch_create(cdugks_t *const *members, int n, cdugks_batch_t **out);
+CDUGKS_API int cdugks_batch_workspace_bytes(const cdugks_batch_t *b, size_t *bytes);
+CDUGKS_API int cdugks_batch_bind(cdugks_batch_t *b, void *device_ptr, size_t bytes, void *cuda_stream);
+/* Capture steps_per_graph batched steps in a CUDA graph (0 drops it); later
+ * cdugks_batch_step calls replay it for whole multiples.  Needs a non-default
+ * stream.  The buffer parity of each member lives on the device, so replays
+ * are valid for any number of steps. */
+CDUGKS_API int cdugks_batch_capture(cdugks_batch_t *b, int steps_per_graph);
+/* Enqueue nsteps steps of every member (asynchronous). */
+CDUGKS_API int cdugks_batch_step(cdugks_batch_t *b, int nsteps);
+/* Synchronise the batch stream and report the first member status error. */
+CDUGKS_API int cdugks_batch_sync(cdugks_batch_t *b);
+CDUGKS_API void cdugks_batch_destroy(cdugks_batch_t *b);
 
 CDUGKS_API void cdugks_destroy(cdugks_t *h);
 CDUGKS_API const char *cdugks_strerror(int code);

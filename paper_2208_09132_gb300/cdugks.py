@@ -24,7 +24,9 @@ EXPORTS = [
     "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
-    "cdugks_mu_from_kn", "cdugks_step_noalloc",
+    "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile",
+    "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
+    "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy",
 ]
 
 
@@ -48,7 +50,7 @@ class Info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("ncells", ctypes.c_longlong), ("nvel", ctypes.c_int),
                 ("nvel_padded", ctypes.c_int), ("dt", ctypes.c_double), ("steps", ctypes.c_longlong),
                 ("precision", ctypes.c_int), ("velocity_groups", ctypes.c_int),
-                ("state_bytes", ctypes.c_double)]
+                ("state_bytes", ctypes.c_double), ("tile_id", ctypes.c_int), ("tile", ctypes.c_int * 3)]
 
 
 class CdugksError(RuntimeError):
@@ -97,6 +99,15 @@ def load(build_if_needed: bool = True):
         "cdugks_last_error": (ctypes.c_char_p, []),
         "cdugks_mu_from_kn": (d, [d, d, d, d, d]),
         "cdugks_step_noalloc": (i, [vp, vp, vp, vp, vp]),
+        "cdugks_tile_count": (i, [i, i]),
+        "cdugks_set_tile": (i, [vp, i]),
+        "cdugks_batch_create": (i, [P(vp), i, P(vp)]),
+        "cdugks_batch_workspace_bytes": (i, [vp, P(sz)]),
+        "cdugks_batch_bind": (i, [vp, vp, sz, vp]),
+        "cdugks_batch_capture": (i, [vp, i]),
+        "cdugks_batch_step": (i, [vp, i]),
+        "cdugks_batch_sync": (i, [vp]),
+        "cdugks_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -153,7 +164,7 @@ class Solver:
     """
 
     def __init__(self, cfg: dict, precision: int | None = None, device: str = "cuda:0", stream=None,
-                 velocity_groups: int = 0, workspace=None):
+                 velocity_groups: int = 0, workspace=None, tile_id: int = 0):
         import torch
 
         self._lib = load()
@@ -161,6 +172,8 @@ class Solver:
         h = ctypes.c_void_p()
         _check(self._lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)))
         self._h = h
+        if tile_id:
+            _check(self._lib.cdugks_set_tile(h, int(tile_id)))
         if velocity_groups:
             _check(self._lib.cdugks_set_velocity_groups(h, int(velocity_groups)))
         nbytes = ctypes.c_size_t()
@@ -239,6 +252,44 @@ class Solver:
     def set_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(self._lib.cdugks_set_state(self._h, buf, ctypes.c_size_t(len(blob))))
+
+
+class Batch:
+    """Many Solvers stepped together in one launch per kernel (see include/cdugks.h)."""
+
+    def __init__(self, solvers, stream=None, device: str = "cuda:0"):
+        import torch
+
+        self._lib = load()
+        self.members = list(solvers)
+        arr = (ctypes.c_void_p * len(self.members))(*[s._h.value for s in self.members])
+        h = ctypes.c_void_p()
+        _check(self._lib.cdugks_batch_create(arr, len(self.members), ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_size_t()
+        _check(self._lib.cdugks_batch_workspace_bytes(h, ctypes.byref(n)))
+        dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self._ws = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=dev)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        _check(self._lib.cdugks_batch_bind(h, ctypes.c_void_p(aligned), ctypes.c_size_t(self._ws.numel() - (aligned - base)),
+                                           ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.cdugks_batch_destroy(h)
+            self._h = None
+
+    def capture(self, steps_per_graph: int):
+        _check(self._lib.cdugks_batch_capture(self._h, int(steps_per_graph)))
+
+    def step(self, nsteps: int = 1):
+        _check(self._lib.cdugks_batch_step(self._h, int(nsteps)))
+
+    def sync(self) -> int:
+        return int(self._lib.cdugks_batch_sync(self._h))
 
 
 def mu_from_kn(kn, rho_ref, T_ref, R=0.5, length=1.0) -> float:

@@ -16,10 +16,14 @@
 #include "../../include/cdugks.h"
 #include "launch.cuh"
 
+using cdg::BatchPlan;
 using cdg::Bufs;
 using cdg::CellC;
 using cdg::FaceC;
 using cdg::Geo;
+using cdg::Inst;
+using cdg::Item;
+using cdg::RItem;
 using cdg::VC;
 
 namespace {
@@ -39,7 +43,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t phi[2], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, total;
+    size_t phi[2], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
 };
 
 }  // namespace
@@ -89,6 +93,18 @@ bool vgrid_1d(int n, double lo, double hi, int rule, std::vector<double>& x, std
     return true;
 }
 
+cdg::TileShape tile_of(int prec, int D, int id) {
+    return prec == CDUGKS_FP32 ? cdg::tile_shape_f32(D, id) : cdg::tile_shape_f64(D, id);
+}
+int tile_count(int prec, int D) { return prec == CDUGKS_FP32 ? cdg::tile_count_f32(D) : cdg::tile_count_f64(D); }
+
+void set_tiles(cdugks* h, int id) {
+    Geo& g = h->g;
+    g.tile_id = id;
+    const cdg::TileShape ts = tile_of(h->prec, g.D, id);
+    for (int a = 0; a < 3; ++a) g.tiles[a] = a < g.D ? (g.n[a] + ts.t[a] - 1) / ts.t[a] : 1;
+}
+
 int groups_for(const cdugks* h, int requested) {
     const Geo& g = h->g;
     if (requested > 0) return std::min(requested, g.NVT);
@@ -133,6 +149,7 @@ void make_layout(cdugks* h) {
     L.refl = take(sizeof(int) * 8 * g.Nvp);
     L.io = take(sizeof(double) * NM * g.Nc);
     L.status = take(256);
+    L.inst = take(std::max(sizeof(Inst<float>), sizeof(Inst<double>)));
     L.total = off;
 }
 
@@ -162,6 +179,36 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
     std::vector<T> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
     return o;
+}
+
+template <typename T>
+Inst<T> inst_of(const cdugks* h) {
+    Inst<T> in;
+    in.g = h->g;
+    in.b[0] = bufs<T>(h, 0);
+    in.b[1] = bufs<T>(h, 1);
+    return in;
+}
+
+// The instance record every kernel of this handle reads (geometry + buffers).
+int upload_inst(cdugks* h) {
+    cudaError_t e;
+    if (h->prec == CDUGKS_FP32) {
+        const Inst<float> in = inst_of<float>(h);
+        e = cudaMemcpyAsync(h->base + h->lay.inst, &in, sizeof(in), cudaMemcpyHostToDevice, h->stream);
+        if (!e) e = cudaStreamSynchronize(h->stream);
+    } else {
+        const Inst<double> in = inst_of<double>(h);
+        e = cudaMemcpyAsync(h->base + h->lay.inst, &in, sizeof(in), cudaMemcpyHostToDevice, h->stream);
+        if (!e) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e) return cuda_fail(e, "upload instance record");
+    return CDUGKS_OK;
+}
+
+template <typename T>
+const Inst<T>* dinst(const cdugks* h) {
+    return reinterpret_cast<const Inst<T>*>(h->base + h->lay.inst);
 }
 
 int check_ready(const cdugks* h, bool need_init) {
@@ -206,7 +253,6 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     std::memset(&g, 0, sizeof(g));
     g.D = D;
     g.Nc = 1;
-    const cdg::TileShape ts = cdg::tile_shape(h->prec == CDUGKS_FP32 ? 1 : 0, D);
     std::vector<double> nodes[3], wts[3];
     int nv[3] = {1, 1, 1};
     for (int a = 0; a < 3; ++a) {
@@ -239,13 +285,11 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
             g.bc[a][0] = grid->bc[a][0];
             g.bc[a][1] = grid->bc[a][1];
             g.dx[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
-            g.tiles[a] = (g.n[a] + ts.t[a] - 1) / ts.t[a];
         } else {
             nodes[a].assign(1, 0.0);
             wts[a].assign(1, 1.0);
             g.n[a] = 1;
             g.dx[a] = 1.0;
-            g.tiles[a] = 1;
         }
         g.Nc *= g.n[a];
     }
@@ -311,6 +355,7 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     g.T_ref = phys->T_ref;
     g.omega = phys->omega;
     g.Pr = phys->Pr;
+    set_tiles(h, 0);
     h->gsel = 0;
     h->gcap = groups_for(h, 0);
     set_groups(h, h->gcap);
@@ -332,6 +377,29 @@ int cdugks_set_velocity_groups(cdugks_t* h, int groups) {
     }
     h->gsel = groups;
     set_groups(h, G);
+    if (h->bound) return upload_inst(h);
+    return CDUGKS_OK;
+}
+
+int cdugks_tile_count(int precision, int dim) {
+    if ((precision != CDUGKS_FP32 && precision != CDUGKS_FP64) || dim < 1 || dim > 3) return 0;
+    return tile_count(precision, dim);
+}
+
+int cdugks_set_tile(cdugks_t* h, int tile_id) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    if (tile_id < 0 || tile_id >= tile_count(h->prec, h->g.D)) return fail(CDUGKS_ERR_INVALID, "unknown tile id");
+    set_tiles(h, tile_id);
+    const int G = groups_for(h, h->gsel);
+    if (h->bound && G > h->gcap) set_groups(h, h->gcap);
+    else {
+        if (!h->bound && G > h->gcap) {
+            h->gcap = G;
+            make_layout(h);
+        }
+        set_groups(h, G);
+    }
+    if (h->bound) return upload_inst(h);
     return CDUGKS_OK;
 }
 
@@ -372,7 +440,7 @@ int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) 
     (void)g;
     h->bound = true;
     h->initialised = false;
-    return CDUGKS_OK;
+    return upload_inst(h);
 }
 
 int cdugks_init(cdugks_t* h, const double* rho_u_T) {
@@ -392,8 +460,8 @@ int cdugks_init(cdugks_t* h, const double* rho_u_T) {
     if ((e = cudaMemcpyAsync(io, rho_u_T, sizeof(double) * NM * g.Nc, cudaMemcpyHostToDevice, h->stream)))
         return cuda_fail(e, "upload fields");
     // initial state goes to buffer 0: launch with phi_in = buffer 1, phi_out = buffer 0
-    if (h->prec == CDUGKS_FP32) e = cdg::launch_init_f32(g, bufs<float>(h, 1), io, h->stream);
-    else e = cdg::launch_init_f64(g, bufs<double>(h, 1), io, h->stream);
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_init_f32(g, dinst<float>(h), 1, io, h->stream);
+    else e = cdg::launch_init_f64(g, dinst<double>(h), 1, io, h->stream);
     if (e) return cuda_fail(e, "init kernel");
     if ((e = cudaMemsetAsync(h->base + h->lay.status, 0, 256, h->stream))) return cuda_fail(e, "clear status");
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "init");
@@ -409,8 +477,8 @@ int cdugks_step(cdugks_t* h, int nsteps) {
     if (nsteps < 0) return fail(CDUGKS_ERR_INVALID, "nsteps < 0");
     for (int s = 0; s < nsteps; ++s) {
         cudaError_t e;
-        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, bufs<float>(h, h->cur), h->stream);
-        else e = cdg::launch_step_f64(h->g, bufs<double>(h, h->cur), h->stream);
+        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream);
+        else e = cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream);
         if (e) return cuda_fail(e, "step launch");
         h->cur = 1 - h->cur;
         h->steps += 1;
@@ -430,8 +498,8 @@ int cdugks_profile_step(cdugks_t* h, int nsteps, double* ms_out) {
         if ((e = cudaEventCreate(&ev[made]))) break;
     for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
         cudaEvent_t* es = &ev[(size_t)s * 5];
-        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, bufs<float>(h, h->cur), h->stream, es);
-        else e = cdg::launch_step_f64(h->g, bufs<double>(h, h->cur), h->stream, es);
+        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream, es);
+        else e = cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream, es);
         if (e) break;
         h->cur = 1 - h->cur;
         h->steps += 1;
@@ -487,8 +555,8 @@ int cdugks_distributions(cdugks_t* h, double* gout, double* bout) {
     if (!gout || !bout) return fail(CDUGKS_ERR_INVALID, "null output");
     const Geo& g = h->g;
     cudaError_t e;
-    if (h->prec == CDUGKS_FP32) e = cdg::launch_finalise_f32(g, bufs<float>(h, h->cur), h->stream);
-    else e = cdg::launch_finalise_f64(g, bufs<double>(h, h->cur), h->stream);
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_finalise_f32(g, dinst<float>(h), h->cur, h->stream);
+    else e = cdg::launch_finalise_f64(g, dinst<double>(h), h->cur, h->stream);
     if (e) return cuda_fail(e, "finalise kernel");
     const size_t n = (size_t)g.Nvp * g.Nc * 2;
     std::vector<unsigned char> host(n * h->elt);
@@ -569,8 +637,8 @@ int cdugks_set_state(cdugks_t* h, const void* host, size_t bytes) {
                              cudaMemcpyHostToDevice, h->stream)))
         return cuda_fail(e, "upload state");
     h->cur = 0;
-    if (h->prec == CDUGKS_FP32) e = cdg::launch_cellc_f32(g, bufs<float>(h, 0), h->stream);
-    else e = cdg::launch_cellc_f64(g, bufs<double>(h, 0), h->stream);
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_cellc_f32(g, dinst<float>(h), 0, h->stream);
+    else e = cdg::launch_cellc_f64(g, dinst<double>(h), 0, h->stream);
     if (e) return cuda_fail(e, "cell constants");
     if (!h->initialised) {
         // Dirichlet ghost constants: the restored state stands in for the initial one
@@ -594,6 +662,11 @@ int cdugks_info(const cdugks_t* h, cdugks_info_t* info) {
     info->steps = h->steps;
     info->precision = h->prec;
     info->velocity_groups = h->g.G;
+    info->tile_id = h->g.tile_id;
+    {
+        const cdg::TileShape ts = tile_of(h->prec, h->g.D, h->g.tile_id);
+        for (int a = 0; a < 3; ++a) info->tile[a] = ts.t[a];
+    }
     info->state_bytes = (double)h->g.Nvp * (double)h->g.Nc * 2.0 * (double)h->elt;
     return CDUGKS_OK;
 }
@@ -615,6 +688,253 @@ const char* cdugks_strerror(int code) {
 }
 
 const char* cdugks_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct cdugks_batch {
+    std::vector<cdugks*> mem;
+    int prec, D;
+    std::vector<int> tile_ids;                 // distinct tile shapes, in plan order
+    std::vector<std::vector<Item>> sweep_items;
+    std::vector<RItem> face_items, cell_items;
+    std::vector<unsigned char> insts;          // host image of the Inst<T> table
+    std::vector<int> cur;
+    size_t off_insts, off_cur, off_sweep[4], off_face, off_cell, total;
+    unsigned char* base;
+    cudaStream_t stream;
+    bool bound;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int graph_steps;
+    long long steps;
+};
+
+namespace {
+
+template <typename T>
+void fill_insts(cdugks_batch* b) {
+    b->insts.assign(sizeof(Inst<T>) * b->mem.size(), 0);
+    Inst<T>* in = reinterpret_cast<Inst<T>*>(b->insts.data());
+    for (size_t i = 0; i < b->mem.size(); ++i) {
+        in[i].g = b->mem[i]->g;
+        in[i].b[0] = bufs<T>(b->mem[i], 0);
+        in[i].b[1] = bufs<T>(b->mem[i], 1);
+    }
+}
+
+BatchPlan plan_of(const cdugks_batch* b) {
+    BatchPlan p;
+    std::memset(&p, 0, sizeof(p));
+    p.D = b->D;
+    p.ntile = (int)b->tile_ids.size();
+    for (int k = 0; k < p.ntile; ++k) {
+        p.tile_id[k] = b->tile_ids[k];
+        p.sweep_items[k] = reinterpret_cast<const Item*>(b->base + b->off_sweep[k]);
+        p.n_sweep[k] = (int)b->sweep_items[k].size();
+    }
+    p.face_items = reinterpret_cast<const RItem*>(b->base + b->off_face);
+    p.n_face = (int)b->face_items.size();
+    p.cell_items = reinterpret_cast<const RItem*>(b->base + b->off_cell);
+    p.n_cell = (int)b->cell_items.size();
+    return p;
+}
+
+cudaError_t batch_launch(cdugks_batch* b) {
+    const BatchPlan p = plan_of(b);
+    int* cur = reinterpret_cast<int*>(b->base + b->off_cur);
+    if (b->prec == CDUGKS_FP32)
+        return cdg::launch_batch_step_f32(p, reinterpret_cast<const Inst<float>*>(b->base + b->off_insts), cur,
+                                          b->stream);
+    return cdg::launch_batch_step_f64(p, reinterpret_cast<const Inst<double>*>(b->base + b->off_insts), cur,
+                                      b->stream);
+}
+
+void batch_advance_host(cdugks_batch* b, int nsteps) {
+    for (cdugks* m : b->mem) {
+        m->cur ^= (nsteps & 1);
+        m->steps += nsteps;
+    }
+    b->steps += nsteps;
+}
+
+void batch_drop_graph(cdugks_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_steps = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
+    if (!out) return fail(CDUGKS_ERR_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!members || n < 1) return fail(CDUGKS_ERR_INVALID, "a batch needs at least one member");
+    const int prec = members[0] ? members[0]->prec : -1, D = members[0] ? members[0]->g.D : -1;
+    for (int i = 0; i < n; ++i) {
+        const cdugks* m = members[i];
+        if (!m || !m->bound || !m->initialised)
+            return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
+        if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == m) return fail(CDUGKS_ERR_INVALID, "a member appears twice");
+    }
+    cdugks_batch* b = new (std::nothrow) cdugks_batch();
+    if (!b) return fail(CDUGKS_ERR_OOM, "host allocation failed");
+    b->mem.assign(members, members + n);
+    b->prec = prec;
+    b->D = D;
+    // sweep work items grouped by tile shape, largest per-item work first
+    for (int i = 0; i < n; ++i) {
+        const int id = b->mem[i]->g.tile_id;
+        if (std::find(b->tile_ids.begin(), b->tile_ids.end(), id) == b->tile_ids.end()) b->tile_ids.push_back(id);
+    }
+    std::sort(b->tile_ids.begin(), b->tile_ids.end());
+    b->sweep_items.resize(b->tile_ids.size());
+    for (int i = 0; i < n; ++i) {
+        const Geo& g = b->mem[i]->g;
+        const int k = (int)(std::find(b->tile_ids.begin(), b->tile_ids.end(), g.tile_id) - b->tile_ids.begin());
+        const int tiles = g.tiles[0] * g.tiles[1] * g.tiles[2];
+        for (int t = 0; t < tiles; ++t)
+            for (int gr = 0; gr < g.G; ++gr) b->sweep_items[k].push_back(Item{i, t, gr, 0});
+    }
+    for (auto& v : b->sweep_items)
+        std::stable_sort(v.begin(), v.end(), [&](const Item& x, const Item& y) {
+            const Geo& gx = b->mem[x.inst]->g;
+            const Geo& gy = b->mem[y.inst]->g;
+            const int wx = std::min(gx.ntpg, gx.NVT - x.grp * gx.ntpg), wy = std::min(gy.ntpg, gy.NVT - y.grp * gy.ntpg);
+            return wx > wy;
+        });
+    const long long R = 1024;
+    for (int i = 0; i < n; ++i) {
+        const Geo& g = b->mem[i]->g;
+        for (int a = 0; a < D; ++a)
+            for (long long s0 = 0; s0 < g.nf[a]; s0 += R) b->face_items.push_back(RItem{i, a, s0, std::min(R, g.nf[a] - s0)});
+        for (long long s0 = 0; s0 < g.Nc; s0 += R) b->cell_items.push_back(RItem{i, 0, s0, std::min(R, g.Nc - s0)});
+    }
+    if (prec == CDUGKS_FP32) fill_insts<float>(b);
+    else fill_insts<double>(b);
+    b->cur.resize(n);
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    b->off_insts = take(b->insts.size());
+    b->off_cur = take(sizeof(int) * n);
+    for (size_t k = 0; k < b->sweep_items.size(); ++k) b->off_sweep[k] = take(sizeof(Item) * b->sweep_items[k].size());
+    b->off_face = take(sizeof(RItem) * b->face_items.size());
+    b->off_cell = take(sizeof(RItem) * b->cell_items.size());
+    b->total = off;
+    if (b->tile_ids.size() > 4) {
+        delete b;
+        return fail(CDUGKS_ERR_INVALID, "too many tile shapes in one batch");
+    }
+    *out = b;
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_workspace_bytes(const cdugks_batch_t* b, size_t* bytes) {
+    if (!b || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
+    *bytes = b->total;
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_bind(cdugks_batch_t* b, void* device_ptr, size_t bytes, void* cuda_stream) {
+    if (!b || !device_ptr) return fail(CDUGKS_ERR_INVALID, "null argument");
+    if (((uintptr_t)device_ptr) % kAlign) return fail(CDUGKS_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (bytes < b->total) return fail(CDUGKS_ERR_OOM, "workspace smaller than cdugks_batch_workspace_bytes");
+    batch_drop_graph(b);
+    b->base = static_cast<unsigned char*>(device_ptr);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (size_t i = 0; i < b->mem.size(); ++i) b->cur[i] = b->mem[i]->cur;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->base + b->off_insts, b->insts.data(), b->insts.size(), cudaMemcpyHostToDevice,
+                             b->stream)) ||
+        (e = cudaMemcpyAsync(b->base + b->off_cur, b->cur.data(), sizeof(int) * b->cur.size(),
+                             cudaMemcpyHostToDevice, b->stream)))
+        return cuda_fail(e, "upload batch tables");
+    for (size_t k = 0; k < b->sweep_items.size(); ++k)
+        if ((e = cudaMemcpyAsync(b->base + b->off_sweep[k], b->sweep_items[k].data(),
+                                 sizeof(Item) * b->sweep_items[k].size(), cudaMemcpyHostToDevice, b->stream)))
+            return cuda_fail(e, "upload sweep items");
+    if ((e = cudaMemcpyAsync(b->base + b->off_face, b->face_items.data(), sizeof(RItem) * b->face_items.size(),
+                             cudaMemcpyHostToDevice, b->stream)) ||
+        (e = cudaMemcpyAsync(b->base + b->off_cell, b->cell_items.data(), sizeof(RItem) * b->cell_items.size(),
+                             cudaMemcpyHostToDevice, b->stream)))
+        return cuda_fail(e, "upload range items");
+    // members' own streams may still be working on their state
+    for (cdugks* m : b->mem)
+        if ((e = cudaStreamSynchronize(m->stream))) return cuda_fail(e, "member stream");
+    if ((e = cudaStreamSynchronize(b->stream))) return cuda_fail(e, "batch bind");
+    b->bound = true;
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_capture(cdugks_batch_t* b, int steps_per_graph) {
+    if (!b || !b->bound) return fail(CDUGKS_ERR_UNBOUND, "batch not bound");
+    if (steps_per_graph < 0 || steps_per_graph > 4096) return fail(CDUGKS_ERR_INVALID, "steps_per_graph in [0, 4096]");
+    batch_drop_graph(b);
+    if (steps_per_graph == 0) return CDUGKS_OK;
+    if (!b->stream) return fail(CDUGKS_ERR_INVALID, "graph capture needs a non-default stream");
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e) return cuda_fail(e, "cudaStreamBeginCapture");
+    for (int s = 0; s < steps_per_graph && e == cudaSuccess; ++s) e = batch_launch(b);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e || e2) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e ? e : e2, "capture batch steps");
+    }
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0))) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    b->graph = graph;
+    b->exec = exec;
+    b->graph_steps = steps_per_graph;
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_step(cdugks_batch_t* b, int nsteps) {
+    if (!b || !b->bound) return fail(CDUGKS_ERR_UNBOUND, "batch not bound");
+    if (nsteps < 0) return fail(CDUGKS_ERR_INVALID, "nsteps < 0");
+    int done = 0;
+    cudaError_t e = cudaSuccess;
+    if (b->exec)
+        for (; done + b->graph_steps <= nsteps; done += b->graph_steps)
+            if ((e = cudaGraphLaunch(b->exec, b->stream))) return cuda_fail(e, "cudaGraphLaunch");
+    for (; done < nsteps; ++done)
+        if ((e = batch_launch(b))) return cuda_fail(e, "batch step launch");
+    batch_advance_host(b, nsteps);
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_sync(cdugks_batch_t* b) {
+    if (!b || !b->bound) return fail(CDUGKS_ERR_UNBOUND, "batch not bound");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e) return cuda_fail(e, "batch sync");
+    int worst = CDUGKS_OK;
+    for (cdugks* m : b->mem) {
+        const int rc = cdugks_sync_status(m);
+        if (rc != CDUGKS_OK && worst == CDUGKS_OK) worst = rc;
+    }
+    return worst;
+}
+
+void cdugks_batch_destroy(cdugks_batch_t* b) {
+    if (!b) return;
+    batch_drop_graph(b);
+    delete b;
+}
 
 }  // extern "C"
 
@@ -666,7 +986,7 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
     if (rc) return rc;
     // scratch layout; fewer velocity groups when the partial sums would not fit
     size_t need = 0, off_cellc = 0, off_facec[3] = {0, 0, 0}, off_wf[3] = {0, 0, 0}, off_mf[3] = {0, 0, 0};
-    size_t off_vel = 0, off_refl = 0, off_status = 0;
+    size_t off_vel = 0, off_refl = 0, off_status = 0, off_inst = 0;
     for (int G = std::max(1, g.G);; G = std::max(1, G / 2)) {
         g.ntpg = (g.NVT + G - 1) / G;
         g.G = (g.NVT + g.ntpg - 1) / g.ntpg;
@@ -686,6 +1006,7 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
         off_vel = take(sizeof(T) * 8 * (size_t)g.Nvp);
         off_refl = take(sizeof(int) * 8 * (size_t)g.Nvp);
         off_status = take(256);
+        off_inst = take(sizeof(Inst<T>));
         need = off;
         if (need <= kNoallocScratchBytes || G == 1) break;
     }
@@ -710,23 +1031,32 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
     b.vel = reinterpret_cast<const T*>(base + off_vel);
     b.refl = reinterpret_cast<const int*>(base + off_refl);
     b.status = reinterpret_cast<int*>(base + off_status);
-    // the array keeps whatever the last call left: reload the tables, clear the status word
+    // the array keeps whatever the last call left: reload the tables and the
+    // instance record, clear the status word
+    Inst<T> in;
+    in.g = g;
+    in.b[0] = b;
+    in.b[1] = b;
     cudaError_t e;
     const void* vel = h->prec == CDUGKS_FP32 ? static_cast<const void*>(h->vel32.data())
                                              : static_cast<const void*>(h->vel.data());
     if ((e = cudaMemcpyAsync(base + off_vel, vel, sizeof(T) * 8 * (size_t)g.Nvp, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(base + off_refl, h->refl.data(), sizeof(int) * h->refl.size(), cudaMemcpyHostToDevice,
                              st)) ||
-        (e = cudaMemsetAsync(base + off_status, 0, 256, st)))
+        (e = cudaMemsetAsync(base + off_status, 0, 256, st)) ||
+        (e = cudaMemcpyAsync(base + off_inst, &in, sizeof(in), cudaMemcpyHostToDevice, st)))
         return cuda_fail(e, "prepare scratch");
+    const Inst<T>* din = reinterpret_cast<const Inst<T>*>(base + off_inst);
     if constexpr (std::is_same<T, float>::value) {
-        e = cdg::launch_cellc_f32(g, b, st);
-        if (!e) e = cdg::launch_step_f32(g, b, st);
+        e = cdg::launch_cellc_f32(g, din, 0, st);
+        if (!e) e = cdg::launch_step_f32(g, din, 0, st);
     } else {
-        e = cdg::launch_cellc_f64(g, b, st);
-        if (!e) e = cdg::launch_step_f64(g, b, st);
+        e = cdg::launch_cellc_f64(g, din, 0, st);
+        if (!e) e = cdg::launch_step_f64(g, din, 0, st);
     }
     if (e) return cuda_fail(e, "allocation-free step launch");
+    // (copies from pageable host memory return once the source has been staged,
+    // so the stack copy of the instance record may go out of scope here)
     return CDUGKS_OK;
 }
 

@@ -47,6 +47,7 @@ struct Geo {
     int ntpg;         // velocity chunks per group
     int G;            // velocity groups
     int tiles[3];     // spatial tiles per axis
+    int tile_id;      // which instantiated tile shape the sweeps use
     int fn[3][3];     // face-array extents per axis a: fn[a][b] = n[b] + (a == b)
     long long nf[3];  // faces per axis
     double dx[3];
@@ -72,6 +73,25 @@ struct Bufs {
     const T* vel;         // [Nvp][8] per velocity: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0 (w = 0 on padding)
     const int* refl;      // [8][Nvp] velocity index with the components of mask reversed
     int* status;
+};
+
+// An instance as the kernels see it: geometry and both ping-pong orientations
+// of its buffers (b[c] reads state buffer c and writes the other), kept in
+// device memory.  Single-instance launches and batched launches read the same
+// table, so a member computes the same numbers alone and inside a batch.
+template <typename T>
+struct Inst {
+    Geo g;
+    Bufs<T> b[2];
+};
+// Batched work items: one sweep CTA = (instance, tile, velocity group); one
+// face/cell CTA = a range [start, start + count) of one instance.
+struct Item {
+    int inst, tile, grp, pad;
+};
+struct RItem {
+    int inst, axis;
+    long long start, count;
 };
 
 // ------------------------------------------------------------------ numerics
@@ -384,7 +404,7 @@ struct Smem {
 };
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Bufs<T> bf) {
+__device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using SM = Smem<T, D, T0_, T1_, T2_>;
     using Q = V4<T>;
@@ -392,7 +412,6 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    extern __shared__ __align__(32) unsigned char smem[];
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][BOX] phibar+ chunk per cell
     Q* const S = P + SM::nP;                      // [D][2][SB] raw van Leer slopes (times dx)
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
@@ -405,13 +424,12 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = TL::NT / 32;
-    int tb = blockIdx.x;
+    int tb = tile;
     int org[3] = {0, 0, 0};
     org[0] = (tb % g.tiles[0]) * TL::T0;
     tb /= g.tiles[0];
     if (D >= 2) { org[1] = (tb % g.tiles[1]) * TL::T1; tb /= g.tiles[1]; }
     if (D >= 3) org[2] = tb * TL::T2;
-    const int grp = blockIdx.y;
     const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
 
     // this thread's cell
@@ -853,12 +871,43 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_sweep(Geo g, Buf
     }
 }
 
+// CTAs per SM that the shared memory of a sweep allows (at least 1, at most 4);
+// the launch bounds ask the compiler to fit the registers to the same count.
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+struct Occ {
+    static constexpr size_t kSmemPerSM = 228 * 1024;
+    static constexpr size_t per = Smem<T, D, T0_, T1_, T2_>::bytes(SWEEP_B) + 1024;
+    static constexpr int by_smem = (int)(kSmemPerSM / per);
+    static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
+    static constexpr int v0 = by_smem < by_threads ? by_smem : by_threads;
+    static constexpr int value = v0 < 1 ? 1 : (v0 > 4 ? 4 : v0);
+};
+
+// One problem instance: grid (tiles, velocity groups).
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B>::value))
+    k_sweep(const Inst<T>* __restrict__ in, int cur) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+}
+
+// Many instances in one launch: the device table of instances and a work list
+// of items, one per CTA.  The current parity of each instance lives on the
+// device and the W-update kernel flips it, so a captured graph replays.
+
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B>::value))
+    k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Item it = items[blockIdx.x];
+    const Inst<T>& in = insts[it.inst];
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+}
+
 // Face constants from the group-summed face W (fixed summation order).
 template <typename T, int D>
-__global__ void k_facec(Geo g, Bufs<T> bf, int a) {
+__device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a, long long f) {
     constexpr int NM = 2 + D;
-    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= g.nf[a]) return;
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int m = 0; m < NM; ++m) {
         double s = 0.0;
@@ -868,12 +917,25 @@ __global__ void k_facec(Geo g, Bufs<T> bf, int a) {
     make_face<T>(g, W, bf.facec[a][f]);
 }
 
+template <typename T, int D>
+__global__ void k_facec(const Inst<T>* __restrict__ in, int cur, int a) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < in->g.nf[a]) facec_body<T, D>(in->g, in->b[cur], a, f);
+}
+
+template <typename T, int D>
+__global__ void k_facec_batch(const RItem* __restrict__ items, const Inst<T>* __restrict__ insts,
+                              const int* __restrict__ cur) {
+    const RItem it = items[blockIdx.x];
+    const Inst<T>& in = insts[it.inst];
+    for (long long k = threadIdx.x; k < it.count; k += blockDim.x)
+        facec_body<T, D>(in.g, in.b[cur[it.inst] & 1], it.axis, it.start + k);
+}
+
 // W^{n+1} = W^n - dt sum_a (M_a(right face) - M_a(left face)) / dx_a (outward
 // normals), the status check, and the cell constants of W^{n+1}.
 template <typename T, int D>
-__global__ void k_wupdate(Geo g, Bufs<T> bf) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.Nc) return;
+__device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long long c) {
     constexpr int NM = 2 + D;
     int q[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long long)g.n[0] * g.n[1]))};
     double dW[NM];
@@ -909,9 +971,32 @@ __global__ void k_wupdate(Geo g, Bufs<T> bf) {
     make_cell<T>(g, W, bf.cellc[c]);
 }
 
+template <typename T, int D>
+__global__ void k_wupdate(const Inst<T>* __restrict__ in, int cur) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < in->g.Nc) wupdate_body<T, D>(in->g, in->b[cur], c);
+}
+
+// Batched W update; the item that starts at cell 0 of an instance flips its
+// buffer parity (no other kernel of the step reads it afterwards).
+template <typename T, int D>
+__global__ void k_wupdate_batch(const RItem* __restrict__ items, const Inst<T>* __restrict__ insts,
+                                int* __restrict__ cur) {
+    const RItem it = items[blockIdx.x];
+    const Inst<T>& in = insts[it.inst];
+    const int c0 = cur[it.inst] & 1;
+    for (long long k = threadIdx.x; k < it.count; k += blockDim.x) wupdate_body<T, D>(in.g, in.b[c0], it.start + k);
+    if (it.start == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur[it.inst] = c0 ^ 1;
+    }
+}
+
 // Cell constants from the stored W (after a state restore).
 template <typename T, int D>
-__global__ void k_cellc(Geo g, Bufs<T> bf) {
+__global__ void k_cellc(const Inst<T>* __restrict__ in, int cur) {
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.Nc) return;
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -923,7 +1008,9 @@ __global__ void k_cellc(Geo g, Bufs<T> bf) {
 // kept as the Dirichlet ghost constants), phi* = phi_eq(W^0) (the stored
 // pre-update value whose finalisation gives phi^0 = phi_eq).
 template <typename T, int D>
-__global__ void k_init(Geo g, Bufs<T> bf, const double* __restrict__ fields) {
+__global__ void k_init(const Inst<T>* __restrict__ in, int cur, const double* __restrict__ fields) {
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
     constexpr int NM = 2 + D;
     const long long c = blockIdx.x;
     const double* f = fields + (size_t)c * NM;
@@ -974,7 +1061,9 @@ __global__ void k_moments(Geo g, const double* __restrict__ W, double* __restric
 // The finalised distributions phi = fa phi* + fb phi_eq at the current time
 // level, written in the state layout into the idle buffer.
 template <typename T, int D>
-__global__ void k_finalise(Geo g, Bufs<T> bf) {
+__global__ void k_finalise(const Inst<T>* __restrict__ in, int cur) {
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
     const long long c = blockIdx.x;
     const CellC<T> cc = bf.cellc[c];
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {

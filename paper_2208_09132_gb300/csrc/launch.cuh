@@ -12,23 +12,45 @@ struct TileShape {
     int t[3];
 };
 
-// Tile shape and dynamic shared memory of the sweeps for a precision (0 FP64, 1 FP32) and dimension.
-TileShape tile_shape(int precision, int D);
-size_t sweep_smem_bytes(int precision, int D);
+// Work of one batched step: sweep items grouped by tile shape, face and cell ranges.
+struct BatchPlan {
+    int D;
+    int ntile;
+    int tile_id[4];
+    const Item* sweep_items[4];
+    int n_sweep[4];
+    const RItem* face_items;
+    int n_face;
+    const RItem* cell_items;
+    int n_cell;
+};
 
+// Instantiated tile shapes of the sweeps per precision (f32 = FP32 storage) and dimension.
+int tile_count_f32(int D);
+int tile_count_f64(int D);
+TileShape tile_shape_f32(int D, int id);
+TileShape tile_shape_f64(int D, int id);
+size_t sweep_smem_f32(int D, int id);
+size_t sweep_smem_f64(int D, int id);
+
+// The single-instance launches read the instance from the device table `in`
+// and use orientation `cur` (read state buffer cur, write the other).
 // One time step: sweep A, face constants, sweep B, W update (+ cell constants of W^{n+1}).
 // ev: null, or five events recorded before, between and after the four phases.
-cudaError_t launch_step_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s, cudaEvent_t* ev = nullptr);
-cudaError_t launch_step_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s, cudaEvent_t* ev = nullptr);
+cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr);
+cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// One time step of every instance of a batch.
+cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s);
+cudaError_t launch_batch_step_f64(const BatchPlan& p, const Inst<double>* insts, int* cur, cudaStream_t s);
 // Maxwellian initial state from device fields [Nc][2+D] (rho, u, T).
-cudaError_t launch_init_f32(const Geo& g, const Bufs<float>& b, const double* fields, cudaStream_t s);
-cudaError_t launch_init_f64(const Geo& g, const Bufs<double>& b, const double* fields, cudaStream_t s);
+cudaError_t launch_init_f32(const Geo& g, const Inst<float>* in, int cur, const double* fields, cudaStream_t s);
+cudaError_t launch_init_f64(const Geo& g, const Inst<double>* in, int cur, const double* fields, cudaStream_t s);
 // Cell constants from the stored W.
-cudaError_t launch_cellc_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s);
-cudaError_t launch_cellc_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s);
+cudaError_t launch_cellc_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s);
+cudaError_t launch_cellc_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s);
 // Finalised distributions into phi_out.
-cudaError_t launch_finalise_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s);
-cudaError_t launch_finalise_f64(const Geo& g, const Bufs<double>& b, cudaStream_t s);
+cudaError_t launch_finalise_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s);
+cudaError_t launch_finalise_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s);
 // rho,u,T (or W) per cell into out[Nc][2+D].
 cudaError_t launch_moments(const Geo& g, const double* W, double* out, int conserved, cudaStream_t s);
 

@@ -3,19 +3,29 @@
 
 namespace cdg {
 
-cudaError_t launch_step_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s, cudaEvent_t* ev) {
-    switch (g.D) {
-        case 1: return run_step<float, 1, 256, 1, 1>(g, b, s, ev);
-        case 2: return run_step<float, 2, 32, 8, 1>(g, b, s, ev);
-        default: return run_step<float, 3, 8, 4, 4>(g, b, s, ev);
-    }
+namespace {
+using Table32 = ShapeTable<float, Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>,
+                           Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 3, 8, 4, 4>>;
 }
-cudaError_t launch_init_f32(const Geo& g, const Bufs<float>& b, const double* f, cudaStream_t s) {
-    return run_init<float>(g, b, f, s);
+
+int tile_count_f32(int D) { return Table32::count(D); }
+TileShape tile_shape_f32(int D, int id) { return Table32::shape(D, id); }
+size_t sweep_smem_f32(int D, int id) { return Table32::smem(D, id); }
+
+cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
+    return Table32::step(g, in, cur, s, ev);
 }
-cudaError_t launch_cellc_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s) { return run_cellc<float>(g, b, s); }
-cudaError_t launch_finalise_f32(const Geo& g, const Bufs<float>& b, cudaStream_t s) {
-    return run_finalise<float>(g, b, s);
+cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s) {
+    return run_batch_step<Table32, float>(p, insts, cur, s);
+}
+cudaError_t launch_init_f32(const Geo& g, const Inst<float>* in, int cur, const double* f, cudaStream_t s) {
+    return run_init<float>(g, in, cur, f, s);
+}
+cudaError_t launch_cellc_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s) {
+    return run_cellc<float>(g, in, cur, s);
+}
+cudaError_t launch_finalise_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s) {
+    return run_finalise<float>(g, in, cur, s);
 }
 
 }  // namespace cdg
