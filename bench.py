@@ -130,10 +130,15 @@ def measured_peak_hbm():
 
 
 def kernel_source_sha():
-    h = hashlib.sha256()
-    for f in ("kernels.cuh", "sweeps_impl.cuh"):
-        with open(os.path.join(ROOT, "paper_2208_09132_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    """Hash of the sweep kernels' source (the section of kernels.cuh that holds
+    them, and their launch helpers): profile counters taken on other source
+    are not reported."""
+    csrc = os.path.join(ROOT, "paper_2208_09132_gb300", "csrc")
+    txt = open(os.path.join(csrc, "kernels.cuh")).read()
+    a = txt.index("// --------------------------------------------------------------- the sweep")
+    b = txt.index("// Face constants from the group-summed face W")
+    h = hashlib.sha256(txt[a:b].encode())
+    h.update(open(os.path.join(csrc, "sweeps_impl.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 

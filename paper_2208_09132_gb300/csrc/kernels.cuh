@@ -1024,12 +1024,14 @@ __global__ void k_init(const Inst<T>* __restrict__ in, int cur, const double* __
     }
     Wc[1 + D] = f[0] * (0.5 * u2 + cv * f[1 + D]);
     if (threadIdx.x < NM) bf.W[(size_t)threadIdx.x * g.Nc + c] = Wc[threadIdx.x];
-    CellC<T> cc;
-    make_cell<T>(g, Wc, cc);
-    if (threadIdx.x == 0) {
-        bf.cellc[c] = cc;
-        bf.cellc0[c] = cc;
+    __shared__ CellC<T> shc;
+    if (threadIdx.x == 0) {       // the FP64 constants once per cell, not once per thread
+        make_cell<T>(g, Wc, shc);
+        bf.cellc[c] = shc;
+        bf.cellc0[c] = shc;
     }
+    __syncthreads();
+    const CellC<T> cc = shc;
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
