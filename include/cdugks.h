@@ -187,6 +187,11 @@ CDUGKS_API int cdugks_set_velocity_groups(cdugks_t *h, int groups);
  * depend on the shape. */
 CDUGKS_API int cdugks_tile_count(int precision, int dim);
 CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
+/* out[0..2]: cells per axis of a tile shape; out[3] = 1 for a prepared-shift
+ * shape, which forms phibar+ of every point in its own pass each step (one
+ * more state-size buffer in the workspace: select such a shape before
+ * cdugks_bind; not usable inside batches). */
+CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances stepped together: every kernel of a time step

@@ -24,7 +24,7 @@ EXPORTS = [
     "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
-    "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile",
+    "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
     "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy",
 ]
@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
         "cdugks_step_noalloc": (i, [vp, vp, vp, vp, vp]),
         "cdugks_tile_count": (i, [i, i]),
         "cdugks_set_tile": (i, [vp, i]),
+        "cdugks_tile_shape": (i, [i, i, i, P(i)]),
         "cdugks_batch_create": (i, [P(vp), i, P(vp)]),
         "cdugks_batch_workspace_bytes": (i, [vp, P(sz)]),
         "cdugks_batch_bind": (i, [vp, vp, sz, vp]),
@@ -290,6 +291,13 @@ class Batch:
 
     def sync(self) -> int:
         return int(self._lib.cdugks_batch_sync(self._h))
+
+
+def tile_shape(precision: int, dim: int, tile_id: int):
+    """(cells per axis, prepared-shift flag) of an instantiated tile shape."""
+    out = (ctypes.c_int * 4)()
+    _check(load().cdugks_tile_shape(int(precision), int(dim), int(tile_id), out))
+    return tuple(out[:3]), bool(out[3])
 
 
 def mu_from_kn(kn, rho_ref, T_ref, R=0.5, length=1.0) -> float:

@@ -64,6 +64,7 @@ template <typename T>
 struct Bufs {
     const T* phi_in;
     T* phi_out;
+    T* phibar;            // phibar+ of every point (state layout), when a prepared-shift shape is used
     double* W;            // [2+D][Nc] tracked conserved variables, updated in place
     CellC<T>* cellc;      // [Nc] constants of W^n (written by the W update / init)
     CellC<T>* cellc0;     // [Nc] constants of W^0 (Dirichlet ghosts)
@@ -385,7 +386,7 @@ struct alignas(4 * sizeof(T)) V4 {
     T v[4];
 };
 
-template <typename T, int D, int T0, int T1, int T2>
+template <typename T, int D, int T0, int T1, int T2, bool PREP = false>
 struct Smem {
     using TL = Tile<D, T0, T1, T2>;
     static constexpr int NCC = D + 11;           // phase-1 constants per box cell
@@ -394,7 +395,7 @@ struct Smem {
     static constexpr int NFCV = (NFC + 3) / 4;
     static constexpr size_t nP = (size_t)2 * TL::BOX;          // V4 units
     static constexpr size_t nS = (size_t)D * 2 * TL::SB;
-    static constexpr size_t nCC = (size_t)NCCV * TL::BOX;
+    static constexpr size_t nCC = PREP ? 0 : (size_t)NCCV * TL::BOX;   // prepared shapes read phibar+ instead
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
     __host__ __device__ static constexpr size_t vcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
@@ -403,10 +404,48 @@ struct Smem {
     }
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+// phibar+ (eq. phibarplus) of every point, for the prepared-shift shapes:
+// one thread per cell over a run of velocity chunks, constants read once.
+template <typename T, int D>
+__global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_thread) {
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.Nc) return;
+    const CellC<T> cs = bf.cellc[c];
+    const int vt0 = blockIdx.y * chunks_per_thread, vt1 = min(g.NVT, vt0 + chunks_per_thread);
+    for (int vt = vt0; vt < vt1; ++vt) {
+        const size_t ad = phi_addr(g, c, vt * VC, 0);
+        T gs[VC], bs[VC], pg[VC], pb[VC];
+        Chunk<T>::load(bf.phi_in + ad, gs);
+        Chunk<T>::load(bf.phi_in + ad + VC, bs);
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const T* rec = bf.vel + (size_t)(vt * VC + v) * 8;
+            T c2 = T(0), z = -cs.hu2;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const T d = rec[a] - cs.u[a];
+                c2 = fma(d, d, c2);
+                z = fma(rec[a], cs.u[a], z);
+            }
+            const T ge = cs.pref * Num<T>::expo(cs.cexp * c2);
+            const T be = (rec[4] + cs.eb) * ge;
+            const T gg = fma(cs.fa_g, gs[v], cs.fb_g * ge);
+            const T bb = fma(cs.fa_b, bs[v], cs.fb_b * be);
+            const T dg = gg - ge;
+            pg[v] = fma(cs.sa_g, dg, ge);
+            pb[v] = fma(cs.ssrc * z, dg, fma(cs.sa_b, bb - be, be));
+        }
+        Chunk<T>::store(bf.phibar + ad, pg);
+        Chunk<T>::store(bf.phibar + ad + VC, pb);
+    }
+}
+
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
 __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
-    using SM = Smem<T, D, T0_, T1_, T2_>;
+    using SM = Smem<T, D, T0_, T1_, T2_, PREP>;
     using Q = V4<T>;
     constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
@@ -464,6 +503,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         bool dir;
         resolve(g, q, refl, dir);
         const long long c = cell_index(g, q);
+        csrc[k] = (int)c;
+        cfl[k] = refl | (dir ? 8 : 0);
+        if (PREP) continue;
         const CellC<T>& cs = dir ? bf.cellc0[c] : bf.cellc[c];
         T cst[4 * NCCV];
 #pragma unroll
@@ -488,8 +530,6 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
             CC[j * BOX + k] = qv;
         }
-        csrc[k] = (int)c;
-        cfl[k] = refl | (dir ? 8 : 0);
     }
     {   // halo list in box order (warp ballots), so neighbouring threads touch neighbouring cells
         constexpr int PER = ((BOX + NW - 1) / NW + 31) / 32 * 32;
@@ -544,11 +584,12 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     }
     // constants of the owned cell for the distribution update
     T um_g = T(0), um_b = T(0), usrc = T(0);
+    CellC<T> own;       // all of them (prepared shapes: phase 4 recomputes phi and phi_eq)
     if (SWEEP_B && valid) {
-        const CellC<T>& cs = bf.cellc[cell_index(g, qa)];
-        um_g = cs.um_g;
-        um_b = cs.um_b;
-        usrc = cs.usrc;
+        own = bf.cellc[cell_index(g, qa)];
+        um_g = own.um_g;
+        um_b = own.um_b;
+        usrc = own.usrc;
     }
     // which faces this thread computes: left faces; right faces where no other thread does
     bool right[3] = {false, false, false};
@@ -658,8 +699,47 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             P[0 * BOX + k] = qg;
             P[1 * BOX + k] = qb;
         };
-        cell(kc, valid);
-        for (int h = t; h < NH; h += TL::NT) cell(halo[h], false);
+        // prepared shapes: phibar+ comes from the prepared buffer (Dirichlet ghosts: their equilibrium)
+        auto pcell = [&](int k) {
+            const int fl = cfl[k];
+            const long long c = csrc[k];
+            Q qg, qb;
+            if (fl & 8) {
+                const CellC<T> cs = bf.cellc0[c];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    T c2 = T(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const T ua = (fl & (1 << a)) ? -cs.u[a] : cs.u[a];
+                        const T d = xi[v][a] - ua;
+                        c2 = fma(d, d, c2);
+                    }
+                    qg.v[v] = cs.pref * Num<T>::expo(cs.cexp * c2);
+                    qb.v[v] = (hx[v] + cs.eb) * qg.v[v];
+                }
+            } else if (fl & 7) {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    const int is = bf.refl[(fl & 7) * g.Nvp + vt * VC + v];
+                    qg.v[v] = bf.phibar[phi_addr(g, c, is, 0)];
+                    qb.v[v] = bf.phibar[phi_addr(g, c, is, 1)];
+                }
+            } else {
+                const size_t ad = phi_addr(g, c, vt * VC, 0);
+                Chunk<T>::load(bf.phibar + ad, qg.v);
+                Chunk<T>::load(bf.phibar + ad + VC, qb.v);
+            }
+            P[0 * BOX + k] = qg;
+            P[1 * BOX + k] = qb;
+        };
+        if (PREP) {
+            pcell(kc);
+            for (int h = t; h < NH; h += TL::NT) pcell(halo[h]);
+        } else {
+            cell(kc, valid);
+            for (int h = t; h < NH; h += TL::NT) cell(halo[h], false);
+        }
         __syncthreads();
 
         // ---- phase 2: van Leer slopes (times dx) of the cells [-1, T] around the tile
@@ -827,12 +907,34 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                         dFb[v] = fma(idx, b1.v[v] - b0.v[v], dFb[v]);
                     }
                 }
-                const Q c0 = CC[0 * BOX + kc];
-                T u[D];
+                T u[D], hu2;
+                if (PREP) {
 #pragma unroll
-                for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
-                const T hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
-                (void)c0;
+                    for (int a = 0; a < D; ++a) u[a] = own.u[a];
+                    hu2 = own.hu2;
+                    // phi and phi_eq of the owned cell (not kept from phase 1 on this path)
+                    T gs[VC], bs[VC];
+                    const size_t ad0 = phi_addr(g, cell_index(g, qa), vt * VC, 0);
+                    Chunk<T>::load(bf.phi_in + ad0, gs);
+                    Chunk<T>::load(bf.phi_in + ad0 + VC, bs);
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        T c2 = T(0);
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const T d = xi[v][a] - u[a];
+                            c2 = fma(d, d, c2);
+                        }
+                        oge[v] = own.pref * Num<T>::expo(own.cexp * c2);
+                        obe[v] = (hx[v] + own.eb) * oge[v];
+                        og[v] = fma(own.fa_g, gs[v], own.fb_g * oge[v]);
+                        ob[v] = fma(own.fa_b, bs[v], own.fb_b * obe[v]);
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
+                    hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
+                }
                 T ng[VC], nb[VC];
                 const T dt = (T)g.dt;
 #pragma unroll
@@ -873,22 +975,24 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 
 // CTAs per SM that the shared memory of a sweep allows (at least 1, at most 4);
 // the launch bounds ask the compiler to fit the registers to the same count.
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
 struct Occ {
     static constexpr size_t kSmemPerSM = 228 * 1024;
-    static constexpr size_t per = Smem<T, D, T0_, T1_, T2_>::bytes(SWEEP_B) + 1024;
+    static constexpr size_t per = Smem<T, D, T0_, T1_, T2_, PREP>::bytes(SWEEP_B) + 1024;
     static constexpr int by_smem = (int)(kSmemPerSM / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
-    static constexpr int v0 = by_smem < by_threads ? by_smem : by_threads;
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 64);   // keep >= 64 registers
+    static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
+    static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
     static constexpr int value = v0 < 1 ? 1 : (v0 > 4 ? 4 : v0);
 };
 
 // One problem instance: grid (tiles, velocity groups).
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B>::value))
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, PREP>::value))
     k_sweep(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(32) unsigned char smem[];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, PREP>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list
@@ -896,12 +1000,12 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 // device and the W-update kernel flips it, so a captured graph replays.
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B>::value))
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, false>::value))
     k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(32) unsigned char smem[];
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, false>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
 // Face constants from the group-summed face W (fixed summation order).

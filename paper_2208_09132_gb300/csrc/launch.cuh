@@ -32,6 +32,9 @@ TileShape tile_shape_f32(int D, int id);
 TileShape tile_shape_f64(int D, int id);
 size_t sweep_smem_f32(int D, int id);
 size_t sweep_smem_f64(int D, int id);
+// Whether a shape forms phibar+ in its own pass (needs the extra state-size buffer).
+bool tile_prep_f32(int D, int id);
+bool tile_prep_f64(int D, int id);
 
 // The single-instance launches read the instance from the device table `in`
 // and use orientation `cur` (read state buffer cur, write the other).

@@ -9,28 +9,32 @@ namespace cdg {
 // constant computations of a small problem spread over many SMs.
 constexpr int kSmallBlock = 64;
 
-// One instantiated tile shape of the sweeps and its launches.
-template <typename T, int D, int TX, int TY, int TZ>
+// One instantiated tile shape of the sweeps and its launches.  PREP shapes
+// form phibar+ of every point once per step (k_prep) and the sweeps load it.
+template <typename T, int D, int TX, int TY, int TZ, bool PREP = false>
 struct Shape {
-    using SM = Smem<T, D, TX, TY, TZ>;
+    using SM = Smem<T, D, TX, TY, TZ, PREP>;
     using TL = Tile<D, TX, TY, TZ>;
+    static constexpr bool prep = PREP;
 
     static cudaError_t configure() {
         static bool done = false;
         if (done) return cudaSuccess;
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SM::bytes(false))))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SM::bytes(true))))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false>,
+        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false, PREP>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
             return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, true>,
+        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, PREP>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
             return e;
+        if (!PREP) {
+            if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
+                return e;
+            if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
+                return e;
+        }
         done = true;
         return cudaSuccess;
     }
@@ -40,14 +44,19 @@ struct Shape {
         if (e) return e;
         const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
         if (ev) cudaEventRecord(ev[0], s);
-        k_sweep<T, D, TX, TY, TZ, false><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
+        if (PREP) {
+            constexpr int kChunks = 8;
+            const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
+            k_prep<T, D><<<pg, 128, 0, s>>>(in, cur, kChunks);
+        }
+        k_sweep<T, D, TX, TY, TZ, false, PREP><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[1], s);
         for (int a = 0; a < D; ++a) {
             const unsigned blocks = (unsigned)((g.nf[a] + kSmallBlock - 1) / kSmallBlock);
             k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
         }
         if (ev) cudaEventRecord(ev[2], s);
-        k_sweep<T, D, TX, TY, TZ, true><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
+        k_sweep<T, D, TX, TY, TZ, true, PREP><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[3], s);
         k_wupdate<T, D><<<(unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock), kSmallBlock, 0, s>>>(in, cur);
         if (ev) cudaEventRecord(ev[4], s);
@@ -56,6 +65,7 @@ struct Shape {
 
     static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
                                    cudaStream_t s) {
+        if (PREP) return cudaErrorNotSupported;
         cudaError_t e = configure();
         if (e) return e;
         if (n <= 0) return cudaSuccess;
@@ -63,46 +73,63 @@ struct Shape {
         else k_sweep_batch<T, D, TX, TY, TZ, false><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
         return cudaGetLastError();
     }
+
+    static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }
 };
 
-// The shapes of one precision, indexed by tile id: Shapes<...>::get(D, id).
-template <typename T, typename S1a, typename S1b, typename S1c, typename S2a, typename S2b, typename S3a>
+// A list of shapes for one dimension, indexed by tile id.
+template <typename... S>
+struct ShapeList;
+template <>
+struct ShapeList<> {
+    static constexpr int count = 0;
+    template <typename T>
+    static cudaError_t step(int, const Geo&, const Inst<T>*, int, cudaStream_t, cudaEvent_t*) {
+        return cudaErrorInvalidValue;
+    }
+    template <typename T>
+    static cudaError_t sweep_batch(int, bool, const Item*, int, const Inst<T>*, const int*, cudaStream_t) {
+        return cudaErrorInvalidValue;
+    }
+    static TileShape shape(int) { return {{0, 0, 0}}; }
+    static size_t smem(int) { return 0; }
+    static bool prep(int) { return false; }
+};
+template <typename H, typename... R>
+struct ShapeList<H, R...> {
+    using Rest = ShapeList<R...>;
+    static constexpr int count = 1 + Rest::count;
+    template <typename T>
+    static cudaError_t step(int id, const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
+        return id == 0 ? H::step(g, in, cur, s, ev) : Rest::template step<T>(id - 1, g, in, cur, s, ev);
+    }
+    template <typename T>
+    static cudaError_t sweep_batch(int id, bool B, const Item* it, int n, const Inst<T>* in, const int* cur,
+                                   cudaStream_t s) {
+        return id == 0 ? H::sweep_batch(B, it, n, in, cur, s) : Rest::template sweep_batch<T>(id - 1, B, it, n, in, cur, s);
+    }
+    static TileShape shape(int id) { return id == 0 ? H::shape() : Rest::shape(id - 1); }
+    static size_t smem(int id) { return id == 0 ? H::SM::bytes(true) : Rest::smem(id - 1); }
+    static bool prep(int id) { return id == 0 ? H::prep : Rest::prep(id - 1); }
+};
+
+// The shapes of one precision for D = 1, 2, 3.
+template <typename T, typename L1, typename L2, typename L3>
 struct ShapeTable {
-    static int count(int D) { return D == 1 ? 3 : (D == 2 ? 2 : 1); }
-    static TileShape shape(int D, int id) {
-        if (D == 1) {
-            const int t[3] = {S1a::TL::T0, S1b::TL::T0, S1c::TL::T0};
-            return {{t[id < 3 ? id : 0], 1, 1}};
-        }
-        if (D == 2) {
-            if (id == 1) return {{S2b::TL::T0, S2b::TL::T1, 1}};
-            return {{S2a::TL::T0, S2a::TL::T1, 1}};
-        }
-        return {{S3a::TL::T0, S3a::TL::T1, S3a::TL::T2}};
-    }
-    static size_t smem(int D, int id) {
-        if (D == 1) return id == 1 ? S1b::SM::bytes(true) : (id == 2 ? S1c::SM::bytes(true) : S1a::SM::bytes(true));
-        if (D == 2) return id == 1 ? S2b::SM::bytes(true) : S2a::SM::bytes(true);
-        return S3a::SM::bytes(true);
-    }
+    static int count(int D) { return D == 1 ? L1::count : (D == 2 ? L2::count : L3::count); }
+    static TileShape shape(int D, int id) { return D == 1 ? L1::shape(id) : (D == 2 ? L2::shape(id) : L3::shape(id)); }
+    static size_t smem(int D, int id) { return D == 1 ? L1::smem(id) : (D == 2 ? L2::smem(id) : L3::smem(id)); }
+    static bool prep(int D, int id) { return D == 1 ? L1::prep(id) : (D == 2 ? L2::prep(id) : L3::prep(id)); }
     static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
-        if (g.D == 1) {
-            if (g.tile_id == 1) return S1b::step(g, in, cur, s, ev);
-            if (g.tile_id == 2) return S1c::step(g, in, cur, s, ev);
-            return S1a::step(g, in, cur, s, ev);
-        }
-        if (g.D == 2) return g.tile_id == 1 ? S2b::step(g, in, cur, s, ev) : S2a::step(g, in, cur, s, ev);
-        return S3a::step(g, in, cur, s, ev);
+        if (g.D == 1) return L1::template step<T>(g.tile_id, g, in, cur, s, ev);
+        if (g.D == 2) return L2::template step<T>(g.tile_id, g, in, cur, s, ev);
+        return L3::template step<T>(g.tile_id, g, in, cur, s, ev);
     }
     static cudaError_t sweep_batch(int D, int id, bool B, const Item* it, int n, const Inst<T>* in, const int* cur,
                                    cudaStream_t s) {
-        if (D == 1) {
-            if (id == 1) return S1b::sweep_batch(B, it, n, in, cur, s);
-            if (id == 2) return S1c::sweep_batch(B, it, n, in, cur, s);
-            return S1a::sweep_batch(B, it, n, in, cur, s);
-        }
-        if (D == 2) return id == 1 ? S2b::sweep_batch(B, it, n, in, cur, s) : S2a::sweep_batch(B, it, n, in, cur, s);
-        return S3a::sweep_batch(B, it, n, in, cur, s);
+        if (D == 1) return L1::template sweep_batch<T>(id, B, it, n, in, cur, s);
+        if (D == 2) return L2::template sweep_batch<T>(id, B, it, n, in, cur, s);
+        return L3::template sweep_batch<T>(id, B, it, n, in, cur, s);
     }
 };
 

@@ -54,11 +54,12 @@ def size_key(cfg, precision, context):
     return f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}"
 
 
-def candidates(cfg, precision):
+def candidates(cfg, precision, context="alone"):
     nt = cdugks.load().cdugks_tile_count(precision, cfg["dim"])
     nvt = (wl.nvel(cfg) + 3) // 4
     groups = [g for g in (1, 2, 4, 8, 16, 32) if g <= nvt]
-    return [(t, g) for t in range(nt) for g in groups]
+    tiles = [t for t in range(nt) if context == "alone" or not cdugks.tile_shape(precision, cfg["dim"], t)[1]]
+    return [(t, g) for t in tiles for g in groups]
 
 
 def _uniform_fields(cfg):
@@ -117,7 +118,7 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
     if key in d and not refresh:
         return tuple(d[key]["choice"])
     results = []
-    for tile, groups in candidates(cfg, precision):
+    for tile, groups in candidates(cfg, precision, context):
         results.append((_time(cfg, precision, tile, groups, context, steps, device), tile, groups))
     results.sort()
     best = results[0]

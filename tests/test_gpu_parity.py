@@ -185,3 +185,22 @@ def test_status_flags_report_a_broken_state():
     s.set_state(bytes(blob))
     s.step(1)
     assert s.sync_status() in (cdugks.ERR_NEGATIVE, cdugks.ERR_NONFINITE)
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+@pytest.mark.parametrize("name", ["1d_periodic_ragged_padded", "2d_dirichlet_x_specular_y",
+                                  "2d_periodic_ragged", "3d_mixed_bc", "3d_periodic_ragged"])
+def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
+    """All instantiated tile shapes, the prepared-shift ones included, give the oracle's result."""
+    (cfg, f), steps = case(name)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    ref = o.moments()
+    for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
+        s = cdugks.Solver(cfg, precision=precision, tile_id=t, velocity_groups=2)
+        s.init(f)
+        s.step(steps)
+        assert s.sync_status() == 0
+        err = rel_linf(s.moments(), ref)
+        assert np.all(err <= tol), (name, t, err)
