@@ -154,6 +154,12 @@ CDUGKS_API int cdugks_conserved(cdugks_t *h, double *out);
  * on the device as scratch.  Synchronous. */
 CDUGKS_API int cdugks_distributions(cdugks_t *h, double *g, double *b);
 
+/* The distributions of n selected cells (indices in [0, Nc)), host
+ * [n][Nv] each as double, at the current time level.  Uses the idle state
+ * buffer on the device as scratch; copies only the selected cells back.
+ * Synchronous. */
+CDUGKS_API int cdugks_cell_distributions(cdugks_t *h, const long long *cells, int n, double *g, double *b);
+
 /* Checkpoint: opaque host image of the device state (distributions in their
  * storage form, W, step count).  cdugks_set_state restores it bitwise, so a
  * restarted run reproduces an uninterrupted one exactly. */

@@ -24,7 +24,7 @@ EXPORTS = [
     "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
-    "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape",
+    "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
     "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy",
 ]
@@ -102,6 +102,7 @@ def load(build_if_needed: bool = True):
         "cdugks_tile_count": (i, [i, i]),
         "cdugks_set_tile": (i, [vp, i]),
         "cdugks_tile_shape": (i, [i, i, i, P(i)]),
+        "cdugks_cell_distributions": (i, [vp, P(ctypes.c_longlong), i, dp, dp]),
         "cdugks_batch_create": (i, [P(vp), i, P(vp)]),
         "cdugks_batch_workspace_bytes": (i, [vp, P(sz)]),
         "cdugks_batch_bind": (i, [vp, vp, sz, vp]),
@@ -241,6 +242,15 @@ class Solver:
         g = np.empty((self.Nc, self.Nv))
         b = np.empty((self.Nc, self.Nv))
         _check(self._lib.cdugks_distributions(self._h, _dptr(g), _dptr(b)))
+        return g, b
+
+    def cell_distributions(self, cells):
+        """g, b of the selected cells, [n][Nv] each."""
+        idx = np.ascontiguousarray(cells, dtype=np.int64)
+        g = np.empty((idx.size, self.Nv))
+        b = np.empty((idx.size, self.Nv))
+        _check(self._lib.cdugks_cell_distributions(self._h, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                                   int(idx.size), _dptr(g), _dptr(b)))
         return g, b
 
     def get_state(self) -> bytes:

@@ -604,6 +604,43 @@ int cdugks_distributions(cdugks_t* h, double* gout, double* bout) {
     return CDUGKS_OK;
 }
 
+int cdugks_cell_distributions(cdugks_t* h, const long long* cells, int n, double* gout, double* bout) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!cells || n < 0 || (n > 0 && (!gout || !bout))) return fail(CDUGKS_ERR_INVALID, "bad arguments");
+    const Geo& g = h->g;
+    for (int k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= g.Nc) return fail(CDUGKS_ERR_INVALID, "cell index out of range");
+    cudaError_t e;
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_finalise_f32(g, dinst<float>(h), h->cur, h->stream);
+    else e = cdg::launch_finalise_f64(g, dinst<double>(h), h->cur, h->stream);
+    if (e) return cuda_fail(e, "finalise kernel");
+    // one cell's chunks are 2*VC values every Nc*2*VC values: one strided copy per cell
+    const size_t row = 2 * VC * h->elt, pitch = (size_t)g.Nc * row;
+    std::vector<unsigned char> host((size_t)g.NVT * row);
+    const unsigned char* src = h->base + h->lay.phi[1 - h->cur];
+    for (int k = 0; k < n; ++k) {
+        if ((e = cudaMemcpy2DAsync(host.data(), row, src + (size_t)cells[k] * row, pitch, row, (size_t)g.NVT,
+                                   cudaMemcpyDeviceToHost, h->stream)))
+            return cuda_fail(e, "download cell");
+        if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cell distributions");
+        for (int i = 0; i < h->Nv; ++i) {
+            const size_t ad = (size_t)(i / VC) * (2 * VC) + (i % VC);
+            double gv, bv;
+            if (h->prec == CDUGKS_FP32) {
+                gv = reinterpret_cast<const float*>(host.data())[ad];
+                bv = reinterpret_cast<const float*>(host.data())[ad + VC];
+            } else {
+                gv = reinterpret_cast<const double*>(host.data())[ad];
+                bv = reinterpret_cast<const double*>(host.data())[ad + VC];
+            }
+            gout[(size_t)k * h->Nv + i] = gv;
+            bout[(size_t)k * h->Nv + i] = bv;
+        }
+    }
+    return CDUGKS_OK;
+}
+
 int cdugks_state_bytes(const cdugks_t* h, size_t* bytes) {
     if (!h || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
     const Geo& g = h->g;

@@ -1,0 +1,96 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+The oracle cannot run the full 2D and 3D workloads, but one step of one cell
+depends only on the cells within two of it (its faces need the slopes of their
+upwind neighbours, which need one more neighbour).  For sampled cells the test
+copies a periodic patch of 7 cells per axis around the cell from the GPU state
+at step n into the oracle, advances the oracle one step, and compares the
+centre cell's W and distributions with the GPU's step n+1.  At full size it
+also checks conservation and the device status over the steps taken.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_09132_gb300 import cdugks, tune, workloads as wl
+
+pytestmark = pytest.mark.gpu
+R = 3
+
+
+def _patch(cfg, centre):
+    D = cfg["dim"]
+    n = cfg["n"]
+    q = [centre % n[0], (centre // n[0]) % n[1], centre // (n[0] * n[1])]
+    rng = [range(-R, R + 1) if a < D else range(1) for a in range(3)]
+    cells = []
+    for dz in rng[2]:
+        for dy in rng[1]:
+            for dx in rng[0]:
+                x, y, z = (q[0] + dx) % n[0], (q[1] + dy) % n[1], (q[2] + dz) % n[2]
+                cells.append(x + n[0] * (y + n[1] * z))
+    return np.array(cells, dtype=np.int64)
+
+
+def _check(oracle_mod, cfg, f, steps_before, nsamples, tile, groups, tol_W, tol_phi):
+    D, NM = cfg["dim"], 2 + cfg["dim"]
+    s = cdugks.Solver(cfg, precision=cdugks.FP32, tile_id=tile, velocity_groups=groups)
+    s.init(f)
+    S0 = s.conserved().sum(0)
+    s.step(steps_before)
+    rng = np.random.default_rng(7)
+    centres = rng.integers(0, s.Nc, nsamples)
+    patches = [_patch(cfg, int(c)) for c in centres]
+    allc = np.unique(np.concatenate(patches))
+    g_n, b_n = s.cell_distributions(allc)
+    W_n = s.conserved()
+    s.step(1)
+    assert s.sync_status() == 0
+    g1, b1 = s.cell_distributions(centres)
+    W1 = s.conserved()
+    # conservation over the steps taken (periodic)
+    S1 = W1.sum(0)
+    scale = np.array([S0[0]] * (1 + D) + [S0[-1]])
+    assert np.all(np.abs(S1 - S0) <= 1e-6 * scale), (S1 - S0) / scale
+    pos = {int(c): i for i, c in enumerate(allc)}
+    centre_local = R + (2 * R + 1) * (R if D >= 2 else 0) + (2 * R + 1) ** 2 * (R if D >= 3 else 0)
+    for k, c in enumerate(centres):
+        sub = {key: (list(v) if isinstance(v, list) else v) for key, v in cfg.items()}
+        sub["n"] = [2 * R + 1 if a < D else 1 for a in range(3)]
+        sub["lo"] = [0.0, 0.0, 0.0]
+        sub["hi"] = [(2 * R + 1) * (cfg["hi"][a] - cfg["lo"][a]) / cfg["n"][a] if a < D else 1.0 for a in range(3)]
+        sub["bc"] = [[wl.BC_PERIODIC] * 2 for _ in range(3)]
+        sub["dt"] = s.dt
+        o = oracle_mod.Oracle(sub)
+        idx = [pos[int(cc)] for cc in patches[k]]
+        Wp = W_n[patches[k]]
+        fields = np.zeros((len(idx), NM))
+        fields[:, 0] = 1.0
+        fields[:, -1] = 1.0
+        o.init(fields)
+        o.set_state(g_n[idx], b_n[idx], Wp)
+        o.step(1)
+        Wo = o.conserved()[centre_local]
+        go, bo = o.distributions()
+        Wscale = np.abs(W_n).max(axis=0)
+        Wscale[1:1 + D] = Wscale[1:1 + D].max()
+        assert np.all(np.abs(W1[c] - Wo) <= tol_W * Wscale), (k, W1[c], Wo)
+        assert np.abs(g1[k] - go[centre_local]).max() <= tol_phi * np.abs(go).max()
+        assert np.abs(b1[k] - bo[centre_local]).max() <= tol_phi * np.abs(bo).max()
+
+
+def test_kelvin_helmholtz_full_size(oracle_mod):
+    """256^2 cells x 32^2 velocities, FP32, the tuned launch shape."""
+    cfg, f = wl.workload_c2()
+    tile, groups = tune.tune(cfg, cdugks.FP32, context="alone")
+    _check(oracle_mod, cfg, f, steps_before=5, nsamples=4, tile=tile, groups=groups, tol_W=1e-5, tol_phi=1e-5)
+
+
+def test_shear_3d_full_size(oracle_mod):
+    """64^3 cells x 24^3 velocities, FP32 (about 29 GB per state buffer), the tuned shape."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    cfg, f = wl.workload_c3(kn=1e-2)
+    if free < 120e9:
+        pytest.skip("needs about 120 GB of free device memory")
+    tile, groups = tune.tune(cfg, cdugks.FP32, context="alone", steps=2)
+    _check(oracle_mod, cfg, f, steps_before=2, nsamples=2, tile=tile, groups=groups, tol_W=1e-5, tol_phi=1e-5)
