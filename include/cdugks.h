@@ -193,10 +193,14 @@ CDUGKS_API int cdugks_set_velocity_groups(cdugks_t *h, int groups);
  * depend on the shape. */
 CDUGKS_API int cdugks_tile_count(int precision, int dim);
 CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
-/* out[0..2]: cells per axis of a tile shape; out[3] = 1 for a prepared-shift
- * shape, which forms phibar+ of every point in its own pass each step (one
- * more state-size buffer in the workspace: select such a shape before
- * cdugks_bind; not usable inside batches). */
+/* out[0..2]: cells per axis of a tile shape; out[3] its sweep mode:
+ *   0  the sweeps form phibar+ and the van Leer slopes on their halo boxes;
+ *   1  phibar+ of every point is formed once per step in its own pass (one
+ *      more state-size buffer in the workspace);
+ *   2  phibar+ and the slopes of every point are formed once per step in a
+ *      stencil pass (one more state-size buffer and D more for the slopes;
+ *      periodic and specular boundaries only).
+ * Modes 1 and 2 must be selected before cdugks_bind and are not batched. */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 
 /* ---------------------------------------------------------------- batches

@@ -304,10 +304,11 @@ class Batch:
 
 
 def tile_shape(precision: int, dim: int, tile_id: int):
-    """(cells per axis, prepared-shift flag) of an instantiated tile shape."""
+    """(cells per axis, sweep mode) of an instantiated tile shape (mode 0 fused,
+    1 prepared phibar+, 2 stored phibar+ and slopes)."""
     out = (ctypes.c_int * 4)()
     _check(load().cdugks_tile_shape(int(precision), int(dim), int(tile_id), out))
-    return tuple(out[:3]), bool(out[3])
+    return tuple(out[:3]), int(out[3])
 
 
 def mu_from_kn(kn, rho_ref, T_ref, R=0.5, length=1.0) -> float:

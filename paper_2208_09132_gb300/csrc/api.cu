@@ -43,7 +43,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t phi[2], pb, W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
+    size_t phi[2], pb, sg, W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
 };
 
 }  // namespace
@@ -58,7 +58,7 @@ struct cdugks {
     size_t cellc_bytes, facec_bytes;
     int Nv;
     int gcap;              // velocity groups the workspace is laid out for
-    bool prep_cap;         // the workspace holds the phibar+ buffer of prepared-shift shapes
+    int mode_cap;          // the workspace holds the phibar+ buffer (>= 1) and the slope buffer (2)
     int gsel;              // requested groups (0 = auto)
     Layout lay;
     unsigned char* base;
@@ -98,8 +98,8 @@ cdg::TileShape tile_of(int prec, int D, int id) {
     return prec == CDUGKS_FP32 ? cdg::tile_shape_f32(D, id) : cdg::tile_shape_f64(D, id);
 }
 int tile_count(int prec, int D) { return prec == CDUGKS_FP32 ? cdg::tile_count_f32(D) : cdg::tile_count_f64(D); }
-bool tile_prep(int prec, int D, int id) {
-    return prec == CDUGKS_FP32 ? cdg::tile_prep_f32(D, id) : cdg::tile_prep_f64(D, id);
+int tile_mode(int prec, int D, int id) {
+    return prec == CDUGKS_FP32 ? cdg::tile_mode_f32(D, id) : cdg::tile_mode_f64(D, id);
 }
 
 void set_tiles(cdugks* h, int id) {
@@ -140,7 +140,8 @@ void make_layout(cdugks* h) {
     const size_t state = (size_t)g.Nvp * (size_t)g.Nc * 2 * h->elt;
     L.phi[0] = take(state);
     L.phi[1] = take(state);
-    L.pb = h->prep_cap ? take(state) : 0;
+    L.pb = h->mode_cap >= cdg::MODE_PREP ? take(state) : 0;
+    L.sg = h->mode_cap >= cdg::MODE_STORED ? take(state * g.D) : 0;
     L.W = take(sizeof(double) * NM * g.Nc);
     L.cellc = take(h->cellc_bytes * g.Nc);
     L.cellc0 = take(h->cellc_bytes * g.Nc);
@@ -165,7 +166,8 @@ Bufs<T> bufs(const cdugks* h, int in) {
     const Layout& L = h->lay;
     b.phi_in = reinterpret_cast<const T*>(p + L.phi[in]);
     b.phi_out = reinterpret_cast<T*>(p + L.phi[1 - in]);
-    b.phibar = h->prep_cap ? reinterpret_cast<T*>(p + L.pb) : nullptr;
+    b.phibar = h->mode_cap >= cdg::MODE_PREP ? reinterpret_cast<T*>(p + L.pb) : nullptr;
+    b.sigma = h->mode_cap >= cdg::MODE_STORED ? reinterpret_cast<T*>(p + L.sg) : nullptr;
     b.W = reinterpret_cast<double*>(p + L.W);
     b.cellc = reinterpret_cast<CellC<T>*>(p + L.cellc);
     b.cellc0 = reinterpret_cast<CellC<T>*>(p + L.cellc0);
@@ -398,17 +400,22 @@ int cdugks_tile_shape(int precision, int dim, int tile_id, int* out) {
         return fail(CDUGKS_ERR_INVALID, "unknown tile");
     const cdg::TileShape ts = tile_of(precision, dim, tile_id);
     for (int a = 0; a < 3; ++a) out[a] = ts.t[a];
-    out[3] = tile_prep(precision, dim, tile_id) ? 1 : 0;
+    out[3] = tile_mode(precision, dim, tile_id);
     return CDUGKS_OK;
 }
 
 int cdugks_set_tile(cdugks_t* h, int tile_id) {
     if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
     if (tile_id < 0 || tile_id >= tile_count(h->prec, h->g.D)) return fail(CDUGKS_ERR_INVALID, "unknown tile id");
-    if (tile_prep(h->prec, h->g.D, tile_id) && !h->prep_cap) {
+    const int mode = tile_mode(h->prec, h->g.D, tile_id);
+    if (mode == cdg::MODE_STORED)
+        for (int a = 0; a < h->g.D; ++a)
+            if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
+                return fail(CDUGKS_ERR_INVALID, "stored-slope shapes support periodic and specular boundaries only");
+    if (mode > h->mode_cap) {
         if (h->bound)
-            return fail(CDUGKS_ERR_INVALID, "this shape needs the phibar+ buffer: select it before cdugks_bind");
-        h->prep_cap = true;
+            return fail(CDUGKS_ERR_INVALID, "this shape needs more workspace buffers: select it before cdugks_bind");
+        h->mode_cap = mode;
         make_layout(h);
     }
     set_tiles(h, tile_id);
@@ -840,8 +847,8 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
         if (!m || !m->bound || !m->initialised)
             return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
         if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
-        if (tile_prep(m->prec, m->g.D, m->g.tile_id))
-            return fail(CDUGKS_ERR_INVALID, "prepared-shift tile shapes are not batched; choose another shape");
+        if (tile_mode(m->prec, m->g.D, m->g.tile_id) != cdg::MODE_FUSED)
+            return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
         for (int j = 0; j < i; ++j)
             if (members[j] == m) return fail(CDUGKS_ERR_INVALID, "a member appears twice");
     }
@@ -1041,7 +1048,7 @@ int noalloc_scratch(void** out) {
 template <typename T>
 int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStream_t st) {
     Geo g = h->g;
-    if (tile_prep(h->prec, g.D, g.tile_id)) {   // no room for a phibar+ buffer here
+    if (tile_mode(h->prec, g.D, g.tile_id) != cdg::MODE_FUSED) {   // no room for phibar+ / slope buffers here
         g.tile_id = 0;
         const cdg::TileShape ts = tile_of(h->prec, g.D, 0);
         for (int a = 0; a < 3; ++a) g.tiles[a] = a < g.D ? (g.n[a] + ts.t[a] - 1) / ts.t[a] : 1;
@@ -1087,6 +1094,7 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
     b.phi_in = static_cast<const T*>(phi_in);
     b.phi_out = static_cast<T*>(phi_out);
     b.phibar = nullptr;
+    b.sigma = nullptr;
     b.W = W;
     b.cellc = reinterpret_cast<CellC<T>*>(base + off_cellc);
     b.cellc0 = b.cellc;   // no Dirichlet ghosts on this path

@@ -64,7 +64,8 @@ template <typename T>
 struct Bufs {
     const T* phi_in;
     T* phi_out;
-    T* phibar;            // phibar+ of every point (state layout), when a prepared-shift shape is used
+    T* phibar;            // phibar+ of every point (state layout), for the prepared and stored shapes
+    T* sigma;             // van Leer slopes of every point, [chunk][cell][axis][g|b][VC] (stored shapes)
     double* W;            // [2+D][Nc] tracked conserved variables, updated in place
     CellC<T>* cellc;      // [Nc] constants of W^n (written by the W update / init)
     CellC<T>* cellc0;     // [Nc] constants of W^0 (Dirichlet ghosts)
@@ -386,16 +387,22 @@ struct alignas(4 * sizeof(T)) V4 {
     T v[4];
 };
 
-template <typename T, int D, int T0, int T1, int T2, bool PREP = false>
+// Sweep modes: 0 forms phibar+ and the slopes on the halo box itself; 1
+// (prepared) loads phibar+ formed by k_prep and forms the slopes; 2 (stored)
+// loads phibar+ and the slopes formed by k_shslope.
+enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2 };
+
+template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
     using TL = Tile<D, T0, T1, T2>;
     static constexpr int NCC = D + 11;           // phase-1 constants per box cell
     static constexpr int NCCV = (NCC + 3) / 4;   // ... packed in V4
     static constexpr int NFC = D + 7;            // face constants
     static constexpr int NFCV = (NFC + 3) / 4;
-    static constexpr size_t nP = (size_t)2 * TL::BOX;          // V4 units
+    static constexpr int PN = MODE == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
+    static constexpr size_t nP = (size_t)2 * PN;                       // V4 units
     static constexpr size_t nS = (size_t)D * 2 * TL::SB;
-    static constexpr size_t nCC = PREP ? 0 : (size_t)NCCV * TL::BOX;   // prepared shapes read phibar+ instead
+    static constexpr size_t nCC = MODE == MODE_FUSED ? (size_t)NCCV * TL::BOX : 0;
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
     __host__ __device__ static constexpr size_t vcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
@@ -403,6 +410,12 @@ struct Smem {
         return vcount(B) * sizeof(V4<T>) + sizeof(int) * (2 * TL::BOX + TL::NH + 32);
     }
 };
+
+// Offset of (cell, velocity i, axis a, field f) in the slope layout.
+template <int D>
+__device__ __forceinline__ size_t sig_addr(const Geo& g, long long cell, int i, int a, int f) {
+    return ((size_t)(i / VC) * (size_t)g.Nc + (size_t)cell) * (2 * D * VC) + (size_t)(a * 2 + f) * VC + (i % VC);
+}
 
 // phibar+ (eq. phibarplus) of every point, for the prepared-shift shapes:
 // one thread per cell over a run of velocity chunks, constants read once.
@@ -442,16 +455,181 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
     }
 }
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
+// phibar+ and its van Leer slopes for every point, for the stored shapes: one
+// CTA per tile of cells and group of velocity chunks, phibar+ formed on the
+// tile and a one-cell halo in shared memory, slopes of the tile's own cells,
+// both written in their layouts.
+template <int D, int T0_, int T1_, int T2_>
+struct ShTile {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    static constexpr int NT = TL::NT;
+    static constexpr int SB = TL::SB;     // the box: local cells [-1, T] per axis
+};
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+__host__ __device__ constexpr size_t shslope_smem_bytes() {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    return ((size_t)2 * TL::SB + (size_t)((D + 11 + 3) / 4) * TL::SB) * sizeof(V4<T>) + sizeof(int) * 2 * TL::SB;
+}
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const Inst<T>* __restrict__ in, int cur) {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    using Q = V4<T>;
+    constexpr int SB = TL::SB, NCCV = (D + 11 + 3) / 4;
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
+    Q* const P = reinterpret_cast<Q*>(smem);      // [2][SB]
+    Q* const CC = P + 2 * SB;                     // [NCCV][SB]
+    int* const csrc = reinterpret_cast<int*>(CC + NCCV * SB);
+    int* const cfl = csrc + SB;
+    const int t = threadIdx.x;
+    int tb = blockIdx.x;
+    int org[3] = {0, 0, 0};
+    org[0] = (tb % g.tiles[0]) * TL::T0;
+    tb /= g.tiles[0];
+    if (D >= 2) { org[1] = (tb % g.tiles[1]) * TL::T1; tb /= g.tiles[1]; }
+    if (D >= 3) org[2] = tb * TL::T2;
+    const int vt0 = blockIdx.y * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
+    auto local = [&](int s2, int l[3]) {
+        l[0] = s2 % TL::F0 - 1;
+        l[1] = D >= 2 ? (s2 / TL::F0) % TL::F1 - 1 : 0;
+        l[2] = D >= 3 ? s2 / (TL::F0 * TL::F1) - 1 : 0;
+    };
+    for (int s2 = t; s2 < SB; s2 += TL::NT) {
+        int l[3];
+        local(s2, l);
+        int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
+        int refl;
+        bool dir;
+        resolve(g, q, refl, dir);
+        const long long c = cell_index(g, q);
+        const CellC<T>& cs = bf.cellc[c];
+        T cst[4 * NCCV];
+#pragma unroll
+        for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
+        cst[D + 0] = cs.cexp;
+        cst[D + 1] = cs.pref;
+        cst[D + 2] = cs.eb;
+        cst[D + 3] = cs.hu2;
+        cst[D + 4] = cs.fa_g;
+        cst[D + 5] = cs.fb_g;
+        cst[D + 6] = cs.fa_b;
+        cst[D + 7] = cs.fb_b;
+        cst[D + 8] = cs.sa_g;
+        cst[D + 9] = cs.sa_b;
+        cst[D + 10] = cs.ssrc;
+#pragma unroll
+        for (int j = D + 11; j < 4 * NCCV; ++j) cst[j] = T(0);
+#pragma unroll
+        for (int j = 0; j < NCCV; ++j) {
+            Q qv;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
+            CC[j * SB + s2] = qv;
+        }
+        csrc[s2] = (int)c;
+        cfl[s2] = refl;
+    }
+    __syncthreads();
+    const int la[3] = {t % TL::T0, D >= 2 ? (t / TL::T0) % TL::T1 : 0, D >= 3 ? t / (TL::T0 * TL::T1) : 0};
+    const int qa[3] = {org[0] + la[0], org[1] + la[1], org[2] + la[2]};
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
+    const int sc = TL::sbox_of(la[0], la[1], la[2]);
+    const long long own = valid ? cell_index(g, qa) : 0;
+    for (int vt = vt0; vt < vt1; ++vt) {
+        T xi[VC][D], hx[VC];
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const T* rec = bf.vel + (size_t)(vt * VC + v) * 8;
+#pragma unroll
+            for (int a = 0; a < D; ++a) xi[v][a] = rec[a];
+            hx[v] = rec[4];
+        }
+        for (int s2 = t; s2 < SB; s2 += TL::NT) {
+            const int rf = cfl[s2];
+            const long long c = csrc[s2];
+            T cst[4 * NCCV];
+#pragma unroll
+            for (int j = 0; j < NCCV; ++j) {
+                const Q qv = CC[j * SB + s2];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cst[4 * j + e] = qv.v[e];
+            }
+            T gs[VC], bs[VC];
+            if (rf) {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    const int is = bf.refl[rf * g.Nvp + vt * VC + v];
+                    gs[v] = bf.phi_in[phi_addr(g, c, is, 0)];
+                    bs[v] = bf.phi_in[phi_addr(g, c, is, 1)];
+                }
+            } else {
+                const size_t ad = phi_addr(g, c, vt * VC, 0);
+                Chunk<T>::load(bf.phi_in + ad, gs);
+                Chunk<T>::load(bf.phi_in + ad + VC, bs);
+            }
+            Q qg, qb;
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                T c2 = T(0), z = -cst[D + 3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const T d = xi[v][a] - cst[a];
+                    c2 = fma(d, d, c2);
+                    z = fma(xi[v][a], cst[a], z);
+                }
+                const T ge = cst[D + 1] * Num<T>::expo(cst[D + 0] * c2);
+                const T be = (hx[v] + cst[D + 2]) * ge;
+                const T gg = fma(cst[D + 4], gs[v], cst[D + 5] * ge);
+                const T bb = fma(cst[D + 6], bs[v], cst[D + 7] * be);
+                const T dg = gg - ge;
+                qg.v[v] = fma(cst[D + 8], dg, ge);
+                qb.v[v] = fma(cst[D + 10] * z, dg, fma(cst[D + 9], bb - be, be));
+            }
+            P[0 * SB + s2] = qg;
+            P[1 * SB + s2] = qb;
+        }
+        __syncthreads();
+        if (valid) {
+            const size_t ad = phi_addr(g, own, vt * VC, 0);
+            Chunk<T>::store(bf.phibar + ad, P[0 * SB + sc].v);
+            Chunk<T>::store(bf.phibar + ad + VC, P[1 * SB + sc].v);
+            const size_t as = sig_addr<D>(g, own, vt * VC, 0, 0);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const Q c = P[f * SB + sc];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int st = TL::sstride(a);
+                    const Q l = P[f * SB + sc - st], r = P[f * SB + sc + st];
+                    T o[VC];
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) o[v] = Num<T>::vanleer(c.v[v] - l.v[v], r.v[v] - c.v[v]);
+                    Chunk<T>::store(bf.sigma + as + (a * 2 + f) * VC, o);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
-    using SM = Smem<T, D, T0_, T1_, T2_, PREP>;
+    using SM = Smem<T, D, T0_, T1_, T2_, MODE>;
+    constexpr bool PREP = MODE != MODE_FUSED;      // phibar+ comes from a prepared buffer
+    constexpr bool STORED = MODE == MODE_STORED;   // ... and so do the slopes
+    constexpr int PN = SM::PN;
     using Q = V4<T>;
     constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    Q* const P = reinterpret_cast<Q*>(smem);      // [2][BOX] phibar+ chunk per cell
+    Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
     Q* const S = P + SM::nP;                      // [D][2][SB] raw van Leer slopes (times dx)
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
@@ -733,7 +911,49 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             P[0 * BOX + k] = qg;
             P[1 * BOX + k] = qb;
         };
-        if (PREP) {
+        if (STORED) {
+            // phibar+ and slopes of the cells [-1, T] around the tile from the stored arrays;
+            // a mirrored cell takes the reflected velocity and flips the mirrored slope components
+            for (int s2 = t; s2 < SB; s2 += TL::NT) {
+                const int sl0 = s2 % TL::F0 - 1, sl1 = D >= 2 ? (s2 / TL::F0) % TL::F1 - 1 : 0;
+                const int sl2 = D >= 3 ? s2 / (TL::F0 * TL::F1) - 1 : 0;
+                const int k = TL::box_of(sl0, sl1, sl2);
+                const int rf = cfl[k] & 7;
+                const long long c = csrc[k];
+                Q qg, qb, qs[D][2];
+                if (rf == 0) {
+                    const size_t ad = phi_addr(g, c, vt * VC, 0);
+                    Chunk<T>::load(bf.phibar + ad, qg.v);
+                    Chunk<T>::load(bf.phibar + ad + VC, qb.v);
+                    const size_t as = sig_addr<D>(g, c, vt * VC, 0, 0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        Chunk<T>::load(bf.sigma + as + (a * 2 + 0) * VC, qs[a][0].v);
+                        Chunk<T>::load(bf.sigma + as + (a * 2 + 1) * VC, qs[a][1].v);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        const int is = bf.refl[rf * g.Nvp + vt * VC + v];
+                        qg.v[v] = bf.phibar[phi_addr(g, c, is, 0)];
+                        qb.v[v] = bf.phibar[phi_addr(g, c, is, 1)];
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const T sgn_a = (rf & (1 << a)) ? T(-1) : T(1);
+                            qs[a][0].v[v] = sgn_a * bf.sigma[sig_addr<D>(g, c, is, a, 0)];
+                            qs[a][1].v[v] = sgn_a * bf.sigma[sig_addr<D>(g, c, is, a, 1)];
+                        }
+                    }
+                }
+                P[0 * PN + s2] = qg;
+                P[1 * PN + s2] = qb;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    S[(a * 2 + 0) * SB + s2] = qs[a][0];
+                    S[(a * 2 + 1) * SB + s2] = qs[a][1];
+                }
+            }
+        } else if (PREP) {
             pcell(kc);
             for (int h = t; h < NH; h += TL::NT) pcell(halo[h]);
         } else {
@@ -743,7 +963,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         __syncthreads();
 
         // ---- phase 2: van Leer slopes (times dx) of the cells [-1, T] around the tile
-        for (int s = t; s < SB; s += TL::NT) {
+        for (int s = t; s < (STORED ? 0 : SB); s += TL::NT) {
             const int sl0 = s % TL::F0 - 1, sl1 = D >= 2 ? (s / TL::F0) % TL::F1 - 1 : 0;
             const int sl2 = D >= 3 ? s / (TL::F0 * TL::F1) - 1 : 0;
             const int k = TL::box_of(sl0, sl1, sl2);
@@ -761,7 +981,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 }
             }
         }
-        __syncthreads();
+        if (!STORED) __syncthreads();
 
         // ---- phase 3: faces of the owned cell
         if (valid) {
@@ -781,7 +1001,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     if (sgn[a] != 0) {
                         const bool lft = sgn[a] > 0;
                         const int up = lft ? Lb : Rb, ups = lft ? Ls : Rs;
-                        const Q pg = P[0 * BOX + up], pb = P[1 * BOX + up];
+                        const int pu = STORED ? ups : up;
+                        const Q pg = P[0 * PN + pu], pb = P[1 * PN + pu];
                         Q sg[D], sb[D];
 #pragma unroll
                         for (int b = 0; b < D; ++b) {
@@ -805,8 +1026,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                         const T* Ps = reinterpret_cast<const T*>(P);
                         const T* Ss = reinterpret_cast<const T*>(S);
                         auto recon = [&](int v, int up, int ups, T ka, T& rg, T& rb) {
-                            rg = Ps[(0 * BOX + up) * VC + v];
-                            rb = Ps[(1 * BOX + up) * VC + v];
+                            const int pu = STORED ? ups : up;
+                            rg = Ps[(0 * PN + pu) * VC + v];
+                            rb = Ps[(1 * PN + pu) * VC + v];
 #pragma unroll
                             for (int b = 0; b < D; ++b) {
                                 const T k = (b == a) ? ka : -nu[v][b];
@@ -975,24 +1197,24 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 
 // CTAs per SM that the shared memory of a sweep allows (at least 1, at most 4);
 // the launch bounds ask the compiler to fit the registers to the same count.
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 struct Occ {
     static constexpr size_t kSmemPerSM = 228 * 1024;
-    static constexpr size_t per = Smem<T, D, T0_, T1_, T2_, PREP>::bytes(SWEEP_B) + 1024;
+    static constexpr size_t per = Smem<T, D, T0_, T1_, T2_, MODE>::bytes(SWEEP_B) + 1024;
     static constexpr int by_smem = (int)(kSmemPerSM / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
-    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 64);   // keep >= 64 registers
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 80);   // keep >= 80 registers
     static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
     static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
     static constexpr int value = v0 < 1 ? 1 : (v0 > 4 ? 4 : v0);
 };
 
 // One problem instance: grid (tiles, velocity groups).
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, bool PREP>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, PREP>::value))
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
     k_sweep(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(32) unsigned char smem[];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, PREP>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list
@@ -1000,12 +1222,12 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 // device and the W-update kernel flips it, so a captured graph replays.
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, false>::value))
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE_FUSED>::value))
     k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(32) unsigned char smem[];
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, false>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE_FUSED>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
 // Face constants from the group-summed face W (fixed summation order).

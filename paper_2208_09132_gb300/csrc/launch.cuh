@@ -32,9 +32,10 @@ TileShape tile_shape_f32(int D, int id);
 TileShape tile_shape_f64(int D, int id);
 size_t sweep_smem_f32(int D, int id);
 size_t sweep_smem_f64(int D, int id);
-// Whether a shape forms phibar+ in its own pass (needs the extra state-size buffer).
-bool tile_prep_f32(int D, int id);
-bool tile_prep_f64(int D, int id);
+// Sweep mode of a shape (MODE_FUSED / MODE_PREP / MODE_STORED): prepared and
+// stored shapes need a phibar+ buffer, stored shapes also a slope buffer.
+int tile_mode_f32(int D, int id);
+int tile_mode_f64(int D, int id);
 
 // The single-instance launches read the instance from the device table `in`
 // and use orientation `cur` (read state buffer cur, write the other).

@@ -6,14 +6,16 @@ namespace cdg {
 namespace {
 using Table32 = ShapeTable<
     float, ShapeList<Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>>,
-    ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, true>>,
-    ShapeList<Shape<float, 3, 8, 4, 4>, Shape<float, 3, 8, 8, 4, true>>>;
+    ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, MODE_PREP>,
+              Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>>,
+    ShapeList<Shape<float, 3, 8, 4, 4>, Shape<float, 3, 8, 8, 4, MODE_PREP>, Shape<float, 3, 8, 8, 4, MODE_STORED>,
+              Shape<float, 3, 8, 4, 4, MODE_STORED>>>;
 }
 
 int tile_count_f32(int D) { return Table32::count(D); }
 TileShape tile_shape_f32(int D, int id) { return Table32::shape(D, id); }
 size_t sweep_smem_f32(int D, int id) { return Table32::smem(D, id); }
-bool tile_prep_f32(int D, int id) { return Table32::prep(D, id); }
+int tile_mode_f32(int D, int id) { return Table32::mode(D, id); }
 
 cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
     return Table32::step(g, in, cur, s, ev);

@@ -7,14 +7,14 @@ namespace cdg {
 namespace {
 using Table64 = ShapeTable<
     double, ShapeList<Shape<double, 1, 256, 1, 1>, Shape<double, 1, 128, 1, 1>, Shape<double, 1, 64, 1, 1>>,
-    ShapeList<Shape<double, 2, 16, 8, 1>, Shape<double, 2, 8, 8, 1>>,
-    ShapeList<Shape<double, 3, 4, 4, 4>, Shape<double, 3, 8, 4, 4, true>>>;
+    ShapeList<Shape<double, 2, 16, 8, 1>, Shape<double, 2, 8, 8, 1>, Shape<double, 2, 16, 8, 1, MODE_STORED>>,
+    ShapeList<Shape<double, 3, 4, 4, 4>, Shape<double, 3, 8, 4, 4, MODE_PREP>, Shape<double, 3, 8, 4, 4, MODE_STORED>>>;
 }
 
 int tile_count_f64(int D) { return Table64::count(D); }
 TileShape tile_shape_f64(int D, int id) { return Table64::shape(D, id); }
 size_t sweep_smem_f64(int D, int id) { return Table64::smem(D, id); }
-bool tile_prep_f64(int D, int id) { return Table64::prep(D, id); }
+int tile_mode_f64(int D, int id) { return Table64::mode(D, id); }
 
 cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
     return Table64::step(g, in, cur, s, ev);

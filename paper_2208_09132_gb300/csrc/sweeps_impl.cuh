@@ -9,25 +9,32 @@ namespace cdg {
 // constant computations of a small problem spread over many SMs.
 constexpr int kSmallBlock = 64;
 
-// One instantiated tile shape of the sweeps and its launches.  PREP shapes
-// form phibar+ of every point once per step (k_prep) and the sweeps load it.
-template <typename T, int D, int TX, int TY, int TZ, bool PREP = false>
+// One instantiated tile shape of the sweeps and its launches.  Prepared
+// shapes (MODE_PREP) form phibar+ of every point once per step (k_prep);
+// stored shapes (MODE_STORED) form phibar+ and the slopes (k_shslope); the
+// sweeps of both load what was formed instead of recomputing it on the halo.
+template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED>
 struct Shape {
-    using SM = Smem<T, D, TX, TY, TZ, PREP>;
+    using SM = Smem<T, D, TX, TY, TZ, MODE>;
     using TL = Tile<D, TX, TY, TZ>;
-    static constexpr bool prep = PREP;
+    static constexpr int mode = MODE;
 
     static cudaError_t configure() {
         static bool done = false;
         if (done) return cudaSuccess;
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false, PREP>,
+        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false, MODE>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
             return e;
-        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, PREP>,
+        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, MODE>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
             return e;
-        if (!PREP) {
+        if constexpr (MODE == MODE_STORED) {
+            if ((e = cudaFuncSetAttribute(k_shslope<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shslope_smem_bytes<T, D, TX, TY, TZ>())))
+                return e;
+        }
+        if constexpr (MODE == MODE_FUSED) {
             if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
                 return e;
@@ -44,19 +51,21 @@ struct Shape {
         if (e) return e;
         const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
         if (ev) cudaEventRecord(ev[0], s);
-        if (PREP) {
+        if constexpr (MODE == MODE_PREP) {
             constexpr int kChunks = 8;
             const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
             k_prep<T, D><<<pg, 128, 0, s>>>(in, cur, kChunks);
+        } else if constexpr (MODE == MODE_STORED) {
+            k_shslope<T, D, TX, TY, TZ><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ>(), s>>>(in, cur);
         }
-        k_sweep<T, D, TX, TY, TZ, false, PREP><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
+        k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[1], s);
         for (int a = 0; a < D; ++a) {
             const unsigned blocks = (unsigned)((g.nf[a] + kSmallBlock - 1) / kSmallBlock);
             k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
         }
         if (ev) cudaEventRecord(ev[2], s);
-        k_sweep<T, D, TX, TY, TZ, true, PREP><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
+        k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[3], s);
         k_wupdate<T, D><<<(unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock), kSmallBlock, 0, s>>>(in, cur);
         if (ev) cudaEventRecord(ev[4], s);
@@ -65,13 +74,16 @@ struct Shape {
 
     static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
                                    cudaStream_t s) {
-        if (PREP) return cudaErrorNotSupported;
-        cudaError_t e = configure();
-        if (e) return e;
-        if (n <= 0) return cudaSuccess;
-        if (B) k_sweep_batch<T, D, TX, TY, TZ, true><<<n, TL::NT, SM::bytes(true), s>>>(items, insts, cur);
-        else k_sweep_batch<T, D, TX, TY, TZ, false><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
-        return cudaGetLastError();
+        if constexpr (MODE != MODE_FUSED) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e = configure();
+            if (e) return e;
+            if (n <= 0) return cudaSuccess;
+            if (B) k_sweep_batch<T, D, TX, TY, TZ, true><<<n, TL::NT, SM::bytes(true), s>>>(items, insts, cur);
+            else k_sweep_batch<T, D, TX, TY, TZ, false><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
+            return cudaGetLastError();
+        }
     }
 
     static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }
@@ -93,7 +105,7 @@ struct ShapeList<> {
     }
     static TileShape shape(int) { return {{0, 0, 0}}; }
     static size_t smem(int) { return 0; }
-    static bool prep(int) { return false; }
+    static int mode(int) { return 0; }
 };
 template <typename H, typename... R>
 struct ShapeList<H, R...> {
@@ -110,7 +122,7 @@ struct ShapeList<H, R...> {
     }
     static TileShape shape(int id) { return id == 0 ? H::shape() : Rest::shape(id - 1); }
     static size_t smem(int id) { return id == 0 ? H::SM::bytes(true) : Rest::smem(id - 1); }
-    static bool prep(int id) { return id == 0 ? H::prep : Rest::prep(id - 1); }
+    static int mode(int id) { return id == 0 ? H::mode : Rest::mode(id - 1); }
 };
 
 // The shapes of one precision for D = 1, 2, 3.
@@ -119,7 +131,7 @@ struct ShapeTable {
     static int count(int D) { return D == 1 ? L1::count : (D == 2 ? L2::count : L3::count); }
     static TileShape shape(int D, int id) { return D == 1 ? L1::shape(id) : (D == 2 ? L2::shape(id) : L3::shape(id)); }
     static size_t smem(int D, int id) { return D == 1 ? L1::smem(id) : (D == 2 ? L2::smem(id) : L3::smem(id)); }
-    static bool prep(int D, int id) { return D == 1 ? L1::prep(id) : (D == 2 ? L2::prep(id) : L3::prep(id)); }
+    static int mode(int D, int id) { return D == 1 ? L1::mode(id) : (D == 2 ? L2::mode(id) : L3::mode(id)); }
     static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
         if (g.D == 1) return L1::template step<T>(g.tile_id, g, in, cur, s, ev);
         if (g.D == 2) return L2::template step<T>(g.tile_id, g, in, cur, s, ev);

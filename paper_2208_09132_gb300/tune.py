@@ -58,7 +58,15 @@ def candidates(cfg, precision, context="alone"):
     nt = cdugks.load().cdugks_tile_count(precision, cfg["dim"])
     nvt = (wl.nvel(cfg) + 3) // 4
     groups = [g for g in (1, 2, 4, 8, 16, 32) if g <= nvt]
-    tiles = [t for t in range(nt) if context == "alone" or not cdugks.tile_shape(precision, cfg["dim"], t)[1]]
+    dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
+    tiles = []
+    for t in range(nt):
+        mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
+        if context != "alone" and mode != 0:
+            continue                      # only fused shapes are batched
+        if mode == 2 and dirichlet:
+            continue                      # stored slopes: periodic / specular only
+        tiles.append(t)
     return [(t, g) for t in tiles for g in groups]
 
 

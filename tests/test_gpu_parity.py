@@ -189,7 +189,8 @@ def test_status_flags_report_a_broken_state():
 
 @pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
 @pytest.mark.parametrize("name", ["1d_periodic_ragged_padded", "2d_dirichlet_x_specular_y",
-                                  "2d_periodic_ragged", "3d_mixed_bc", "3d_periodic_ragged"])
+                                  "2d_specular_x_periodic_y", "2d_periodic_ragged", "3d_mixed_bc",
+                                  "3d_specular_corners", "3d_periodic_ragged"])
 def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     """All instantiated tile shapes, the prepared-shift ones included, give the oracle's result."""
     (cfg, f), steps = case(name)
@@ -197,7 +198,10 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     o.init(f)
     o.step(steps)
     ref = o.moments()
+    dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
+        if cdugks.tile_shape(precision, cfg["dim"], t)[1] == 2 and dirichlet:
+            continue      # stored-slope shapes take periodic and specular boundaries only
         s = cdugks.Solver(cfg, precision=precision, tile_id=t, velocity_groups=2)
         s.init(f)
         s.step(steps)
