@@ -339,7 +339,6 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
             }
     for (long long i = Nv; i < g.Nvp; ++i)
         for (int m = 0; m < 8; ++m) h->refl[(size_t)m * g.Nvp + i] = (int)i;
-    h->vel32 = cast_vec<float>(h->vel);
     // time step: fixed CFL rule of Sec. 4 unless given
     double dt = phys->dt;
     if (!(dt > 0)) {
@@ -357,6 +356,9 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
         g.hdx[a] = g.h / g.dx[a];
         g.idx[a] = 1.0 / g.dx[a];
     }
+    // reconstruction coefficients 2 h xi_a / dx_a in the velocity records
+    for (long long i = 0; i < Nv; ++i)
+        for (int a = 0; a < D; ++a) h->vel[(size_t)i * 8 + 5 + a] = 2.0 * g.hdx[a] * h->vel[(size_t)i * 8 + a];
     g.K = phys->K;
     g.R = phys->R;
     g.mu_ref = phys->mu_ref;
@@ -364,6 +366,7 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     g.omega = phys->omega;
     g.Pr = phys->Pr;
     set_tiles(h, 0);
+    h->vel32 = cast_vec<float>(h->vel);
     h->gsel = 0;
     h->gcap = groups_for(h, 0);
     set_groups(h, h->gcap);

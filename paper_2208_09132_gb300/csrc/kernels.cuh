@@ -72,7 +72,8 @@ struct Bufs {
     FaceC<T>* facec[3];   // [nf_a] constants of the face W (between the sweeps)
     double* wf[3];        // [G][2+D][nf_a] face W partial sums (sweep A)
     double* mf[3];        // [G][2+D][nf_a] face flux-moment partial sums (sweep B)
-    const T* vel;         // [Nvp][8] per velocity: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0 (w = 0 on padding)
+    const T* vel;         // [Nvp][8] per velocity: xi_0, xi_1, xi_2, w, |xi|^2/2, 2h xi_0/dx_0, 2h xi_1/dx_1,
+                          // 2h xi_2/dx_2 (w = 0 on padding)
     const int* refl;      // [8][Nvp] velocity index with the components of mask reversed
     int* status;
 };
@@ -107,9 +108,11 @@ template <> struct Num<float> {
         return y;
     }
     static __host__ __device__ __forceinline__ double cexp_scale() { return 1.4426950408889634; }
+    // half the van Leer slope: s1 s2 / (s1 + s2) (the factor 2 is folded into the
+    // reconstruction coefficients)
     static __device__ __forceinline__ float vanleer(float s1, float s2) {
         float p = s1 * s2;
-        return p > 0.f ? __fdividef(2.f * p, s1 + s2) : 0.f;
+        return p > 0.f ? __fdividef(p, s1 + s2) : 0.f;
     }
 };
 template <> struct Num<double> {
@@ -117,7 +120,7 @@ template <> struct Num<double> {
     static __host__ __device__ __forceinline__ double cexp_scale() { return 1.0; }
     static __device__ __forceinline__ double vanleer(double s1, double s2) {
         double p = s1 * s2;
-        return p > 0.0 ? 2.0 * p / (s1 + s2) : 0.0;
+        return p > 0.0 ? p / (s1 + s2) : 0.0;
     }
 };
 
@@ -630,7 +633,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
-    Q* const S = P + SM::nP;                      // [D][2][SB] raw van Leer slopes (times dx)
+    Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
@@ -788,18 +791,19 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NH = TL::NH;
 
     for (int vt = vt0; vt < vt1; ++vt) {
-        // velocity records of the chunk (same for every thread)
+        // velocity records of the chunk (same for every thread); nu = 2 h xi / dx
         T xi[VC][D], nu[VC][D], w[VC], hx[VC];
 #pragma unroll
         for (int v = 0; v < VC; ++v) {
-            const T* rec = bf.vel + (size_t)(vt * VC + v) * 8;
+            const Q* rec = reinterpret_cast<const Q*>(bf.vel + (size_t)(vt * VC + v) * 8);
+            const Q r0 = rec[0], r1 = rec[1];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                xi[v][a] = rec[a];
-                nu[v][a] = (T)g.hdx[a] * xi[v][a];
+                xi[v][a] = r0.v[a];
+                nu[v][a] = a == 0 ? r1.v[1] : (a == 1 ? r1.v[2] : r1.v[3]);
             }
-            w[v] = rec[3];
-            hx[v] = rec[4];
+            w[v] = r0.v[3];
+            hx[v] = r1.v[0];
         }
         // per axis: +1 / -1 when the chunk's four xi_a share a strict sign, else 0
         int sgn[D];
@@ -962,7 +966,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         }
         __syncthreads();
 
-        // ---- phase 2: van Leer slopes (times dx) of the cells [-1, T] around the tile
+        // ---- phase 2: half van Leer slopes (times dx) of the cells [-1, T] around the tile
         for (int s = t; s < (STORED ? 0 : SB); s += TL::NT) {
             const int sl0 = s % TL::F0 - 1, sl1 = D >= 2 ? (s / TL::F0) % TL::F1 - 1 : 0;
             const int sl2 = D >= 3 ? s / (TL::F0 * TL::F1) - 1 : 0;
@@ -1009,13 +1013,13 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                             sg[b] = S[(b * 2 + 0) * SB + ups];
                             sb[b] = S[(b * 2 + 1) * SB + ups];
                         }
-                        const T half = lft ? T(0.5) : T(-0.5);
+                        const T one = lft ? T(1) : T(-1);   // (x_f - x_up)/(dx/2) along the normal
 #pragma unroll
                         for (int v = 0; v < VC; ++v) {
                             T rg = pg.v[v], rb = pb.v[v];
 #pragma unroll
                             for (int b = 0; b < D; ++b) {
-                                const T k = (b == a) ? half - nu[v][a] : -nu[v][b];
+                                const T k = (b == a) ? one - nu[v][a] : -nu[v][b];
                                 rg = fma(k, sg[b].v[v], rg);
                                 rb = fma(k, sb[b].v[v], rb);
                             }
@@ -1041,11 +1045,11 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                             const T x = xi[v][a];
                             if (x != T(0)) {
                                 const bool lft = x > T(0);
-                                recon(v, lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(0.5) : T(-0.5)) - nu[v][a], gb[v], bb[v]);
+                                recon(v, lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(1) : T(-1)) - nu[v][a], gb[v], bb[v]);
                             } else {   // xi . n = 0: mean of both one-sided values
                                 T g1, b1, g2, b2;
-                                recon(v, Lb, Ls, T(0.5), g1, b1);
-                                recon(v, Rb, Rs, T(-0.5), g2, b2);
+                                recon(v, Lb, Ls, T(1), g1, b1);
+                                recon(v, Rb, Rs, T(-1), g2, b2);
                                 gb[v] = T(0.5) * (g1 + g2);
                                 bb[v] = T(0.5) * (b1 + b2);
                             }

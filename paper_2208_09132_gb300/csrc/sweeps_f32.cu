@@ -7,7 +7,8 @@ namespace {
 using Table32 = ShapeTable<
     float, ShapeList<Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>>,
     ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, MODE_PREP>,
-              Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>>,
+              Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>,
+              Shape<float, 2, 32, 16, 1>>,
     ShapeList<Shape<float, 3, 8, 4, 4>, Shape<float, 3, 8, 8, 4, MODE_PREP>, Shape<float, 3, 8, 8, 4, MODE_STORED>,
               Shape<float, 3, 8, 4, 4, MODE_STORED>>>;
 }
