@@ -367,7 +367,9 @@ def run_ours(args, ws, rank, local):
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
     tile, groups = 0, 0
-    if args.tune:
+    if args.tile is not None:
+        tile, groups = args.tile, args.groups or 0
+    elif args.tune:
         from paper_2208_09132_gb300 import tune
         tile, groups = tune.tune(cfg, prec, context="alone", device=dev)
     s = cdugks.Solver(cfg, precision=prec, device=dev, tile_id=tile, velocity_groups=groups)
@@ -527,6 +529,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 plain comparison")
     ap.add_argument("--no-tune", dest="tune", action="store_false", help="default tile / group choice")
+    ap.add_argument("--tile", type=int, default=None, help="pin the tile shape id (skips tuning)")
+    ap.add_argument("--groups", type=int, default=None, help="with --tile: velocity groups")
     ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
     ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")
     args = ap.parse_args()
