@@ -193,14 +193,18 @@ CDUGKS_API int cdugks_set_velocity_groups(cdugks_t *h, int groups);
  * depend on the shape. */
 CDUGKS_API int cdugks_tile_count(int precision, int dim);
 CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
-/* out[0..2]: cells per axis of a tile shape; out[3] its sweep mode:
- *   0  the sweeps form phibar+ and the van Leer slopes on their halo boxes;
+/* out[0..2]: cells per axis of a tile shape; out[3] its sweep mode.  Bits
+ * 0-1 say where the sweeps take phibar+ and the van Leer slopes from:
+ *   0  they form both on their halo boxes;
  *   1  phibar+ of every point is formed once per step in its own pass (one
  *      more state-size buffer in the workspace);
  *   2  phibar+ and the slopes of every point are formed once per step in a
  *      stencil pass (one more state-size buffer and D more for the slopes;
  *      periodic and specular boundaries only).
- * Modes 1 and 2 must be selected before cdugks_bind and are not batched. */
+ * Bit 2 (value 4, face store): sweep A keeps the reconstructed phibar of
+ * every face and velocity (about D more state-size buffers) and sweep B only
+ * forms the fluxes from them instead of reconstructing again.
+ * Every mode but 0 must be selected before cdugks_bind and is not batched. */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 
 /* ---------------------------------------------------------------- batches

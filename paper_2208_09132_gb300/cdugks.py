@@ -304,8 +304,9 @@ class Batch:
 
 
 def tile_shape(precision: int, dim: int, tile_id: int):
-    """(cells per axis, sweep mode) of an instantiated tile shape (mode 0 fused,
-    1 prepared phibar+, 2 stored phibar+ and slopes)."""
+    """(cells per axis, sweep mode) of an instantiated tile shape.  Mode bits
+    0-1: 0 fused, 1 prepared phibar+, 2 stored phibar+ and slopes; bit 2 (4):
+    face store (sweep A keeps the face values, sweep B only forms fluxes)."""
     out = (ctypes.c_int * 4)()
     _check(load().cdugks_tile_shape(int(precision), int(dim), int(tile_id), out))
     return tuple(out[:3]), int(out[3])

@@ -43,8 +43,18 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t phi[2], pb, sg, W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
+    size_t phi[2], pb, sg, fv[3], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
 };
+
+// Optional workspace buffers, by the sweep modes that need them.
+enum { BUF_PHIBAR = 1, BUF_SLOPES = 2, BUF_FACES = 4 };
+int buffers_of(int mode) {
+    int b = 0;
+    if (cdg::mode_source(mode) != cdg::MODE_FUSED) b |= BUF_PHIBAR;
+    if (cdg::mode_source(mode) == cdg::MODE_STORED) b |= BUF_SLOPES;
+    if (cdg::mode_faces(mode)) b |= BUF_FACES;
+    return b;
+}
 
 }  // namespace
 
@@ -58,7 +68,7 @@ struct cdugks {
     size_t cellc_bytes, facec_bytes;
     int Nv;
     int gcap;              // velocity groups the workspace is laid out for
-    int mode_cap;          // the workspace holds the phibar+ buffer (>= 1) and the slope buffer (2)
+    int bufs_cap;          // optional buffers the workspace holds (BUF_* bits)
     int gsel;              // requested groups (0 = auto)
     Layout lay;
     unsigned char* base;
@@ -140,8 +150,10 @@ void make_layout(cdugks* h) {
     const size_t state = (size_t)g.Nvp * (size_t)g.Nc * 2 * h->elt;
     L.phi[0] = take(state);
     L.phi[1] = take(state);
-    L.pb = h->mode_cap >= cdg::MODE_PREP ? take(state) : 0;
-    L.sg = h->mode_cap >= cdg::MODE_STORED ? take(state * g.D) : 0;
+    L.pb = (h->bufs_cap & BUF_PHIBAR) ? take(state) : 0;
+    L.sg = (h->bufs_cap & BUF_SLOPES) ? take(state * g.D) : 0;
+    for (int a = 0; a < 3; ++a)
+        L.fv[a] = (h->bufs_cap & BUF_FACES) && a < g.D ? take((size_t)g.Nvp * (size_t)g.nf[a] * 2 * h->elt) : 0;
     L.W = take(sizeof(double) * NM * g.Nc);
     L.cellc = take(h->cellc_bytes * g.Nc);
     L.cellc0 = take(h->cellc_bytes * g.Nc);
@@ -166,8 +178,10 @@ Bufs<T> bufs(const cdugks* h, int in) {
     const Layout& L = h->lay;
     b.phi_in = reinterpret_cast<const T*>(p + L.phi[in]);
     b.phi_out = reinterpret_cast<T*>(p + L.phi[1 - in]);
-    b.phibar = h->mode_cap >= cdg::MODE_PREP ? reinterpret_cast<T*>(p + L.pb) : nullptr;
-    b.sigma = h->mode_cap >= cdg::MODE_STORED ? reinterpret_cast<T*>(p + L.sg) : nullptr;
+    b.phibar = (h->bufs_cap & BUF_PHIBAR) ? reinterpret_cast<T*>(p + L.pb) : nullptr;
+    b.sigma = (h->bufs_cap & BUF_SLOPES) ? reinterpret_cast<T*>(p + L.sg) : nullptr;
+    for (int a = 0; a < 3; ++a)
+        b.face[a] = (h->bufs_cap & BUF_FACES) && a < h->g.D ? reinterpret_cast<T*>(p + L.fv[a]) : nullptr;
     b.W = reinterpret_cast<double*>(p + L.W);
     b.cellc = reinterpret_cast<CellC<T>*>(p + L.cellc);
     b.cellc0 = reinterpret_cast<CellC<T>*>(p + L.cellc0);
@@ -411,14 +425,15 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
     if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
     if (tile_id < 0 || tile_id >= tile_count(h->prec, h->g.D)) return fail(CDUGKS_ERR_INVALID, "unknown tile id");
     const int mode = tile_mode(h->prec, h->g.D, tile_id);
-    if (mode == cdg::MODE_STORED)
+    if (cdg::mode_source(mode) == cdg::MODE_STORED)
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
                 return fail(CDUGKS_ERR_INVALID, "stored-slope shapes support periodic and specular boundaries only");
-    if (mode > h->mode_cap) {
+    const int need = buffers_of(mode);
+    if (need & ~h->bufs_cap) {
         if (h->bound)
             return fail(CDUGKS_ERR_INVALID, "this shape needs more workspace buffers: select it before cdugks_bind");
-        h->mode_cap = mode;
+        h->bufs_cap |= need;
         make_layout(h);
     }
     set_tiles(h, tile_id);
@@ -1051,7 +1066,7 @@ int noalloc_scratch(void** out) {
 template <typename T>
 int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStream_t st) {
     Geo g = h->g;
-    if (tile_mode(h->prec, g.D, g.tile_id) != cdg::MODE_FUSED) {   // no room for phibar+ / slope buffers here
+    if (tile_mode(h->prec, g.D, g.tile_id) != cdg::MODE_FUSED) {   // no room for phibar+ / slope / face buffers here
         g.tile_id = 0;
         const cdg::TileShape ts = tile_of(h->prec, g.D, 0);
         for (int a = 0; a < 3; ++a) g.tiles[a] = a < g.D ? (g.n[a] + ts.t[a] - 1) / ts.t[a] : 1;
@@ -1098,6 +1113,7 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
     b.phi_out = static_cast<T*>(phi_out);
     b.phibar = nullptr;
     b.sigma = nullptr;
+    for (int a = 0; a < 3; ++a) b.face[a] = nullptr;
     b.W = W;
     b.cellc = reinterpret_cast<CellC<T>*>(base + off_cellc);
     b.cellc0 = b.cellc;   // no Dirichlet ghosts on this path

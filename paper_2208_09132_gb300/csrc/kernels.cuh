@@ -66,6 +66,7 @@ struct Bufs {
     T* phi_out;
     T* phibar;            // phibar+ of every point (state layout), for the prepared and stored shapes
     T* sigma;             // van Leer slopes of every point, [chunk][cell][axis][g|b][VC] (stored shapes)
+    T* face[3];           // reconstructed phibar at every face of axis a, [chunk][face][g|b][VC] (face-store shapes)
     double* W;            // [2+D][Nc] tracked conserved variables, updated in place
     CellC<T>* cellc;      // [Nc] constants of W^n (written by the W update / init)
     CellC<T>* cellc0;     // [Nc] constants of W^0 (Dirichlet ghosts)
@@ -279,13 +280,15 @@ template <> struct Kahan<double> {
 // ghost layers of later axes overwrite corners), periodic wrap, specular
 // mirror (reflection bit set), Dirichlet clamp (flag).  Coordinates beyond the
 // ghost layer (ragged tiles) are clamped; they are never read.
+template <int D>
 __device__ __forceinline__ void resolve(const Geo& g, int q[3], int& refl, bool& dir) {
     refl = 0;
     dir = false;
-    for (int a = g.D - 1; a >= 0; --a) {
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
         const int k = q[a], n = g.n[a];
-        if (k >= 0 && k < n) continue;
-        const int bc = g.bc[a][k < 0 ? 0 : 1];
+        if (dir || (k >= 0 && k < n)) continue;
+        const int bc = k < 0 ? g.bc[a][0] : g.bc[a][1];
         if (bc == BC_PERIODIC) {
             q[a] = ((k % n) + n) % n;
         } else if (bc == BC_SPECULAR) {
@@ -293,10 +296,10 @@ __device__ __forceinline__ void resolve(const Geo& g, int q[3], int& refl, bool&
             refl ^= 1 << a;
         } else {
             dir = true;
-            break;
         }
     }
-    for (int a = 0; a < g.D; ++a) q[a] = min(max(q[a], 0), g.n[a] - 1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) q[a] = min(max(q[a], 0), g.n[a] - 1);
 }
 
 __device__ __forceinline__ long long cell_index(const Geo& g, const int q[3]) {
@@ -369,7 +372,9 @@ struct Tile {
     __host__ __device__ static constexpr int bstride(int a) { return a == 0 ? 1 : (a == 1 ? E0 : E0 * E1); }
     __host__ __device__ static constexpr int sstride(int a) { return a == 0 ? 1 : (a == 1 ? F0 : F0 * F1); }
     __host__ __device__ static constexpr int tdim(int a) { return a == 0 ? T0 : (a == 1 ? T1 : T2); }
-    __host__ __device__ static constexpr int foff(int a) { return a == 0 ? 0 : (a == 1 ? NF0 : NF0 + NF1); }
+    __host__ __device__ static constexpr int foff(int a) {
+        return a == 0 ? 0 : (a == 1 ? NF0 : (a == 2 ? NF0 + NF1 : NFT));
+    }
     __device__ static __forceinline__ int box_of(int l0, int l1, int l2) {
         return (l0 + 2) + E0 * ((D >= 2 ? l1 + 2 : 0) + E1 * (D >= 3 ? l2 + 2 : 0));
     }
@@ -390,10 +395,15 @@ struct alignas(4 * sizeof(T)) V4 {
     T v[4];
 };
 
-// Sweep modes: 0 forms phibar+ and the slopes on the halo box itself; 1
-// (prepared) loads phibar+ formed by k_prep and forms the slopes; 2 (stored)
-// loads phibar+ and the slopes formed by k_shslope.
-enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2 };
+// Sweep modes.  The low two bits say where sweep A (and a recomputing sweep
+// B) takes phibar+ and the slopes from: 0 forms both on the halo box itself;
+// 1 (prepared) loads phibar+ formed by k_prep and forms the slopes; 2 (stored)
+// loads phibar+ and the slopes formed by k_shslope.  Bit 2 (face store):
+// sweep A also writes the reconstructed face values, and sweep B is k_flux,
+// which reads them instead of reconstructing them again.
+enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4 };
+__host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
+__host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
@@ -402,10 +412,10 @@ struct Smem {
     static constexpr int NCCV = (NCC + 3) / 4;   // ... packed in V4
     static constexpr int NFC = D + 7;            // face constants
     static constexpr int NFCV = (NFC + 3) / 4;
-    static constexpr int PN = MODE == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
-    static constexpr size_t nP = (size_t)2 * PN;                       // V4 units
+    static constexpr int PN = mode_source(MODE) == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
+    static constexpr size_t nP = (size_t)2 * PN;                                    // V4 units
     static constexpr size_t nS = (size_t)D * 2 * TL::SB;
-    static constexpr size_t nCC = MODE == MODE_FUSED ? (size_t)NCCV * TL::BOX : 0;
+    static constexpr size_t nCC = mode_source(MODE) == MODE_FUSED ? (size_t)NCCV * TL::BOX : 0;
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
     __host__ __device__ static constexpr size_t vcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
@@ -413,6 +423,11 @@ struct Smem {
         return vcount(B) * sizeof(V4<T>) + sizeof(int) * (2 * TL::BOX + TL::NH + 32);
     }
 };
+
+// Offset of the chunk vt of face f (axis a) in the face-value layout.
+__device__ __forceinline__ size_t face_addr(const Geo& g, int a, long long f, int vt) {
+    return ((size_t)vt * (size_t)g.nf[a] + (size_t)f) * (2 * VC);
+}
 
 // Offset of (cell, velocity i, axis a, field f) in the slope layout.
 template <int D>
@@ -506,7 +521,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
         int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
         int refl;
         bool dir;
-        resolve(g, q, refl, dir);
+        resolve<D>(g, q, refl, dir);
         const long long c = cell_index(g, q);
         const CellC<T>& cs = bf.cellc[c];
         T cst[4 * NCCV];
@@ -620,12 +635,192 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
     }
 }
 
+// ---- pieces shared by the recomputing sweep B and k_flux
+
+// First owned cell of tile number `tile` (tiles numbered x fastest).
+template <typename TL, int D>
+__device__ __forceinline__ void tile_origin(const Geo& g, int tile, int org[3]) {
+    int tb = tile;
+    org[0] = (tb % g.tiles[0]) * TL::T0;
+    org[1] = org[2] = 0;
+    tb /= g.tiles[0];
+    if (D >= 2) { org[1] = (tb % g.tiles[1]) * TL::T1; tb /= g.tiles[1]; }
+    if (D >= 3) org[2] = tb * TL::T2;
+}
+
+// Face constants packed per face: u (D), cexp, pref, eb, hu2, alpha_g, alpha_b, gamma_b.
+template <int D>
+struct FacePack {
+    static constexpr int N = D + 7;
+    static constexpr int NV = (N + 3) / 4;   // V4 units
+};
+
+// The packed constants of every face of the tile (both ends of each axis)
+// into shared memory, FC[j * NFT + local face].
+template <typename T, int D, typename TL>
+__device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& bf, const int org[3], V4<T>* FC) {
+    constexpr int NFCV = FacePack<D>::NV, NFT = TL::NFT;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+    for (int r = threadIdx.x; r < TL::foff(a + 1) - TL::foff(a); r += TL::NT) {
+        const int f = TL::foff(a) + r;
+        const int d0 = TL::T0 + (a == 0), d1 = TL::T1 + (a == 1);
+        int q[3] = {org[0] + r % d0, org[1] + (D >= 2 ? (r / d0) % d1 : 0), org[2] + (D >= 3 ? r / (d0 * d1) : 0)};
+        bool ok = true;
+#pragma unroll
+        for (int b = 0; b < D; ++b) ok = ok && q[b] <= g.n[b] - (b == a ? 0 : 1);
+        if (!ok) continue;
+        const FaceC<T>& fs = bf.facec[a][face_index(g, a, q)];
+        T cst[4 * NFCV];
+#pragma unroll
+        for (int b = 0; b < D; ++b) cst[b] = fs.u[b];
+        cst[D + 0] = fs.cexp;
+        cst[D + 1] = fs.pref;
+        cst[D + 2] = fs.eb;
+        cst[D + 3] = fs.hu2;
+        cst[D + 4] = fs.al_g;
+        cst[D + 5] = fs.al_b;
+        cst[D + 6] = fs.gam_b;
+#pragma unroll
+        for (int j = D + 7; j < 4 * NFCV; ++j) cst[j] = T(0);
+#pragma unroll
+        for (int j = 0; j < NFCV; ++j) {
+            V4<T> qv;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
+            FC[j * NFT + f] = qv;
+        }
+    }
+}
+
+// One face and chunk: the face equilibrium (eqs. geq, beq) from the packed
+// constants fc, the inverse of eq. phibar applied to the reconstructed values
+// (gb, bb), the microflux xi_a phi (eq. flux) into (fg, fb), and its moments
+// with the quadrature weights added to sm.
+template <typename T, int D>
+__device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], const T (&w)[VC], const T (&hx)[VC],
+                                          int a, const T (&gb)[VC], const T (&bb)[VC], V4<T>& fg, V4<T>& fb,
+                                          T* sm) {
+    const T fcexp = fc[D + 0], fpref = fc[D + 1], feb = fc[D + 2], fhu2 = fc[D + 3];
+    const T alg = fc[D + 4], alb = fc[D + 5], gmb = fc[D + 6];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        T c2 = T(0), z = -fhu2;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            const T d = xi[v][b] - fc[b];
+            c2 = fma(d, d, c2);
+            z = fma(xi[v][b], fc[b], z);
+        }
+        const T ge = fpref * Num<T>::expo(fcexp * c2);
+        const T be = (hx[v] + feb) * ge;
+        const T gf = fma(alg, gb[v] - ge, ge);
+        const T bfv = fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+        const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
+        fg.v[v] = Fg;
+        fb.v[v] = Fb;
+        const T wg = w[v] * Fg;
+        sm[0] += wg;
+#pragma unroll
+        for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
+        sm[1 + D] = fma(w[v], Fb, sm[1 + D]);
+    }
+}
+
+// phi^n and phi_eq^n of one cell chunk: the deferred last factor of eq.
+// phiupdate applied to the stored phi* (gs, bs) with the cell constants.
+template <typename T, int D>
+__device__ __forceinline__ void own_state(const CellC<T>& own, const T (&xi)[VC][D], const T (&hx)[VC],
+                                          const T (&gs)[VC], const T (&bs)[VC], T (&og)[VC], T (&ob)[VC],
+                                          T (&oge)[VC], T (&obe)[VC]) {
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        T c2 = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const T d = xi[v][a] - own.u[a];
+            c2 = fma(d, d, c2);
+        }
+        oge[v] = own.pref * Num<T>::expo(own.cexp * c2);
+        obe[v] = (hx[v] + own.eb) * oge[v];
+        og[v] = fma(own.fa_g, gs[v], own.fb_g * oge[v]);
+        ob[v] = fma(own.fa_b, bs[v], own.fb_b * obe[v]);
+    }
+}
+
+// Net flux sum_a (F(right face) - F(left face)) / dx_a of the owned cell (local
+// coordinates la) from the staged face fluxes FF[field * NFT + local face].
+template <typename T, int D, typename TL>
+__device__ __forceinline__ void net_flux(const Geo& g, const V4<T>* FF, const int la[3], T (&dFg)[VC], T (&dFb)[VC]) {
+    constexpr int NFT = TL::NFT;
+#pragma unroll
+    for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int fl0 = TL::face_local(a, la[0], la[1], la[2]);
+        const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
+        const V4<T> g0 = FF[0 * NFT + fl0], g1 = FF[0 * NFT + fl1];
+        const V4<T> b0 = FF[1 * NFT + fl0], b1 = FF[1 * NFT + fl1];
+        const T idx = (T)g.idx[a];
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            dFg[v] = fma(idx, g1.v[v] - g0.v[v], dFg[v]);
+            dFb[v] = fma(idx, b1.v[v] - b0.v[v], dFb[v]);
+        }
+    }
+}
+
+// phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
+// (eq. phiupdate, the last factor deferred) of one cell chunk, stored at dst.
+template <typename T, int D>
+__device__ __forceinline__ void store_phi_star(const Geo& g, const T (&xi)[VC][D], const T (&u)[D], T hu2, T um_g,
+                                               T um_b, T usrc, const T (&og)[VC], const T (&ob)[VC],
+                                               const T (&oge)[VC], const T (&obe)[VC], const T (&dFg)[VC],
+                                               const T (&dFb)[VC], T* dst) {
+    T ng[VC], nb[VC];
+    const T dt = (T)g.dt;
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        T z = -hu2;
+#pragma unroll
+        for (int a = 0; a < D; ++a) z = fma(xi[v][a], u[a], z);
+        const T dg = og[v] - oge[v];
+        ng[v] = fma(-dt, dFg[v], fma(um_g, dg, oge[v]));
+        nb[v] = fma(-dt, dFb[v], fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
+    }
+    Chunk<T>::store(dst, ng);
+    Chunk<T>::store(dst + VC, nb);
+}
+
+// A group's partial sums of the faces a thread owns (its left faces, and its
+// right faces at the domain's right end) into dst[a][(grp * (2+D) + m) * nf_a + face].
+template <typename T, int D>
+__device__ __forceinline__ void write_face_sums(const Geo& g, double* const* dst, int grp, const int qa[3],
+                                                const bool own_right[3], const Kahan<T> (&acc)[D][2][2 + D]) {
+    constexpr int NM = 2 + D;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const long long f0 = face_index(g, a, qa);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][0][m].value();
+        if (own_right[a]) {
+            int qr[3] = {qa[0], qa[1], qa[2]};
+            qr[a] += 1;
+            const long long f1 = face_index(g, a, qr);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f1] = acc[a][1][m].value();
+        }
+    }
+}
+
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using SM = Smem<T, D, T0_, T1_, T2_, MODE>;
-    constexpr bool PREP = MODE != MODE_FUSED;      // phibar+ comes from a prepared buffer
-    constexpr bool STORED = MODE == MODE_STORED;   // ... and so do the slopes
+    constexpr bool PREP = mode_source(MODE) != MODE_FUSED;      // phibar+ comes from a prepared buffer
+    constexpr bool STORED = mode_source(MODE) == MODE_STORED;   // ... and so do the slopes
+    constexpr bool FACES = mode_faces(MODE);                     // sweep A stores the face values
+    static_assert(!(SWEEP_B && FACES), "sweep B of the face-store shapes is k_flux");
     constexpr int PN = SM::PN;
     using Q = V4<T>;
     constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
@@ -644,12 +839,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = TL::NT / 32;
-    int tb = tile;
-    int org[3] = {0, 0, 0};
-    org[0] = (tb % g.tiles[0]) * TL::T0;
-    tb /= g.tiles[0];
-    if (D >= 2) { org[1] = (tb % g.tiles[1]) * TL::T1; tb /= g.tiles[1]; }
-    if (D >= 3) org[2] = tb * TL::T2;
+    int org[3];
+    tile_origin<TL, D>(g, tile, org);
     const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
 
     // this thread's cell
@@ -682,7 +873,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         int q[3] = {org[0] + l[0], org[1] + l[1], org[2] + l[2]};
         int refl;
         bool dir;
-        resolve(g, q, refl, dir);
+        resolve<D>(g, q, refl, dir);
         const long long c = cell_index(g, q);
         csrc[k] = (int)c;
         cfl[k] = refl | (dir ? 8 : 0);
@@ -732,37 +923,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             base += __popc(m);
         }
     }
-    if (SWEEP_B) {
-        for (int f = t; f < NFT; f += TL::NT) {
-            const int a = f < TL::NF0 ? 0 : (f < TL::NF0 + TL::NF1 ? 1 : 2);
-            const int r = f - TL::foff(a);
-            const int d0 = TL::T0 + (a == 0), d1 = TL::T1 + (a == 1);
-            int q[3] = {org[0] + r % d0, org[1] + (D >= 2 ? (r / d0) % d1 : 0), org[2] + (D >= 3 ? r / (d0 * d1) : 0)};
-            bool ok = true;
-            for (int b = 0; b < D; ++b) ok = ok && q[b] <= g.n[b] - (b == a ? 0 : 1);
-            if (!ok) continue;
-            const FaceC<T>& fs = bf.facec[a][face_index(g, a, q)];
-            T cst[4 * NFCV];
-#pragma unroll
-            for (int b = 0; b < D; ++b) cst[b] = fs.u[b];
-            cst[D + 0] = fs.cexp;
-            cst[D + 1] = fs.pref;
-            cst[D + 2] = fs.eb;
-            cst[D + 3] = fs.hu2;
-            cst[D + 4] = fs.al_g;
-            cst[D + 5] = fs.al_b;
-            cst[D + 6] = fs.gam_b;
-#pragma unroll
-            for (int j = D + 7; j < 4 * NFCV; ++j) cst[j] = T(0);
-#pragma unroll
-            for (int j = 0; j < NFCV; ++j) {
-                Q qv;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
-                FC[j * NFT + f] = qv;
-            }
-        }
-    }
+    if (SWEEP_B) stage_face_consts<T, D, TL>(g, bf, org, FC);
     // constants of the owned cell for the distribution update
     T um_g = T(0), um_b = T(0), usrc = T(0);
     CellC<T> own;       // all of them (prepared shapes: phase 4 recomputes phi and phi_eq)
@@ -1058,6 +1219,13 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     T sm[NM];
 #pragma unroll
                     for (int m = 0; m < NM; ++m) sm[m] = T(0);
+                    if (FACES) {   // sweep A computes each face once: keep it for k_flux
+                        int qf[3] = {qa[0], qa[1], qa[2]};
+                        qf[a] += side;
+                        T* const dst = bf.face[a] + face_addr(g, a, face_index(g, a, qf), vt);
+                        Chunk<T>::store(dst, gb);
+                        Chunk<T>::store(dst + VC, bb);
+                    }
                     if (!SWEEP_B) {
                         // face conserved variables (eqs. rhobar-rhoEbar, a = 0)
 #pragma unroll
@@ -1077,31 +1245,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 #pragma unroll
                             for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
                         }
-                        const T fcexp = fcst[D + 0], fpref = fcst[D + 1], feb = fcst[D + 2], fhu2 = fcst[D + 3];
-                        const T alg = fcst[D + 4], alb = fcst[D + 5], gmb = fcst[D + 6];
                         Q fg, fb;
-#pragma unroll
-                        for (int v = 0; v < VC; ++v) {
-                            T c2 = T(0), z = -fhu2;
-#pragma unroll
-                            for (int b = 0; b < D; ++b) {
-                                const T d = xi[v][b] - fcst[b];
-                                c2 = fma(d, d, c2);
-                                z = fma(xi[v][b], fcst[b], z);
-                            }
-                            const T ge = fpref * Num<T>::expo(fcexp * c2);
-                            const T be = (hx[v] + feb) * ge;
-                            const T gf = fma(alg, gb[v] - ge, ge);
-                            const T bfv = fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
-                            const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
-                            fg.v[v] = Fg;
-                            fb.v[v] = Fb;
-                            const T wg = w[v] * Fg;
-                            sm[0] += wg;
-#pragma unroll
-                            for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
-                            sm[1 + D] = fma(w[v], Fb, sm[1 + D]);
-                        }
+                        face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, fg, fb, sm);
                         FF[0 * NFT + fl] = fg;
                         FF[1 * NFT + fl] = fb;
                     }
@@ -1118,21 +1263,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             // ---- phase 4: phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
             if (valid) {
                 T dFg[VC], dFb[VC];
-#pragma unroll
-                for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const int fl0 = TL::face_local(a, la[0], la[1], la[2]);
-                    const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
-                    const Q g0 = FF[0 * NFT + fl0], g1 = FF[0 * NFT + fl1];
-                    const Q b0 = FF[1 * NFT + fl0], b1 = FF[1 * NFT + fl1];
-                    const T idx = (T)g.idx[a];
-#pragma unroll
-                    for (int v = 0; v < VC; ++v) {
-                        dFg[v] = fma(idx, g1.v[v] - g0.v[v], dFg[v]);
-                        dFb[v] = fma(idx, b1.v[v] - b0.v[v], dFb[v]);
-                    }
-                }
+                net_flux<T, D, TL>(g, FF, la, dFg, dFb);
                 T u[D], hu2;
                 if (PREP) {
 #pragma unroll
@@ -1143,60 +1274,21 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     const size_t ad0 = phi_addr(g, cell_index(g, qa), vt * VC, 0);
                     Chunk<T>::load(bf.phi_in + ad0, gs);
                     Chunk<T>::load(bf.phi_in + ad0 + VC, bs);
-#pragma unroll
-                    for (int v = 0; v < VC; ++v) {
-                        T c2 = T(0);
-#pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const T d = xi[v][a] - u[a];
-                            c2 = fma(d, d, c2);
-                        }
-                        oge[v] = own.pref * Num<T>::expo(own.cexp * c2);
-                        obe[v] = (hx[v] + own.eb) * oge[v];
-                        og[v] = fma(own.fa_g, gs[v], own.fb_g * oge[v]);
-                        ob[v] = fma(own.fa_b, bs[v], own.fb_b * obe[v]);
-                    }
+                    own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
                 } else {
 #pragma unroll
                     for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
                     hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
                 }
-                T ng[VC], nb[VC];
-                const T dt = (T)g.dt;
-#pragma unroll
-                for (int v = 0; v < VC; ++v) {
-                    T z = -hu2;
-#pragma unroll
-                    for (int a = 0; a < D; ++a) z = fma(xi[v][a], u[a], z);
-                    const T dg = og[v] - oge[v];
-                    ng[v] = fma(-dt, dFg[v], fma(um_g, dg, oge[v]));
-                    nb[v] = fma(-dt, dFb[v], fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
-                }
-                const size_t ad = phi_addr(g, cell_index(g, qa), vt * VC, 0);
-                Chunk<T>::store(bf.phi_out + ad, ng);
-                Chunk<T>::store(bf.phi_out + ad + VC, nb);
+                store_phi_star<T, D>(g, xi, u, hu2, um_g, um_b, usrc, og, ob, oge, obe, dFg, dFb,
+                                     bf.phi_out + phi_addr(g, cell_index(g, qa), vt * VC, 0));
             }
         }
         __syncthreads();
     }
 
     // ---- epilogue: this group's partial face sums
-    if (valid) {
-        double* const* dst = SWEEP_B ? bf.mf : bf.wf;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const long long f0 = face_index(g, a, qa);
-#pragma unroll
-            for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][0][m].value();
-            if (own_right[a]) {
-                int qr[3] = {qa[0], qa[1], qa[2]};
-                qr[a] += 1;
-                const long long f1 = face_index(g, a, qr);
-#pragma unroll
-                for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f1] = acc[a][1][m].value();
-            }
-        }
-    }
+    if (valid) write_face_sums<T, D>(g, SWEEP_B ? bf.mf : bf.wf, grp, qa, own_right, acc);
 }
 
 // CTAs per SM that the shared memory of a sweep allows (at least 1, at most 4);
@@ -1219,6 +1311,179 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
     k_sweep(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(32) unsigned char smem[];
     sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+}
+
+// ---- sweep B of the face-store shapes
+//
+// One CTA per (tile, velocity group), one thread per owned cell, the tiling
+// of the sweeps.  Per chunk each thread forms the flux of its left faces (and
+// of its right faces at the tile's right end) from the face values sweep A
+// stored, stages it in shared memory and, after a barrier, forms phi* of its
+// cell from the net flux.  A face's moments are summed by its owner (the cell
+// on its right; the last cell for the domain's right end), in chunk order.
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+struct FluxSmem {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    // cells on a tile face normal to axis a, and where their sums start
+    __host__ __device__ static constexpr int plane(int a) { return TL::NT / TL::tdim(a); }
+    __host__ __device__ static constexpr int poff(int a) {
+        return (a > 0 ? plane(0) : 0) + (a > 1 ? plane(1) : 0) + (a > 2 ? plane(2) : 0);
+    }
+    static constexpr int NPL = poff(D);                       // all planes
+    static_assert(NPL == (D >= 1 ? TL::NT / TL::T0 : 0) + (D >= 2 ? TL::NT / TL::T1 : 0) + (D >= 3 ? TL::NT / TL::T2 : 0),
+                  "one slot per cell of each tile face");
+    static constexpr size_t nV4 = (size_t)2 * TL::NFT + (size_t)FacePack<D>::NV * TL::NFT;
+    static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
+};
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+__device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
+    using TL = Tile<D, T0_, T1_, T2_>;
+    using FS = FluxSmem<T, D, T0_, T1_, T2_>;
+    using Q = V4<T>;
+    constexpr int NM = 2 + D, NFT = TL::NFT, NFCV = FacePack<D>::NV;
+    Q* const FF = reinterpret_cast<Q*>(smem);     // [2][NFT] face fluxes of the chunk
+    Q* const FC = FF + 2 * NFT;                   // [NFCV][NFT] packed face constants
+    // running sums of the faces at the domain's right end, [NM][plane cell] per axis
+    Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + FS::nV4 * sizeof(Q));
+    const int t = threadIdx.x;
+    int org[3];
+    tile_origin<TL, D>(g, tile, org);
+    const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
+    const int la[3] = {t % TL::T0, D >= 2 ? (t / TL::T0) % TL::T1 : 0, D >= 3 ? t / (TL::T0 * TL::T1) : 0};
+    const int qa[3] = {org[0] + la[0], org[1] + la[1], org[2] + la[2]};
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
+    stage_face_consts<T, D, TL>(g, bf, org, FC);
+    for (int k = t; k < FS::NPL * NM; k += TL::NT) RS[k].zero();
+    CellC<T> own;
+    if (valid) own = bf.cellc[cell_index(g, qa)];
+    const size_t cell_ad = valid ? phi_addr(g, cell_index(g, qa), 0, 0) : 0;
+    const size_t chunk_stride = (size_t)g.Nc * (2 * VC);
+    bool right[3] = {false, false, false}, own_right[3] = {false, false, false};
+    int pl[3] = {0, 0, 0};   // this cell's slot in the right-end sums of axis a
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        own_right[a] = valid && qa[a] == g.n[a] - 1;
+        right[a] = valid && (la[a] == TL::tdim(a) - 1 || own_right[a]);
+        const int p = a == 0 ? la[1] + TL::T1 * la[2] : (a == 1 ? la[0] + TL::T0 * la[2] : la[0] + TL::T0 * la[1]);
+        pl[a] = FS::poff(a) * NM + p;
+    }
+    Kahan<T> acc[D][NM];      // the left faces
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[a][m].zero();
+    __syncthreads();
+
+    for (int vt = vt0; vt < vt1; ++vt) {
+        T xi[VC][D], w[VC], hx[VC];
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const Q* rec = reinterpret_cast<const Q*>(bf.vel + (size_t)(vt * VC + v) * 8);
+            const Q r0 = rec[0];
+#pragma unroll
+            for (int a = 0; a < D; ++a) xi[v][a] = r0.v[a];
+            w[v] = r0.v[3];
+            hx[v] = rec[1].v[0];
+        }
+        const size_t ad = cell_ad + (size_t)vt * chunk_stride;
+        T gs[VC], bs[VC];
+        if (valid) {
+            Chunk<T>::load(bf.phi_in + ad, gs);      // needed after the barrier; issued early
+            Chunk<T>::load(bf.phi_in + ad + VC, bs);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 1 && !right[a]) continue;
+                    int qf[3] = {qa[0], qa[1], qa[2]};
+                    qf[a] += side;
+                    const T* src = bf.face[a] + face_addr(g, a, face_index(g, a, qf), vt);
+                    T gb[VC], bb[VC];
+                    Chunk<T>::load(src, gb);
+                    Chunk<T>::load(src + VC, bb);
+                    const int fl = TL::face_local(a, la[0] + (a == 0 ? side : 0), la[1] + (a == 1 ? side : 0),
+                                                  la[2] + (a == 2 ? side : 0));
+                    T fcst[4 * NFCV];
+#pragma unroll
+                    for (int j = 0; j < NFCV; ++j) {
+                        const Q qv = FC[j * NFT + fl];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
+                    }
+                    T sm[NM];
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) sm[m] = T(0);
+                    Q fg, fb;
+                    face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, fg, fb, sm);
+                    FF[0 * NFT + fl] = fg;
+                    FF[1 * NFT + fl] = fb;
+                    if (side == 0) {
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
+                    } else if (own_right[a]) {
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            Kahan<T> k = RS[pl[a] + m * FS::plane(a)];
+                            k.add(sm[m]);
+                            RS[pl[a] + m * FS::plane(a)] = k;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            T dFg[VC], dFb[VC];
+            net_flux<T, D, TL>(g, FF, la, dFg, dFb);
+            T og[VC], ob[VC], oge[VC], obe[VC];
+            own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
+            T u[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = own.u[a];
+            store_phi_star<T, D>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
+                                 bf.phi_out + ad);
+        }
+        __syncthreads();
+    }
+    if (valid) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const long long f0 = face_index(g, a, qa);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][m].value();
+            if (own_right[a]) {
+                int qr[3] = {qa[0], qa[1], qa[2]};
+                qr[a] += 1;
+                const long long f1 = face_index(g, a, qr);
+#pragma unroll
+                for (int m = 0; m < NM; ++m)
+                    bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + f1] = RS[pl[a] + m * FS::plane(a)].value();
+            }
+        }
+    }
+}
+
+// CTAs per SM for k_flux: shared memory and threads, keeping >= 80 registers.
+template <typename T, int D, int T0_, int T1_, int T2_>
+struct FluxOcc {
+    static constexpr size_t per = FluxSmem<T, D, T0_, T1_, T2_>::bytes + 1024;
+    static constexpr int by_smem = (int)((228 * 1024) / per);
+    static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 80);
+    static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
+    static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
+    static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
+};
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
+    k_flux(const Inst<T>* __restrict__ in, int cur) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    flux_body<T, D, T0_, T1_, T2_>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list

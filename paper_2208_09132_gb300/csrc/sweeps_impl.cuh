@@ -13,11 +13,22 @@ constexpr int kSmallBlock = 64;
 // shapes (MODE_PREP) form phibar+ of every point once per step (k_prep);
 // stored shapes (MODE_STORED) form phibar+ and the slopes (k_shslope); the
 // sweeps of both load what was formed instead of recomputing it on the halo.
+// Face-store shapes (MODE_FACES bit) have sweep A keep the reconstructed
+// face values and run k_flux as sweep B.
 template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED>
 struct Shape {
     using SM = Smem<T, D, TX, TY, TZ, MODE>;
+    using FS = FluxSmem<T, D, TX, TY, TZ>;
     using TL = Tile<D, TX, TY, TZ>;
     static constexpr int mode = MODE;
+    static constexpr int SRC = mode_source(MODE);
+    static constexpr bool FACES = mode_faces(MODE);
+
+    // dynamic shared memory of the larger of the two sweeps
+    static size_t smem_bytes() {
+        const size_t b = FACES ? FS::bytes : SM::bytes(true);
+        return SM::bytes(false) > b ? SM::bytes(false) : b;
+    }
 
     static cudaError_t configure() {
         static bool done = false;
@@ -26,10 +37,16 @@ struct Shape {
         if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false, MODE>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
             return e;
-        if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
-            return e;
-        if constexpr (MODE == MODE_STORED) {
+        if constexpr (FACES) {
+            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)FS::bytes)))
+                return e;
+        } else {
+            if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, MODE>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
+                return e;
+        }
+        if constexpr (SRC == MODE_STORED) {
             if ((e = cudaFuncSetAttribute(k_shslope<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shslope_smem_bytes<T, D, TX, TY, TZ>())))
                 return e;
@@ -51,11 +68,11 @@ struct Shape {
         if (e) return e;
         const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
         if (ev) cudaEventRecord(ev[0], s);
-        if constexpr (MODE == MODE_PREP) {
+        if constexpr (SRC == MODE_PREP) {
             constexpr int kChunks = 8;
             const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
             k_prep<T, D><<<pg, 128, 0, s>>>(in, cur, kChunks);
-        } else if constexpr (MODE == MODE_STORED) {
+        } else if constexpr (SRC == MODE_STORED) {
             k_shslope<T, D, TX, TY, TZ><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ>(), s>>>(in, cur);
         }
         k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
@@ -65,7 +82,8 @@ struct Shape {
             k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
         }
         if (ev) cudaEventRecord(ev[2], s);
-        k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
+        if constexpr (FACES) k_flux<T, D, TX, TY, TZ><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
+        else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[3], s);
         k_wupdate<T, D><<<(unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock), kSmallBlock, 0, s>>>(in, cur);
         if (ev) cudaEventRecord(ev[4], s);
@@ -121,7 +139,7 @@ struct ShapeList<H, R...> {
         return id == 0 ? H::sweep_batch(B, it, n, in, cur, s) : Rest::template sweep_batch<T>(id - 1, B, it, n, in, cur, s);
     }
     static TileShape shape(int id) { return id == 0 ? H::shape() : Rest::shape(id - 1); }
-    static size_t smem(int id) { return id == 0 ? H::SM::bytes(true) : Rest::smem(id - 1); }
+    static size_t smem(int id) { return id == 0 ? H::smem_bytes() : Rest::smem(id - 1); }
     static int mode(int id) { return id == 0 ? H::mode : Rest::mode(id - 1); }
 };
 

@@ -64,7 +64,7 @@ def candidates(cfg, precision, context="alone"):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
         if context != "alone" and mode != 0:
             continue                      # only fused shapes are batched
-        if mode == 2 and dirichlet:
+        if mode & 3 == 2 and dirichlet:
             continue                      # stored slopes: periodic / specular only
         tiles.append(t)
     return [(t, g) for t in tiles for g in groups]
@@ -125,9 +125,17 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
     key = size_key(cfg, precision, context)
     if key in d and not refresh:
         return tuple(d[key]["choice"])
+    import torch
+
     results = []
     for tile, groups in candidates(cfg, precision, context):
-        results.append((_time(cfg, precision, tile, groups, context, steps, device), tile, groups))
+        try:
+            results.append((_time(cfg, precision, tile, groups, context, steps, device), tile, groups))
+        except torch.OutOfMemoryError:     # this shape's extra buffers do not fit beside the state
+            pass
+        torch.cuda.empty_cache()
+    if not results:
+        raise RuntimeError(f"no tile shape fits on {device} for {key}")
     results.sort()
     best = results[0]
     d = _load_cache(path)

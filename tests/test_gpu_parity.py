@@ -200,7 +200,7 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     ref = o.moments()
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
-        if cdugks.tile_shape(precision, cfg["dim"], t)[1] == 2 and dirichlet:
+        if cdugks.tile_shape(precision, cfg["dim"], t)[1] & 3 == 2 and dirichlet:
             continue      # stored-slope shapes take periodic and specular boundaries only
         s = cdugks.Solver(cfg, precision=precision, tile_id=t, velocity_groups=2)
         s.init(f)
