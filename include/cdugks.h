@@ -204,7 +204,8 @@ CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
  * Bit 2 (value 4, face store): sweep A keeps the reconstructed phibar of
  * every face and velocity (about D more state-size buffers) and sweep B only
  * forms the fluxes from them instead of reconstructing again.
- * Every mode but 0 must be selected before cdugks_bind and is not batched. */
+ * Every mode but 0 must be selected before cdugks_bind; modes with bits 0-1
+ * nonzero are not batched (modes 0 and 4 are). */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 
 /* ---------------------------------------------------------------- batches

@@ -865,7 +865,7 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
         if (!m || !m->bound || !m->initialised)
             return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
         if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
-        if (tile_mode(m->prec, m->g.D, m->g.tile_id) != cdg::MODE_FUSED)
+        if (cdg::mode_source(tile_mode(m->prec, m->g.D, m->g.tile_id)) != cdg::MODE_FUSED)
             return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
         for (int j = 0; j < i; ++j)
             if (members[j] == m) return fail(CDUGKS_ERR_INVALID, "a member appears twice");

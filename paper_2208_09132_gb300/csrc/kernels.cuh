@@ -1316,11 +1316,13 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 // ---- sweep B of the face-store shapes
 //
 // One CTA per (tile, velocity group), one thread per owned cell, the tiling
-// of the sweeps.  Per chunk each thread forms the flux of its left faces (and
-// of its right faces at the tile's right end) from the face values sweep A
-// stored, stages it in shared memory and, after a barrier, forms phi* of its
-// cell from the net flux.  A face's moments are summed by its owner (the cell
-// on its right; the last cell for the domain's right end), in chunk order.
+// of the sweeps.  Per chunk each thread reads the stored values of both faces
+// of its cell along every axis, forms their fluxes and phi* of its cell from
+// the net flux.  A face shared by two cells is formed by both, from the same
+// values with the same arithmetic, so both see the same flux; there is no
+// exchange between threads and no barrier inside the chunk loop.  A face's
+// moments are summed by its owner (the cell on its right; the last cell for
+// the domain's right end), in chunk order.
 
 template <typename T, int D, int T0_, int T1_, int T2_>
 struct FluxSmem {
@@ -1330,10 +1332,10 @@ struct FluxSmem {
     __host__ __device__ static constexpr int poff(int a) {
         return (a > 0 ? plane(0) : 0) + (a > 1 ? plane(1) : 0) + (a > 2 ? plane(2) : 0);
     }
-    static constexpr int NPL = poff(D);                       // all planes
+    static constexpr int NPL = poff(D);
     static_assert(NPL == (D >= 1 ? TL::NT / TL::T0 : 0) + (D >= 2 ? TL::NT / TL::T1 : 0) + (D >= 3 ? TL::NT / TL::T2 : 0),
                   "one slot per cell of each tile face");
-    static constexpr size_t nV4 = (size_t)2 * TL::NFT + (size_t)FacePack<D>::NV * TL::NFT;
+    static constexpr size_t nV4 = (size_t)FacePack<D>::NV * TL::NFT;
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
 
@@ -1343,8 +1345,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     using FS = FluxSmem<T, D, T0_, T1_, T2_>;
     using Q = V4<T>;
     constexpr int NM = 2 + D, NFT = TL::NFT, NFCV = FacePack<D>::NV;
-    Q* const FF = reinterpret_cast<Q*>(smem);     // [2][NFT] face fluxes of the chunk
-    Q* const FC = FF + 2 * NFT;                   // [NFCV][NFT] packed face constants
+    Q* const FC = reinterpret_cast<Q*>(smem);     // [NFCV][NFT] packed face constants
     // running sums of the faces at the domain's right end, [NM][plane cell] per axis
     Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + FS::nV4 * sizeof(Q));
     const int t = threadIdx.x;
@@ -1358,25 +1359,33 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
     stage_face_consts<T, D, TL>(g, bf, org, FC);
     for (int k = t; k < FS::NPL * NM; k += TL::NT) RS[k].zero();
-    CellC<T> own;
-    if (valid) own = bf.cellc[cell_index(g, qa)];
-    const size_t cell_ad = valid ? phi_addr(g, cell_index(g, qa), 0, 0) : 0;
+    __syncthreads();
+    if (!valid) return;          // no barrier below
+
+    const CellC<T> own = bf.cellc[cell_index(g, qa)];
+    const size_t cell_ad = phi_addr(g, cell_index(g, qa), 0, 0);
     const size_t chunk_stride = (size_t)g.Nc * (2 * VC);
-    bool right[3] = {false, false, false}, own_right[3] = {false, false, false};
-    int pl[3] = {0, 0, 0};   // this cell's slot in the right-end sums of axis a
+    bool own_right[3] = {false, false, false};
+    int pl[3] = {0, 0, 0};       // this cell's slot in the right-end sums of axis a
+    long long ff[3][2];          // global faces: left, right
+    int fl[3][2];                // local faces
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        own_right[a] = valid && qa[a] == g.n[a] - 1;
-        right[a] = valid && (la[a] == TL::tdim(a) - 1 || own_right[a]);
+        own_right[a] = qa[a] == g.n[a] - 1;
         const int p = a == 0 ? la[1] + TL::T1 * la[2] : (a == 1 ? la[0] + TL::T0 * la[2] : la[0] + TL::T0 * la[1]);
         pl[a] = FS::poff(a) * NM + p;
+        int qr[3] = {qa[0], qa[1], qa[2]};
+        qr[a] += 1;
+        ff[a][0] = face_index(g, a, qa);
+        ff[a][1] = face_index(g, a, qr);
+        fl[a][0] = TL::face_local(a, la[0], la[1], la[2]);
+        fl[a][1] = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
     }
-    Kahan<T> acc[D][NM];      // the left faces
+    Kahan<T> acc[D][NM];         // the left faces
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int m = 0; m < NM; ++m) acc[a][m].zero();
-    __syncthreads();
 
     for (int vt = vt0; vt < vt1; ++vt) {
         T xi[VC][D], w[VC], hx[VC];
@@ -1391,78 +1400,66 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
         }
         const size_t ad = cell_ad + (size_t)vt * chunk_stride;
         T gs[VC], bs[VC];
-        if (valid) {
-            Chunk<T>::load(bf.phi_in + ad, gs);      // needed after the barrier; issued early
-            Chunk<T>::load(bf.phi_in + ad + VC, bs);
+        Chunk<T>::load(bf.phi_in + ad, gs);
+        Chunk<T>::load(bf.phi_in + ad + VC, bs);
+        T dFg[VC], dFb[VC];
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
+        for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    if (side == 1 && !right[a]) continue;
-                    int qf[3] = {qa[0], qa[1], qa[2]};
-                    qf[a] += side;
-                    const T* src = bf.face[a] + face_addr(g, a, face_index(g, a, qf), vt);
-                    T gb[VC], bb[VC];
-                    Chunk<T>::load(src, gb);
-                    Chunk<T>::load(src + VC, bb);
-                    const int fl = TL::face_local(a, la[0] + (a == 0 ? side : 0), la[1] + (a == 1 ? side : 0),
-                                                  la[2] + (a == 2 ? side : 0));
-                    T fcst[4 * NFCV];
+        for (int a = 0; a < D; ++a) {
+            Q F[2][2];           // [side][g|b]
 #pragma unroll
-                    for (int j = 0; j < NFCV; ++j) {
-                        const Q qv = FC[j * NFT + fl];
+            for (int side = 0; side < 2; ++side) {
+                const T* src = bf.face[a] + face_addr(g, a, ff[a][side], vt);
+                T gb[VC], bb[VC];
+                Chunk<T>::load(src, gb);
+                Chunk<T>::load(src + VC, bb);
+                T fcst[4 * NFCV];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
-                    }
-                    T sm[NM];
+                for (int j = 0; j < NFCV; ++j) {
+                    const Q qv = FC[j * NFT + fl[a][side]];
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) sm[m] = T(0);
-                    Q fg, fb;
-                    face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, fg, fb, sm);
-                    FF[0 * NFT + fl] = fg;
-                    FF[1 * NFT + fl] = fb;
-                    if (side == 0) {
+                    for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
+                }
+                T sm[NM];
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
-                    } else if (own_right[a]) {
+                for (int m = 0; m < NM; ++m) sm[m] = T(0);
+                face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm);
+                if (side == 0) {
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) {
-                            Kahan<T> k = RS[pl[a] + m * FS::plane(a)];
-                            k.add(sm[m]);
-                            RS[pl[a] + m * FS::plane(a)] = k;
-                        }
+                    for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
+                } else if (own_right[a]) {
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        Kahan<T> k = RS[pl[a] + m * FS::plane(a)];
+                        k.add(sm[m]);
+                        RS[pl[a] + m * FS::plane(a)] = k;
                     }
                 }
             }
-        }
-        __syncthreads();
-        if (valid) {
-            T dFg[VC], dFb[VC];
-            net_flux<T, D, TL>(g, FF, la, dFg, dFb);
-            T og[VC], ob[VC], oge[VC], obe[VC];
-            own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
-            T u[D];
+            const T idx = (T)g.idx[a];
 #pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = own.u[a];
-            store_phi_star<T, D>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
-                                 bf.phi_out + ad);
-        }
-        __syncthreads();
-    }
-    if (valid) {
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const long long f0 = face_index(g, a, qa);
-#pragma unroll
-            for (int m = 0; m < NM; ++m) bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][m].value();
-            if (own_right[a]) {
-                int qr[3] = {qa[0], qa[1], qa[2]};
-                qr[a] += 1;
-                const long long f1 = face_index(g, a, qr);
-#pragma unroll
-                for (int m = 0; m < NM; ++m)
-                    bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + f1] = RS[pl[a] + m * FS::plane(a)].value();
+            for (int v = 0; v < VC; ++v) {
+                dFg[v] = fma(idx, F[1][0].v[v] - F[0][0].v[v], dFg[v]);
+                dFb[v] = fma(idx, F[1][1].v[v] - F[0][1].v[v], dFb[v]);
             }
+        }
+        T og[VC], ob[VC], oge[VC], obe[VC];
+        own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
+        T u[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a] = own.u[a];
+        store_phi_star<T, D>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
+                             bf.phi_out + ad);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a][0]] = acc[a][m].value();
+        if (own_right[a]) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a][1]] = RS[pl[a] + m * FS::plane(a)].value();
         }
     }
 }
@@ -1473,7 +1470,7 @@ struct FluxOcc {
     static constexpr size_t per = FluxSmem<T, D, T0_, T1_, T2_>::bytes + 1024;
     static constexpr int by_smem = (int)((228 * 1024) / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
-    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 80);
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 128);
     static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
     static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
     static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
@@ -1490,13 +1487,22 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_
 // of items, one per CTA.  The current parity of each instance lives on the
 // device and the W-update kernel flips it, so a captured graph replays.
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE_FUSED>::value))
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE = MODE_FUSED>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
     k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(32) unsigned char smem[];
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE_FUSED>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+}
+
+template <typename T, int D, int T0_, int T1_, int T2_>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
+    k_flux_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Item it = items[blockIdx.x];
+    const Inst<T>& in = insts[it.inst];
+    flux_body<T, D, T0_, T1_, T2_>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
 // Face constants from the group-summed face W (fixed summation order).

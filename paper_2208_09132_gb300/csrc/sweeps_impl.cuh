@@ -51,13 +51,19 @@ struct Shape {
                                           (int)shslope_smem_bytes<T, D, TX, TY, TZ>())))
                 return e;
         }
-        if constexpr (MODE == MODE_FUSED) {
-            if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false>,
+        if constexpr (SRC == MODE_FUSED) {
+            if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false, MODE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
                 return e;
-            if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
-                return e;
+            if constexpr (FACES) {
+                if ((e = cudaFuncSetAttribute(k_flux_batch<T, D, TX, TY, TZ>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::bytes)))
+                    return e;
+            } else {
+                if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, true, MODE>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
+                    return e;
+            }
         }
         done = true;
         return cudaSuccess;
@@ -92,14 +98,15 @@ struct Shape {
 
     static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
                                    cudaStream_t s) {
-        if constexpr (MODE != MODE_FUSED) {
+        if constexpr (SRC != MODE_FUSED) {
             return cudaErrorNotSupported;
         } else {
             cudaError_t e = configure();
             if (e) return e;
             if (n <= 0) return cudaSuccess;
-            if (B) k_sweep_batch<T, D, TX, TY, TZ, true><<<n, TL::NT, SM::bytes(true), s>>>(items, insts, cur);
-            else k_sweep_batch<T, D, TX, TY, TZ, false><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
+            if (!B) k_sweep_batch<T, D, TX, TY, TZ, false, MODE><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
+            else if constexpr (FACES) k_flux_batch<T, D, TX, TY, TZ><<<n, TL::NT, FS::bytes, s>>>(items, insts, cur);
+            else k_sweep_batch<T, D, TX, TY, TZ, true, MODE><<<n, TL::NT, SM::bytes(true), s>>>(items, insts, cur);
             return cudaGetLastError();
         }
     }

@@ -62,8 +62,8 @@ def candidates(cfg, precision, context="alone"):
     tiles = []
     for t in range(nt):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
-        if context != "alone" and mode != 0:
-            continue                      # only fused shapes are batched
+        if context != "alone" and mode & 3 != 0:
+            continue                      # only shapes that form phibar+ themselves are batched
         if mode & 3 == 2 and dirichlet:
             continue                      # stored slopes: periodic / specular only
         tiles.append(t)
