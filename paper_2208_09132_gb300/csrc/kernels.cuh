@@ -149,23 +149,43 @@ struct Macro {
     double rho, u[3], T, RT, tg, tb, itbg;
 };
 
+// The FP64 constants below are written with explicitly rounded operations
+// (no multiply-add contraction), so every kernel that forms them -- single
+// instance or batched, any inlining context -- gets the same bits.
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// x^omega for the viscosity law mu = mu_ref (T/T_ref)^omega: the hard-sphere
+// (1/2) and Maxwell (1) exponents without the general power function, whose
+// FP64 cost dominates the per-cell constants.
+__device__ __forceinline__ double visc_power(double x, double omega) {
+    return omega == 0.5 ? __dsqrt_rn(x) : (omega == 1.0 ? x : pow(x, omega));
+}
+// x^(-D/2): the normalisation of a D-dimensional Maxwellian.
+__device__ __forceinline__ double gauss_norm(double x, int D) {
+    return D == 2 ? ddiv(1.0, x) : (D == 1 ? ddiv(1.0, __dsqrt_rn(x)) : ddiv(1.0, dmul(x, __dsqrt_rn(x))));
+}
+
 __device__ __forceinline__ Macro macro_of(const Geo& g, const double* W) {
     Macro m;
     m.rho = W[0];
+    const double irho = ddiv(1.0, m.rho);
     double u2 = 0.0;
     for (int a = 0; a < 3; ++a) m.u[a] = 0.0;
     for (int a = 0; a < g.D; ++a) {
-        m.u[a] = W[1 + a] / m.rho;
-        u2 += m.u[a] * m.u[a];
+        m.u[a] = dmul(W[1 + a], irho);
+        u2 = dadd(u2, dmul(m.u[a], m.u[a]));
     }
-    double E = W[1 + g.D] / m.rho;
-    double gam = (g.K + 5.0) / (g.K + 3.0);
-    m.T = (gam - 1.0) / g.R * (E - 0.5 * u2);
-    m.RT = g.R * m.T;
-    double mu = g.mu_ref * pow(m.T / g.T_ref, g.omega);
-    m.tg = mu / (m.rho * m.RT);
-    m.tb = m.tg / g.Pr;
-    m.itbg = 1.0 / m.tb - 1.0 / m.tg;
+    const double E = dmul(W[1 + g.D], irho);
+    // T = (gamma - 1)/R (E - u^2/2), gamma = (K+5)/(K+3)
+    m.T = dmul(ddiv(2.0, dmul(dadd(g.K, 3.0), g.R)), dsub(E, dmul(0.5, u2)));
+    m.RT = dmul(g.R, m.T);
+    const double mu = dmul(g.mu_ref, visc_power(ddiv(m.T, g.T_ref), g.omega));
+    m.tg = ddiv(mu, dmul(m.rho, m.RT));
+    m.tb = ddiv(m.tg, g.Pr);
+    m.itbg = ddiv(dsub(g.Pr, 1.0), m.tg);      // 1/tau_b - 1/tau_g
     return m;
 }
 
@@ -174,12 +194,12 @@ __device__ __forceinline__ void eq_consts(const Geo& g, const Macro& m, T u[3], 
     double u2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         u[a] = (T)m.u[a];
-        u2 += m.u[a] * m.u[a];
+        u2 = dadd(u2, dmul(m.u[a], m.u[a]));
     }
-    cexp = (T)(-Num<T>::cexp_scale() / (2.0 * m.RT));
-    pref = (T)(m.rho * pow(2.0 * 3.14159265358979323846 * m.RT, -0.5 * g.D));
-    eb = (T)(0.5 * (3.0 - g.D + g.K) * m.RT);
-    hu2 = (T)(0.5 * u2);
+    cexp = (T)ddiv(-0.5 * Num<T>::cexp_scale(), m.RT);
+    pref = (T)dmul(m.rho, gauss_norm(dmul(2.0 * 3.14159265358979323846, m.RT), g.D));
+    eb = (T)dmul(0.5 * (3.0 - g.D + g.K), m.RT);
+    hu2 = (T)dmul(0.5, u2);
 }
 
 template <typename T>
@@ -187,16 +207,20 @@ __device__ __forceinline__ void make_cell(const Geo& g, const double* W, CellC<T
     Macro m = macro_of(g, W);
     eq_consts<T>(g, m, c.u, c.cexp, c.pref, c.eb, c.hu2);
     const double dt = g.dt, h = g.h;
-    c.fa_g = (T)(2.0 * m.tg / (2.0 * m.tg + dt));
-    c.fb_g = (T)(dt / (2.0 * m.tg + dt));
-    c.fa_b = (T)(2.0 * m.tb / (2.0 * m.tb + dt));
-    c.fb_b = (T)(dt / (2.0 * m.tb + dt));
-    c.sa_g = (T)(1.0 - h / (2.0 * m.tg));
-    c.sa_b = (T)(1.0 - h / (2.0 * m.tb));
-    c.ssrc = (T)(0.5 * h * m.itbg);
-    c.um_g = (T)(1.0 - dt / (2.0 * m.tg));
-    c.um_b = (T)(1.0 - dt / (2.0 * m.tb));
-    c.usrc = (T)(dt * m.itbg);
+    const double itg = ddiv(1.0, m.tg), itb = dmul(g.Pr, itg);
+    const double tg2 = dmul(2.0, m.tg), tb2 = dmul(2.0, m.tb);
+    const double rg = ddiv(1.0, dadd(tg2, dt)), rb = ddiv(1.0, dadd(tb2, dt));
+    const double hh = dmul(0.5, h), hdt = dmul(0.5, dt);
+    c.fa_g = (T)dmul(tg2, rg);
+    c.fb_g = (T)dmul(dt, rg);
+    c.fa_b = (T)dmul(tb2, rb);
+    c.fb_b = (T)dmul(dt, rb);
+    c.sa_g = (T)dsub(1.0, dmul(hh, itg));
+    c.sa_b = (T)dsub(1.0, dmul(hh, itb));
+    c.ssrc = (T)dmul(hh, m.itbg);
+    c.um_g = (T)dsub(1.0, dmul(hdt, itg));
+    c.um_b = (T)dsub(1.0, dmul(hdt, itb));
+    c.usrc = (T)dmul(dt, m.itbg);
 }
 
 template <typename T>
@@ -204,9 +228,11 @@ __device__ __forceinline__ void make_face(const Geo& g, const double* W, FaceC<T
     Macro m = macro_of(g, W);
     eq_consts<T>(g, m, f.u, f.cexp, f.pref, f.eb, f.hu2);
     const double h = g.h;
-    f.al_g = (T)(2.0 * m.tg / (2.0 * m.tg + h));
-    f.al_b = (T)(2.0 * m.tb / (2.0 * m.tb + h));
-    f.gam_b = (T)(h * m.tb * m.itbg / (2.0 * m.tb + h));
+    const double tg2 = dmul(2.0, m.tg), tb2 = dmul(2.0, m.tb);
+    const double rg = ddiv(1.0, dadd(tg2, h)), rb = ddiv(1.0, dadd(tb2, h));
+    f.al_g = (T)dmul(tg2, rg);
+    f.al_b = (T)dmul(tb2, rb);
+    f.gam_b = (T)dmul(dmul(dmul(h, m.tb), m.itbg), rb);
 }
 
 // Per-lane velocity data of one tile.
@@ -1549,16 +1575,16 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
         for (int m = 0; m < NM; ++m) {
             double sr = 0.0, sl = 0.0;
             for (int gg = 0; gg < g.G; ++gg) {
-                sr += bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fr];
-                sl += bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fl];
+                sr = dadd(sr, bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fr]);
+                sl = dadd(sl, bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fl]);
             }
-            dW[m] += (sr - sl) * g.idx[a];
+            dW[m] = __fma_rn(dsub(sr, sl), g.idx[a], dW[m]);
         }
     }
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     bool finite = true;
     for (int m = 0; m < NM; ++m) {
-        W[m] = bf.W[(size_t)m * g.Nc + c] - g.dt * dW[m];
+        W[m] = __fma_rn(-g.dt, dW[m], bf.W[(size_t)m * g.Nc + c]);
         finite = finite && isfinite(W[m]);
         bf.W[(size_t)m * g.Nc + c] = W[m];
     }
