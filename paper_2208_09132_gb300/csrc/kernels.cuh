@@ -133,8 +133,17 @@ struct CellC {
     T u[3];
     T cexp, pref, eb, hu2;      // g_eq = pref exp(cexp |xi-u|^2), b_eq = (|xi|^2/2 + eb) g_eq, Z = xi.u - hu2
     T fa_g, fb_g, fa_b, fb_b;   // phi = fa phi* + fb phi_eq        (deferred end of eq. phiupdate)
-    T sa_g, sa_b, ssrc;         // phibar+ = eq + sa (phi - eq) [+ ssrc Z (g - g_eq)]   (eq. phibarplus)
+    T kp_g, kp_b, kp_s;         // phibar+ = eq + kp (phi* - eq) [+ kp_s Z (g* - g_eq)] (eq. phibarplus with
+                                //   phi - eq = fa (phi* - eq): kp = sa fa, kp_s = ssrc fa_g)
     T um_g, um_b, usrc;         // phi* = eq + um (phi - eq) [+ usrc Z (g - g_eq)] - dt dF (eq. phiupdate)
+};
+
+// The phibar+ constants of a cell as packed in shared memory: u (D), cexp,
+// pref, eb, hu2, kp_g, kp_b, kp_s.
+template <int D>
+struct CellPack {
+    static constexpr int N = D + 7;
+    static constexpr int NV = (N + 3) / 4;
 };
 
 // Face constants from the face W (eq. phibar inverted: phi = eq + alpha (phibar - eq) [+ gb Z (g - g_eq)]).
@@ -215,9 +224,10 @@ __device__ __forceinline__ void make_cell(const Geo& g, const double* W, CellC<T
     c.fb_g = (T)dmul(dt, rg);
     c.fa_b = (T)dmul(tb2, rb);
     c.fb_b = (T)dmul(dt, rb);
-    c.sa_g = (T)dsub(1.0, dmul(hh, itg));
-    c.sa_b = (T)dsub(1.0, dmul(hh, itb));
-    c.ssrc = (T)dmul(hh, m.itbg);
+    const double fa_g = dmul(tg2, rg), fa_b = dmul(tb2, rb);
+    c.kp_g = (T)dmul(dsub(1.0, dmul(hh, itg)), fa_g);   // (1 - h/2tau_g) fa_g
+    c.kp_b = (T)dmul(dsub(1.0, dmul(hh, itb)), fa_b);
+    c.kp_s = (T)dmul(dmul(hh, m.itbg), fa_g);           // h/2 (1/tau_b - 1/tau_g) fa_g
     c.um_g = (T)dsub(1.0, dmul(hdt, itg));
     c.um_b = (T)dsub(1.0, dmul(hdt, itb));
     c.usrc = (T)dmul(dt, m.itbg);
@@ -434,8 +444,7 @@ __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FA
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
     using TL = Tile<D, T0, T1, T2>;
-    static constexpr int NCC = D + 11;           // phase-1 constants per box cell
-    static constexpr int NCCV = (NCC + 3) / 4;   // ... packed in V4
+    static constexpr int NCCV = CellPack<D>::NV;  // phase-1 constants per box cell, packed in V4
     static constexpr int NFC = D + 7;            // face constants
     static constexpr int NFCV = (NFC + 3) / 4;
     static constexpr int PN = mode_source(MODE) == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
@@ -459,6 +468,40 @@ __device__ __forceinline__ size_t face_addr(const Geo& g, int a, long long f, in
 template <int D>
 __device__ __forceinline__ size_t sig_addr(const Geo& g, long long cell, int i, int a, int f) {
     return ((size_t)(i / VC) * (size_t)g.Nc + (size_t)cell) * (2 * D * VC) + (size_t)(a * 2 + f) * VC + (i % VC);
+}
+
+// phibar+ of one point (eq. phibarplus) from the stored phi* (gs, bs), the
+// equilibrium (ge, be), Z = xi.u - |u|^2/2 and the cell constants.
+template <typename T>
+__device__ __forceinline__ void phibar_plus(T ge, T be, T gs, T bs, T z, T kp_g, T kp_b, T kp_s, T& pg, T& pb) {
+    const T dg = gs - ge;
+    pg = fma(kp_g, dg, ge);
+    pb = fma(kp_s * z, dg, fma(kp_b, bs - be, be));
+}
+
+// Pack a cell's phibar+ constants (CellPack order; u with the components of a
+// mirror image reversed) into V4 slots dst[j * stride].
+template <typename T, int D>
+__device__ __forceinline__ void pack_cell(const CellC<T>& cs, int refl, V4<T>* dst, int stride) {
+    T cst[4 * CellPack<D>::NV];
+#pragma unroll
+    for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
+    cst[D + 0] = cs.cexp;
+    cst[D + 1] = cs.pref;
+    cst[D + 2] = cs.eb;
+    cst[D + 3] = cs.hu2;
+    cst[D + 4] = cs.kp_g;
+    cst[D + 5] = cs.kp_b;
+    cst[D + 6] = cs.kp_s;
+#pragma unroll
+    for (int j = D + 7; j < 4 * CellPack<D>::NV; ++j) cst[j] = T(0);
+#pragma unroll
+    for (int j = 0; j < CellPack<D>::NV; ++j) {
+        V4<T> qv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
+        dst[j * stride] = qv;
+    }
 }
 
 // phibar+ (eq. phibarplus) of every point, for the prepared-shift shapes:
@@ -488,11 +531,7 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
             }
             const T ge = cs.pref * Num<T>::expo(cs.cexp * c2);
             const T be = (rec[4] + cs.eb) * ge;
-            const T gg = fma(cs.fa_g, gs[v], cs.fb_g * ge);
-            const T bb = fma(cs.fa_b, bs[v], cs.fb_b * be);
-            const T dg = gg - ge;
-            pg[v] = fma(cs.sa_g, dg, ge);
-            pb[v] = fma(cs.ssrc * z, dg, fma(cs.sa_b, bb - be, be));
+            phibar_plus<T>(ge, be, gs[v], bs[v], z, cs.kp_g, cs.kp_b, cs.kp_s, pg[v], pb[v]);
         }
         Chunk<T>::store(bf.phibar + ad, pg);
         Chunk<T>::store(bf.phibar + ad + VC, pb);
@@ -513,14 +552,14 @@ struct ShTile {
 template <typename T, int D, int T0_, int T1_, int T2_>
 __host__ __device__ constexpr size_t shslope_smem_bytes() {
     using TL = Tile<D, T0_, T1_, T2_>;
-    return ((size_t)2 * TL::SB + (size_t)((D + 11 + 3) / 4) * TL::SB) * sizeof(V4<T>) + sizeof(int) * 2 * TL::SB;
+    return ((size_t)2 * TL::SB + (size_t)CellPack<D>::NV * TL::SB) * sizeof(V4<T>) + sizeof(int) * 2 * TL::SB;
 }
 
 template <typename T, int D, int T0_, int T1_, int T2_>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const Inst<T>* __restrict__ in, int cur) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using Q = V4<T>;
-    constexpr int SB = TL::SB, NCCV = (D + 11 + 3) / 4;
+    constexpr int SB = TL::SB, NCCV = CellPack<D>::NV;
     extern __shared__ __align__(32) unsigned char smem[];
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
@@ -549,30 +588,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
         bool dir;
         resolve<D>(g, q, refl, dir);
         const long long c = cell_index(g, q);
-        const CellC<T>& cs = bf.cellc[c];
-        T cst[4 * NCCV];
-#pragma unroll
-        for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
-        cst[D + 0] = cs.cexp;
-        cst[D + 1] = cs.pref;
-        cst[D + 2] = cs.eb;
-        cst[D + 3] = cs.hu2;
-        cst[D + 4] = cs.fa_g;
-        cst[D + 5] = cs.fb_g;
-        cst[D + 6] = cs.fa_b;
-        cst[D + 7] = cs.fb_b;
-        cst[D + 8] = cs.sa_g;
-        cst[D + 9] = cs.sa_b;
-        cst[D + 10] = cs.ssrc;
-#pragma unroll
-        for (int j = D + 11; j < 4 * NCCV; ++j) cst[j] = T(0);
-#pragma unroll
-        for (int j = 0; j < NCCV; ++j) {
-            Q qv;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
-            CC[j * SB + s2] = qv;
-        }
+        pack_cell<T, D>(bf.cellc[c], refl, CC + s2, SB);
         csrc[s2] = (int)c;
         cfl[s2] = refl;
     }
@@ -628,11 +644,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
                 }
                 const T ge = cst[D + 1] * Num<T>::expo(cst[D + 0] * c2);
                 const T be = (hx[v] + cst[D + 2]) * ge;
-                const T gg = fma(cst[D + 4], gs[v], cst[D + 5] * ge);
-                const T bb = fma(cst[D + 6], bs[v], cst[D + 7] * be);
-                const T dg = gg - ge;
-                qg.v[v] = fma(cst[D + 8], dg, ge);
-                qb.v[v] = fma(cst[D + 10] * z, dg, fma(cst[D + 9], bb - be, be));
+                phibar_plus<T>(ge, be, gs[v], bs[v], z, cst[D + 4], cst[D + 5], cst[D + 6], qg.v[v], qb.v[v]);
             }
             P[0 * SB + s2] = qg;
             P[1 * SB + s2] = qb;
@@ -904,30 +916,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         csrc[k] = (int)c;
         cfl[k] = refl | (dir ? 8 : 0);
         if (PREP) continue;
-        const CellC<T>& cs = dir ? bf.cellc0[c] : bf.cellc[c];
-        T cst[4 * NCCV];
-#pragma unroll
-        for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
-        cst[D + 0] = cs.cexp;
-        cst[D + 1] = cs.pref;
-        cst[D + 2] = cs.eb;
-        cst[D + 3] = cs.hu2;
-        cst[D + 4] = cs.fa_g;
-        cst[D + 5] = cs.fb_g;
-        cst[D + 6] = cs.fa_b;
-        cst[D + 7] = cs.fb_b;
-        cst[D + 8] = cs.sa_g;
-        cst[D + 9] = cs.sa_b;
-        cst[D + 10] = cs.ssrc;
-#pragma unroll
-        for (int j = D + 11; j < 4 * NCCV; ++j) cst[j] = T(0);
-#pragma unroll
-        for (int j = 0; j < NCCV; ++j) {
-            Q qv;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
-            CC[j * BOX + k] = qv;
-        }
+        pack_cell<T, D>(dir ? bf.cellc0[c] : bf.cellc[c], refl, CC + k, BOX);
     }
     {   // halo list in box order (warp ballots), so neighbouring threads touch neighbouring cells
         constexpr int PER = ((BOX + NW - 1) / NW + 31) / 32 * 32;
@@ -1034,8 +1023,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 Chunk<T>::load(bf.phi_in + ad + VC, bs);
             }
             const T cexp = cst[D + 0], pref = cst[D + 1], eb = cst[D + 2], hu2 = cst[D + 3];
-            const T fa_g = cst[D + 4], fb_g = cst[D + 5], fa_b = cst[D + 6], fb_b = cst[D + 7];
-            const T sa_g = cst[D + 8], sa_b = cst[D + 9], ssrc = cst[D + 10];
+            const T kp_g = cst[D + 4], kp_b = cst[D + 5], kp_s = cst[D + 6];
             Q qg, qb;
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
@@ -1052,14 +1040,10 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     qg.v[v] = ge;
                     qb.v[v] = be;
                 } else {
-                    const T gg = fma(fa_g, gs[v], fb_g * ge);
-                    const T bb = fma(fa_b, bs[v], fb_b * be);
-                    const T dg = gg - ge;
-                    qg.v[v] = fma(sa_g, dg, ge);
-                    qb.v[v] = fma(ssrc * z, dg, fma(sa_b, bb - be, be));
-                    if (SWEEP_B && keep) {
-                        og[v] = gg;
-                        ob[v] = bb;
+                    phibar_plus<T>(ge, be, gs[v], bs[v], z, kp_g, kp_b, kp_s, qg.v[v], qb.v[v]);
+                    if (SWEEP_B && keep) {   // phi^n of the owned cell (the deferred end of eq. phiupdate)
+                        og[v] = fma(own.fa_g, gs[v], own.fb_g * ge);
+                        ob[v] = fma(own.fa_b, bs[v], own.fb_b * be);
                         oge[v] = ge;
                         obe[v] = be;
                     }
