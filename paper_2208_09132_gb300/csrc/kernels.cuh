@@ -453,10 +453,21 @@ struct Smem {
     static constexpr size_t nCC = mode_source(MODE) == MODE_FUSED ? (size_t)NCCV * TL::BOX : 0;
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
-    __host__ __device__ static constexpr size_t vcount(bool B) { return nP + nS + nCC + (B ? nFF + nFC : 0); }
-    __host__ __device__ static constexpr size_t bytes(bool B) {
-        return vcount(B) * sizeof(V4<T>) + sizeof(int) * (2 * TL::BOX + TL::NH + 32);
+    static constexpr size_t nInt = (size_t)2 * TL::BOX + TL::NH + 32;
+    // CTAs per SM that a dynamic shared-memory size allows, and the limit of threads and >= 80 registers
+    __host__ __device__ static constexpr int fit(size_t b) { return (int)((size_t)(228 * 1024) / (b + 1024)); }
+    static constexpr int lim = (2048 / TL::NT) < (65536 / (TL::NT * 80)) ? (2048 / TL::NT) : (65536 / (TL::NT * 80));
+    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + sizeof(int) * nInt;   // sweep A, one P
+    static constexpr bool dbl_fits = fit(a1 + nP * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
+    // Sweep A of the shapes that form phibar+ in phase 1 alternates two phibar+
+    // arrays between chunks (where that costs no occupancy), which lets it drop
+    // the barrier at the end of a chunk.
+    __host__ __device__ static constexpr bool double_p(bool B) {
+        return !B && mode_source(MODE) != MODE_STORED && dbl_fits;
     }
+    __host__ __device__ static constexpr size_t nPB(bool B) { return double_p(B) ? 2 * nP : nP; }
+    __host__ __device__ static constexpr size_t vcount(bool B) { return nPB(B) + nS + nCC + (B ? nFF + nFC : 0); }
+    __host__ __device__ static constexpr size_t bytes(bool B) { return vcount(B) * sizeof(V4<T>) + sizeof(int) * nInt; }
 };
 
 // Offset of the chunk vt of face f (axis a) in the face-value layout.
@@ -865,8 +876,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
-    Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
+    constexpr bool DBL = SM::double_p(SWEEP_B);
+    Q* const P0 = reinterpret_cast<Q*>(smem);     // [1 or 2][2][PN] phibar+ chunk per cell
+    Q* const S = P0 + SM::nPB(SWEEP_B);           // [D][2][SB] half van Leer slopes times dx
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
@@ -967,6 +979,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NH = TL::NH;
 
     for (int vt = vt0; vt < vt1; ++vt) {
+        Q* const P = DBL && (vt & 1) ? P0 + SM::nP : P0;   // this chunk's phibar+ array
         // velocity records of the chunk (same for every thread); nu = 2 h xi / dx
         T xi[VC][D], nu[VC][D], w[VC], hx[VC];
 #pragma unroll
@@ -1294,7 +1307,11 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                                      bf.phi_out + phi_addr(g, cell_index(g, qa), vt * VC, 0));
             }
         }
-        __syncthreads();
+        // Before the next chunk overwrites P and S.  With two P arrays this is not
+        // needed: a thread writes S of chunk vt+1 only after the barrier behind its
+        // phase 1, which the others reach after their phase 3 of chunk vt, and its
+        // phase-1 writes go to the array that chunk vt-1 used.
+        if (!DBL) __syncthreads();
     }
 
     // ---- epilogue: this group's partial face sums
