@@ -154,27 +154,47 @@ struct FaceC {
     T al_g, al_b, gam_b;
 };
 
+// Macroscopic state of a cell or face from its conserved variables (FP64).
 struct Macro {
-    double rho, u[3], T, RT, tg, tb, itbg;
+    double rho, u[3], T, RT;
 };
 
-// The FP64 constants below are written with explicitly rounded operations
-// (no multiply-add contraction), so every kernel that forms them -- single
-// instance or batched, any inlining context -- gets the same bits.
+// Explicitly rounded arithmetic in precision R (no multiply-add contraction),
+// so every kernel that forms the constants below -- single instance or
+// batched, any inlining context -- gets the same bits.
+template <typename R> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+    static __device__ __forceinline__ double pow_(double a, double b) { return pow(a, b); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+    static __device__ __forceinline__ float pow_(float a, float b) { return powf(a, b); }
+};
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
 // x^omega for the viscosity law mu = mu_ref (T/T_ref)^omega: the hard-sphere
-// (1/2) and Maxwell (1) exponents without the general power function, whose
-// FP64 cost dominates the per-cell constants.
-__device__ __forceinline__ double visc_power(double x, double omega) {
-    return omega == 0.5 ? __dsqrt_rn(x) : (omega == 1.0 ? x : pow(x, omega));
+// (1/2) and Maxwell (1) exponents without the general power function.
+template <typename R>
+__device__ __forceinline__ R visc_power(R x, R omega) {
+    return omega == R(0.5) ? Ar<R>::sqrt_(x) : (omega == R(1) ? x : Ar<R>::pow_(x, omega));
 }
 // x^(-D/2): the normalisation of a D-dimensional Maxwellian.
-__device__ __forceinline__ double gauss_norm(double x, int D) {
-    return D == 2 ? ddiv(1.0, x) : (D == 1 ? ddiv(1.0, __dsqrt_rn(x)) : ddiv(1.0, dmul(x, __dsqrt_rn(x))));
+template <typename R>
+__device__ __forceinline__ R gauss_norm(R x, int D) {
+    using A = Ar<R>;
+    return D == 2 ? A::div(R(1), x) : (D == 1 ? A::div(R(1), A::sqrt_(x)) : A::div(R(1), A::mul(x, A::sqrt_(x))));
 }
 
 __device__ __forceinline__ Macro macro_of(const Geo& g, const double* W) {
@@ -191,58 +211,80 @@ __device__ __forceinline__ Macro macro_of(const Geo& g, const double* W) {
     // T = (gamma - 1)/R (E - u^2/2), gamma = (K+5)/(K+3)
     m.T = dmul(ddiv(2.0, dmul(dadd(g.K, 3.0), g.R)), dsub(E, dmul(0.5, u2)));
     m.RT = dmul(g.R, m.T);
-    const double mu = dmul(g.mu_ref, visc_power(ddiv(m.T, g.T_ref), g.omega));
-    m.tg = ddiv(mu, dmul(m.rho, m.RT));
-    m.tb = ddiv(m.tg, g.Pr);
-    m.itbg = ddiv(dsub(g.Pr, 1.0), m.tg);      // 1/tau_b - 1/tau_g
     return m;
+}
+
+// Inverse relaxation times in the storage precision R: 1/tau_g = p/mu,
+// 1/tau_b = Pr/tau_g, 1/tau_b - 1/tau_g.  Inverse times stay finite in both
+// limits (1/tau -> 0 as mu -> infinity), so every constant below is formed from
+// them.  FP64 storage keeps all constants in FP64; FP32 storage forms them in
+// FP32 from the FP64 macroscopic state (they are stored in FP32 either way).
+template <typename R>
+struct Relax {
+    R itg, itb, itbg;
+};
+template <typename R>
+__device__ __forceinline__ Relax<R> relax_of(const Geo& g, const Macro& m) {
+    using A = Ar<R>;
+    Relax<R> r;
+    const R mu = A::mul((R)g.mu_ref, visc_power<R>(A::div((R)m.T, (R)g.T_ref), (R)g.omega));
+    r.itg = A::div(A::mul((R)m.rho, (R)m.RT), mu);
+    r.itb = A::mul((R)g.Pr, r.itg);
+    r.itbg = A::mul(A::sub((R)g.Pr, R(1)), r.itg);
+    return r;
 }
 
 template <typename T>
 __device__ __forceinline__ void eq_consts(const Geo& g, const Macro& m, T u[3], T& cexp, T& pref, T& eb, T& hu2) {
+    using A = Ar<T>;
     double u2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         u[a] = (T)m.u[a];
         u2 = dadd(u2, dmul(m.u[a], m.u[a]));
     }
-    cexp = (T)ddiv(-0.5 * Num<T>::cexp_scale(), m.RT);
-    pref = (T)dmul(m.rho, gauss_norm(dmul(2.0 * 3.14159265358979323846, m.RT), g.D));
-    eb = (T)dmul(0.5 * (3.0 - g.D + g.K), m.RT);
+    const T RT = (T)m.RT;
+    cexp = A::div((T)(-0.5 * Num<T>::cexp_scale()), RT);
+    pref = A::mul((T)m.rho, gauss_norm<T>(A::mul((T)(2.0 * 3.14159265358979323846), RT), g.D));
+    eb = A::mul((T)(0.5 * (3.0 - g.D + g.K)), RT);
     hu2 = (T)dmul(0.5, u2);
 }
 
+// Cell constants from W: equilibrium parameters and, with x = dt/(2 tau),
+// fa = 1/(1 + x), fb = x fa (phi = fa phi* + fb phi_eq), kp = (1 - h/(2 tau)) fa,
+// kp_s = (h/2)(1/tau_b - 1/tau_g) fa_g, um = 1 - x, usrc = dt (1/tau_b - 1/tau_g).
 template <typename T>
 __device__ __forceinline__ void make_cell(const Geo& g, const double* W, CellC<T>& c) {
-    Macro m = macro_of(g, W);
+    using A = Ar<T>;
+    const Macro m = macro_of(g, W);
+    const Relax<T> r = relax_of<T>(g, m);
     eq_consts<T>(g, m, c.u, c.cexp, c.pref, c.eb, c.hu2);
-    const double dt = g.dt, h = g.h;
-    const double itg = ddiv(1.0, m.tg), itb = dmul(g.Pr, itg);
-    const double tg2 = dmul(2.0, m.tg), tb2 = dmul(2.0, m.tb);
-    const double rg = ddiv(1.0, dadd(tg2, dt)), rb = ddiv(1.0, dadd(tb2, dt));
-    const double hh = dmul(0.5, h), hdt = dmul(0.5, dt);
-    c.fa_g = (T)dmul(tg2, rg);
-    c.fb_g = (T)dmul(dt, rg);
-    c.fa_b = (T)dmul(tb2, rb);
-    c.fb_b = (T)dmul(dt, rb);
-    const double fa_g = dmul(tg2, rg), fa_b = dmul(tb2, rb);
-    c.kp_g = (T)dmul(dsub(1.0, dmul(hh, itg)), fa_g);   // (1 - h/2tau_g) fa_g
-    c.kp_b = (T)dmul(dsub(1.0, dmul(hh, itb)), fa_b);
-    c.kp_s = (T)dmul(dmul(hh, m.itbg), fa_g);           // h/2 (1/tau_b - 1/tau_g) fa_g
-    c.um_g = (T)dsub(1.0, dmul(hdt, itg));
-    c.um_b = (T)dsub(1.0, dmul(hdt, itb));
-    c.usrc = (T)dmul(dt, m.itbg);
+    const T dt = (T)g.dt, hh = (T)(0.5 * g.h), hdt = (T)(0.5 * g.dt);
+    const T xg = A::mul(hdt, r.itg), xb = A::mul(hdt, r.itb);
+    const T fa_g = A::div(T(1), A::add(T(1), xg)), fa_b = A::div(T(1), A::add(T(1), xb));
+    c.fa_g = fa_g;
+    c.fb_g = A::mul(xg, fa_g);
+    c.fa_b = fa_b;
+    c.fb_b = A::mul(xb, fa_b);
+    c.kp_g = A::mul(A::sub(T(1), A::mul(hh, r.itg)), fa_g);
+    c.kp_b = A::mul(A::sub(T(1), A::mul(hh, r.itb)), fa_b);
+    c.kp_s = A::mul(A::mul(hh, r.itbg), fa_g);
+    c.um_g = A::sub(T(1), xg);
+    c.um_b = A::sub(T(1), xb);
+    c.usrc = A::mul(dt, r.itbg);
 }
 
+// Face constants from the face W: equilibrium parameters, alpha = 1/(1 + h/(2 tau))
+// (the inverse of eq. phibar) and gamma_b = (h/2)(1/tau_b - 1/tau_g) alpha_b.
 template <typename T>
 __device__ __forceinline__ void make_face(const Geo& g, const double* W, FaceC<T>& f) {
-    Macro m = macro_of(g, W);
+    using A = Ar<T>;
+    const Macro m = macro_of(g, W);
+    const Relax<T> r = relax_of<T>(g, m);
     eq_consts<T>(g, m, f.u, f.cexp, f.pref, f.eb, f.hu2);
-    const double h = g.h;
-    const double tg2 = dmul(2.0, m.tg), tb2 = dmul(2.0, m.tb);
-    const double rg = ddiv(1.0, dadd(tg2, h)), rb = ddiv(1.0, dadd(tb2, h));
-    f.al_g = (T)dmul(tg2, rg);
-    f.al_b = (T)dmul(tb2, rb);
-    f.gam_b = (T)dmul(dmul(dmul(h, m.tb), m.itbg), rb);
+    const T hh = (T)(0.5 * g.h);
+    f.al_g = A::div(T(1), A::add(T(1), A::mul(hh, r.itg)));
+    f.al_b = A::div(T(1), A::add(T(1), A::mul(hh, r.itb)));
+    f.gam_b = A::mul(A::mul(hh, r.itbg), f.al_b);
 }
 
 // Per-lane velocity data of one tile.
@@ -1589,12 +1631,12 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
         finite = finite && isfinite(W[m]);
         bf.W[(size_t)m * g.Nc + c] = W[m];
     }
-    double u2 = 0.0;
-    for (int a = 0; a < D; ++a) u2 += (W[1 + a] / W[0]) * (W[1 + a] / W[0]);
-    const double e = W[1 + D] / W[0] - 0.5 * u2;
+    // internal energy rho e = rho E - |rho u|^2 / (2 rho) > 0  <=>  2 rho (rho E) > |rho u|^2 (rho > 0)
+    double m2 = 0.0;
+    for (int a = 0; a < D; ++a) m2 += W[1 + a] * W[1 + a];
     int st = 0;
     if (!finite) st |= ST_NONFINITE;
-    else if (!(W[0] > 0.0) || !(e > 0.0)) st |= ST_NEGATIVE;
+    else if (!(W[0] > 0.0) || !(2.0 * W[0] * W[1 + D] > m2)) st |= ST_NEGATIVE;
     if (st) atomicOr(bf.status, st);
     make_cell<T>(g, W, bf.cellc[c]);
 }
