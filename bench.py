@@ -41,6 +41,23 @@ ALGO_BYTES = {  # algorithmic bytes per phase-space point per launch (state read
     "sweep_a": {"fp32": 8, "fp64": 16},     # read g*, b*
     "sweep_b": {"fp32": 16, "fp64": 32},    # read g*, b*; write g*, b*
 }
+MODE_NAMES = {0: "fused", 1: "prepared phibar+", 2: "stored phibar+ and slopes", 4: "fused, face store",
+              5: "prepared phibar+, face store", 6: "stored phibar+ and slopes, face store"}
+
+
+def design_bytes(mode, D, elt):
+    """Bytes per phase-space point each launch of a sweep mode moves by design
+    (state, prepared arrays, stored face values; halo re-reads not counted)."""
+    src, faces = mode & 3, bool(mode & 4)
+    d = {}
+    if src == 1:
+        d["prep"] = 4 * elt                                   # read phi*, write phibar+
+    elif src == 2:
+        d["slopes"] = (4 + 2 * D) * elt                       # read phi*, write phibar+ and D slopes
+    a_in = {0: 2, 1: 2, 2: 2 + 2 * D}[src] * elt
+    d["sweep_a"] = a_in + (2 * D * elt if faces else 0)       # (+ write the face values)
+    d["sweep_b"] = (2 * D + 4) * elt if faces else a_in + (2 if src else 0) * elt + 2 * elt
+    return d
 
 
 def pick_workload(name):
@@ -309,7 +326,8 @@ def run_batched(args, ws, rank, local):
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                      "algorithmic_bytes_per_point": 24, "traffic": None},
         "cpu_baseline": None, "e2e": None, "fp64_plain": fp64,
-        "gpu_launches": K * 6, "clocks": clk, "status_ok": status == 0,
+        # per batched step: sweep A and sweep B per tile shape, face constants, W update
+        "gpu_launches": K * (2 * len({t for t, _ in choices}) + 2), "clocks": clk, "status_ok": status == 0,
     }
 
 
@@ -322,11 +340,14 @@ def run_served(args, ws, rank, local):
 
     dev = f"cuda:{local}"
     torch.cuda.set_device(local)
-    reqs = serving.stream_c5(count=args.requests, t_end=args.t_end)
+    from paper_2208_09132_gb300 import cdugks
+
+    tile = cdugks.find_tile(cdugks.FP32, 2, (32, 8), 4)     # fused sweep A + face store, batchable
+    reqs = serving.stream_c5(count=args.requests, t_end=args.t_end, tile_id=tile)
     free, _ = torch.cuda.mem_get_info()
     srv = serving.Server(budget_bytes=int(0.6 * free), max_slots=64, max_round=32, device=dev)
     # warm-up: one tiny request compiles/loads everything
-    warm = serving.stream_c5(count=1, t_end=0.002)
+    warm = serving.stream_c5(count=1, t_end=0.002, tile_id=tile)
     serving.Server(budget_bytes=int(0.6 * free), device=dev).run(warm)
     clocks = ClockSampler(local)
     clocks.start()
@@ -347,11 +368,12 @@ def run_served(args, ws, rank, local):
         "config": {"workload": f"served_stream_{len(reqs)}_requests", "arrivals": "Poisson 50/s, seed 1",
                    "requests": len(reqs), "t_end": args.t_end,
                    "sizes": "cells 32^2-128^2, velocities 8^2-24^2, Gresho or Kelvin-Helmholtz, Kn 1e-4..1",
-                   "admission": "device-memory footprint within 60% of free memory, <= 64 slots"},
+                   "admission": "device-memory footprint within 60% of free memory, <= 64 slots",
+                   "tile_id": tile, "sweep_mode": MODE_NAMES[cdugks.tile_shape(cdugks.FP32, 2, tile)[1]]},
         "latency_ms": {"p50": rep["p50_time_to_solution_s"] * 1e3, "p99": rep["p99_time_to_solution_s"] * 1e3,
                        "what": "time to solution from arrival"},
         "served": rep, "cpu_baseline": None, "e2e": None, "roofline": None,
-        "gpu_launches": None, "clocks": clk,
+        "gpu_launches": rep["kernel_launches"], "clocks": clk,
     }
 
 
@@ -407,6 +429,7 @@ def run_ours(args, ws, rank, local):
     dom = max(("sweep_a", "sweep_b"), key=lambda k: ph[names.index(k)])
     t_dom = ph[names.index(dom)] / 1e3
     abytes = ALGO_BYTES[dom][pname] * P
+    mode = cdugks.tile_shape(prec, cfg["dim"], s.info().tile_id)[1]
     peak, peak_kind = measured_peak_hbm()
     achieved = abytes / t_dom / 1e9
     traffic_pp = ncu_traffic(args.workload, dom, pname)
@@ -415,6 +438,7 @@ def run_ours(args, ws, rank, local):
                 "algorithmic_bytes_per_point": ALGO_BYTES[dom][pname],
                 "traffic": None if traffic_pp is None else traffic_pp * P,
                 "phase_ms": {n: round(float(v), 4) for n, v in zip(names, ph)},
+                "design_bytes_per_point": design_bytes(mode, cfg["dim"], 4 if pname == "fp32" else 8),
                 "step_bytes_per_point": ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname],
                 "step_hbm_frac": round((ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname]) * P
                                        / (total_ms / args.steps / 1e3) / 1e9 / peak, 4)}
@@ -458,7 +482,7 @@ def run_ours(args, ws, rank, local):
     result = None
     if rank == 0:
         cpu = cpu_baseline(cfg) if (ws == 1 and not args.skip_cpu) else None
-        launches_per_step = 3 + cfg["dim"]
+        launches_per_step = 3 + cfg["dim"] + (1 if mode & 3 else 0)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -468,6 +492,7 @@ def run_ours(args, ws, rank, local):
                        "velocities": wl.nvel(cfg), "points": P, "dt": s.dt,
                        "state_bytes": s.info().state_bytes,
                        "tile": list(s.info().tile)[:cfg["dim"]], "velocity_groups": s.info().velocity_groups,
+                       "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode, str(mode)),
                        "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
                              else "state fits in L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},

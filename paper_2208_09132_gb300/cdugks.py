@@ -312,5 +312,15 @@ def tile_shape(precision: int, dim: int, tile_id: int):
     return tuple(out[:3]), int(out[3])
 
 
+def find_tile(precision: int, dim: int, shape, mode: int) -> int:
+    """Id of the instantiated tile shape with these cells per axis and sweep mode (0 if none)."""
+    want = tuple(list(shape) + [1] * (3 - len(shape)))
+    for t in range(load().cdugks_tile_count(int(precision), int(dim))):
+        cells, m = tile_shape(precision, dim, t)
+        if tuple(c if a < dim else 1 for a, c in enumerate(cells)) == want and m == mode:
+            return t
+    return 0
+
+
 def mu_from_kn(kn, rho_ref, T_ref, R=0.5, length=1.0) -> float:
     return float(load().cdugks_mu_from_kn(kn, rho_ref, T_ref, R, length))

@@ -97,6 +97,7 @@ class Server:
         self.point_updates = 0
         self.rounds = 0
         self.rebuilds = 0
+        self.launches = 0          # kernels of this library launched by the server
 
     # -- admission --------------------------------------------------------
     def submit(self, req: Request):
@@ -115,6 +116,7 @@ class Server:
             s = cdugks.Solver(req.cfg, precision=req.precision, device=self.device, tile_id=req.tile_id,
                               velocity_groups=req.velocity_groups)
             s.init(req.fields)
+            self.launches += 1                    # the initial state
             req.solver = s
             req.admitted_at = now
             self.used += req.footprint
@@ -128,6 +130,7 @@ class Server:
         for req in self.active:
             if req.done_steps >= req.nsteps:
                 req.result = req.solver.moments()
+                self.launches += 1                # the moments
                 req.finished_at = now
                 req.solver = None                  # frees its workspace
                 self.used -= req.footprint
@@ -149,6 +152,8 @@ class Server:
             q.done_steps += r
         self.point_updates += r * sum(q.points for q in self.active)
         self.rounds += 1
+        # per batched step: sweep A and sweep B per tile shape, face constants, W update
+        self.launches += r * (2 * len({q.tile_id for q in self.active}) + 2)
 
     def run(self, requests, time_limit: float | None = None):
         """Serve requests whose ``arrival`` times are seconds after the start.
@@ -185,14 +190,17 @@ class Server:
             "aggregate_point_updates_per_s": self.point_updates / wall_s if wall_s > 0 else None,
             "rounds": self.rounds,
             "batch_rebuilds": self.rebuilds,
+            "kernel_launches": self.launches,
         }
 
 
-def stream_c5(count=64, seed=1, rate=50.0, side_range=(32, 128), vside_range=(8, 24), t_end=0.05):
+def stream_c5(count=64, seed=1, rate=50.0, side_range=(32, 128), vside_range=(8, 24), t_end=0.05, tile_id=0):
     """The served workload: Poisson arrivals of 2D Gresho-vortex and
-    Kelvin-Helmholtz solves of varied size, Kn and velocity grid (FP32)."""
+    Kelvin-Helmholtz solves of varied size, Kn and velocity grid (FP32), all
+    with the sweep tile shape tile_id."""
     out = []
     for k, (t, cfg, f) in enumerate(wl.workload_c5(count=count, seed=seed, rate=rate, side_range=side_range,
                                                    vside_range=vside_range, t_end=t_end)):
-        out.append(Request(rid=k, cfg=cfg, fields=f, t_end=t_end, arrival=t, precision=cdugks.FP32))
+        out.append(Request(rid=k, cfg=cfg, fields=f, t_end=t_end, arrival=t, precision=cdugks.FP32,
+                           tile_id=tile_id))
     return out
