@@ -159,9 +159,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, kernel, precision):
+def ncu_traffic(workload, kernel, precision, tile_id=None, groups=None):
     """DRAM bytes per point for a kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+    was taken on the current kernel source in the same launch configuration;
+    else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
@@ -170,7 +171,11 @@ def ncu_traffic(workload, kernel, precision):
     if d.get("kernel_source_sha") != kernel_source_sha():
         return None
     e = d.get("entries", {}).get(f"{workload}:{precision}:{kernel}")
-    return None if e is None else float(e["dram_bytes_per_point"])
+    if e is None:
+        return None
+    if (tile_id is not None and e.get("tile_id") != tile_id) or (groups is not None and e.get("velocity_groups") != groups):
+        return None
+    return float(e["dram_bytes_per_point"])
 
 
 def cpu_baseline(cfg, budget_s=12.0):
@@ -432,7 +437,7 @@ def run_ours(args, ws, rank, local):
     mode = cdugks.tile_shape(prec, cfg["dim"], s.info().tile_id)[1]
     peak, peak_kind = measured_peak_hbm()
     achieved = abytes / t_dom / 1e9
-    traffic_pp = ncu_traffic(args.workload, dom, pname)
+    traffic_pp = ncu_traffic(args.workload, dom, pname, s.info().tile_id, s.info().velocity_groups)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "algorithmic_bytes_per_point": ALGO_BYTES[dom][pname],
