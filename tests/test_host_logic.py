@@ -1,0 +1,64 @@
+"""Host-side logic that needs no GPU: tile-shape tables, tuner candidates,
+design-byte accounting of the bench, and the serving step count."""
+import math
+
+from paper_2208_09132_gb300 import cdugks, serving, tune
+from paper_2208_09132_gb300 import workloads as wl
+
+import bench
+
+
+def _modes(prec, dim):
+    return [cdugks.tile_shape(prec, dim, t)[1] for t in range(cdugks.load().cdugks_tile_count(prec, dim))]
+
+
+def test_every_dimension_has_a_fused_default_and_a_face_store_shape():
+    for prec in (cdugks.FP32, cdugks.FP64):
+        for dim in (1, 2, 3):
+            modes = _modes(prec, dim)
+            assert modes[0] == 0                       # tile 0: fused, batchable, no extra buffers
+            assert any(m & 4 for m in modes), (prec, dim, modes)
+
+
+def test_find_tile_returns_the_matching_shape():
+    t = cdugks.find_tile(cdugks.FP32, 2, (32, 8), 4)
+    assert cdugks.tile_shape(cdugks.FP32, 2, t) == ((32, 8, 1), 4)
+    assert cdugks.find_tile(cdugks.FP32, 2, (7, 7), 4) == 0
+
+
+def test_tuner_candidates_respect_batching_and_boundaries():
+    cfg, _ = wl.workload_c2()
+    alone = tune.candidates(cfg, cdugks.FP32, "alone")
+    batch = tune.candidates(cfg, cdugks.FP32, "batch")
+    modes = _modes(cdugks.FP32, 2)
+    assert {t for t, _ in alone} == set(range(len(modes)))              # periodic: every shape
+    assert {t for t, _ in batch} == {t for t, m in enumerate(modes) if m & 3 == 0}
+    assert all(g <= (wl.nvel(cfg) + 3) // 4 for _, g in alone)
+    dcfg, _ = wl.random_smooth(dim=2, n=(8, 8), nv=(4, 4), seed=1, amp=0.1, kn=1e-2)
+    dcfg = dict(dcfg, bc=[[wl.BC_DIRICHLET] * 2, [wl.BC_PERIODIC] * 2, [wl.BC_PERIODIC] * 2])
+    ts = {t for t, _ in tune.candidates(dcfg, cdugks.FP32, "alone")}
+    assert any(m & 3 == 2 for m in modes)                               # there are stored shapes ...
+    assert ts and all(modes[t] & 3 != 2 for t in ts)                    # ... but not with Dirichlet walls
+
+
+def test_size_key_buckets_by_powers_of_two():
+    cfg, _ = wl.workload_c2()
+    k = tune.size_key(cfg, cdugks.FP32, "alone")
+    assert k == "fp32:alone:D2:cells~65536:nv1024"
+
+
+def test_design_bytes_of_each_mode():
+    # FP32, 2D: fused sweeps read phi* (8 B) / read and write it (16 B)
+    assert bench.design_bytes(0, 2, 4) == {"sweep_a": 8, "sweep_b": 16}
+    # face store: sweep A also writes D face values (2 fields), k_flux reads them
+    assert bench.design_bytes(4, 2, 4) == {"sweep_a": 24, "sweep_b": 32}
+    # stored slopes + face store, 3D: the pre-pass writes phibar+ and 3 slopes
+    assert bench.design_bytes(6, 3, 4) == {"slopes": 40, "sweep_a": 56, "sweep_b": 40}
+    assert bench.design_bytes(1, 1, 8) == {"prep": 32, "sweep_a": 16, "sweep_b": 48}
+
+
+def test_served_step_count_reaches_the_end_time():
+    assert serving.steps_to(0.1, 1.0) == 10
+    assert serving.steps_to(0.3, 1.0) == 4
+    assert serving.steps_to(0.5, 1e-9) == 1
+    assert math.isclose(serving.steps_to(1e-3, 0.05) * 1e-3, 0.05)
