@@ -453,6 +453,16 @@ struct Tile {
     __host__ __device__ static constexpr int foff(int a) {
         return a == 0 ? 0 : (a == 1 ? NF0 : (a == 2 ? NF0 + NF1 : NFT));
     }
+    // cells on a tile face normal to axis a, and where their slots start in a list over all axes
+    __host__ __device__ static constexpr int plane(int a) { return NT / tdim(a); }
+    __host__ __device__ static constexpr int poff(int a) {
+        return (a > 0 ? plane(0) : 0) + (a > 1 && D >= 2 ? plane(1) : 0) + (a > 2 && D >= 3 ? plane(2) : 0);
+    }
+    static constexpr int NPL = (D >= 1 ? NT / T0 : 0) + (D >= 2 ? NT / T1 : 0) + (D >= 3 ? NT / T2 : 0);
+    // this cell's slot on the tile face normal to axis a
+    __device__ static __forceinline__ int plane_pos(int a, const int la[3]) {
+        return a == 0 ? la[1] + T1 * la[2] : (a == 1 ? la[0] + T0 * la[2] : la[0] + T0 * la[1]);
+    }
     __device__ static __forceinline__ int box_of(int l0, int l1, int l2) {
         return (l0 + 2) + E0 * ((D >= 2 ? l1 + 2 : 0) + E1 * (D >= 3 ? l2 + 2 : 0));
     }
@@ -496,10 +506,13 @@ struct Smem {
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
     static constexpr size_t nInt = (size_t)2 * TL::BOX + TL::NH + 32;
+    // Kahan sums of the faces at the domain's right end, [NM][plane slot] per axis (owned by the last cells)
+    static constexpr size_t nRS = (size_t)TL::NPL * (2 + D);
+    static constexpr size_t rs_bytes = nRS * sizeof(Kahan<T>);
     // CTAs per SM that a dynamic shared-memory size allows, and the limit of threads and >= 80 registers
     __host__ __device__ static constexpr int fit(size_t b) { return (int)((size_t)(228 * 1024) / (b + 1024)); }
     static constexpr int lim = (2048 / TL::NT) < (65536 / (TL::NT * 80)) ? (2048 / TL::NT) : (65536 / (TL::NT * 80));
-    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + sizeof(int) * nInt;   // sweep A, one P
+    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A, one P
     static constexpr bool dbl_fits = fit(a1 + nP * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
     // Sweep A of the shapes that form phibar+ in phase 1 alternates two phibar+
     // arrays between chunks (where that costs no occupancy), which lets it drop
@@ -509,7 +522,9 @@ struct Smem {
     }
     __host__ __device__ static constexpr size_t nPB(bool B) { return double_p(B) ? 2 * nP : nP; }
     __host__ __device__ static constexpr size_t vcount(bool B) { return nPB(B) + nS + nCC + (B ? nFF + nFC : 0); }
-    __host__ __device__ static constexpr size_t bytes(bool B) { return vcount(B) * sizeof(V4<T>) + sizeof(int) * nInt; }
+    __host__ __device__ static constexpr size_t bytes(bool B) {
+        return vcount(B) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;
+    }
 };
 
 // Offset of the chunk vt of face f (axis a) in the face-value layout.
@@ -884,22 +899,25 @@ __device__ __forceinline__ void store_phi_star(const Geo& g, const T (&xi)[VC][D
 }
 
 // A group's partial sums of the faces a thread owns (its left faces, and its
-// right faces at the domain's right end) into dst[a][(grp * (2+D) + m) * nf_a + face].
-template <typename T, int D>
+// right faces at the domain's right end, summed in RS) into
+// dst[a][(grp * (2+D) + m) * nf_a + face].
+template <typename T, int D, typename TL>
 __device__ __forceinline__ void write_face_sums(const Geo& g, double* const* dst, int grp, const int qa[3],
-                                                const bool own_right[3], const Kahan<T> (&acc)[D][2][2 + D]) {
+                                                const bool own_right[3], const Kahan<T> (&acc)[D][2 + D],
+                                                const Kahan<T>* RS, const int pl[3]) {
     constexpr int NM = 2 + D;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const long long f0 = face_index(g, a, qa);
 #pragma unroll
-        for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][0][m].value();
+        for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f0] = acc[a][m].value();
         if (own_right[a]) {
             int qr[3] = {qa[0], qa[1], qa[2]};
             qr[a] += 1;
             const long long f1 = face_index(g, a, qr);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) dst[a][((size_t)grp * NM + m) * g.nf[a] + f1] = acc[a][1][m].value();
+            for (int m = 0; m < NM; ++m)
+                dst[a][((size_t)grp * NM + m) * g.nf[a] + f1] = RS[pl[a] + m * TL::plane(a)].value();
         }
     }
 }
@@ -924,7 +942,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
-    int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
+    Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
+    int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B) + SM::rs_bytes);
     int* const cfl = csrc + BOX;
     int* const halo = cfl + BOX;
     int* const wcount = halo + TL::NH;            // [32] per-warp halo counts
@@ -1010,13 +1029,15 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         own_right[a] = valid && qa[a] == g.n[a] - 1;
         right[a] = valid && (SWEEP_B ? (la[a] == TL::tdim(a) - 1 || own_right[a]) : own_right[a]);
     }
-    Kahan<T> acc[D][2][NM];
+    Kahan<T> acc[D][NM];          // the left faces; the domain's right end sums in RS
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2)
+        for (int m = 0; m < NM; ++m) acc[a][m].zero();
+    int pl[3] = {0, 0, 0};        // this cell's slot in RS per axis
 #pragma unroll
-            for (int m = 0; m < NM; ++m) acc[a][s2][m].zero();
+    for (int a = 0; a < D; ++a) pl[a] = TL::poff(a) * NM + TL::plane_pos(a, la);
+    for (int k = t; k < (int)SM::nRS; k += TL::NT) RS[k].zero();
     __syncthreads();
     constexpr int NH = TL::NH;
 
@@ -1315,9 +1336,16 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                         FF[0 * NFT + fl] = fg;
                         FF[1 * NFT + fl] = fb;
                     }
-                    if (own) {
+                    if (side == 0) {
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) acc[a][side][m].add(sm[m]);
+                        for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
+                    } else if (own) {           // the domain's right end
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            Kahan<T> k = RS[pl[a] + m * TL::plane(a)];
+                            k.add(sm[m]);
+                            RS[pl[a] + m * TL::plane(a)] = k;
+                        }
                     }
                 }
             }
@@ -1357,7 +1385,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     }
 
     // ---- epilogue: this group's partial face sums
-    if (valid) write_face_sums<T, D>(g, SWEEP_B ? bf.mf : bf.wf, grp, qa, own_right, acc);
+    if (valid) write_face_sums<T, D, TL>(g, SWEEP_B ? bf.mf : bf.wf, grp, qa, own_right, acc, RS, pl);
 }
 
 // CTAs per SM that the shared memory of a sweep allows (at least 1, at most 4);
@@ -1396,14 +1424,10 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 template <typename T, int D, int T0_, int T1_, int T2_>
 struct FluxSmem {
     using TL = Tile<D, T0_, T1_, T2_>;
-    // cells on a tile face normal to axis a, and where their sums start
-    __host__ __device__ static constexpr int plane(int a) { return TL::NT / TL::tdim(a); }
-    __host__ __device__ static constexpr int poff(int a) {
-        return (a > 0 ? plane(0) : 0) + (a > 1 ? plane(1) : 0) + (a > 2 ? plane(2) : 0);
-    }
-    static constexpr int NPL = poff(D);
-    static_assert(NPL == (D >= 1 ? TL::NT / TL::T0 : 0) + (D >= 2 ? TL::NT / TL::T1 : 0) + (D >= 3 ? TL::NT / TL::T2 : 0),
-                  "one slot per cell of each tile face");
+    static constexpr int NPL = TL::NPL;
+    __host__ __device__ static constexpr int plane(int a) { return TL::plane(a); }
+    __host__ __device__ static constexpr int poff(int a) { return TL::poff(a); }
+    static_assert(TL::poff(D) == TL::NPL, "one slot per cell of each tile face");
     static constexpr size_t nV4 = (size_t)FacePack<D>::NV * TL::NFT;
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
@@ -1441,8 +1465,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         own_right[a] = qa[a] == g.n[a] - 1;
-        const int p = a == 0 ? la[1] + TL::T1 * la[2] : (a == 1 ? la[0] + TL::T0 * la[2] : la[0] + TL::T0 * la[1]);
-        pl[a] = FS::poff(a) * NM + p;
+        pl[a] = FS::poff(a) * NM + TL::plane_pos(a, la);
         int qr[3] = {qa[0], qa[1], qa[2]};
         qr[a] += 1;
         ff[a][0] = face_index(g, a, qa);
