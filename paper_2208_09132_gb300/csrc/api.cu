@@ -326,6 +326,10 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) g.fn[a][b] = g.n[b] + (a == b && a < D ? 1 : 0);
         g.nf[a] = (long long)g.fn[a][0] * g.fn[a][1] * g.fn[a][2];
+        if (g.nf[a] >= (1LL << 31)) {      // cell and face numbers are 32-bit in the kernels
+            delete h;
+            return fail(CDUGKS_ERR_INVALID, "problem too large");
+        }
     }
     // velocity tables (padding: xi = 0, w = 0)
     h->vel.assign(8 * (size_t)g.Nvp, 0.0);

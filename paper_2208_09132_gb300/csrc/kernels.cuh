@@ -1459,19 +1459,11 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     const size_t cell_ad = phi_addr(g, cell_index(g, qa), 0, 0);
     const size_t chunk_stride = (size_t)g.Nc * (2 * VC);
     bool own_right[3] = {false, false, false};
-    int pl[3] = {0, 0, 0};       // this cell's slot in the right-end sums of axis a
-    long long ff[3][2];          // global faces: left, right
-    int fl[3][2];                // local faces
+    int ff[3];                   // global left face per axis (the right one is ff + face stride; < 2^31)
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         own_right[a] = qa[a] == g.n[a] - 1;
-        pl[a] = FS::poff(a) * NM + TL::plane_pos(a, la);
-        int qr[3] = {qa[0], qa[1], qa[2]};
-        qr[a] += 1;
-        ff[a][0] = face_index(g, a, qa);
-        ff[a][1] = face_index(g, a, qr);
-        fl[a][0] = TL::face_local(a, la[0], la[1], la[2]);
-        fl[a][1] = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
+        ff[a] = (int)face_index(g, a, qa);
     }
     Kahan<T> acc[D][NM];         // the left faces
 #pragma unroll
@@ -1502,14 +1494,18 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
             Q F[2][2];           // [side][g|b]
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                const T* src = bf.face[a] + face_addr(g, a, ff[a][side], vt);
+                // the right face of axis a is the left face of the next cell along a
+                const int fs = a == 0 ? 1 : (a == 1 ? g.fn[1][0] : g.fn[2][0] * g.fn[2][1]);
+                const T* src = bf.face[a] + face_addr(g, a, ff[a] + side * fs, vt);
                 T gb[VC], bb[VC];
                 Chunk<T>::load(src, gb);
                 Chunk<T>::load(src + VC, bb);
+                const int fl = TL::face_local(a, la[0] + (a == 0 ? side : 0), la[1] + (a == 1 ? side : 0),
+                                              la[2] + (a == 2 ? side : 0));
                 T fcst[4 * NFCV];
 #pragma unroll
                 for (int j = 0; j < NFCV; ++j) {
-                    const Q qv = FC[j * NFT + fl[a][side]];
+                    const Q qv = FC[j * NFT + fl];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
                 }
@@ -1521,11 +1517,12 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 #pragma unroll
                     for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
                 } else if (own_right[a]) {
+                    const int pl = FS::poff(a) * NM + TL::plane_pos(a, la);
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
-                        Kahan<T> k = RS[pl[a] + m * FS::plane(a)];
+                        Kahan<T> k = RS[pl + m * FS::plane(a)];
                         k.add(sm[m]);
-                        RS[pl[a] + m * FS::plane(a)] = k;
+                        RS[pl + m * FS::plane(a)] = k;
                     }
                 }
             }
@@ -1547,11 +1544,13 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 #pragma unroll
     for (int a = 0; a < D; ++a) {
 #pragma unroll
-        for (int m = 0; m < NM; ++m) bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a][0]] = acc[a][m].value();
+        for (int m = 0; m < NM; ++m) bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a]] = acc[a][m].value();
         if (own_right[a]) {
+            const int fs = a == 0 ? 1 : (a == 1 ? g.fn[1][0] : g.fn[2][0] * g.fn[2][1]);
+            const int pl = FS::poff(a) * NM + TL::plane_pos(a, la);
 #pragma unroll
             for (int m = 0; m < NM; ++m)
-                bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a][1]] = RS[pl[a] + m * FS::plane(a)].value();
+                bf.mf[a][((size_t)grp * NM + m) * g.nf[a] + ff[a] + fs] = RS[pl + m * FS::plane(a)].value();
         }
     }
 }
