@@ -483,6 +483,30 @@ struct alignas(4 * sizeof(T)) V4 {
     T v[4];
 };
 
+// Asynchronous global -> shared copies (cp.async): one VC chunk (16-byte
+// pieces; both addresses 16-byte aligned by the layouts) or one element.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(__cvta_generic_to_global(gsrc))
+                 : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_chunk(V4<T>* sdst, const T* gsrc) {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(V4<T>) / 16); ++i)
+        cp_async16(reinterpret_cast<char*>(sdst) + 16 * i, reinterpret_cast<const char*>(gsrc) + 16 * i);
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(__cvta_generic_to_global(gsrc)),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+
 // Sweep modes.  The low two bits say where sweep A (and a recomputing sweep
 // B) takes phibar+ and the slopes from: 0 forms both on the halo box itself;
 // 1 (prepared) loads phibar+ formed by k_prep and forms the slopes; 2 (stored)
@@ -512,16 +536,18 @@ struct Smem {
     // CTAs per SM that a dynamic shared-memory size allows, and the limit of threads and >= 80 registers
     __host__ __device__ static constexpr int fit(size_t b) { return (int)((size_t)(228 * 1024) / (b + 1024)); }
     static constexpr int lim = (2048 / TL::NT) < (65536 / (TL::NT * 80)) ? (2048 / TL::NT) : (65536 / (TL::NT * 80));
-    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A, one P
-    static constexpr bool dbl_fits = fit(a1 + nP * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
-    // Sweep A of the shapes that form phibar+ in phase 1 alternates two phibar+
-    // arrays between chunks (where that costs no occupancy), which lets it drop
-    // the barrier at the end of a chunk.
-    __host__ __device__ static constexpr bool double_p(bool B) {
-        return !B && mode_source(MODE) != MODE_STORED && dbl_fits;
+    static constexpr size_t nST = (size_t)2 * TL::BOX;      // staged phi* chunk (g, b) per box cell
+    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A
+    static constexpr bool st_fits = fit(a1 + nST * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
+    // Sweep A of the fused shapes stages the next chunk's phi* of its halo box in
+    // shared memory with asynchronous copies (where that costs no occupancy), so
+    // the loads overlap phases 2-3 of the current chunk.
+    __host__ __device__ static constexpr bool stage(bool B) {
+        return !B && mode_source(MODE) == MODE_FUSED && st_fits;
     }
-    __host__ __device__ static constexpr size_t nPB(bool B) { return double_p(B) ? 2 * nP : nP; }
-    __host__ __device__ static constexpr size_t vcount(bool B) { return nPB(B) + nS + nCC + (B ? nFF + nFC : 0); }
+    __host__ __device__ static constexpr size_t vcount(bool B) {
+        return nP + nS + nCC + (B ? nFF + nFC : 0) + (stage(B) ? nST : 0);
+    }
     __host__ __device__ static constexpr size_t bytes(bool B) {
         return vcount(B) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;
     }
@@ -936,12 +962,13 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    constexpr bool DBL = SM::double_p(SWEEP_B);
-    Q* const P0 = reinterpret_cast<Q*>(smem);     // [1 or 2][2][PN] phibar+ chunk per cell
-    Q* const S = P0 + SM::nPB(SWEEP_B);           // [D][2][SB] half van Leer slopes times dx
+    constexpr bool STAGE = SM::stage(SWEEP_B);
+    Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
+    Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
     Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
+    Q* const ST = CC + SM::nCC + (SWEEP_B ? SM::nFF + SM::nFC : 0);   // [2][BOX] staged phi* (STAGE)
     Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
     int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B) + SM::rs_bytes);
     int* const cfl = csrc + BOX;
@@ -1041,8 +1068,36 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     __syncthreads();
     constexpr int NH = TL::NH;
 
+    // Asynchronous copies of chunk vt's phi* for the box cells this thread forms
+    // in phase 1 (its own cell and its halo cells), into its own ST slots: a
+    // mirror image takes the reflected velocities element by element, a
+    // Dirichlet ghost needs none.  Each thread reads back only what it copied.
+    auto fetch = [&](int vt) {
+        auto one = [&](int k) {
+            const int fl = cfl[k];
+            if (fl & 8) return;
+            const long long c = csrc[k];
+            if (fl & 7) {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    const int is = bf.refl[(fl & 7) * g.Nvp + vt * VC + v];
+                    cp_async_elem(&ST[k].v[v], bf.phi_in + phi_addr(g, c, is, 0));
+                    cp_async_elem(&ST[BOX + k].v[v], bf.phi_in + phi_addr(g, c, is, 1));
+                }
+            } else {
+                const size_t ad = phi_addr(g, c, vt * VC, 0);
+                cp_async_chunk(&ST[k], bf.phi_in + ad);
+                cp_async_chunk(&ST[BOX + k], bf.phi_in + ad + VC);
+            }
+        };
+        one(kc);
+        for (int h = t; h < NH; h += TL::NT) one(halo[h]);
+        cp_async_commit();
+    };
+    if (STAGE && vt0 < vt1) fetch(vt0);
+
     for (int vt = vt0; vt < vt1; ++vt) {
-        Q* const P = DBL && (vt & 1) ? P0 + SM::nP : P0;   // this chunk's phibar+ array
+        if (STAGE) cp_async_wait_all();            // this thread's copies of chunk vt have landed
         // velocity records of the chunk (same for every thread); nu = 2 h xi / dx
         T xi[VC][D], nu[VC][D], w[VC], hx[VC];
 #pragma unroll
@@ -1086,6 +1141,13 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             if (fl & 8) {
 #pragma unroll
                 for (int v = 0; v < VC; ++v) gs[v] = bs[v] = T(0);
+            } else if (STAGE) {
+                const Q sg = ST[k], sb = ST[BOX + k];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    gs[v] = sg.v[v];
+                    bs[v] = sb.v[v];
+                }
             } else if (fl & 7) {
 #pragma unroll
                 for (int v = 0; v < VC; ++v) {
@@ -1210,6 +1272,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         } else {
             cell(kc, valid);
             for (int h = t; h < NH; h += TL::NT) cell(halo[h], false);
+            if (STAGE && vt + 1 < vt1) fetch(vt + 1);    // this thread's slots are read: refill them
         }
         __syncthreads();
 
@@ -1377,11 +1440,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                                      bf.phi_out + phi_addr(g, cell_index(g, qa), vt * VC, 0));
             }
         }
-        // Before the next chunk overwrites P and S.  With two P arrays this is not
-        // needed: a thread writes S of chunk vt+1 only after the barrier behind its
-        // phase 1, which the others reach after their phase 3 of chunk vt, and its
-        // phase-1 writes go to the array that chunk vt-1 used.
-        if (!DBL) __syncthreads();
+        __syncthreads();   // before the next chunk overwrites P and S
     }
 
     // ---- epilogue: this group's partial face sums
