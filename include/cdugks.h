@@ -127,8 +127,20 @@ CDUGKS_API int cdugks_bind(cdugks_t *h, void *device_ptr, size_t bytes, void *cu
 CDUGKS_API int cdugks_init(cdugks_t *h, const double *rho_u_T);
 
 /* Enqueue nsteps time steps of Sec. 2.1 on the bound stream (asynchronous).
+ * With a captured graph (cdugks_capture) whole multiples of its step count
+ * are replayed from it, the rest launched one by one; results are the same.
  * Errors: UNBOUND, INVALID (nsteps < 0), CUDA (launch failure). */
 CDUGKS_API int cdugks_step(cdugks_t *h, int nsteps);
+
+/* Capture steps_per_graph time steps in CUDA graphs (one per parity of the
+ * ping-pong state buffer the replay starts from) so that later cdugks_step
+ * calls replay them: one launch per steps_per_graph steps instead of 4 + D,
+ * which matters for small problems whose steps last microseconds.  0 drops
+ * the graphs.  Needs a non-default stream; changing the tile shape or the
+ * velocity groups, or binding again, drops the graphs.  Capturing enqueues
+ * no work.  Errors: UNBOUND, INVALID (steps_per_graph outside [0, 4096] or
+ * the default stream), CUDA. */
+CDUGKS_API int cdugks_capture(cdugks_t *h, int steps_per_graph);
 
 /* Advance nsteps steps exactly as cdugks_step does, timing each phase with
  * CUDA events on the bound stream: ms_out[0..3] = mean milliseconds per step

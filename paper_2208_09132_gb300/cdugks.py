@@ -20,7 +20,8 @@ RULE_TRAPEZOID, RULE_BOOLE = 0, 1
 FP64, FP32 = 0, 1
 
 EXPORTS = [
-    "cdugks_create", "cdugks_workspace_bytes", "cdugks_bind", "cdugks_init", "cdugks_step", "cdugks_profile_step",
+    "cdugks_create", "cdugks_workspace_bytes", "cdugks_bind", "cdugks_init", "cdugks_step", "cdugks_capture",
+    "cdugks_profile_step",
     "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
@@ -84,6 +85,7 @@ def load(build_if_needed: bool = True):
         "cdugks_bind": (i, [vp, vp, sz, vp]),
         "cdugks_init": (i, [vp, dp]),
         "cdugks_step": (i, [vp, i]),
+        "cdugks_capture": (i, [vp, i]),
         "cdugks_profile_step": (i, [vp, i, dp]),
         "cdugks_sync_status": (i, [vp]),
         "cdugks_moments": (i, [vp, dp]),
@@ -217,6 +219,10 @@ class Solver:
 
     def step(self, nsteps: int = 1):
         _check(self._lib.cdugks_step(self._h, int(nsteps)))
+
+    def capture(self, steps_per_graph: int):
+        """Replay whole multiples of steps_per_graph steps from CUDA graphs (0 drops them)."""
+        _check(self._lib.cdugks_capture(self._h, int(steps_per_graph)))
 
     def profile_step(self, nsteps: int):
         """Advance nsteps steps; mean ms per step of (sweep A, face constants, sweep B, W update)."""

@@ -80,6 +80,10 @@ struct cdugks {
     std::vector<double> vel;  // [Nvp][8]: xi_0, xi_1, xi_2, w, |xi|^2/2, 0, 0, 0
     std::vector<float> vel32; // the same table rounded to float (FP32 storage)
     std::vector<int> refl;    // [8][Nvp]
+    // captured steps (cdugks_capture): one graph per parity of the state buffer it starts from
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_steps = 0;
 };
 
 namespace {
@@ -194,6 +198,16 @@ Bufs<T> bufs(const cdugks* h, int in) {
     b.refl = reinterpret_cast<const int*>(p + L.refl);
     b.status = reinterpret_cast<int*>(p + L.status);
     return b;
+}
+
+void drop_graphs(cdugks* h) {
+    for (int c = 0; c < 2; ++c) {
+        if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
+        if (h->graph[c]) cudaGraphDestroy(h->graph[c]);
+        h->gexec[c] = nullptr;
+        h->graph[c] = nullptr;
+    }
+    h->graph_steps = 0;
 }
 
 template <typename T>
@@ -404,6 +418,7 @@ int cdugks_set_velocity_groups(cdugks_t* h, int groups) {
         h->gcap = G;
         make_layout(h);
     }
+    drop_graphs(h);
     h->gsel = groups;
     set_groups(h, G);
     if (h->bound) return upload_inst(h);
@@ -433,6 +448,7 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
                 return fail(CDUGKS_ERR_INVALID, "stored-slope shapes support periodic and specular boundaries only");
+    drop_graphs(h);
     const int need = buffers_of(mode);
     if (need & ~h->bufs_cap) {
         if (h->bound)
@@ -462,6 +478,7 @@ int cdugks_workspace_bytes(const cdugks_t* h, size_t* bytes) {
 
 int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) {
     if (!h || !device_ptr) return fail(CDUGKS_ERR_INVALID, "null argument");
+    drop_graphs(h);
     if (((uintptr_t)device_ptr) % kAlign) return fail(CDUGKS_ERR_INVALID, "workspace must be 256-byte aligned");
     if (bytes < h->lay.total) return fail(CDUGKS_ERR_OOM, "workspace smaller than cdugks_workspace_bytes");
     cudaPointerAttributes attr;
@@ -522,18 +539,63 @@ int cdugks_init(cdugks_t* h, const double* rho_u_T) {
     return CDUGKS_OK;
 }
 
+namespace {
+cudaError_t launch_one_step(cdugks* h) {
+    if (h->prec == CDUGKS_FP32) return cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream);
+    return cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream);
+}
+}  // namespace
+
 int cdugks_step(cdugks_t* h, int nsteps) {
     int rc = check_ready(h, true);
     if (rc) return rc;
     if (nsteps < 0) return fail(CDUGKS_ERR_INVALID, "nsteps < 0");
-    for (int s = 0; s < nsteps; ++s) {
-        cudaError_t e;
-        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream);
-        else e = cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream);
-        if (e) return cuda_fail(e, "step launch");
+    int done = 0;
+    cudaError_t e;
+    if (h->graph_steps > 0)
+        for (; done + h->graph_steps <= nsteps; done += h->graph_steps) {
+            if ((e = cudaGraphLaunch(h->gexec[h->cur], h->stream))) return cuda_fail(e, "cudaGraphLaunch");
+            h->cur ^= h->graph_steps & 1;
+            h->steps += h->graph_steps;
+        }
+    for (; done < nsteps; ++done) {
+        if ((e = launch_one_step(h))) return cuda_fail(e, "step launch");
         h->cur = 1 - h->cur;
         h->steps += 1;
     }
+    return CDUGKS_OK;
+}
+
+int cdugks_capture(cdugks_t* h, int steps_per_graph) {
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    if (steps_per_graph < 0 || steps_per_graph > 4096) return fail(CDUGKS_ERR_INVALID, "steps_per_graph in [0, 4096]");
+    drop_graphs(h);
+    if (steps_per_graph == 0) return CDUGKS_OK;
+    if (!h->stream) return fail(CDUGKS_ERR_INVALID, "graph capture needs a non-default stream");
+    const int cur0 = h->cur;
+    for (int c = 0; c < 2; ++c) {          // a graph for each parity the state can start from
+        h->cur = c;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e) {
+            h->cur = cur0;
+            drop_graphs(h);
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        for (int s = 0; s < steps_per_graph && e == cudaSuccess; ++s) {
+            e = launch_one_step(h);
+            h->cur = 1 - h->cur;
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(h->stream, &h->graph[c]);
+        if (!e && !e2) e = cudaGraphInstantiate(&h->gexec[c], h->graph[c], 0);
+        if (e || e2) {
+            h->cur = cur0;
+            drop_graphs(h);
+            return cuda_fail(e ? e : e2, "capture steps");
+        }
+    }
+    h->cur = cur0;
+    h->graph_steps = steps_per_graph;
     return CDUGKS_OK;
 }
 
@@ -759,7 +821,11 @@ int cdugks_info(const cdugks_t* h, cdugks_info_t* info) {
     return CDUGKS_OK;
 }
 
-void cdugks_destroy(cdugks_t* h) { delete h; }
+void cdugks_destroy(cdugks_t* h) {
+    if (!h) return;
+    drop_graphs(h);
+    delete h;
+}
 
 const char* cdugks_strerror(int code) {
     switch (code) {

@@ -172,6 +172,34 @@ def test_checkpoint_restart_is_bitwise(precision):
     assert a.get_state() == b.get_state()
 
 
+@pytest.mark.parametrize("precision", [cdugks.FP64, cdugks.FP32])
+@pytest.mark.parametrize("graph_steps", [3, 4])
+def test_graph_replay_is_bitwise(precision, graph_steps):
+    """Steps replayed from captured graphs (odd and even step counts, both
+    parities of the starting buffer, remainders launched one by one) equal
+    steps launched one at a time."""
+    cfg, f = wl.random_smooth(dim=2, n=(20, 12), nv=(8, 8), seed=15, amp=0.3, kn=3e-3)
+    a = cdugks.Solver(cfg, precision=precision)
+    a.init(f)
+    a.step(1)
+    a.step(13)
+    import torch
+    b = cdugks.Solver(cfg, precision=precision, stream=torch.cuda.Stream())   # capture needs its own stream
+    b.init(f)
+    b.step(1)                      # start the replays from the other buffer
+    b.capture(graph_steps)
+    b.step(5)
+    b.step(8)
+    assert b.sync_status() == 0
+    assert b.info().steps == a.info().steps == 14
+    assert np.array_equal(a.moments(), b.moments())
+    assert a.get_state() == b.get_state()
+    b.capture(0)                   # dropped: plain launches again
+    a.step(2)
+    b.step(2)
+    assert a.get_state() == b.get_state()
+
+
 def test_status_flags_report_a_broken_state():
     cfg, f = wl.random_smooth(dim=1, n=(32,), nv=(16,), seed=14, amp=0.2, kn=3e-3)
     s = cdugks.Solver(cfg, precision=cdugks.FP64)
