@@ -78,6 +78,7 @@ def _load():
         for name in ("oracle_moments", "oracle_conserved", "oracle_discrete_moments"):
             getattr(lib, name).argtypes = [ctypes.c_void_p, dp]
         lib.oracle_distributions.argtypes = [ctypes.c_void_p, dp, dp]
+        lib.oracle_stress_heat_flux.argtypes = [ctypes.c_void_p, dp]
         lib.oracle_equilibrium.argtypes = [ctypes.c_void_p, d, dp, d, dp, dp]
         lib.oracle_set_state.argtypes = [ctypes.c_void_p, dp, dp, dp]
         lib.oracle_face_W.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
@@ -181,6 +182,13 @@ class Oracle:
         out = np.zeros((self.Nc, 2 + self.D))
         self._lib.oracle_discrete_moments(self._h, _ptr(out))
         return out
+
+    def stress_heat_flux(self):
+        """Per cell: pressure tensor P [Nc, D, D] and heat flux q [Nc, D] of the distributions."""
+        D = self.D
+        out = np.zeros((self.Nc, D * D + D))
+        self._lib.oracle_stress_heat_flux(self._h, _ptr(out))
+        return out[:, : D * D].reshape(self.Nc, D, D), out[:, D * D:]
 
     def distributions(self):
         g = np.zeros((self.Nc, self.Nv))

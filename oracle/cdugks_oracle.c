@@ -649,6 +649,52 @@ void oracle_discrete_moments(const oracle_t *o, double *out) {
     }
 }
 
+/* Pressure tensor and heat flux of every cell from its distributions (a
+ * diagnostic; the scheme itself does not use them).  With rho = sum w g,
+ * rho u = sum w xi g and rho E = sum w b (the moments of Sec. 2), the pressure
+ * tensor is the central second moment P_ab = sum w (xi - u)_a (xi - u)_b g,
+ * and the heat flux q is what the flux of total energy sum w xi_a b carries
+ * beyond convection and pressure work:
+ *     q_a = sum w xi_a b - u_a rho E - sum_b P_ab u_b.
+ * out: [Nc][D*D + D], P row-major, then q. */
+void oracle_stress_heat_flux(const oracle_t *o, double *out) {
+    int D = o->D;
+    long Nv = o->Nv;
+    for (long ic = 0; ic < o->Nc; ++ic) {
+        long c = interior_ext(o, ic);
+        const double *g = &o->g[c * Nv], *b = &o->b[c * Nv];
+        nsum m0, m1[3], mE, mF[3], mP[3][3];
+        memset(&m0, 0, sizeof(m0));
+        memset(m1, 0, sizeof(m1));
+        memset(&mE, 0, sizeof(mE));
+        memset(mF, 0, sizeof(mF));
+        memset(mP, 0, sizeof(mP));
+        for (long i = 0; i < Nv; ++i) {
+            nsum_add(&m0, o->w[i] * g[i]);
+            nsum_add(&mE, o->w[i] * b[i]);
+            for (int a = 0; a < D; ++a) {
+                nsum_add(&m1[a], o->w[i] * o->xi[3 * i + a] * g[i]);
+                nsum_add(&mF[a], o->w[i] * o->xi[3 * i + a] * b[i]);
+            }
+        }
+        double rho = nsum_val(&m0), u[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) u[a] = nsum_val(&m1[a]) / rho;
+        for (long i = 0; i < Nv; ++i)
+            for (int a = 0; a < D; ++a)
+                for (int bb = 0; bb < D; ++bb)
+                    nsum_add(&mP[a][bb], o->w[i] * (o->xi[3 * i + a] - u[a]) * (o->xi[3 * i + bb] - u[bb]) * g[i]);
+        double *dst = &out[ic * (D * D + D)];
+        for (int a = 0; a < D; ++a)
+            for (int bb = 0; bb < D; ++bb) dst[a * D + bb] = nsum_val(&mP[a][bb]);
+        double rhoE = nsum_val(&mE);
+        for (int a = 0; a < D; ++a) {
+            double q = nsum_val(&mF[a]) - u[a] * rhoE;
+            for (int bb = 0; bb < D; ++bb) q -= dst[a * D + bb] * u[bb];
+            dst[D * D + a] = q;
+        }
+    }
+}
+
 /* Equilibria g_eq, b_eq at every node for one state (eqs. geq, beq). */
 void oracle_equilibrium(const oracle_t *o, double rho, const double *u, double T, double *geq, double *beq) {
     double uu[3] = {0, 0, 0};

@@ -43,6 +43,7 @@ void oracle_moments(const oracle_t *o, double *out);          /* [Nc][2+D] rho,u
 void oracle_conserved(const oracle_t *o, double *out);        /* [Nc][2+D] W */
 void oracle_distributions(const oracle_t *o, double *g, double *b);   /* [Nc][Nv] */
 void oracle_discrete_moments(const oracle_t *o, double *out); /* [Nc][2+D] */
+void oracle_stress_heat_flux(const oracle_t *o, double *out); /* [Nc][D*D+D]: P row-major, q */
 void oracle_equilibrium(const oracle_t *o, double rho, const double *u, double T, double *geq, double *beq);
 int oracle_set_state(oracle_t *o, const double *g, const double *b, const double *W);
 void oracle_face_W(const oracle_t *o, int a, double *out);

@@ -101,6 +101,62 @@ def test_equilibrium_moments(oracle_mod, D, K):
     assert abs((w * be).sum() - rhoE) < 1e-12 * rhoE
 
 
+# ------------------------------------------------- stress and heat-flux diagnostic
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_stress_and_heat_flux_of_a_drifting_maxwellian(oracle_mod, D):
+    """A Maxwellian has P_ab = rho R T delta_ab and q = 0, whatever its drift."""
+    nv = {1: 96, 2: 48, 3: 28}[D]
+    rho, T = 1.3, 1.7
+    u = (0.4, -0.3, 0.2)
+    cfg, f = wl.uniform(dim=D, n=(3, 2, 2), nv=(nv, nv, nv), vmax=9.0, u=u, T=T, rho=rho)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    P, q = o.stress_heat_flux()
+    RT = R * T
+    assert np.abs(P - rho * RT * np.eye(D)).max() < 1e-11 * rho * RT
+    # |q| against the energy flux rho E |u|, which the formula subtracts
+    assert np.abs(q).max() < 1e-11 * rho * (0.5 * np.dot(u[:D], u[:D]) + 2.0 * RT) * 0.5
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_stress_and_heat_flux_are_galilean_invariant(oracle_mod, D):
+    """A non-equilibrium state and its copy moving at U (velocity grid shifted
+    by U, b carrying the kinetic energy of the shift) have the same P and q;
+    a slip in any drift term (-rho u u, -u rho E, -P u) breaks this."""
+    nv = {1: 64, 2: 40}[D]
+    U = np.array([0.7, -0.45])[:D]
+    cfgs = []
+    for shift in (np.zeros(D), U):
+        c, f = wl.uniform(dim=D, n=(2, 1, 1), nv=(nv, nv, nv), vmax=9.0)
+        c = dict(c)
+        c["vlo"] = [c["vlo"][a] + (shift[a] if a < D else 0.0) for a in range(3)]
+        c["vhi"] = [c["vhi"][a] + (shift[a] if a < D else 0.0) for a in range(3)]
+        cfgs.append((c, f))
+    res = []
+    for (c, f), shift in zip(cfgs, (np.zeros(D), U)):
+        o = oracle_mod.Oracle(c)
+        o.init(f)
+        xi, w = o.velocities()
+        xr = xi[:, :D] - shift                 # velocities relative to the frame of the state
+        T0 = 1.2
+        m = np.exp(-(xr ** 2).sum(1) / (2 * R * T0))
+        pert = 1 + 0.2 * xr[:, 0] * (xr ** 2).sum(1) / (R * T0) - 0.1 * xr[:, 0] * xr[:, -1]
+        g_rel = m * pert
+        b_rel = (0.5 * (xr ** 2).sum(1) + 0.8) * g_rel * (1 + 0.15 * xr[:, -1])
+        # total-energy distribution in the frame of the grid: + (xi_rel . U + |U|^2/2) g
+        b = b_rel + (xr @ shift + 0.5 * shift @ shift) * g_rel
+        Nc = o.Nc
+        g2, b2 = np.tile(g_rel, (Nc, 1)), np.tile(b, (Nc, 1))
+        o.set_state(g2, b2, np.zeros((Nc, 2 + D)))
+        res.append(o.stress_heat_flux())
+    (P0, q0), (P1, q1) = res
+    assert np.abs(q0).max() > 1e-2                     # a state with a real heat flux
+    assert np.abs(P0[:, 0, 0] - P0[:, -1, -1]).max() > 1e-3 or D == 1
+    assert np.abs(P1 - P0).max() < 1e-11 * np.abs(P0).max()
+    assert np.abs(q1 - q0).max() < 1e-11 * np.abs(q0).max()
+
+
 # ----------------------------------------------------------------- fixed point
 
 @pytest.mark.parametrize("D,nsteps,nv", [(1, 1000, 24), (2, 100, 12), (3, 10, 8)])
