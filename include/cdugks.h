@@ -158,6 +158,16 @@ CDUGKS_API int cdugks_sync_status(cdugks_t *h);
  * Synchronous (device-to-host copy of Nc*(2+D) doubles). */
 CDUGKS_API int cdugks_moments(cdugks_t *h, double *out);
 
+/* Pressure tensor and heat flux of every cell from its distributions at the
+ * current time level (a diagnostic; the step does not use them).  With rho,
+ * rho u, rho E the moments of g and b (Sec. 2):
+ *     P_ab = sum_i w_i (xi - u)_a (xi - u)_b g_i,
+ *     q_a  = sum_i w_i xi_a b_i - u_a rho E - sum_b P_ab u_b
+ * (the total-energy flux less convection and pressure work).  Host
+ * out[Nc][D*D + D]: P row-major, then q; sums in FP64 on the device.
+ * Synchronous.  Errors: UNBOUND, INVALID (null out), CUDA. */
+CDUGKS_API int cdugks_stress_heat_flux(cdugks_t *h, double *out);
+
 /* The tracked conserved variables W: host out[Nc][2+D]. Synchronous. */
 CDUGKS_API int cdugks_conserved(cdugks_t *h, double *out);
 

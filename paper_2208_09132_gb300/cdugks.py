@@ -22,7 +22,7 @@ FP64, FP32 = 0, 1
 EXPORTS = [
     "cdugks_create", "cdugks_workspace_bytes", "cdugks_bind", "cdugks_init", "cdugks_step", "cdugks_capture",
     "cdugks_profile_step",
-    "cdugks_sync_status", "cdugks_moments", "cdugks_conserved", "cdugks_distributions",
+    "cdugks_sync_status", "cdugks_moments", "cdugks_stress_heat_flux", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
     "cdugks_set_velocity_groups", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
     "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
@@ -89,6 +89,7 @@ def load(build_if_needed: bool = True):
         "cdugks_profile_step": (i, [vp, i, dp]),
         "cdugks_sync_status": (i, [vp]),
         "cdugks_moments": (i, [vp, dp]),
+        "cdugks_stress_heat_flux": (i, [vp, dp]),
         "cdugks_conserved": (i, [vp, dp]),
         "cdugks_distributions": (i, [vp, dp, dp]),
         "cdugks_state_bytes": (i, [vp, P(sz)]),
@@ -238,6 +239,13 @@ class Solver:
             out = np.empty((self.Nc, 2 + self.D))
         _check(self._lib.cdugks_moments(self._h, _dptr(out)))
         return out
+
+    def stress_heat_flux(self):
+        """Per cell: pressure tensor P [Nc, D, D] and heat flux q [Nc, D] of the distributions."""
+        D = self.D
+        out = np.empty((self.Nc, D * D + D))
+        _check(self._lib.cdugks_stress_heat_flux(self._h, _dptr(out)))
+        return out[:, : D * D].reshape(self.Nc, D, D), out[:, D * D:]
 
     def conserved(self) -> np.ndarray:
         out = np.empty((self.Nc, 2 + self.D))

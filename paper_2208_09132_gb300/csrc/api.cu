@@ -169,7 +169,7 @@ void make_layout(cdugks* h) {
     }
     L.vel = take(h->elt * 8 * g.Nvp);
     L.refl = take(sizeof(int) * 8 * g.Nvp);
-    L.io = take(sizeof(double) * NM * g.Nc);
+    L.io = take(sizeof(double) * std::max(NM, g.D * g.D + g.D) * g.Nc);   // moments, or P and q
     L.status = take(256);
     L.inst = take(std::max(sizeof(Inst<float>), sizeof(Inst<double>)));
     L.total = off;
@@ -660,6 +660,23 @@ static int fetch_cells(cdugks_t* h, double* out, int conserved) {
 }
 
 int cdugks_moments(cdugks_t* h, double* out) { return fetch_cells(h, out, 0); }
+
+int cdugks_stress_heat_flux(cdugks_t* h, double* out) {
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!out) return fail(CDUGKS_ERR_INVALID, "null output");
+    const Geo& g = h->g;
+    double* io = reinterpret_cast<double*>(h->base + h->lay.io);
+    cudaError_t e;
+    if (h->prec == CDUGKS_FP32) e = cdg::launch_stress_f32(g, dinst<float>(h), h->cur, io, h->stream);
+    else e = cdg::launch_stress_f64(g, dinst<double>(h), h->cur, io, h->stream);
+    if (e) return cuda_fail(e, "stress kernel");
+    if ((e = cudaMemcpyAsync(out, io, sizeof(double) * (g.D * g.D + g.D) * g.Nc, cudaMemcpyDeviceToHost,
+                             h->stream)))
+        return cuda_fail(e, "download stress and heat flux");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "stress and heat flux");
+    return CDUGKS_OK;
+}
 int cdugks_conserved(cdugks_t* h, double* out) { return fetch_cells(h, out, 1); }
 
 int cdugks_distributions(cdugks_t* h, double* gout, double* bout) {

@@ -1811,6 +1811,82 @@ __global__ void k_moments(Geo g, const double* __restrict__ W, double* __restric
     out[(size_t)c * NM + 1 + D] = mc.T;
 }
 
+// Pressure tensor and heat flux of every cell from its finalised distributions
+// (a diagnostic output; the step does not use them).  One CTA per cell sums
+// the raw moments over the velocities in FP64 (tree of fixed order), then
+//   P_ab = sum w xi_a xi_b g - rho u_a u_b  (= sum w (xi - u)_a (xi - u)_b g),
+//   q_a  = sum w xi_a b - u_a rho E - sum_b P_ab u_b,
+// with rho, rho u, rho E the moments of the same distributions.
+// out: [Nc][D*D + D], P row-major, then q.
+constexpr int kStressThreads = 128;
+template <typename T, int D>
+__global__ void __launch_bounds__(kStressThreads) k_stress(const Inst<T>* __restrict__ in, int cur,
+                                                           double* __restrict__ out) {
+    constexpr int NA = 1 + D + D * (D + 1) / 2 + 1 + D;     // rho, rho u, second moments, rho E, energy flux
+    __shared__ double red[NA][kStressThreads];
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
+    const long long c = blockIdx.x;
+    const int t = threadIdx.x;
+    const CellC<T> cc = bf.cellc[c];
+    double acc[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+    for (int i = t; i < g.Nvp; i += kStressThreads) {
+        const Vel<T, D> v = load_vel<T, D>(g, bf, i);
+        T ge, be;
+        equilibrium<T, D>(cc, v, ge, be);
+        const size_t ad = phi_addr(g, c, i, 0);
+        const double gv = (double)fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
+        const double bv = (double)fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);
+        const double wg = (double)v.w * gv, wb = (double)v.w * bv;
+        int k = 0;
+        acc[k++] += wg;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[k++] += (double)v.xi[a] * wg;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b2 = a; b2 < D; ++b2) acc[k++] += (double)v.xi[a] * (double)v.xi[b2] * wg;
+        acc[k++] += wb;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[k++] += (double)v.xi[a] * wb;
+    }
+#pragma unroll
+    for (int k = 0; k < NA; ++k) red[k][t] = acc[k];
+    __syncthreads();
+    for (int s2 = kStressThreads / 2; s2 > 0; s2 >>= 1) {
+        if (t < s2)
+#pragma unroll
+            for (int k = 0; k < NA; ++k) red[k][t] += red[k][t + s2];
+        __syncthreads();
+    }
+    if (t != 0) return;
+    const double rho = red[0][0];
+    double u[D], P[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = red[1 + a][0] / rho;
+    int k = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b2 = a; b2 < D; ++b2) {
+            P[a][b2] = red[k++][0] - rho * u[a] * u[b2];
+            P[b2][a] = P[a][b2];
+        }
+    const double rhoE = red[k++][0];
+    double* dst = out + (size_t)c * (D * D + D);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) dst[a * D + b2] = P[a][b2];
+        double q = red[k + a][0] - u[a] * rhoE;
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) q -= P[a][b2] * u[b2];
+        dst[D * D + a] = q;
+    }
+}
+
 // The finalised distributions phi = fa phi* + fb phi_eq at the current time
 // level, written in the state layout into the idle buffer.
 template <typename T, int D>

@@ -52,6 +52,9 @@ cudaError_t launch_init_f64(const Geo& g, const Inst<double>* in, int cur, const
 // Cell constants from the stored W.
 cudaError_t launch_cellc_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s);
 cudaError_t launch_cellc_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s);
+// Pressure tensor and heat flux per cell into out[Nc][D*D + D] (device).
+cudaError_t launch_stress_f32(const Geo& g, const Inst<float>* in, int cur, double* out, cudaStream_t s);
+cudaError_t launch_stress_f64(const Geo& g, const Inst<double>* in, int cur, double* out, cudaStream_t s);
 // Finalised distributions into phi_out.
 cudaError_t launch_finalise_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s);
 cudaError_t launch_finalise_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s);

@@ -34,6 +34,9 @@ cudaError_t launch_init_f32(const Geo& g, const Inst<float>* in, int cur, const 
 cudaError_t launch_cellc_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s) {
     return run_cellc<float>(g, in, cur, s);
 }
+cudaError_t launch_stress_f32(const Geo& g, const Inst<float>* in, int cur, double* out, cudaStream_t s) {
+    return run_stress<float>(g, in, cur, out, s);
+}
 cudaError_t launch_finalise_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s) {
     return run_finalise<float>(g, in, cur, s);
 }

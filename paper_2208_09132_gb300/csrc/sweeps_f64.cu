@@ -33,6 +33,9 @@ cudaError_t launch_init_f64(const Geo& g, const Inst<double>* in, int cur, const
 cudaError_t launch_cellc_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s) {
     return run_cellc<double>(g, in, cur, s);
 }
+cudaError_t launch_stress_f64(const Geo& g, const Inst<double>* in, int cur, double* out, cudaStream_t s) {
+    return run_stress<double>(g, in, cur, out, s);
+}
 cudaError_t launch_finalise_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s) {
     return run_finalise<double>(g, in, cur, s);
 }

@@ -219,6 +219,17 @@ cudaError_t run_cellc(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s) 
 }
 
 template <typename T>
+cudaError_t run_stress(const Geo& g, const Inst<T>* in, int cur, double* out, cudaStream_t s) {
+    const dim3 grid((unsigned)g.Nc);
+    switch (g.D) {
+        case 1: k_stress<T, 1><<<grid, kStressThreads, 0, s>>>(in, cur, out); break;
+        case 2: k_stress<T, 2><<<grid, kStressThreads, 0, s>>>(in, cur, out); break;
+        default: k_stress<T, 3><<<grid, kStressThreads, 0, s>>>(in, cur, out); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t run_finalise(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s) {
     const dim3 grid((unsigned)g.Nc);
     switch (g.D) {

@@ -172,6 +172,30 @@ def test_checkpoint_restart_is_bitwise(precision):
     assert a.get_state() == b.get_state()
 
 
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+@pytest.mark.parametrize("name", ["1d_sod_specular", "2d_kh_small", "3d_shear_small"])
+def test_stress_and_heat_flux_match_oracle(oracle_mod, name, precision, tol):
+    """The per-cell pressure tensor and heat flux after a few steps.  Scales:
+    max |P| for P; for q the energy-flux magnitude it is the remainder of,
+    max|P| times the largest |xi| of the grid."""
+    (cfg, f), steps = case(name)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    Po, qo = o.stress_heat_flux()
+    s = cdugks.Solver(cfg, precision=precision)
+    s.init(f)
+    s.step(steps)
+    assert s.sync_status() == 0
+    Pg, qg = s.stress_heat_flux()
+    xi, _ = o.velocities()
+    sP = np.abs(Po).max()
+    sq = sP * np.abs(xi).max()
+    assert np.abs(Pg - Po).max() <= tol * sP, np.abs(Pg - Po).max() / sP
+    assert np.abs(qg - qo).max() <= tol * sq, np.abs(qg - qo).max() / sq
+    assert np.abs(qo).max() > 1e-6 * sq                       # a real heat flux to compare
+
+
 @pytest.mark.parametrize("precision", [cdugks.FP64, cdugks.FP32])
 @pytest.mark.parametrize("graph_steps", [3, 4])
 def test_graph_replay_is_bitwise(precision, graph_steps):
