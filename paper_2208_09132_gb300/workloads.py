@@ -166,6 +166,23 @@ def gresho(n=100, nv=101, kn=1e-4, Pr=2.0 / 3.0, K=2.0, cfl=0.8, steps=1, vmax=1
     return cfg, _fields(rho, [ux, uy], p / (rho * R_GAS))
 
 
+def sine_wave(nx=128, nv=129, T0=0.1, mu_ref=1e-5, rho0=1.0, v0=1.0, K=2.0, Pr=2.0 / 3.0, cfl=0.5, vmax=6.0,
+              rule=RULE_BOOLE, t_end=0.1):
+    """Sine-wave perturbation (Sec. 3.7): rho = rho0, v = v0 sin(2 pi x),
+    E = c_v T0 + v^2/2 on the periodic unit interval, velocities on
+    [-vmax, vmax] (Newton-Cotes / Boole weights by default: nv = 4m + 1).
+    With T = 1 it is the smooth case of the paper's convergence study
+    (Sec. 4).  The time step is the largest one within the CFL bound that
+    reaches t_end in a whole number of steps (cfg["steps"])."""
+    cfg = _base(1, [nx], [0.0], [1.0], [[BC_PERIODIC, BC_PERIODIC]], [nv], [-vmax], [vmax], K=K,
+                mu_ref=mu_ref, T_ref=T0, Pr=Pr, cfl=cfl, rule=rule, name=f"sine_wave_T{T0:g}_mu{mu_ref:g}")
+    steps = int(np.ceil(t_end / (cfl * (1.0 / nx) / (2.0 * vmax)) - 1e-9))
+    cfg["steps"] = steps
+    cfg["dt"] = t_end / steps           # within the CFL bound, ending exactly at t_end
+    _, (x,) = cell_centres(cfg)
+    return cfg, _fields(np.full(nx, rho0), [v0 * np.sin(2 * np.pi * x)], np.full(nx, T0))
+
+
 def uniform(dim=1, n=(8, 8, 8), nv=(8, 8, 8), rho=1.0, u=(0.0, 0.0, 0.0), T=1.0, vmax=6.0,
             kn=1e-2, Pr=2.0 / 3.0, K=2.0, cfl=0.5, bc=BC_PERIODIC):
     """A uniform Maxwellian state (the scheme's fixed point)."""

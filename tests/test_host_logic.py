@@ -2,6 +2,8 @@
 design-byte accounting of the bench, and the serving step count."""
 import math
 
+import numpy as np
+
 from paper_2208_09132_gb300 import cdugks, serving, tune
 from paper_2208_09132_gb300 import workloads as wl
 
@@ -62,3 +64,16 @@ def test_served_step_count_reaches_the_end_time():
     assert serving.steps_to(0.3, 1.0) == 4
     assert serving.steps_to(0.5, 1e-9) == 1
     assert math.isclose(serving.steps_to(1e-3, 0.05) * 1e-3, 0.05)
+
+
+def test_sine_wave_reaches_its_end_time_within_the_cfl_bound():
+    for nx in (64, 100, 1024):
+        cfg, f = wl.sine_wave(nx=nx, nv=65, T0=1.0, t_end=0.1)
+        dt_cfl = cfg["cfl"] * (1.0 / nx) / (2.0 * 6.0)
+        assert cfg["dt"] <= dt_cfl * (1 + 1e-12)
+        assert math.isclose(cfg["dt"] * cfg["steps"], 0.1, rel_tol=1e-12)
+        assert cfg["rule"] == wl.RULE_BOOLE and (cfg["nv"][0] - 1) % 4 == 0
+        # rho0 = 1, v = sin(2 pi x), T = T0 (c_v = (3 + K) R / 2 = 1 with K = 2, R = 1/2)
+        _, (x,) = wl.cell_centres(cfg)
+        assert (f[:, 0] == 1.0).all() and (f[:, 2] == 1.0).all()
+        assert abs(f[:, 1] - np.sin(2 * np.pi * x)).max() < 1e-15
