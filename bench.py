@@ -10,7 +10,7 @@ periodic cells x 32^2 velocities on [-6,6]^2, Kn = 1e-3, Pr = 1 (synthetic
 initial fields).  One bench step = one full time step of the scheme.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c3|c3s|c4|c5] [--no-tune]
+                  [--workload c1|c2|c3|c3s|c4|c5|einfeldt] [--no-tune]
 
 N > 1 runs independent replicas (the path does not shard across GPUs on this
 build), one per rank under torch.distributed.run; value = all points / max time.
@@ -69,6 +69,10 @@ def pick_workload(name):
         return wl.workload_c3(kn=1e-4)
     if name == "c3s":        # 3D shear at half resolution in space and velocity
         return wl.workload_c3(kn=1e-4, scale=2, nv=12)
+    if name == "einfeldt":   # the paper's high-resolution Einfeldt run (Sec. 3.2), FP64, to t = 0.125
+        cfg, f = wl.einfeldt(nx=8192, nv=129)
+        cfg["precision"] = "fp64"
+        return cfg, f
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -501,6 +505,7 @@ def run_ours(args, ws, rank, local):
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "time_to_solution_s": (total_ms / args.steps * cfg["steps"] / 1e3) if args.workload == "einfeldt" else None,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if pname == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": cfg["name"], "precision": pname, "cells": wl.ncells(cfg),
@@ -564,7 +569,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 1000; einfeldt: to t_end)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
@@ -579,6 +584,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.steps is None:   # the einfeldt workload runs its whole solve; the others 1000 steps
+        args.steps = pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt" else 1000
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, ws, rank)

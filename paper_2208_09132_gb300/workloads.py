@@ -166,6 +166,25 @@ def gresho(n=100, nv=101, kn=1e-4, Pr=2.0 / 3.0, K=2.0, cfl=0.8, steps=1, vmax=1
     return cfg, _fields(rho, [ux, uy], p / (rho * R_GAS))
 
 
+def einfeldt(nx=256, nv=129, mu_ref=1e-6, T_ref=1.0, K=2.0, Pr=2.0 / 3.0, cfl=0.4, vmax=10.0, t_end=0.125,
+             rule=RULE_TRAPEZOID, bc=BC_DIRICHLET):
+    """Einfeldt 1-2-0-3 rarefaction (Sec. 3.2): rho = 1, rho E = 3,
+    u = 2 sgn(x - 1/2) on [0, 1] (so c_v T = 1, T = 0.8 with K = 2), hard-sphere
+    viscosity, Pr = 2/3, velocities on [-10, 10], CFL 0.4, to t = 0.125.  The
+    ends hold the initial equilibrium (Dirichlet; no signal reaches them by
+    t_end).  The paper's high-resolution run has nx = 8192, nv = 129."""
+    cfg = _base(1, [nx], [0.0], [1.0], [[bc, bc]], [nv], [-vmax], [vmax], K=K, mu_ref=mu_ref, T_ref=T_ref,
+                Pr=Pr, cfl=cfl, rule=rule, name=f"einfeldt_1203_{nx}x{nv}")
+    steps = int(np.ceil(t_end / (cfl * (1.0 / nx) / (2.0 * vmax)) - 1e-9))
+    cfg["steps"] = steps
+    cfg["dt"] = t_end / steps
+    _, (x,) = cell_centres(cfg)
+    cv = (3.0 + K) * R_GAS / 2.0
+    u = 2.0 * np.sign(x - 0.5)
+    T = (3.0 - 0.5 * u ** 2) / cv
+    return cfg, _fields(np.ones(nx), [u], T)
+
+
 def sine_wave(nx=128, nv=129, T0=0.1, mu_ref=1e-5, rho0=1.0, v0=1.0, K=2.0, Pr=2.0 / 3.0, cfl=0.5, vmax=6.0,
               rule=RULE_BOOLE, t_end=0.1):
     """Sine-wave perturbation (Sec. 3.7): rho = rho0, v = v0 sin(2 pi x),

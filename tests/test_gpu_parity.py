@@ -71,6 +71,9 @@ def case(name):
     if name == "3d_mixed_bc":
         cfg, f = wl.random_smooth(dim=3, n=(6, 5, 5), nv=(4, 4, 6), seed=10, amp=0.3, kn=5e-3)
         return (_bc(cfg, [(DI, DI), (P, P), (S, S)]), f), 5
+    if name == "1d_einfeldt":
+        cfg, f = wl.einfeldt(nx=64, nv=33, mu_ref=1e-4)
+        return (cfg, f), 30
     if name == "3d_shear_small":
         return wl.shear3d(n=8, nv=6, kn=1e-2), 5
     raise KeyError(name)
@@ -79,7 +82,7 @@ def case(name):
 CASES = ["1d_periodic_ragged_padded", "1d_sod_dirichlet", "1d_sod_specular", "1d_boole_odd_grid",
          "1d_free_streaming", "1d_near_euler", "2d_periodic_ragged", "2d_specular_x_periodic_y",
          "2d_dirichlet_x_specular_y", "2d_kh_small", "3d_periodic_ragged", "3d_specular_corners",
-         "3d_mixed_bc", "3d_shear_small"]
+         "3d_mixed_bc", "3d_shear_small", "1d_einfeldt"]
 
 
 def run_both(oracle_mod, cfg, f, steps, precision, groups=0):
