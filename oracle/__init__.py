@@ -57,6 +57,7 @@ class _Params(ctypes.Structure):
         ("Pr", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("cfl", ctypes.c_double),
+        ("recon", ctypes.c_int),
     ]
 
 
@@ -143,6 +144,7 @@ class Oracle:
         p.Pr = float(cfg["Pr"])
         p.dt = float(cfg.get("dt", 0.0) or 0.0)
         p.cfl = float(cfg.get("cfl", 0.5))
+        p.recon = int(cfg.get("recon", 0))
         h = lib.oracle_create(ctypes.byref(p))
         if not h:
             raise ValueError("oracle_create rejected the problem description")

@@ -15,7 +15,8 @@
  * Style: plain nested loops in the order the paper gives the steps, every
  * intermediate kept in a full array, std libm exp/pow, compensated
  * (Neumaier) summation for every velocity-space integral, explicit ghost
- * layers (two deep) filled before each step.  No fusion, no reordering.
+ * layers (two deep; three with recon = 1) filled before each step.  No
+ * fusion, no reordering.
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
@@ -41,6 +42,13 @@
  *   R-j  Specular walls mirror the neighbouring interior cells with the
  *        normal velocity component reversed; Dirichlet ghosts hold the
  *        equilibrium of the initial state of the nearest interior cell.
+ *   R-c2 (recon = 1, selectable) The paper's variant of the reconstruction
+ *        (Sec. 2.1: the slopes themselves are reconstructed at the face from
+ *        their own limited gradients): phibar+(x_f) = phibar+_up +
+ *        (x_f - x_up).sigma_up, sigma_f = sigma_up + (x_f - x_up).grad sigma_up
+ *        (the derivative along the face normal of each slope component, van
+ *        Leer limited like the slopes), and phibar(x_f, t+h) = phibar+(x_f) -
+ *        h xi.sigma_f.  It needs three ghost layers.
  *
  * Pinning (tests/test_oracle_pins.py): every step above is checked against a
  * closed form, an invariant or a textbook limit, except two O(h) pieces whose
@@ -56,11 +64,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NG 2            /* ghost layers per side (stencil j-2 .. j+1) */
+#define NG (o->ng)      /* ghost layers per side: 2 (stencil j-2 .. j+1), 3 with recon = 1 */
 #define NW 5            /* stored conserved variables (rho, rho u[3], rho E) */
 
 struct oracle {
     oracle_params p;
+    int ng;             /* ghost layers per side */
     int D;
     int n[3];           /* interior cells per axis (1 for unused axes) */
     int ne[3];          /* extended cells per axis (with ghosts on active axes) */
@@ -79,6 +88,7 @@ struct oracle {
     double *geq, *beq, *Sb;     /* [Ne][Nv] cell equilibria and b-source at t_n */
     double *gp, *bp;            /* [Ne][Nv] phibar+ (eq. phibarplus) */
     double *sg, *sb;            /* [Ne][3][Nv] limited slopes (eq. VanLeer) */
+    double *s2g, *s2b;          /* [Ne][3][3][Nv] limited derivative along a of slope b (recon = 1) */
     double *gfb, *bfb;          /* [3][Ne][Nv] phibar at faces, t + h (eq. relation) */
     double *Wf;                 /* [3][Ne][NW] face conserved variables (eqs. rhobar-rhoEbar) */
     double *gf, *bf;            /* [3][Ne][Nv] phi at faces, t + h (inverse of eq. phibar) */
@@ -248,6 +258,7 @@ oracle_t *oracle_create(const oracle_params *p) {
     struct oracle *o = (struct oracle *)xalloc(sizeof(*o));
     if (!o) return NULL;
     o->p = *p;
+    o->ng = p->recon ? 3 : 2;
     o->D = p->D;
     o->gam = (p->K + 5.0) / (p->K + 3.0);
     o->Nc = 1; o->Ne = 1; o->Nv = 1;
@@ -303,6 +314,7 @@ oracle_t *oracle_create(const oracle_params *p) {
     o->geq = xalloc(F); o->beq = xalloc(F); o->Sb = xalloc(F);
     o->gp = xalloc(F); o->bp = xalloc(F);
     o->sg = xalloc(3 * F); o->sb = xalloc(3 * F);
+    if (p->recon) { o->s2g = xalloc(9 * F); o->s2b = xalloc(9 * F); }
     o->gfb = xalloc(3 * F); o->bfb = xalloc(3 * F);
     o->gf = xalloc(3 * F); o->bf = xalloc(3 * F);
     o->dFg = xalloc(F); o->dFb = xalloc(F);
@@ -311,6 +323,7 @@ oracle_t *oracle_create(const oracle_params *p) {
     o->Wdir = xalloc(sizeof(double) * NW * Ne);
     o->Wf = xalloc(sizeof(double) * 3 * NW * Ne);
     if (!o->g || !o->b || !o->geq || !o->beq || !o->Sb || !o->gp || !o->bp || !o->sg || !o->sb ||
+        (p->recon && (!o->s2g || !o->s2b)) ||
         !o->gfb || !o->bfb || !o->gf || !o->bf || !o->dFg || !o->dFb || !o->W || !o->Wn ||
         !o->Wdir || !o->Wf || !o->xi || !o->w) {
         oracle_destroy(o);
@@ -338,7 +351,7 @@ void oracle_destroy(oracle_t *o) {
     free(o->xi); free(o->w);
     for (int a = 0; a < 3; ++a) free(o->refl[a]);
     free(o->g); free(o->b); free(o->geq); free(o->beq); free(o->Sb);
-    free(o->gp); free(o->bp); free(o->sg); free(o->sb);
+    free(o->gp); free(o->bp); free(o->sg); free(o->sb); free(o->s2g); free(o->s2b);
     free(o->gfb); free(o->bfb); free(o->gf); free(o->bf);
     free(o->dFg); free(o->dFb);
     free(o->W); free(o->Wn); free(o->Wdir); free(o->Wf);
@@ -453,6 +466,30 @@ static void one_step(struct oracle *o) {
         }
     }
 
+    /* (2b) recon = 1 (reading R-c2): the limited derivative along every axis a
+     *      of every slope component b, in the same van Leer form, for every
+     *      cell whose two neighbours along each axis have slopes. */
+    if (o->p.recon) {
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < Ne; ++c) {
+            int q[3];
+            ccoord(o, c, q);
+            int ok = 1;
+            for (int a = 0; a < D; ++a) if (q[a] < 2 || q[a] > o->ne[a] - 3) ok = 0;
+            if (!ok) continue;
+            for (int a = 0; a < D; ++a) {
+                long s = step_of(o, a);
+                for (int bax = 0; bax < D; ++bax)
+                    for (long i = 0; i < Nv; ++i) {
+                        long k0 = (c * 3 + bax) * Nv + i, km = ((c - s) * 3 + bax) * Nv + i, kp = ((c + s) * 3 + bax) * Nv + i;
+                        long d = ((c * 3 + a) * 3 + bax) * Nv + i;
+                        o->s2g[d] = oracle_vanleer((o->sg[k0] - o->sg[km]) / o->dx[a], (o->sg[kp] - o->sg[k0]) / o->dx[a]);
+                        o->s2b[d] = oracle_vanleer((o->sb[k0] - o->sb[km]) / o->dx[a], (o->sb[kp] - o->sb[k0]) / o->dx[a]);
+                    }
+            }
+        }
+    }
+
     /* (3)-(5) every face of every interior cell.  The face of axis a with
      *     right cell R and left cell L = R - e_a is stored at index R.  Faces
      *     with R_a in [NG, NG + n_a] and interior tangential coordinates. */
@@ -479,10 +516,24 @@ static void one_step(struct oracle *o) {
                 for (int side = 0; side < 2; ++side) {
                     long up = ups[side];
                     double rg = o->gp[up * Nv + i], rb = o->bp[up * Nv + i];
-                    for (int bax = 0; bax < D; ++bax) {
-                        double d = (bax == a ? dn[side] : 0.0) - h * xi[bax];
-                        rg += d * o->sg[(up * 3 + bax) * Nv + i];
-                        rb += d * o->sb[(up * 3 + bax) * Nv + i];
+                    if (!o->p.recon) {
+                        for (int bax = 0; bax < D; ++bax) {
+                            double d = (bax == a ? dn[side] : 0.0) - h * xi[bax];
+                            rg += d * o->sg[(up * 3 + bax) * Nv + i];
+                            rb += d * o->sb[(up * 3 + bax) * Nv + i];
+                        }
+                    } else {
+                        /* R-c2: phibar+ at the face from the upwind cell, the slope
+                         * vector carried to the face along e_a, then back along the
+                         * characteristic by h xi with that face slope */
+                        rg += dn[side] * o->sg[(up * 3 + a) * Nv + i];
+                        rb += dn[side] * o->sb[(up * 3 + a) * Nv + i];
+                        for (int bax = 0; bax < D; ++bax) {
+                            double sfg = o->sg[(up * 3 + bax) * Nv + i] + dn[side] * o->s2g[((up * 3 + a) * 3 + bax) * Nv + i];
+                            double sfb = o->sb[(up * 3 + bax) * Nv + i] + dn[side] * o->s2b[((up * 3 + a) * 3 + bax) * Nv + i];
+                            rg -= h * xi[bax] * sfg;
+                            rb -= h * xi[bax] * sfb;
+                        }
                     }
                     vg[side] = rg;
                     vb[side] = rb;

@@ -31,6 +31,7 @@ typedef struct {
     double Pr;             /* Prandtl number, tau_b = tau_g / Pr */
     double dt;             /* time step; <= 0: CFL rule with cfl below */
     double cfl;
+    int recon;             /* 0: reconstruction R-c; 1: the face-gradient variant R-c2 */
 } oracle_params;
 
 typedef struct oracle oracle_t;

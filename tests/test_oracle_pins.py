@@ -315,6 +315,138 @@ def test_free_streaming_2d_diagonal_second_order(oracle_mod):
     assert e[2] < 6e-4, e
 
 
+# ------------------------------------ the paper's face-gradient reconstruction (R-c2)
+
+def _recon(cfg, recon):
+    cfg = dict(cfg)
+    cfg["recon"] = recon
+    return cfg
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_face_gradient_reconstruction_keeps_fixed_point_and_conserves(oracle_mod, D):
+    cfg, f = wl.uniform(dim=D, n=(6, 5), nv=(16, 12), u=(0.3, -0.2), T=1.2, kn=1e-2)
+    o = oracle_mod.Oracle(_recon(cfg, 1))
+    o.init(f)
+    g0, _ = o.distributions()
+    o.step(40)
+    g1, _ = o.distributions()
+    assert np.abs(g1 - g0).max() <= 1e-14 * np.abs(g0).max()
+    cfg, f = wl.random_smooth(dim=D, n=(16, 10), nv=(16, 10), seed=D, amp=0.3, kn=3e-3)
+    o = oracle_mod.Oracle(_recon(cfg, 1))
+    o.init(f)
+    S0 = o.conserved().sum(0)
+    o.step(40)
+    S1 = o.conserved().sum(0)
+    scale = np.array([S0[0]] * (1 + D) + [S0[-1]])
+    assert np.all(np.abs(S1 - S0) <= 1e-13 * scale)
+    assert np.abs(o.moments()[:, 0] - f[:, 0]).max() > 1e-6
+
+
+def test_face_gradient_reconstruction_walls_are_mirror_images(oracle_mod):
+    """Three ghost layers mirrored: a specular domain equals half of the
+    doubled periodic domain holding its mirror image."""
+    nx, nv = 24, 16
+    cfg, f = wl.random_smooth(dim=1, n=(nx,), nv=(nv,), seed=11, amp=0.3, bc=wl.BC_SPECULAR, kn=5e-3)
+    o = oracle_mod.Oracle(_recon(cfg, 1))
+    o.init(f)
+    cfg2 = dict(cfg)
+    cfg2["n"] = [2 * nx, 1, 1]
+    cfg2["hi"] = [2.0, 1.0, 1.0]
+    cfg2["bc"] = [[wl.BC_PERIODIC] * 2] * 3
+    f2 = np.concatenate([f, f[::-1] * np.array([1.0, -1.0, 1.0])], axis=0)
+    o2 = oracle_mod.Oracle(_recon(cfg2, 1))
+    o2.init(f2)
+    o.step(150)
+    o2.step(150)
+    assert np.abs(o.moments() - o2.moments()[:nx]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_face_gradient_reconstruction_converges_second_order(oracle_mod, D):
+    """Free streaming along (oblique) characteristics: second order to the
+    exact shift, as for the upwind-cell reconstruction."""
+    def err(nx, t_end=0.05, nv=4, vmax=2.0):
+        cfg = wl._base(D, [nx] * D, [0] * D, [1] * D, [[0, 0]] * D, [nv] * D, [-vmax] * D, [vmax] * D,
+                       K=2.0, mu_ref=1e250, T_ref=1.0, omega=0.0, cfl=0.4)
+        cfg["recon"] = 1
+        _, X = wl.cell_centres(cfg)
+        ph = lambda s: 1 + 0.2 * np.sin(2 * math.pi * sum((k + 1) * s[k] for k in range(D)))
+        f = wl._fields(ph(X), [0 * X[0]] * D, np.ones_like(X[0]))
+        n = int(round(t_end / oracle_mod.Oracle(cfg).dt))
+        cfg["dt"] = t_end / n
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        g0, _ = o.distributions()
+        xi, _ = o.velocities()
+        o.step(n)
+        g1, _ = o.distributions()
+        e = 0.0
+        for i in range(g0.shape[1]):
+            pt = ph([X[k] - xi[i, k] * t_end for k in range(D)])
+            e = max(e, np.abs(g1[:, i] / g0[:, i].mean() - pt).mean())
+        return e
+
+    e = [err(nx) for nx in (32, 64, 128)]
+    assert math.log2(e[0] / e[1]) > 1.7 and math.log2(e[1] / e[2]) > 1.8, e
+
+
+@pytest.mark.parametrize("recon", [0, 1])
+def test_face_values_on_a_geometric_profile(oracle_mod, recon):
+    """phi_j = r^j: van Leer reproduces geometric slopes exactly, sigma_j =
+    alpha r^j/dx with alpha = 2(r-1)/(r+1), and geometric slope derivatives
+    alpha^2 r^j/dx^2.  One collisionless step gives face values in closed form
+    with c = h xi/dx and the upwind cell j:
+        upwind cell (R-c):    r^j (1 + s alpha/2 - c alpha),
+        face gradient (R-c2): r^j (1 + s alpha/2 - c (alpha + s alpha^2/2)),
+    s = +1 for the left cell, -1 for the right.  Expanding in ln r, only the
+    face-gradient form carries the -c (ln r)^2/2 term of the exact back-trace
+    r^(j + s/2 - c)."""
+    n, r = 16, 1.15
+    cfg = wl._base(1, [n], [0.0], [1.0], [[wl.BC_DIRICHLET] * 2], [4], [-1.5], [1.5], K=2.0, mu_ref=1e250,
+                   T_ref=1.0, omega=0.0, cfl=0.4)
+    cfg["recon"] = recon
+    o = oracle_mod.Oracle(cfg)
+    xi, w = o.velocities()
+    amp = np.array([0.3, 0.7, 1.1, 0.5])
+    prof = r ** np.arange(n)
+    g = np.outer(prof, amp)
+    W = np.tile([1.0, 0.0, 1.25], (n, 1))
+    o.set_state(g, 2.0 * g, W)
+    o.step(1)
+    fW = o.face_W(0, (n,))                     # faces 0..n, [rho, rho u, rho E]
+    h, dx = 0.5 * o.dt, 1.0 / n
+    alpha = 2 * (r - 1) / (r + 1)
+    for k in range(4, n - 3):                  # faces beyond the reach of the boundary ghosts
+        rho = 0.0
+        for i in range(4):
+            c = h * xi[i, 0] / dx
+            j, sgn = (k - 1, 1.0) if xi[i, 0] > 0 else (k, -1.0)
+            corr = alpha + (sgn * alpha ** 2 / 2 if recon else 0.0)
+            rho += w[i] * amp[i] * r ** j * (1 + sgn * alpha / 2 - c * corr)
+        assert abs(fW[k, 0] - rho) <= 1e-13 * rho, (k, fW[k, 0], rho)
+        assert abs(fW[k, 2] - 2 * rho) <= 1e-13 * rho
+
+
+def test_face_gradient_and_upwind_cell_reconstructions_agree_to_second_order(oracle_mod):
+    """The two readings differ by h xi (x_f - x_up) . grad sigma at each face,
+    O(dt dx) per step: their solutions at a fixed time differ by O(dx^2)."""
+    d = []
+    for nx in (64, 128, 256):
+        cfg, f = wl.random_smooth(dim=1, n=(nx,), nv=(16,), seed=4, amp=0.3, kn=3e-3)
+        n = int(round(0.05 / oracle_mod.Oracle(cfg).dt))
+        cfg["dt"] = 0.05 / n
+        r = []
+        for recon in (0, 1):
+            o = oracle_mod.Oracle(_recon(cfg, recon))
+            o.init(f)
+            o.step(n)
+            r.append(o.moments()[:, 0])
+        d.append(np.abs(r[0] - r[1]).mean())
+    assert d[0] > 1e-8, d                             # the variants do differ
+    assert math.log2(d[0] / d[1]) > 1.75 and math.log2(d[1] / d[2]) > 1.75, d
+
+
 # ------------------------------------------------------------------ Euler limit
 
 def test_euler_limit_sod_against_exact_riemann(oracle_mod):
