@@ -394,6 +394,8 @@ def run_ours(args, ws, rank, local):
     dev = f"cuda:{local}"
     torch.cuda.set_device(local)
     cfg, fields = pick_workload(args.workload)
+    if args.recon:
+        cfg["recon"] = args.recon
     prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
@@ -512,7 +514,8 @@ def run_ours(args, ws, rank, local):
                        "velocities": wl.nvel(cfg), "points": P, "dt": s.dt,
                        "state_bytes": s.info().state_bytes,
                        "tile": list(s.info().tile)[:cfg["dim"]], "velocity_groups": s.info().velocity_groups,
-                       "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode, str(mode)),
+                       "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode & 7, str(mode)),
+                       "reconstruction": "face gradient" if mode & 8 else "upwind cell",
                        "launch": f"CUDA graphs of {gsteps} steps" if gsteps > 1 else "one launch per kernel",
                        "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
                              else "state fits in L2",
@@ -578,6 +581,7 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false", help="default tile / group choice")
     ap.add_argument("--tile", type=int, default=None, help="pin the tile shape id (skips tuning)")
     ap.add_argument("--graph", type=int, default=10, help="steps per captured CUDA graph (1: plain launches)")
+    ap.add_argument("--recon", type=int, default=0, help="1: the face-gradient reconstruction (1D/2D workloads)")
     ap.add_argument("--groups", type=int, default=None, help="with --tile: velocity groups")
     ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
     ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")

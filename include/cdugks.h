@@ -226,9 +226,29 @@ CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
  * Bit 2 (value 4, face store): sweep A keeps the reconstructed phibar of
  * every face and velocity (about D more state-size buffers) and sweep B only
  * forms the fluxes from them instead of reconstructing again.
+ * Bit 3 (value 8): the shape implements the face-gradient reconstruction
+ * (cdugks_set_reconstruction); the others the upwind-cell one.
  * Every mode but 0 must be selected before cdugks_bind; modes with bits 0-1
  * nonzero are not batched (modes 0 and 4 are). */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
+
+/* The reconstruction of phibar at a face (Sec. 2.1).
+ *   CDUGKS_RECON_UPWIND_CELL (default): phibar+ of the upwind cell carried
+ *     along the characteristic with that cell's limited slope vector,
+ *     phibar(x_f, t + h) = phibar+_up + (x_f - h xi - x_up) . sigma_up.
+ *   CDUGKS_RECON_FACE_GRADIENT: the paper's variant, in which the slopes are
+ *     themselves reconstructed at the face from their own limited gradients:
+ *     sigma_f = sigma_up + (x_f - x_up) . grad sigma_up and
+ *     phibar(x_f, t + h) = phibar+_up + (x_f - x_up) . sigma_up - h xi . sigma_f.
+ *     Three halo cells; D = 1 or 2; 3 cells next to a specular wall; not
+ *     in cdugks_step_noalloc.  The two agree to second order.
+ * Select before cdugks_bind; it picks the default shape of that
+ * reconstruction, and cdugks_set_tile then accepts only shapes that
+ * implement it (tile_shape out[3] bit 3).
+ * Errors: INVALID (unknown value, bound handle, no such shape, short wall). */
+#define CDUGKS_RECON_UPWIND_CELL 0
+#define CDUGKS_RECON_FACE_GRADIENT 1
+CDUGKS_API int cdugks_set_reconstruction(cdugks_t *h, int recon);
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances stepped together: every kernel of a time step

@@ -70,6 +70,7 @@ struct cdugks {
     int gcap;              // velocity groups the workspace is laid out for
     int bufs_cap;          // optional buffers the workspace holds (BUF_* bits)
     int gsel;              // requested groups (0 = auto)
+    int recon;             // CDUGKS_RECON_UPWIND_CELL or CDUGKS_RECON_FACE_GRADIENT
     Layout lay;
     unsigned char* base;
     size_t bound_bytes;
@@ -444,6 +445,8 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
     if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
     if (tile_id < 0 || tile_id >= tile_count(h->prec, h->g.D)) return fail(CDUGKS_ERR_INVALID, "unknown tile id");
     const int mode = tile_mode(h->prec, h->g.D, tile_id);
+    if (cdg::mode_r2(mode) != (h->recon == CDUGKS_RECON_FACE_GRADIENT))
+        return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected reconstruction");
     if (cdg::mode_source(mode) == cdg::MODE_STORED)
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
@@ -474,6 +477,24 @@ int cdugks_workspace_bytes(const cdugks_t* h, size_t* bytes) {
     if (!h || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
     *bytes = h->lay.total;
     return CDUGKS_OK;
+}
+
+int cdugks_set_reconstruction(cdugks_t* h, int recon) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    if (recon != CDUGKS_RECON_UPWIND_CELL && recon != CDUGKS_RECON_FACE_GRADIENT)
+        return fail(CDUGKS_ERR_INVALID, "unknown reconstruction");
+    if (h->bound) return fail(CDUGKS_ERR_INVALID, "select the reconstruction before cdugks_bind");
+    int id = -1;
+    for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t)
+        if (cdg::mode_r2(tile_mode(h->prec, h->g.D, t)) == (recon == CDUGKS_RECON_FACE_GRADIENT)) id = t;
+    if (id < 0) return fail(CDUGKS_ERR_INVALID, "no tile shape implements this reconstruction for this dimension");
+    if (recon == CDUGKS_RECON_FACE_GRADIENT)   // a mirror image three cells deep
+        for (int a = 0; a < h->g.D; ++a)
+            for (int s2 = 0; s2 < 2; ++s2)
+                if (h->g.bc[a][s2] == CDUGKS_BC_SPECULAR && h->g.n[a] < 3)
+                    return fail(CDUGKS_ERR_INVALID, "the face-gradient reconstruction needs 3 cells next to a specular wall");
+    h->recon = recon;
+    return cdugks_set_tile(h, id);
 }
 
 int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) {
@@ -872,7 +893,7 @@ struct cdugks_batch {
     std::vector<RItem> face_items, cell_items;
     std::vector<unsigned char> insts;          // host image of the Inst<T> table
     std::vector<int> cur;
-    size_t off_insts, off_cur, off_sweep[4], off_face, off_cell, total;
+    size_t off_insts, off_cur, off_sweep[cdg::kMaxBatchShapes], off_face, off_cell, total;
     unsigned char* base;
     cudaStream_t stream;
     bool bound;
@@ -968,6 +989,10 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
         if (std::find(b->tile_ids.begin(), b->tile_ids.end(), id) == b->tile_ids.end()) b->tile_ids.push_back(id);
     }
     std::sort(b->tile_ids.begin(), b->tile_ids.end());
+    if (b->tile_ids.size() > (size_t)cdg::kMaxBatchShapes) {     // before any per-shape table is filled
+        delete b;
+        return fail(CDUGKS_ERR_INVALID, "too many tile shapes in one batch");
+    }
     b->sweep_items.resize(b->tile_ids.size());
     for (int i = 0; i < n; ++i) {
         const Geo& g = b->mem[i]->g;
@@ -1006,10 +1031,6 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
     b->off_face = take(sizeof(RItem) * b->face_items.size());
     b->off_cell = take(sizeof(RItem) * b->cell_items.size());
     b->total = off;
-    if (b->tile_ids.size() > 4) {
-        delete b;
-        return fail(CDUGKS_ERR_INVALID, "too many tile shapes in one batch");
-    }
     *out = b;
     return CDUGKS_OK;
 }
@@ -1153,6 +1174,8 @@ int noalloc_scratch(void** out) {
 template <typename T>
 int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStream_t st) {
     Geo g = h->g;
+    if (h->recon != CDUGKS_RECON_UPWIND_CELL)
+        return fail(CDUGKS_ERR_INVALID, "the allocation-free step implements the upwind-cell reconstruction only");
     if (tile_mode(h->prec, g.D, g.tile_id) != cdg::MODE_FUSED) {   // no room for phibar+ / slope / face buffers here
         g.tile_id = 0;
         const cdg::TileShape ts = tile_of(h->prec, g.D, 0);

@@ -353,7 +353,7 @@ template <> struct Kahan<double> {
 
 // ------------------------------------------------------------- geometry
 
-// Map a cell coordinate that may lie in the two-deep ghost layer onto the
+// Map a cell coordinate that may lie in the ghost layers (two or three deep) onto the
 // interior: axes resolved from the last to the first (the order in which
 // ghost layers of later axes overwrite corners), periodic wrap, specular
 // mirror (reflection bit set), Dirichlet clamp (flag).  Coordinates beyond the
@@ -432,23 +432,30 @@ template <> struct Chunk<double> {
 // All threads of a warp hold the same velocity, so the upwind choice never
 // diverges.
 
-template <int D, int T0_, int T1_, int T2_>
+template <int D, int T0_, int T1_, int T2_, int HALO_ = 2>
 struct Tile {
     static constexpr int T0 = T0_, T1 = D >= 2 ? T1_ : 1, T2 = D >= 3 ? T2_ : 1;
     static constexpr int NT = T0 * T1 * T2;                                   // threads = owned cells
-    // halo box: local cells [-2, T+1] per active axis
-    static constexpr int E0 = T0 + 4, E1 = D >= 2 ? T1 + 4 : 1, E2 = D >= 3 ? T2 + 4 : 1;
+    // halo box: local cells [-HALO, T + HALO - 1] per active axis (2, or 3 for the
+    // face-gradient reconstruction, which also needs derivatives of the slopes)
+    static constexpr int HALO = HALO_;
+    static constexpr int E0 = T0 + 2 * HALO, E1 = D >= 2 ? T1 + 2 * HALO : 1, E2 = D >= 3 ? T2 + 2 * HALO : 1;
     static constexpr int BOX = E0 * E1 * E2;
     static constexpr int NH = BOX - NT;
-    // slope box: local cells [-1, T] per active axis
-    static constexpr int F0 = T0 + 2, F1 = D >= 2 ? T1 + 2 : 1, F2 = D >= 3 ? T2 + 2 : 1;
+    // slope box: local cells [-(HALO-1), T + HALO - 2] per active axis
+    static constexpr int F0 = T0 + 2 * (HALO - 1), F1 = D >= 2 ? T1 + 2 * (HALO - 1) : 1;
+    static constexpr int F2 = D >= 3 ? T2 + 2 * (HALO - 1) : 1;
     static constexpr int SB = F0 * F1 * F2;
+    // slope-derivative box (HALO = 3): local cells [-1, T] per active axis
+    static constexpr int G0 = T0 + 2, G1 = D >= 2 ? T1 + 2 : 1, G2 = D >= 3 ? T2 + 2 : 1;
+    static constexpr int SB2 = G0 * G1 * G2;
     static constexpr int NF0 = (T0 + 1) * T1 * T2;
     static constexpr int NF1 = D >= 2 ? T0 * (T1 + 1) * T2 : 0;
     static constexpr int NF2 = D >= 3 ? T0 * T1 * (T2 + 1) : 0;
     static constexpr int NFT = NF0 + NF1 + NF2;
     __host__ __device__ static constexpr int bstride(int a) { return a == 0 ? 1 : (a == 1 ? E0 : E0 * E1); }
     __host__ __device__ static constexpr int sstride(int a) { return a == 0 ? 1 : (a == 1 ? F0 : F0 * F1); }
+    __host__ __device__ static constexpr int s2stride(int a) { return a == 0 ? 1 : (a == 1 ? G0 : G0 * G1); }
     __host__ __device__ static constexpr int tdim(int a) { return a == 0 ? T0 : (a == 1 ? T1 : T2); }
     __host__ __device__ static constexpr int foff(int a) {
         return a == 0 ? 0 : (a == 1 ? NF0 : (a == 2 ? NF0 + NF1 : NFT));
@@ -464,10 +471,20 @@ struct Tile {
         return a == 0 ? la[1] + T1 * la[2] : (a == 1 ? la[0] + T0 * la[2] : la[0] + T0 * la[1]);
     }
     __device__ static __forceinline__ int box_of(int l0, int l1, int l2) {
-        return (l0 + 2) + E0 * ((D >= 2 ? l1 + 2 : 0) + E1 * (D >= 3 ? l2 + 2 : 0));
+        return (l0 + HALO) + E0 * ((D >= 2 ? l1 + HALO : 0) + E1 * (D >= 3 ? l2 + HALO : 0));
     }
     __device__ static __forceinline__ int sbox_of(int l0, int l1, int l2) {
-        return (l0 + 1) + F0 * ((D >= 2 ? l1 + 1 : 0) + F1 * (D >= 3 ? l2 + 1 : 0));
+        constexpr int o = HALO - 1;
+        return (l0 + o) + F0 * ((D >= 2 ? l1 + o : 0) + F1 * (D >= 3 ? l2 + o : 0));
+    }
+    __device__ static __forceinline__ int s2box_of(int l0, int l1, int l2) {
+        return (l0 + 1) + G0 * ((D >= 2 ? l1 + 1 : 0) + G1 * (D >= 3 ? l2 + 1 : 0));
+    }
+    // local coordinates of slope-box cell s
+    __device__ static __forceinline__ void sbox_local(int s, int l[3]) {
+        l[0] = s % F0 - (HALO - 1);
+        l[1] = D >= 2 ? (s / F0) % F1 - (HALO - 1) : 0;
+        l[2] = D >= 3 ? s / (F0 * F1) - (HALO - 1) : 0;
     }
     // local face of axis a whose right cell has local coordinates l (l_a in [0, T_a])
     __device__ static __forceinline__ int face_local(int a, int l0, int l1, int l2) {
@@ -513,19 +530,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // loads phibar+ and the slopes formed by k_shslope.  Bit 2 (face store):
 // sweep A also writes the reconstructed face values, and sweep B is k_flux,
 // which reads them instead of reconstructing them again.
-enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4 };
+// Bit 3 (face gradient): the paper's variant of the reconstruction, which also
+// carries the slopes to the face with their own limited derivatives (three
+// halo layers; fused face-store shapes only).
+enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8 };
 __host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
+__host__ __device__ constexpr bool mode_r2(int mode) { return (mode & MODE_R2) != 0; }
+__host__ __device__ constexpr int mode_halo(int mode) { return mode_r2(mode) ? 3 : 2; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
-    using TL = Tile<D, T0, T1, T2>;
+    using TL = Tile<D, T0, T1, T2, mode_halo(MODE)>;
     static constexpr int NCCV = CellPack<D>::NV;  // phase-1 constants per box cell, packed in V4
     static constexpr int NFC = D + 7;            // face constants
     static constexpr int NFCV = (NFC + 3) / 4;
     static constexpr int PN = mode_source(MODE) == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
     static constexpr size_t nP = (size_t)2 * PN;                                    // V4 units
     static constexpr size_t nS = (size_t)D * 2 * TL::SB;
+    static constexpr size_t nS2 = mode_r2(MODE) ? (size_t)D * D * 2 * TL::SB2 : 0;   // slope derivatives
     static constexpr size_t nCC = mode_source(MODE) == MODE_FUSED ? (size_t)NCCV * TL::BOX : 0;
     static constexpr size_t nFF = (size_t)2 * TL::NFT;
     static constexpr size_t nFC = (size_t)NFCV * TL::NFT;
@@ -537,7 +560,7 @@ struct Smem {
     __host__ __device__ static constexpr int fit(size_t b) { return (int)((size_t)(228 * 1024) / (b + 1024)); }
     static constexpr int lim = (2048 / TL::NT) < (65536 / (TL::NT * 80)) ? (2048 / TL::NT) : (65536 / (TL::NT * 80));
     static constexpr size_t nST = (size_t)2 * TL::BOX;      // staged phi* chunk (g, b) per box cell
-    static constexpr size_t a1 = (nP + nS + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A
+    static constexpr size_t a1 = (nP + nS + nS2 + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A
     static constexpr bool st_fits = fit(a1 + nST * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
     // Sweep A of the fused shapes stages the next chunk's phi* of its halo box in
     // shared memory with asynchronous copies (where that costs no occupancy), so
@@ -546,7 +569,7 @@ struct Smem {
         return !B && mode_source(MODE) == MODE_FUSED && st_fits;
     }
     __host__ __device__ static constexpr size_t vcount(bool B) {
-        return nP + nS + nCC + (B ? nFF + nFC : 0) + (stage(B) ? nST : 0);
+        return nP + nS + nS2 + nCC + (B ? nFF + nFC : 0) + (stage(B) ? nST : 0);
     }
     __host__ __device__ static constexpr size_t bytes(bool B) {
         return vcount(B) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;
@@ -950,12 +973,14 @@ __device__ __forceinline__ void write_face_sums(const Geo& g, double* const* dst
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
-    using TL = Tile<D, T0_, T1_, T2_>;
+    using TL = Tile<D, T0_, T1_, T2_, mode_halo(MODE)>;
     using SM = Smem<T, D, T0_, T1_, T2_, MODE>;
     constexpr bool PREP = mode_source(MODE) != MODE_FUSED;      // phibar+ comes from a prepared buffer
     constexpr bool STORED = mode_source(MODE) == MODE_STORED;   // ... and so do the slopes
     constexpr bool FACES = mode_faces(MODE);                     // sweep A stores the face values
+    constexpr bool R2 = mode_r2(MODE);                           // face-gradient reconstruction
     static_assert(!(SWEEP_B && FACES), "sweep B of the face-store shapes is k_flux");
+    static_assert(!R2 || (FACES && !PREP), "the face-gradient reconstruction is built for fused face-store shapes");
     constexpr int PN = SM::PN;
     using Q = V4<T>;
     constexpr int NM = 2 + D, BOX = TL::BOX, SB = TL::SB, NFT = TL::NFT;
@@ -965,10 +990,12 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr bool STAGE = SM::stage(SWEEP_B);
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
     Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
-    Q* const CC = S + SM::nS;                     // [NCCV][BOX] packed cell constants
+    Q* const S2 = S + SM::nS;                     // [D][D][2][SB2] their half van Leer differences (R2)
+    Q* const CC = S2 + SM::nS2;                   // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
     Q* const ST = CC + SM::nCC + (SWEEP_B ? SM::nFF + SM::nFC : 0);   // [2][BOX] staged phi* (STAGE)
+    constexpr int SB2 = TL::SB2;
     Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
     int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B) + SM::rs_bytes);
     int* const cfl = csrc + BOX;
@@ -989,11 +1016,12 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
     const int kc = TL::box_of(la[0], la[1], la[2]);
     const int sc = TL::sbox_of(la[0], la[1], la[2]);
+    const int s2c = TL::s2box_of(la[0], la[1], la[2]);
 
     auto box_local = [&](int k, int l[3]) {
-        l[0] = k % TL::E0 - 2;
-        l[1] = D >= 2 ? (k / TL::E0) % TL::E1 - 2 : 0;
-        l[2] = D >= 3 ? k / (TL::E0 * TL::E1) - 2 : 0;
+        l[0] = k % TL::E0 - TL::HALO;
+        l[1] = D >= 2 ? (k / TL::E0) % TL::E1 - TL::HALO : 0;
+        l[2] = D >= 3 ? k / (TL::E0 * TL::E1) - TL::HALO : 0;
     };
     auto is_halo = [&](int k) {
         int l[3];
@@ -1228,9 +1256,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             // phibar+ and slopes of the cells [-1, T] around the tile from the stored arrays;
             // a mirrored cell takes the reflected velocity and flips the mirrored slope components
             for (int s2 = t; s2 < SB; s2 += TL::NT) {
-                const int sl0 = s2 % TL::F0 - 1, sl1 = D >= 2 ? (s2 / TL::F0) % TL::F1 - 1 : 0;
-                const int sl2 = D >= 3 ? s2 / (TL::F0 * TL::F1) - 1 : 0;
-                const int k = TL::box_of(sl0, sl1, sl2);
+                int sl[3];
+                TL::sbox_local(s2, sl);
+                const int k = TL::box_of(sl[0], sl[1], sl[2]);
                 const int rf = cfl[k] & 7;
                 const long long c = csrc[k];
                 Q qg, qb, qs[D][2];
@@ -1278,9 +1306,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 
         // ---- phase 2: half van Leer slopes (times dx) of the cells [-1, T] around the tile
         for (int s = t; s < (STORED ? 0 : SB); s += TL::NT) {
-            const int sl0 = s % TL::F0 - 1, sl1 = D >= 2 ? (s / TL::F0) % TL::F1 - 1 : 0;
-            const int sl2 = D >= 3 ? s / (TL::F0 * TL::F1) - 1 : 0;
-            const int k = TL::box_of(sl0, sl1, sl2);
+            int sl[3];
+            TL::sbox_local(s, sl);
+            const int k = TL::box_of(sl[0], sl[1], sl[2]);
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const Q c = P[f * BOX + k];
@@ -1297,6 +1325,32 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         }
         if (!STORED) __syncthreads();
 
+        // ---- phase 2b (face gradient): half van Leer differences along every axis a
+        //      of every slope component b, on the cells [-1, T] (the upwind cells)
+        if constexpr (R2) {
+            for (int s2 = t; s2 < SB2; s2 += TL::NT) {
+                const int l0 = s2 % TL::G0 - 1, l1 = D >= 2 ? (s2 / TL::G0) % TL::G1 - 1 : 0;
+                const int l2 = D >= 3 ? s2 / (TL::G0 * TL::G1) - 1 : 0;
+                const int ks = TL::sbox_of(l0, l1, l2);
+#pragma unroll
+                for (int f = 0; f < 2; ++f)
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        const Q c = S[(b * 2 + f) * SB + ks];
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const int st = TL::sstride(a);
+                            const Q l = S[(b * 2 + f) * SB + ks - st], r = S[(b * 2 + f) * SB + ks + st];
+                            Q o;
+#pragma unroll
+                            for (int v = 0; v < VC; ++v) o.v[v] = Num<T>::vanleer(c.v[v] - l.v[v], r.v[v] - c.v[v]);
+                            S2[((a * D + b) * 2 + f) * SB2 + s2] = o;
+                        }
+                    }
+            }
+            __syncthreads();
+        }
+
         // ---- phase 3: faces of the owned cell
         if (valid) {
 #pragma unroll
@@ -1306,6 +1360,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     if (side == 1 && !right[a]) continue;
                     const int Lb = kc + (side - 1) * TL::bstride(a), Rb = Lb + TL::bstride(a);
                     const int Ls = sc + (side - 1) * TL::sstride(a), Rs = Ls + TL::sstride(a);
+                    const int L2 = s2c + (side - 1) * TL::s2stride(a), R2i = L2 + TL::s2stride(a);
                     int lf[3] = {la[0], la[1], la[2]};
                     lf[a] += side;
                     const int fl = TL::face_local(a, lf[0], lf[1], lf[2]);
@@ -1324,6 +1379,15 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                             sb[b] = S[(b * 2 + 1) * SB + ups];
                         }
                         const T one = lft ? T(1) : T(-1);   // (x_f - x_up)/(dx/2) along the normal
+                        Q dg[R2 ? D : 1], db[R2 ? D : 1];   // slope derivatives along a at the upwind cell
+                        if constexpr (R2) {
+                            const int up2 = lft ? L2 : R2i;
+#pragma unroll
+                            for (int b = 0; b < D; ++b) {
+                                dg[b] = S2[((a * D + b) * 2 + 0) * SB2 + up2];
+                                db[b] = S2[((a * D + b) * 2 + 1) * SB2 + up2];
+                            }
+                        }
 #pragma unroll
                         for (int v = 0; v < VC; ++v) {
                             T rg = pg.v[v], rb = pb.v[v];
@@ -1333,21 +1397,37 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                                 rg = fma(k, sg[b].v[v], rg);
                                 rb = fma(k, sb[b].v[v], rb);
                             }
+                            if constexpr (R2) {   // - h xi . (x_f - x_up) grad sigma
+#pragma unroll
+                                for (int b = 0; b < D; ++b) {
+                                    rg = fma(-one * nu[v][b], dg[b].v[v], rg);
+                                    rb = fma(-one * nu[v][b], db[b].v[v], rb);
+                                }
+                            }
                             gb[v] = rg;
                             bb[v] = rb;
                         }
                     } else {
                         const T* Ps = reinterpret_cast<const T*>(P);
                         const T* Ss = reinterpret_cast<const T*>(S);
-                        auto recon = [&](int v, int up, int ups, T ka, T& rg, T& rb) {
+                        const T* S2s = reinterpret_cast<const T*>(S2);
+                        // side one: +1 for the left cell upwind, -1 for the right
+                        auto recon = [&](int v, int up, int ups, int up2, T one, T& rg, T& rb) {
                             const int pu = STORED ? ups : up;
                             rg = Ps[(0 * PN + pu) * VC + v];
                             rb = Ps[(1 * PN + pu) * VC + v];
 #pragma unroll
                             for (int b = 0; b < D; ++b) {
-                                const T k = (b == a) ? ka : -nu[v][b];
+                                const T k = (b == a) ? one - nu[v][a] : -nu[v][b];
                                 rg = fma(k, Ss[((b * 2 + 0) * SB + ups) * VC + v], rg);
                                 rb = fma(k, Ss[((b * 2 + 1) * SB + ups) * VC + v], rb);
+                            }
+                            if constexpr (R2) {
+#pragma unroll
+                                for (int b = 0; b < D; ++b) {
+                                    rg = fma(-one * nu[v][b], S2s[(((a * D + b) * 2 + 0) * SB2 + up2) * VC + v], rg);
+                                    rb = fma(-one * nu[v][b], S2s[(((a * D + b) * 2 + 1) * SB2 + up2) * VC + v], rb);
+                                }
                             }
                         };
 #pragma unroll
@@ -1355,11 +1435,11 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                             const T x = xi[v][a];
                             if (x != T(0)) {
                                 const bool lft = x > T(0);
-                                recon(v, lft ? Lb : Rb, lft ? Ls : Rs, (lft ? T(1) : T(-1)) - nu[v][a], gb[v], bb[v]);
+                                recon(v, lft ? Lb : Rb, lft ? Ls : Rs, lft ? L2 : R2i, lft ? T(1) : T(-1), gb[v], bb[v]);
                             } else {   // xi . n = 0: mean of both one-sided values
                                 T g1, b1, g2, b2;
-                                recon(v, Lb, Ls, T(1), g1, b1);
-                                recon(v, Rb, Rs, T(-1), g2, b2);
+                                recon(v, Lb, Ls, L2, T(1), g1, b1);
+                                recon(v, Rb, Rs, R2i, T(-1), g2, b2);
                                 gb[v] = T(0.5) * (g1 + g2);
                                 bb[v] = T(0.5) * (b1 + b2);
                             }

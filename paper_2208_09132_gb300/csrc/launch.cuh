@@ -13,12 +13,13 @@ struct TileShape {
 };
 
 // Work of one batched step: sweep items grouped by tile shape, face and cell ranges.
+constexpr int kMaxBatchShapes = 8;
 struct BatchPlan {
     int D;
     int ntile;
-    int tile_id[4];
-    const Item* sweep_items[4];
-    int n_sweep[4];
+    int tile_id[kMaxBatchShapes];
+    const Item* sweep_items[kMaxBatchShapes];
+    int n_sweep[kMaxBatchShapes];
     const RItem* face_items;
     int n_face;
     const RItem* cell_items;

@@ -67,6 +67,8 @@ def footprint_bytes(req: Request) -> int:
     h = ctypes.c_void_p()
     cdugks._check(lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)))
     try:
+        if req.cfg.get("recon", 0):
+            cdugks._check(lib.cdugks_set_reconstruction(h, int(req.cfg["recon"])))
         if req.tile_id:
             cdugks._check(lib.cdugks_set_tile(h, int(req.tile_id)))
         if req.velocity_groups:

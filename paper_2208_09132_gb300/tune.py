@@ -51,7 +51,8 @@ def size_key(cfg, precision, context):
     D = cfg["dim"]
     cells = wl.ncells(cfg)
     bucket = 2 ** int(round(math.log2(max(cells, 1))))
-    return f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}"
+    recon = ":faces-gradient" if cfg.get("recon", 0) else ""
+    return f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}{recon}"
 
 
 def candidates(cfg, precision, context="alone"):
@@ -59,9 +60,12 @@ def candidates(cfg, precision, context="alone"):
     nvt = (wl.nvel(cfg) + 3) // 4
     groups = [g for g in (1, 2, 4, 8, 16, 32) if g <= nvt]
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
+    r2 = bool(cfg.get("recon", 0))
     tiles = []
     for t in range(nt):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
+        if bool(mode & 8) != r2:
+            continue                      # shapes of the other reconstruction compute another scheme
         if context != "alone" and mode & 3 != 0:
             continue                      # only shapes that form phibar+ themselves are batched
         if mode & 3 == 2 and dirichlet:

@@ -86,3 +86,32 @@ def test_strerror_and_mu_convention():
     assert lib.cdugks_strerror(cdugks.ERR_NEGATIVE).decode()
     mu = cdugks.mu_from_kn(1e-3, 1.5, (2.5 / 1.5) / 0.5, 0.5, 1.0)
     assert abs(mu - wl.mu_from_kn(1e-3, 1.5, 2.5 / 1.5)) < 1e-15
+
+
+def test_reconstruction_selection_rules():
+    """Face-gradient reconstruction: 1D/2D only, three cells next to a specular
+    wall, before binding; its shapes only (host-side checks, no device)."""
+    lib = cdugks.load()
+
+    def handle(cfg, prec=cdugks.FP32):
+        g, v, p = cdugks.describe(cfg, prec)
+        h = ctypes.c_void_p()
+        assert lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)) == 0
+        return h
+
+    for dim, ok in ((1, True), (2, True), (3, False)):
+        cfg, _ = wl.random_smooth(dim=dim, n=(8, 8, 8), nv=(4, 4, 4), seed=1)
+        h = handle(cfg)
+        assert (lib.cdugks_set_reconstruction(h, 1) == 0) == ok
+        if ok:
+            info = cdugks.Info()
+            assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+            assert cdugks.tile_shape(cdugks.FP32, dim, info.tile_id)[1] & 8
+            assert lib.cdugks_set_tile(h, 0) != 0            # an upwind-cell shape is refused now
+        assert lib.cdugks_set_reconstruction(h, 7) != 0
+        lib.cdugks_destroy(h)
+    cfg, _ = wl.random_smooth(dim=1, n=(2,), nv=(4,), seed=1, bc=wl.BC_SPECULAR)
+    h = handle(cfg)
+    assert lib.cdugks_set_reconstruction(h, 1) != 0          # a wall needs 3 cells
+    assert lib.cdugks_set_reconstruction(h, 0) == 0
+    lib.cdugks_destroy(h)

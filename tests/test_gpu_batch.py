@@ -33,9 +33,11 @@ def _solo(cfg, f, prec, steps, tile=0, groups=0):
 @pytest.mark.parametrize("prec", [cdugks.FP32, cdugks.FP64])
 @pytest.mark.parametrize("graph", [0, 3])
 def test_batch_equals_members_alone(prec, graph):
-    probs = _members_1d()
     steps = 7
-    tiles = [k % cdugks.load().cdugks_tile_count(prec, 1) for k in range(len(probs))]
+    tiles = [k % cdugks.load().cdugks_tile_count(prec, 1) for k in range(len(_members_1d()))]
+    # every shape, a member of a face-gradient shape with that reconstruction
+    probs = [(dict(cfg, recon=1 if cdugks.tile_shape(prec, 1, t)[1] & 8 else 0), f)
+             for (cfg, f), t in zip(_members_1d(), tiles)]
     solvers = []
     for (cfg, f), t in zip(probs, tiles):
         s = cdugks.Solver(cfg, precision=prec, tile_id=t)
@@ -70,10 +72,11 @@ def test_batch_2d_members_and_uneven_steps():
 
 def test_tile_shapes_agree_with_the_oracle(oracle_mod):
     cfg, f = wl.random_smooth(dim=1, n=(300,), nv=(16,), seed=3, amp=0.3, kn=3e-3)
-    o = oracle_mod.Oracle(cfg)
-    o.init(f)
-    o.step(20)
-    ref = o.moments()
     for t in range(cdugks.load().cdugks_tile_count(cdugks.FP64, 1)):
-        got = _solo(cfg, f, cdugks.FP64, 20, tile=t, groups=2)
+        c = dict(cfg, recon=1 if cdugks.tile_shape(cdugks.FP64, 1, t)[1] & 8 else 0)
+        o = oracle_mod.Oracle(c)
+        o.init(f)
+        o.step(20)
+        ref = o.moments()
+        got = _solo(c, f, cdugks.FP64, 20, tile=t, groups=2)
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()

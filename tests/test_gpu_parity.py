@@ -176,6 +176,28 @@ def test_checkpoint_restart_is_bitwise(precision):
 
 
 @pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+@pytest.mark.parametrize("name", [c for c in CASES if not c.startswith("3d")])
+def test_face_gradient_reconstruction_matches_oracle(oracle_mod, name, precision, tol):
+    """The paper's face-gradient reconstruction (oracle reading R-c2) in its
+    default shape, macroscopic fields and every distribution value."""
+    (cfg, f), steps = case(name)
+    cfg = dict(cfg, recon=1)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    s = cdugks.Solver(cfg, precision=precision)
+    assert cdugks.tile_shape(precision, cfg["dim"], s.info().tile_id)[1] & 8
+    s.init(f)
+    s.step(steps)
+    assert s.sync_status() == 0
+    assert np.all(rel_linf(s.moments(), o.moments()) <= tol)
+    g, b = s.distributions()
+    go, bo = o.distributions()
+    assert np.abs(g - go).max() <= tol * np.abs(go).max()
+    assert np.abs(b - bo).max() <= tol * np.abs(bo).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
 @pytest.mark.parametrize("name", ["1d_sod_specular", "2d_kh_small", "3d_shear_small"])
 def test_stress_and_heat_flux_match_oracle(oracle_mod, name, precision, tol):
     """The per-cell pressure tensor and heat flux after a few steps.  Scales:
@@ -249,15 +271,24 @@ def test_status_flags_report_a_broken_state():
 def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     """All instantiated tile shapes, the prepared-shift ones included, give the oracle's result."""
     (cfg, f), steps = case(name)
-    o = oracle_mod.Oracle(cfg)
-    o.init(f)
-    o.step(steps)
-    ref = o.moments()
+    refs = {}
+
+    def ref_of(recon):       # the oracle's result with the reconstruction a shape implements
+        if recon not in refs:
+            o = oracle_mod.Oracle(dict(cfg, recon=recon))
+            o.init(f)
+            o.step(steps)
+            refs[recon] = o.moments()
+        return refs[recon]
+
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
-        if cdugks.tile_shape(precision, cfg["dim"], t)[1] & 3 == 2 and dirichlet:
+        mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
+        if mode & 3 == 2 and dirichlet:
             continue      # stored-slope shapes take periodic and specular boundaries only
-        s = cdugks.Solver(cfg, precision=precision, tile_id=t, velocity_groups=2)
+        recon = 1 if mode & 8 else 0
+        ref = ref_of(recon)
+        s = cdugks.Solver(dict(cfg, recon=recon), precision=precision, tile_id=t, velocity_groups=2)
         s.init(f)
         s.step(steps)
         assert s.sync_status() == 0

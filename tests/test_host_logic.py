@@ -20,6 +20,9 @@ def test_every_dimension_has_a_fused_default_and_a_face_store_shape():
             modes = _modes(prec, dim)
             assert modes[0] == 0                       # tile 0: fused, batchable, no extra buffers
             assert any(m & 4 for m in modes), (prec, dim, modes)
+            # the face-gradient reconstruction: fused face-store shapes, in 1D and 2D
+            assert all(m == 12 for m in modes if m & 8)
+            assert any(m & 8 for m in modes) == (dim < 3)
 
 
 def test_find_tile_returns_the_matching_shape():
@@ -33,8 +36,11 @@ def test_tuner_candidates_respect_batching_and_boundaries():
     alone = tune.candidates(cfg, cdugks.FP32, "alone")
     batch = tune.candidates(cfg, cdugks.FP32, "batch")
     modes = _modes(cdugks.FP32, 2)
-    assert {t for t, _ in alone} == set(range(len(modes)))              # periodic: every shape
-    assert {t for t, _ in batch} == {t for t, m in enumerate(modes) if m & 3 == 0}
+    # periodic: every shape of the default reconstruction; batched: those that form phibar+ themselves
+    assert {t for t, _ in alone} == {t for t, m in enumerate(modes) if not m & 8}
+    assert {t for t, _ in batch} == {t for t, m in enumerate(modes) if m & 3 == 0 and not m & 8}
+    r2 = tune.candidates(dict(cfg, recon=1), cdugks.FP32, "alone")
+    assert r2 and all(modes[t] & 8 for t, _ in r2)                      # the face-gradient shapes only
     assert all(g <= (wl.nvel(cfg) + 3) // 4 for _, g in alone)
     dcfg, _ = wl.random_smooth(dim=2, n=(8, 8), nv=(4, 4), seed=1, amp=0.1, kn=1e-2)
     dcfg = dict(dcfg, bc=[[wl.BC_DIRICHLET] * 2, [wl.BC_PERIODIC] * 2, [wl.BC_PERIODIC] * 2])
