@@ -10,10 +10,17 @@
 //             characteristic (eq. relation) and sum the face conserved variables
 //             (eqs. rhobar-rhoEbar) over the group's velocities.
 //   face      sum the groups' partial face W; face constants (u, T, tau).
-//   sweep B   the same reconstruction, then the face equilibrium (eqs. geq,
-//             beq), the inverse of eq. phibar, the microflux xi.n phi (eq. flux),
-//             its moments (for W) and the per-velocity net flux that gives phi*
-//             of eq. phiupdate, written to the other state buffer.
+//   sweep B   the face equilibrium (eqs. geq, beq), the inverse of eq. phibar,
+//             the microflux xi.n phi (eq. flux), its moments (for W) and the
+//             per-velocity net flux that gives phi* of eq. phiupdate, written to
+//             the other state buffer.  In the face-store modes sweep A keeps the
+//             reconstructed face values and sweep B is k_flux, which reads them;
+//             otherwise sweep B reconstructs them again.
+//
+// Sweep modes (the mode of a tile shape) choose where the stencil work is done:
+// on the halo box by the sweeps, once per point by a pre-pass (k_prep,
+// k_shslope), and whether face values are stored; bit 3 selects the paper's
+// face-gradient variant of the reconstruction (a three-cell halo).
 //   W update  W^{n+1} = W^n - dt sum_faces (M_right - M_left)/dx (eqs.
 //             rhoupdate-rhoEupdate, outward normals), the status check and the
 //             cell constants of W^{n+1}.
@@ -321,13 +328,6 @@ __device__ __forceinline__ void equilibrium(const C& c, const Vel<T, D>& v, T& g
     beq = (v.hxi2 + c.eb) * geq;
 }
 
-template <typename T, int D, typename C>
-__device__ __forceinline__ T zeta(const C& c, const Vel<T, D>& v) {
-    T z = -c.hu2;
-#pragma unroll
-    for (int a = 0; a < D; ++a) z = fma(v.xi[a], c.u[a], z);
-    return z;
-}
 
 // ------------------------------------------------------------- accumulation
 
@@ -659,13 +659,6 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
 // CTA per tile of cells and group of velocity chunks, phibar+ formed on the
 // tile and a one-cell halo in shared memory, slopes of the tile's own cells,
 // both written in their layouts.
-template <int D, int T0_, int T1_, int T2_>
-struct ShTile {
-    using TL = Tile<D, T0_, T1_, T2_>;
-    static constexpr int NT = TL::NT;
-    static constexpr int SB = TL::SB;     // the box: local cells [-1, T] per axis
-};
-
 template <typename T, int D, int T0_, int T1_, int T2_>
 __host__ __device__ constexpr size_t shslope_smem_bytes() {
     using TL = Tile<D, T0_, T1_, T2_>;
