@@ -51,12 +51,12 @@
  *        h xi.sigma_f.  It needs three ghost layers.
  *
  * Pinning (tests/test_oracle_pins.py): every step above is checked against a
- * closed form, an invariant or a textbook limit, except two O(h) pieces whose
- * effect stays below the scheme's own discretisation error in every closed
- * form available: the (h/2) S_b term of phibar+ and the S_b term of the face
- * inversion.  Parity for those two terms is weakly pinned (parity unpinned
- * beyond the consistency of the whole step); the S_b term of the distribution
- * update is pinned by the moving-frame sound-damping check.
+ * closed form, an invariant or a textbook limit.  The S_b term of the
+ * distribution update is pinned by the moving-frame sound-damping check; the
+ * two O(h) shares of S_b (in phibar+ and in the face inversion), whose effect
+ * stays below the discretisation error in every closed form, are pinned by
+ * discrete Galilean invariance: without either, a drifting solution departs
+ * from the resting one at first order in dt instead of second order.
  */
 #include "cdugks_oracle.h"
 
