@@ -8,7 +8,10 @@ the context the instance will run in:
 * ``context="batch"`` -- copies of the instance stepped as one batch, as many
   as needed to give every SM work, scored by time per phase-space point.
 
-The fastest candidate is cached in a JSON file (``CDUGKS_TUNE_CACHE`` or
+Group counts are tried at powers of two, then refined around the best one
+for its shape (how many CTAs a launch has against the SM count decides how
+full its last wave is).  The fastest candidate is cached in a JSON file
+(``CDUGKS_TUNE_CACHE`` or
 ``~/.cache/cdugks_tune.json``) keyed by the size bucket, so a later process
 reuses it.  Choices never change results beyond rounding order: every tile and
 group split computes the same scheme.
@@ -132,14 +135,27 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
     import torch
 
     results = []
-    for tile, groups in candidates(cfg, precision, context):
+
+    def trial(tile, groups):
         try:
             results.append((_time(cfg, precision, tile, groups, context, steps, device), tile, groups))
         except torch.OutOfMemoryError:     # this shape's extra buffers do not fit beside the state
             pass
         torch.cuda.empty_cache()
+
+    for tile, groups in candidates(cfg, precision, context):
+        trial(tile, groups)
     if not results:
         raise RuntimeError(f"no tile shape fits on {device} for {key}")
+    # refine the group count of the best shape between the powers of two (the
+    # number of CTAs against the SM count decides how full the last wave is)
+    results.sort()
+    _, t0, g0 = results[0]
+    nvt = (wl.nvel(cfg) + 3) // 4
+    tried = {(t, g) for _, t, g in results}
+    for g in sorted({g0 - 1, g0 + 1, (3 * g0) // 4, (5 * g0) // 4, (3 * g0) // 2}):
+        if 1 <= g <= nvt and (t0, g) not in tried:
+            trial(t0, g)
     results.sort()
     best = results[0]
     d = _load_cache(path)
