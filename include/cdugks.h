@@ -272,6 +272,17 @@ CDUGKS_API int cdugks_batch_capture(cdugks_batch_t *b, int steps_per_graph);
 CDUGKS_API int cdugks_batch_step(cdugks_batch_t *b, int nsteps);
 /* Synchronise the batch stream and report the first member status error. */
 CDUGKS_API int cdugks_batch_sync(cdugks_batch_t *b);
+/* Change the membership between steps (continuous batching): admit a bound,
+ * initialised handle of the batch's precision and dim, or retire a member
+ * (which keeps its state and may be read or stepped alone afterwards).  Both
+ * first finish the work in flight on the batch stream, then drop the binding
+ * and any captured graph: query cdugks_batch_workspace_bytes and call
+ * cdugks_batch_bind again before the next step.  A batch keeps at least one
+ * member; an admitted handle's own stream is synchronised too.
+ * Errors: INVALID (null, duplicate, not a member, last member, unbatchable
+ * shape, precision or dim mismatch), UNBOUND (member not ready), CUDA. */
+CDUGKS_API int cdugks_batch_admit(cdugks_batch_t *b, cdugks_t *member);
+CDUGKS_API int cdugks_batch_retire(cdugks_batch_t *b, cdugks_t *member);
 CDUGKS_API void cdugks_batch_destroy(cdugks_batch_t *b);
 
 CDUGKS_API void cdugks_destroy(cdugks_t *h);

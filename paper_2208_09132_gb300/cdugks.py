@@ -27,7 +27,7 @@ EXPORTS = [
     "cdugks_set_velocity_groups", "cdugks_set_reconstruction", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
     "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
-    "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy",
+    "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy", "cdugks_batch_admit", "cdugks_batch_retire",
 ]
 
 
@@ -113,6 +113,8 @@ def load(build_if_needed: bool = True):
         "cdugks_batch_capture": (i, [vp, i]),
         "cdugks_batch_step": (i, [vp, i]),
         "cdugks_batch_sync": (i, [vp]),
+        "cdugks_batch_admit": (i, [vp, vp]),
+        "cdugks_batch_retire": (i, [vp, vp]),
         "cdugks_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -294,15 +296,36 @@ class Batch:
         h = ctypes.c_void_p()
         _check(self._lib.cdugks_batch_create(arr, len(self.members), ctypes.byref(h)))
         self._h = h
+        self._dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self._dev)
+        self._ws = None
+        self._bind()
+
+    def _bind(self):
+        """(Re)allocate the table workspace for the current members and bind it."""
+        import torch
+
         n = ctypes.c_size_t()
-        _check(self._lib.cdugks_batch_workspace_bytes(h, ctypes.byref(n)))
-        dev = torch.device(device)
-        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
-        self._ws = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=dev)
+        _check(self._lib.cdugks_batch_workspace_bytes(self._h, ctypes.byref(n)))
+        if self._ws is None or self._ws.numel() < int(n.value) + 256:
+            self._ws = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self._dev)
         base = self._ws.data_ptr()
         aligned = (base + 255) // 256 * 256
-        _check(self._lib.cdugks_batch_bind(h, ctypes.c_void_p(aligned), ctypes.c_size_t(self._ws.numel() - (aligned - base)),
+        _check(self._lib.cdugks_batch_bind(self._h, ctypes.c_void_p(aligned),
+                                           ctypes.c_size_t(self._ws.numel() - (aligned - base)),
                                            ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def admit(self, solver):
+        """Add a member between steps (drops a captured graph)."""
+        _check(self._lib.cdugks_batch_admit(self._h, solver._h))
+        self.members.append(solver)
+        self._bind()
+
+    def retire(self, solver):
+        """Remove a member between steps; it keeps its state (drops a captured graph)."""
+        _check(self._lib.cdugks_batch_retire(self._h, solver._h))
+        self.members.remove(solver)
+        self._bind()
 
     def __del__(self):
         h = getattr(self, "_h", None)

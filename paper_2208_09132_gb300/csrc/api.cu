@@ -959,41 +959,42 @@ void batch_drop_graph(cdugks_batch* b) {
     b->graph_steps = 0;
 }
 
-}  // namespace
+// A handle that may join a batch of this precision and dimension.
+int batch_member_ok(const cdugks* m, int prec, int D) {
+    if (!m || !m->bound || !m->initialised) return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
+    if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
+    if (cdg::mode_source(tile_mode(m->prec, m->g.D, m->g.tile_id)) != cdg::MODE_FUSED)
+        return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
+    return CDUGKS_OK;
+}
 
-extern "C" {
-
-int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
-    if (!out) return fail(CDUGKS_ERR_INVALID, "null output pointer");
-    *out = nullptr;
-    if (!members || n < 1) return fail(CDUGKS_ERR_INVALID, "a batch needs at least one member");
-    const int prec = members[0] ? members[0]->prec : -1, D = members[0] ? members[0]->g.D : -1;
-    for (int i = 0; i < n; ++i) {
-        const cdugks* m = members[i];
-        if (!m || !m->bound || !m->initialised)
-            return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
-        if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
-        if (cdg::mode_source(tile_mode(m->prec, m->g.D, m->g.tile_id)) != cdg::MODE_FUSED)
-            return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
-        for (int j = 0; j < i; ++j)
-            if (members[j] == m) return fail(CDUGKS_ERR_INVALID, "a member appears twice");
+// Before the membership changes: finish the work in flight on the batch stream
+// (the members' state must be final) and drop the binding and the graph.
+int batch_unbind(cdugks_batch* b) {
+    if (b->bound && b->stream) {
+        const cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e) return cuda_fail(e, "batch sync before a membership change");
     }
-    cdugks_batch* b = new (std::nothrow) cdugks_batch();
-    if (!b) return fail(CDUGKS_ERR_OOM, "host allocation failed");
-    b->mem.assign(members, members + n);
-    b->prec = prec;
-    b->D = D;
-    // sweep work items grouped by tile shape, largest per-item work first
+    batch_drop_graph(b);
+    b->bound = false;
+    b->base = nullptr;
+    return CDUGKS_OK;
+}
+
+// Work lists and workspace layout of the current members: sweep items grouped
+// by tile shape (largest per-item work first), face and cell ranges, the
+// instance table.
+int batch_plan(cdugks_batch* b) {
+    const int n = (int)b->mem.size(), D = b->D;
+    b->tile_ids.clear();
     for (int i = 0; i < n; ++i) {
         const int id = b->mem[i]->g.tile_id;
         if (std::find(b->tile_ids.begin(), b->tile_ids.end(), id) == b->tile_ids.end()) b->tile_ids.push_back(id);
     }
     std::sort(b->tile_ids.begin(), b->tile_ids.end());
-    if (b->tile_ids.size() > (size_t)cdg::kMaxBatchShapes) {     // before any per-shape table is filled
-        delete b;
+    if (b->tile_ids.size() > (size_t)cdg::kMaxBatchShapes)     // before any per-shape table is filled
         return fail(CDUGKS_ERR_INVALID, "too many tile shapes in one batch");
-    }
-    b->sweep_items.resize(b->tile_ids.size());
+    b->sweep_items.assign(b->tile_ids.size(), {});
     for (int i = 0; i < n; ++i) {
         const Geo& g = b->mem[i]->g;
         const int k = (int)(std::find(b->tile_ids.begin(), b->tile_ids.end(), g.tile_id) - b->tile_ids.begin());
@@ -1009,16 +1010,17 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
             return wx > wy;
         });
     const long long R = 1024;
+    b->face_items.clear();
+    b->cell_items.clear();
     for (int i = 0; i < n; ++i) {
         const Geo& g = b->mem[i]->g;
         for (int a = 0; a < D; ++a)
             for (long long s0 = 0; s0 < g.nf[a]; s0 += R) b->face_items.push_back(RItem{i, a, s0, std::min(R, g.nf[a] - s0)});
         for (long long s0 = 0; s0 < g.Nc; s0 += R) b->cell_items.push_back(RItem{i, 0, s0, std::min(R, g.Nc - s0)});
     }
-    if (prec == CDUGKS_FP32) fill_insts<float>(b);
+    if (b->prec == CDUGKS_FP32) fill_insts<float>(b);
     else fill_insts<double>(b);
-    b->cur.resize(n);
-    // workspace layout
+    b->cur.assign(n, 0);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -1031,8 +1033,65 @@ int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
     b->off_face = take(sizeof(RItem) * b->face_items.size());
     b->off_cell = take(sizeof(RItem) * b->cell_items.size());
     b->total = off;
+    return CDUGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdugks_batch_create(cdugks_t* const* members, int n, cdugks_batch_t** out) {
+    if (!out) return fail(CDUGKS_ERR_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!members || n < 1) return fail(CDUGKS_ERR_INVALID, "a batch needs at least one member");
+    const int prec = members[0] ? members[0]->prec : -1, D = members[0] ? members[0]->g.D : -1;
+    for (int i = 0; i < n; ++i) {
+        const int rc = batch_member_ok(members[i], prec, D);
+        if (rc) return rc;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(CDUGKS_ERR_INVALID, "a member appears twice");
+    }
+    cdugks_batch* b = new (std::nothrow) cdugks_batch();
+    if (!b) return fail(CDUGKS_ERR_OOM, "host allocation failed");
+    b->mem.assign(members, members + n);
+    b->prec = prec;
+    b->D = D;
+    const int rc = batch_plan(b);
+    if (rc) {
+        delete b;
+        return rc;
+    }
     *out = b;
     return CDUGKS_OK;
+}
+
+int cdugks_batch_admit(cdugks_batch_t* b, cdugks_t* member) {
+    if (!b) return fail(CDUGKS_ERR_INVALID, "null batch");
+    int rc = batch_member_ok(member, b->prec, b->D);
+    if (rc) return rc;
+    if (std::find(b->mem.begin(), b->mem.end(), member) != b->mem.end())
+        return fail(CDUGKS_ERR_INVALID, "already a member");
+    const cudaError_t e = cudaStreamSynchronize(member->stream);   // its own work lands before the batch's
+    if (e) return cuda_fail(e, "member sync before admission");
+    if ((rc = batch_unbind(b))) return rc;
+    b->mem.push_back(member);
+    if ((rc = batch_plan(b))) {
+        b->mem.pop_back();
+        batch_plan(b);
+        return rc;
+    }
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_retire(cdugks_batch_t* b, cdugks_t* member) {
+    if (!b || !member) return fail(CDUGKS_ERR_INVALID, "null argument");
+    const auto it = std::find(b->mem.begin(), b->mem.end(), member);
+    if (it == b->mem.end()) return fail(CDUGKS_ERR_INVALID, "not a member");
+    if (b->mem.size() == 1) return fail(CDUGKS_ERR_INVALID, "a batch needs at least one member");
+    int rc = batch_unbind(b);
+    if (rc) return rc;
+    b->mem.erase(it);
+    return batch_plan(b);
 }
 
 int cdugks_batch_workspace_bytes(const cdugks_batch_t* b, size_t* bytes) {

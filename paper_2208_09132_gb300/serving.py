@@ -12,8 +12,10 @@ The server
   its own step count, so a request computes exactly what it would alone;
 * retires a request when it reaches its end time: reads its macroscopic
   fields back, frees its workspace, and records its time to solution;
-* rebuilds the batch whenever the membership changes, so requests that
-  arrive while others run join them at the next round.
+* changes the batch's membership in place between rounds
+  (``cdugks_batch_admit`` / ``cdugks_batch_retire``), so requests that arrive
+  while others run join them at the next round; a batch is created only when
+  none is running.
 
 All arithmetic runs in the CUDA library; this module only schedules.
 """
@@ -98,7 +100,8 @@ class Server:
         self.batch = None
         self.point_updates = 0
         self.rounds = 0
-        self.rebuilds = 0
+        self.rebuilds = 0          # batches created
+        self.membership_changes = 0
         self.launches = 0          # kernels of this library launched by the server
 
     # -- admission --------------------------------------------------------
@@ -108,8 +111,8 @@ class Server:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the budget {self.budget}")
         self.waiting.append(req)
 
-    def _admit(self, now: float) -> bool:
-        changed = False
+    def _admit(self, now: float) -> list:
+        admitted = []
         while self.waiting and len(self.active) < self.max_slots:
             req = self.waiting[0]
             if self.used + req.footprint > self.budget:
@@ -123,25 +126,27 @@ class Server:
             req.admitted_at = now
             self.used += req.footprint
             self.active.append(req)
-            changed = True
-        return changed
+            admitted.append(req)
+        return admitted
 
     # -- retirement -------------------------------------------------------
-    def _retire(self, now: float) -> bool:
-        keep, changed = [], False
-        for req in self.active:
-            if req.done_steps >= req.nsteps:
-                req.result = req.solver.moments()
-                self.launches += 1                # the moments
-                req.finished_at = now
-                req.solver = None                  # frees its workspace
-                self.used -= req.footprint
-                self.finished.append(req)
-                changed = True
+    def _retire(self, now: float):
+        done = [q for q in self.active if q.done_steps >= q.nsteps]
+        self.active = [q for q in self.active if q.done_steps < q.nsteps]
+        if done and self.batch is not None:
+            if self.active:
+                for req in done:
+                    self.batch.retire(req.solver)
+                    self.membership_changes += 1
             else:
-                keep.append(req)
-        self.active = keep
-        return changed
+                self.batch = None                  # the last members leave: drop the batch first
+        for req in done:
+            req.result = req.solver.moments()
+            self.launches += 1                    # the moments
+            req.finished_at = now
+            req.solver = None                      # frees its workspace
+            self.used -= req.footprint
+            self.finished.append(req)
 
     # -- one round ----------------------------------------------------------
     def _round(self):
@@ -168,17 +173,20 @@ class Server:
                 break
             while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
-            changed = self._admit(now)
+            admitted = self._admit(now)
             if not self.active:
                 if pending:
                     time.sleep(min(0.001, max(0.0, pending[0].arrival - now)))
                 continue
-            if changed or self.batch is None:
+            if self.batch is None:
                 self.batch = cdugks.Batch([q.solver for q in self.active], device=self.device)
                 self.rebuilds += 1
+            else:
+                for req in admitted:
+                    self.batch.admit(req.solver)
+                    self.membership_changes += 1
             self._round()
-            if self._retire(self.clock() - t0):
-                self.batch = None
+            self._retire(self.clock() - t0)
         return self.finished
 
     # -- report ---------------------------------------------------------------
@@ -192,6 +200,7 @@ class Server:
             "aggregate_point_updates_per_s": self.point_updates / wall_s if wall_s > 0 else None,
             "rounds": self.rounds,
             "batch_rebuilds": self.rebuilds,
+            "membership_changes": self.membership_changes,
             "kernel_launches": self.launches,
         }
 

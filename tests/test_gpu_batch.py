@@ -80,3 +80,41 @@ def test_tile_shapes_agree_with_the_oracle(oracle_mod):
         ref = o.moments()
         got = _solo(c, f, cdugks.FP64, 20, tile=t, groups=2)
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("graph", [0, 2])
+def test_admit_and_retire_between_steps(graph):
+    """Continuous batching: membership changes between steps leave every
+    member's trajectory identical to stepping it alone."""
+    probs = _members_1d(seed=9, count=4)
+    prec = cdugks.FP32
+    solvers = []
+    for cfg, f in probs:
+        s = cdugks.Solver(cfg, precision=prec)
+        s.init(f)
+        solvers.append(s)
+    s0, s1, s2, s3 = solvers
+    b = cdugks.Batch([s0, s1])
+    if graph:
+        b.capture(graph)
+    b.step(4)                          # s0, s1: 4
+    b.admit(s2)
+    if graph:
+        b.capture(graph)
+    b.step(3)                          # s0, s1: 7; s2: 3
+    b.retire(s0)
+    b.admit(s3)
+    b.step(5)                          # s1: 12; s2: 8; s3: 5
+    assert b.sync() == 0
+    s0.step(2)                         # a retired member steps alone: 9
+    with pytest.raises(cdugks.CdugksError):
+        b.retire(s0)                   # not a member any more
+    with pytest.raises(cdugks.CdugksError):
+        b.admit(s1)                    # already a member
+    for (cfg, f), s, n in zip(probs, solvers, (9, 12, 8, 5)):
+        assert s.info().steps == n
+        assert np.array_equal(s.moments(), _solo(cfg, f, prec, n))
+    b.retire(s1)
+    b.retire(s2)
+    with pytest.raises(cdugks.CdugksError):
+        b.retire(s3)                   # a batch keeps one member
