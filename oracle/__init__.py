@@ -58,6 +58,7 @@ class _Params(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("cfl", ctypes.c_double),
         ("recon", ctypes.c_int),
+        ("collision", ctypes.c_int),
     ]
 
 
@@ -81,6 +82,8 @@ def _load():
         lib.oracle_distributions.argtypes = [ctypes.c_void_p, dp, dp]
         lib.oracle_stress_heat_flux.argtypes = [ctypes.c_void_p, dp]
         lib.oracle_equilibrium.argtypes = [ctypes.c_void_p, d, dp, d, dp, dp]
+        lib.oracle_shakhov_equilibrium.argtypes = [ctypes.c_void_p, d, dp, d, dp, dp, dp]
+        lib.oracle_cell_heat_flux.argtypes = [ctypes.c_void_p, dp]
         lib.oracle_set_state.argtypes = [ctypes.c_void_p, dp, dp, dp]
         lib.oracle_face_W.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
         lib.oracle_velocities.argtypes = [ctypes.c_void_p, dp, dp]
@@ -118,7 +121,8 @@ class Oracle:
 
     ``cfg`` is a problem description dict (see ``paper_2208_09132_gb300.workloads``):
     keys dim, n, lo, hi, bc, nv, vlo, vhi, rule, K, R, mu_ref, T_ref, omega,
-    Pr, dt, cfl.
+    Pr, dt, cfl; optional recon (0 upwind cell, 1 face gradient) and
+    collision (0 the paper's two relaxation times, 1 Shakhov S-model).
     """
 
     def __init__(self, cfg: dict):
@@ -145,6 +149,7 @@ class Oracle:
         p.dt = float(cfg.get("dt", 0.0) or 0.0)
         p.cfl = float(cfg.get("cfl", 0.5))
         p.recon = int(cfg.get("recon", 0))
+        p.collision = int(cfg.get("collision", 0))
         h = lib.oracle_create(ctypes.byref(p))
         if not h:
             raise ValueError("oracle_create rejected the problem description")
@@ -191,6 +196,23 @@ class Oracle:
         out = np.zeros((self.Nc, D * D + D))
         self._lib.oracle_stress_heat_flux(self._h, _ptr(out))
         return out[:, : D * D].reshape(self.Nc, D, D), out[:, D * D:]
+
+    def cell_heat_flux(self) -> np.ndarray:
+        """The heat flux each cell's equilibrium uses at the current time level,
+        [Nc, D] (Shakhov model; zero otherwise)."""
+        out = np.zeros((self.Nc, self.D))
+        self._lib.oracle_cell_heat_flux(self._h, _ptr(out))
+        return out
+
+    def shakhov_equilibrium(self, rho: float, u, T: float, q):
+        uu = np.zeros(3)
+        uu[: self.D] = np.asarray(u, dtype=np.float64).reshape(-1)[: self.D]
+        qq = np.zeros(3)
+        qq[: self.D] = np.asarray(q, dtype=np.float64).reshape(-1)[: self.D]
+        ge = np.zeros(self.Nv)
+        be = np.zeros(self.Nv)
+        self._lib.oracle_shakhov_equilibrium(self._h, float(rho), _ptr(uu), float(T), _ptr(qq), _ptr(ge), _ptr(be))
+        return ge, be
 
     def distributions(self):
         g = np.zeros((self.Nc, self.Nv))

@@ -49,6 +49,22 @@
  *        (the derivative along the face normal of each slope component, van
  *        Leer limited like the slopes), and phibar(x_f, t+h) = phibar+(x_f) -
  *        h xi.sigma_f.  It needs three ghost layers.
+ *   R-s  (collision = 1, selectable) The Shakhov S-model in place of the
+ *        paper's two relaxation times (Sec. 1 names it as the other route to
+ *        Pr != 1; the paper gives no form, so it is taken from Shakhov's model
+ *        of 1968 as the DUGKS literature applies it to reduced distributions):
+ *        one relaxation time tau = mu/p for g and b, no b-source, and the
+ *        equilibria carry the heat-flux correction (shakhov_equilibrium below).
+ *   R-s1 The heat flux of a cell or face is taken relative to its conserved
+ *        variables W: q_a = sum w xi_a b - u_a rho E - sum_b u_b (sum w xi_a
+ *        xi_b g - rho u_a u_b), with rho, u, E from W (heat_flux below).
+ *   R-s2 The heat flux in the equilibrium at t_{n+1} comes from the update's
+ *        explicit part (every term of eq. phiupdate's numerator but the new
+ *        equilibrium): the collision relaxes q at the rate Pr/tau, so the
+ *        trapezoid rule gives q^{n+1} = q(explicit part)/(1 + dt Pr/(2 tau^{n+1})).
+ *        At a face likewise q = q(phibar)/(1 + h Pr/(2 tau)).  The heat flux
+ *        is tracked per cell like W; the initial Maxwellian state has q = 0,
+ *        and so have Dirichlet ghosts.
  *
  * Pinning (tests/test_oracle_pins.py): every step above is checked against a
  * closed form, an invariant or a textbook limit.  The S_b term of the
@@ -83,6 +99,7 @@ struct oracle {
     /* state */
     double *g, *b;      /* [Ne][Nv] */
     double *W;          /* [Ne][NW] */
+    double *q;          /* [Ne][3] tracked heat flux at t_n (collision = 1, R-s2) */
     double *Wdir;       /* [Ne][NW] fixed Dirichlet ghost state */
     /* intermediates of the step, kept in full */
     double *geq, *beq, *Sb;     /* [Ne][Nv] cell equilibria and b-source at t_n */
@@ -94,6 +111,7 @@ struct oracle {
     double *gf, *bf;            /* [3][Ne][Nv] phi at faces, t + h (inverse of eq. phibar) */
     double *dFg, *dFb;          /* [Ne][Nv] net microflux per cell volume (eq. flux) */
     double *Wn;                 /* [Ne][NW] updated conserved variables */
+    double *qn;                 /* [Ne][3] heat flux at t_{n+1} (collision = 1) */
     long steps;
 };
 
@@ -174,12 +192,13 @@ static void macro_from_W(const struct oracle *o, const double *W, double *rho, d
 }
 
 /* tau_g = mu/p with mu = mu_r (T/T_r)^w (eq. visc), tau_b = tau_g / Pr,
- * 1/tau_bg = 1/tau_b - 1/tau_g (reading R-g). */
+ * 1/tau_bg = 1/tau_b - 1/tau_g (reading R-g).  The Shakhov model (R-s) has
+ * the one time tau_b = tau_g and no b-source. */
 static void relax_times(const struct oracle *o, double rho, double T, double *tg, double *tb, double *inv_tbg) {
     double mu = o->p.mu_ref * pow(T / o->p.T_ref, o->p.omega);
     double p = rho * o->p.R * T;
     *tg = mu / p;
-    *tb = *tg / o->p.Pr;
+    *tb = o->p.collision ? *tg : *tg / o->p.Pr;
     *inv_tbg = 1.0 / *tb - 1.0 / *tg;
 }
 
@@ -202,6 +221,69 @@ static double zeta(const struct oracle *o, const double *xi, const double u[3]) 
     double xu = 0.0, u2 = 0.0;
     for (int a = 0; a < o->D; ++a) { xu += xi[a] * u[a]; u2 += u[a] * u[a]; }
     return xu - 0.5 * u2;
+}
+
+/* Shakhov S-model equilibrium of the reduced distributions (R-s).  With
+ * eta the L = 3 - D + K velocity components and internal degrees of freedom
+ * the D-dimensional grid does not resolve (N = 3 + K in all), the S-model
+ * equilibrium of the full distribution is
+ *     f_S = f_M [1 + (1 - Pr) c.q / ((N + 2) p RT) ((c^2 + eta^2)/RT - (N + 2))],
+ * c = xi - u: Shakhov's form with the monatomic 5 read as N + 2, so that f_S
+ * has the density, momentum, energy and pressure tensor of f_M and the heat
+ * flux (1 - Pr) q.  g = int f deta and b = int (xi^2 + eta^2)/2 f deta with the
+ * Gaussian moments of eta (<1> = 1, <eta^2> = L RT, <eta^4> = L (L+2) RT^2):
+ *     g_S = g_M [1 + A c.q (c^2/RT - D - 2)],
+ *     b_S = b_M + A c.q g_M [(xi^2/2)(c^2/RT - D - 2) + (L/2)(c^2 - D RT)],
+ * A = (1 - Pr)/((K + 5) p RT). */
+static void shakhov_equilibrium(const struct oracle *o, double rho, const double u[3], double T, const double q[3],
+                                const double *xi, double *geq, double *beq) {
+    double gM, bM;
+    equilibrium(o, rho, u, T, xi, &gM, &bM);
+    double RT = o->p.R * T;
+    double c2 = 0.0, xi2 = 0.0, cq = 0.0;
+    for (int a = 0; a < o->D; ++a) {
+        double c = xi[a] - u[a];
+        c2 += c * c;
+        xi2 += xi[a] * xi[a];
+        cq += c * q[a];
+    }
+    double A = (1.0 - o->p.Pr) / ((o->p.K + 5.0) * rho * RT * RT);
+    double L = 3.0 - o->D + o->p.K;
+    double P1 = c2 / RT - o->D - 2.0;
+    *geq = gM * (1.0 + A * cq * P1);
+    *beq = bM + A * cq * gM * (0.5 * xi2 * P1 + 0.5 * L * (c2 - o->D * RT));
+}
+
+/* The equilibria of the selected collision model at one place. */
+static void model_equilibrium(const struct oracle *o, double rho, const double u[3], double T, const double q[3],
+                              const double *xi, double *geq, double *beq) {
+    if (o->p.collision) shakhov_equilibrium(o, rho, u, T, q, xi, geq, beq);
+    else equilibrium(o, rho, u, T, xi, geq, beq);
+}
+
+/* Heat flux of distributions (g, b) [Nv] at one place relative to the
+ * conserved variables W there (R-s1): with rho, u, E from W, the pressure
+ * tensor P_ab = sum w xi_a xi_b g - rho u_a u_b and
+ *     q_a = sum w xi_a b - u_a rho E - sum_b u_b P_ab. */
+static void heat_flux(const struct oracle *o, const double *g, const double *b, const double *W, double q[3]) {
+    int D = o->D;
+    double rho, u[3], T;
+    macro_from_W(o, W, &rho, u, &T);
+    nsum mF[3], mP[3][3];
+    memset(mF, 0, sizeof(mF));
+    memset(mP, 0, sizeof(mP));
+    for (long i = 0; i < o->Nv; ++i) {
+        const double *xi = &o->xi[3 * i];
+        for (int a = 0; a < D; ++a) {
+            nsum_add(&mF[a], o->w[i] * xi[a] * b[i]);
+            for (int bb = 0; bb < D; ++bb) nsum_add(&mP[a][bb], o->w[i] * xi[a] * xi[bb] * g[i]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) q[a] = 0.0;
+    for (int a = 0; a < D; ++a) {
+        q[a] = nsum_val(&mF[a]) - u[a] * W[1 + D];
+        for (int bb = 0; bb < D; ++bb) q[a] -= u[bb] * (nsum_val(&mP[a][bb]) - rho * u[a] * u[bb]);
+    }
 }
 
 /* ------------------------------------------------------------- ghost layers */
@@ -228,6 +310,7 @@ static void fill_axis(struct oracle *o, int a) {
             mirror = 1;
         } else { /* Dirichlet: fixed equilibrium of the initial state */
             memcpy(&o->W[c * NW], &o->Wdir[c * NW], NW * sizeof(double));
+            for (int d = 0; d < 3; ++d) o->q[c * 3 + d] = 0.0;
             double rho, u[3], T;
             macro_from_W(o, &o->W[c * NW], &rho, u, &T);
             for (long i = 0; i < Nv; ++i)
@@ -237,6 +320,8 @@ static void fill_axis(struct oracle *o, int a) {
         long s = cidx(o, src[0], src[1], src[2]);
         memcpy(&o->W[c * NW], &o->W[s * NW], NW * sizeof(double));
         if (mirror) o->W[c * NW + 1 + a] = -o->W[s * NW + 1 + a];
+        for (int d = 0; d < 3; ++d) o->q[c * 3 + d] = o->q[s * 3 + d];
+        if (mirror) o->q[c * 3 + a] = -o->q[s * 3 + a];
         for (long i = 0; i < Nv; ++i) {
             long si = mirror ? o->refl[a][i] : i;
             o->g[c * Nv + i] = o->g[s * Nv + si];
@@ -254,7 +339,7 @@ static void fill_ghosts(struct oracle *o) {
 static void *xalloc(size_t n) { void *p = calloc(n ? n : 1, 1); return p; }
 
 oracle_t *oracle_create(const oracle_params *p) {
-    if (!p || p->D < 1 || p->D > 3) return NULL;
+    if (!p || p->D < 1 || p->D > 3 || p->collision < 0 || p->collision > 1) return NULL;
     struct oracle *o = (struct oracle *)xalloc(sizeof(*o));
     if (!o) return NULL;
     o->p = *p;
@@ -320,11 +405,13 @@ oracle_t *oracle_create(const oracle_params *p) {
     o->dFg = xalloc(F); o->dFb = xalloc(F);
     o->W = xalloc(sizeof(double) * NW * Ne);
     o->Wn = xalloc(sizeof(double) * NW * Ne);
+    o->q = xalloc(sizeof(double) * 3 * Ne);
+    o->qn = xalloc(sizeof(double) * 3 * Ne);
     o->Wdir = xalloc(sizeof(double) * NW * Ne);
     o->Wf = xalloc(sizeof(double) * 3 * NW * Ne);
     if (!o->g || !o->b || !o->geq || !o->beq || !o->Sb || !o->gp || !o->bp || !o->sg || !o->sb ||
         (p->recon && (!o->s2g || !o->s2b)) ||
-        !o->gfb || !o->bfb || !o->gf || !o->bf || !o->dFg || !o->dFb || !o->W || !o->Wn ||
+        !o->gfb || !o->bfb || !o->gf || !o->bf || !o->dFg || !o->dFb || !o->W || !o->Wn || !o->q || !o->qn ||
         !o->Wdir || !o->Wf || !o->xi || !o->w) {
         oracle_destroy(o);
         return NULL;
@@ -354,7 +441,7 @@ void oracle_destroy(oracle_t *o) {
     free(o->gp); free(o->bp); free(o->sg); free(o->sb); free(o->s2g); free(o->s2b);
     free(o->gfb); free(o->bfb); free(o->gf); free(o->bf);
     free(o->dFg); free(o->dFb);
-    free(o->W); free(o->Wn); free(o->Wdir); free(o->Wf);
+    free(o->W); free(o->Wn); free(o->Wdir); free(o->Wf); free(o->q); free(o->qn);
     free(o);
 }
 
@@ -381,6 +468,7 @@ int oracle_init(oracle_t *o, const double *rho_u_T) {
     long Nv = o->Nv;
     long ic = 0;
     memset(o->W, 0, sizeof(double) * NW * o->Ne);
+    memset(o->q, 0, sizeof(double) * 3 * o->Ne);   /* a Maxwellian carries no heat flux (R-s2) */
     for (int z = 0; z < o->n[2]; ++z)
         for (int y = 0; y < o->n[1]; ++y)
             for (int x = 0; x < o->n[0]; ++x, ++ic) {
@@ -427,7 +515,7 @@ static void one_step(struct oracle *o) {
     /* (1) cell equilibria, b-source and the quarter-step-advanced
      *     distributions phibar+ = (2tau-h)/(2tau) phi + h/(2tau) phi_eq + (h/2) S
      *     (eq. phibarplus; S_g = 0, S_b = Z/tau_bg (g - g_eq) for a = 0,
-     *     eqs. gsource/bsource). */
+     *     eqs. gsource/bsource; Shakhov: phi_eq = phi_S with the cell's q, S_b = 0). */
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < Ne; ++c) {
         double rho, u[3], T, tg, tb, itbg;
@@ -436,7 +524,7 @@ static void one_step(struct oracle *o) {
         for (long i = 0; i < Nv; ++i) {
             long k = c * Nv + i;
             const double *xi = &o->xi[3 * i];
-            equilibrium(o, rho, u, T, xi, &o->geq[k], &o->beq[k]);
+            model_equilibrium(o, rho, u, T, &o->q[c * 3], xi, &o->geq[k], &o->beq[k]);
             o->Sb[k] = zeta(o, xi, u) * itbg * (o->g[k] - o->geq[k]);
             o->gp[k] = (2.0 * tg - h) / (2.0 * tg) * o->g[k] + h / (2.0 * tg) * o->geq[k];
             o->bp[k] = (2.0 * tb - h) / (2.0 * tb) * o->b[k] + h / (2.0 * tb) * o->beq[k] + 0.5 * h * o->Sb[k];
@@ -558,6 +646,8 @@ static void one_step(struct oracle *o) {
             double *Wf = &o->Wf[fo * NW];
             for (int k = 0; k < NW; ++k) Wf[k] = 0.0;
             for (int k = 0; k < 2 + D; ++k) Wf[k] = nsum_val(&m[k]);
+            double qf[3] = {0.0, 0.0, 0.0};   /* Shakhov: the face heat flux (R-s1, R-s2) */
+            if (o->p.collision) heat_flux(o, &o->gfb[fo * Nv], &o->bfb[fo * Nv], Wf, qf);
 
             /* (5) face tau and equilibria, then phi = inverse of eq. phibar:
              *     g_f = (2 tau_g gbar + h g_eq)/(2 tau_g + h),
@@ -565,10 +655,11 @@ static void one_step(struct oracle *o) {
             double rho, u[3], T, tg, tb, itbg;
             macro_from_W(o, Wf, &rho, u, &T);
             relax_times(o, rho, T, &tg, &tb, &itbg);
+            for (int d = 0; d < 3; ++d) qf[d] /= 1.0 + h * o->p.Pr / (2.0 * tg);
             for (long i = 0; i < Nv; ++i) {
                 const double *xi = &o->xi[3 * i];
                 double ge, be;
-                equilibrium(o, rho, u, T, xi, &ge, &be);
+                model_equilibrium(o, rho, u, T, qf, xi, &ge, &be);
                 double G = o->gfb[fo * Nv + i], B = o->bfb[fo * Nv + i];
                 double gfv = (2.0 * tg * G + h * ge) / (2.0 * tg + h);
                 double bfv = (2.0 * tb * B + h * be + h * tb * zeta(o, xi, u) * itbg * (gfv - ge)) / (2.0 * tb + h);
@@ -615,10 +706,24 @@ static void one_step(struct oracle *o) {
         double rho1, u1[3], T1, tg1, tb1, itbg1;
         macro_from_W(o, &o->Wn[c * NW], &rho1, u1, &T1);
         relax_times(o, rho1, T1, &tg1, &tb1, &itbg1);
+        double *q1 = &o->qn[c * 3];
+        for (int d = 0; d < 3; ++d) q1[d] = 0.0;
+        if (o->p.collision) {
+            /* R-s2: q^{n+1} from the explicit part of eq. phiupdate's numerator */
+            double *eg = (double *)malloc(sizeof(double) * 2 * Nv), *eb = eg + Nv;
+            for (long i = 0; i < Nv; ++i) {
+                long k = c * Nv + i;
+                eg[i] = o->g[k] + 0.5 * dt * (o->geq[k] - o->g[k]) / tg0 - dt * o->dFg[k];
+                eb[i] = o->b[k] + 0.5 * dt * (o->beq[k] - o->b[k]) / tb0 - dt * o->dFb[k];
+            }
+            heat_flux(o, eg, eb, &o->Wn[c * NW], q1);
+            free(eg);
+            for (int d = 0; d < 3; ++d) q1[d] /= 1.0 + dt * o->p.Pr / (2.0 * tg1);
+        }
         for (long i = 0; i < Nv; ++i) {
             long k = c * Nv + i;
             double ge1, be1;
-            equilibrium(o, rho1, u1, T1, &o->xi[3 * i], &ge1, &be1);
+            model_equilibrium(o, rho1, u1, T1, q1, &o->xi[3 * i], &ge1, &be1);
             double gnew = (o->g[k] + 0.5 * dt * (ge1 / tg1 + (o->geq[k] - o->g[k]) / tg0)
                            - dt * o->dFg[k]) / (1.0 + dt / (2.0 * tg1));
             double bnew = (o->b[k] + 0.5 * dt * (be1 / tb1 + (o->beq[k] - o->b[k]) / tb0)
@@ -631,7 +736,9 @@ static void one_step(struct oracle *o) {
     for (long c = 0; c < Ne; ++c) {
         int q[3];
         ccoord(o, c, q);
-        if (is_interior(o, q)) memcpy(&o->W[c * NW], &o->Wn[c * NW], NW * sizeof(double));
+        if (!is_interior(o, q)) continue;
+        memcpy(&o->W[c * NW], &o->Wn[c * NW], NW * sizeof(double));
+        memcpy(&o->q[c * 3], &o->qn[c * 3], 3 * sizeof(double));
     }
     o->steps += 1;
 }
@@ -764,8 +871,26 @@ int oracle_set_state(oracle_t *o, const double *g, const double *b, const double
         memcpy(&o->b[c * Nv], &b[ic * Nv], sizeof(double) * Nv);
         for (int k = 0; k < NW; ++k) o->W[c * NW + k] = 0.0;
         for (int k = 0; k < 2 + D; ++k) o->W[c * NW + k] = W[ic * (2 + D) + k];
+        for (int d = 0; d < 3; ++d) o->q[c * 3 + d] = 0.0;
+        if (o->p.collision) heat_flux(o, &o->g[c * Nv], &o->b[c * Nv], &o->W[c * NW], &o->q[c * 3]);
     }
     return 0;
+}
+
+/* The Shakhov equilibria at every node for one state and heat flux q[D]. */
+void oracle_shakhov_equilibrium(const oracle_t *o, double rho, const double *u, double T, const double *q,
+                                double *geq, double *beq) {
+    double uu[3] = {0, 0, 0}, qq[3] = {0, 0, 0};
+    for (int a = 0; a < o->D; ++a) { uu[a] = u[a]; qq[a] = q[a]; }
+    for (long i = 0; i < o->Nv; ++i) shakhov_equilibrium(o, rho, uu, T, qq, &o->xi[3 * i], &geq[i], &beq[i]);
+}
+
+/* The tracked heat flux q^n of every interior cell, [Nc][D] (collision = 1). */
+void oracle_cell_heat_flux(const oracle_t *o, double *out) {
+    for (long ic = 0; ic < o->Nc; ++ic) {
+        long c = interior_ext(o, ic);
+        for (int a = 0; a < o->D; ++a) out[ic * o->D + a] = o->q[c * 3 + a];
+    }
 }
 
 /* Face conserved variables of the last step, axis a, [Nfaces_a][2+D] in the

@@ -32,6 +32,7 @@ typedef struct {
     double dt;             /* time step; <= 0: CFL rule with cfl below */
     double cfl;
     int recon;             /* 0: reconstruction R-c; 1: the face-gradient variant R-c2 */
+    int collision;         /* 0: the paper's two relaxation times (TEDDF); 1: Shakhov S-model */
 } oracle_params;
 
 typedef struct oracle oracle_t;
@@ -46,6 +47,9 @@ void oracle_distributions(const oracle_t *o, double *g, double *b);   /* [Nc][Nv
 void oracle_discrete_moments(const oracle_t *o, double *out); /* [Nc][2+D] */
 void oracle_stress_heat_flux(const oracle_t *o, double *out); /* [Nc][D*D+D]: P row-major, q */
 void oracle_equilibrium(const oracle_t *o, double rho, const double *u, double T, double *geq, double *beq);
+void oracle_shakhov_equilibrium(const oracle_t *o, double rho, const double *u, double T, const double *q,
+                                double *geq, double *beq);
+void oracle_cell_heat_flux(const oracle_t *o, double *out);   /* [Nc][D] tracked q (collision = 1) */
 int oracle_set_state(oracle_t *o, const double *g, const double *b, const double *W);
 void oracle_face_W(const oracle_t *o, int a, double *out);
 void oracle_velocities(const oracle_t *o, double *xi, double *w);     /* [Nv][3], [Nv] */

@@ -20,6 +20,9 @@ import numpy as np
 
 BC_PERIODIC, BC_SPECULAR, BC_DIRICHLET = 0, 1, 2
 RULE_TRAPEZOID, RULE_BOOLE = 0, 1
+# collision models: the paper's two relaxation times with the b-source (TEDDF),
+# or the Shakhov S-model (one relaxation time, heat-flux-corrected equilibria)
+COLLISION_TEDDF, COLLISION_SHAKHOV = 0, 1
 R_GAS = 0.5          # the paper's gas constant (Sec. 2, "equal to 0.5 throughout")
 
 
