@@ -57,6 +57,9 @@ def design_bytes(mode, D, elt):
     a_in = {0: 2, 1: 2, 2: 2 + 2 * D}[src] * elt
     d["sweep_a"] = a_in + (2 * D * elt if faces else 0)       # (+ write the face values)
     d["sweep_b"] = (2 * D + 4) * elt if faces else a_in + (2 if src else 0) * elt + 2 * elt
+    if mode & 16:                                             # Shakhov: raw moments of the faces and of phi*
+        d["face_moments"] = 2 * D * elt
+        d["cell_moments"] = 2 * elt
     return d
 
 
@@ -396,6 +399,8 @@ def run_ours(args, ws, rank, local):
     cfg, fields = pick_workload(args.workload)
     if args.recon:
         cfg["recon"] = args.recon
+    if args.collision:
+        cfg["collision"] = args.collision
     prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
@@ -503,7 +508,7 @@ def run_ours(args, ws, rank, local):
     result = None
     if rank == 0:
         cpu = cpu_baseline(cfg) if (ws == 1 and not args.skip_cpu) else None
-        launches_per_step = 3 + cfg["dim"] + (1 if mode & 3 else 0)
+        launches_per_step = 3 + cfg["dim"] + (1 if mode & 3 else 0) + (2 if mode & 16 else 0)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -516,6 +521,7 @@ def run_ours(args, ws, rank, local):
                        "tile": list(s.info().tile)[:cfg["dim"]], "velocity_groups": s.info().velocity_groups,
                        "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode & 7, str(mode)),
                        "reconstruction": "face gradient" if mode & 8 else "upwind cell",
+                       "collision": "Shakhov" if mode & 16 else "two relaxation times (Sec. 2)",
                        "launch": f"CUDA graphs of {gsteps} steps" if gsteps > 1 else "one launch per kernel",
                        "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
                              else "state fits in L2",
@@ -542,6 +548,10 @@ def run_reference(args, ws, rank):
     import oracle
     oracle.build()
     cfg, _ = pick_workload(args.workload)
+    if args.recon:
+        cfg["recon"] = args.recon
+    if args.collision:
+        cfg["collision"] = args.collision
     D = cfg["dim"]
     sample = dict(cfg)
     side = {1: 256, 2: 32, 3: 4}[D]
@@ -582,6 +592,7 @@ def main():
     ap.add_argument("--tile", type=int, default=None, help="pin the tile shape id (skips tuning)")
     ap.add_argument("--graph", type=int, default=10, help="steps per captured CUDA graph (1: plain launches)")
     ap.add_argument("--recon", type=int, default=0, help="1: the face-gradient reconstruction (1D/2D workloads)")
+    ap.add_argument("--collision", type=int, default=0, help="1: the Shakhov collision model")
     ap.add_argument("--groups", type=int, default=None, help="with --tile: velocity groups")
     ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
     ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")

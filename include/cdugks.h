@@ -228,6 +228,8 @@ CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
  * forms the fluxes from them instead of reconstructing again.
  * Bit 3 (value 8): the shape implements the face-gradient reconstruction
  * (cdugks_set_reconstruction); the others the upwind-cell one.
+ * Bit 4 (value 16): the shape implements the Shakhov collision model
+ * (cdugks_set_collision); the others the two-time model.
  * Every mode but 0 must be selected before cdugks_bind; modes with bits 0-1
  * nonzero are not batched (modes 0 and 4 are). */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
@@ -249,6 +251,36 @@ CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 #define CDUGKS_RECON_UPWIND_CELL 0
 #define CDUGKS_RECON_FACE_GRADIENT 1
 CDUGKS_API int cdugks_set_reconstruction(cdugks_t *h, int recon);
+
+/* Collision model (call before cdugks_bind; default TEDDF).
+ *   CDUGKS_COLLISION_TEDDF    the paper's model (Sec. 2): tau_g = mu/p,
+ *                             tau_b = tau_g/Pr and the b-source
+ *                             Z/tau_bg (g - g_eq).
+ *   CDUGKS_COLLISION_SHAKHOV  the Shakhov S-model, the other route to Pr != 1
+ *                             that Sec. 1 names: one relaxation time
+ *                             tau = mu/p for g and b, no b-source, and
+ *                             equilibria with the heat-flux correction
+ *                               g_S = g_M (1 + cq (c^2/RT - D - 2)),
+ *                               b_S = b_M + cq g_M ((|xi|^2/2)(c^2/RT - D - 2)
+ *                                     + (3 - D + K)(c^2 - D RT)/2),
+ *                             cq = (1 - Pr) c.q / ((K + 5) p RT), c = xi - u:
+ *                             Shakhov's model for all 3 + K degrees of
+ *                             freedom, integrated over those the velocity
+ *                             grid does not resolve.  The heat flux q of a
+ *                             face comes from the reconstructed values
+ *                             (divided by 1 + h Pr/(2 tau)), that of a cell
+ *                             at t_{n+1} from the explicit part of the update
+ *                             (divided by 1 + dt Pr/(2 tau)); both relative
+ *                             to the place's conserved variables.  The
+ *                             initial Maxwellian state has q = 0.
+ * Selecting a model selects the first tile shape that implements it (and
+ * the selected reconstruction); the Shakhov shapes are face-store shapes.
+ * Not available in batches or cdugks_step_noalloc.  Errors: INVALID (unknown
+ * model, already bound, no shape for this dimension and reconstruction, or a
+ * Dirichlet boundary with a stored-slope Shakhov shape). */
+#define CDUGKS_COLLISION_TEDDF 0
+#define CDUGKS_COLLISION_SHAKHOV 1
+CDUGKS_API int cdugks_set_collision(cdugks_t *h, int model);
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances stepped together: every kernel of a time step

@@ -43,7 +43,9 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t phi[2], pb, sg, fv[3], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst, total;
+    size_t phi[2], pb, sg, fv[3], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst;
+    size_t hq, qs, qf[3];     // Shakhov model only
+    size_t total;
 };
 
 // Optional workspace buffers, by the sweep modes that need them.
@@ -71,6 +73,7 @@ struct cdugks {
     int bufs_cap;          // optional buffers the workspace holds (BUF_* bits)
     int gsel;              // requested groups (0 = auto)
     int recon;             // CDUGKS_RECON_UPWIND_CELL or CDUGKS_RECON_FACE_GRADIENT
+    int collision;         // CDUGKS_COLLISION_TEDDF or CDUGKS_COLLISION_SHAKHOV
     Layout lay;
     unsigned char* base;
     size_t bound_bytes;
@@ -171,6 +174,11 @@ void make_layout(cdugks* h) {
     L.vel = take(h->elt * 8 * g.Nvp);
     L.refl = take(sizeof(int) * 8 * g.Nvp);
     L.io = take(sizeof(double) * std::max(NM, g.D * g.D + g.D) * g.Nc);   // moments, or P and q
+    const bool sk = h->collision == CDUGKS_COLLISION_SHAKHOV;
+    const int NQ = g.D + g.D * (g.D + 1) / 2;
+    L.hq = sk ? take(sizeof(double) * g.D * g.Nc) : 0;
+    L.qs = sk ? take(sizeof(double) * (size_t)h->gcap * NQ * g.Nc) : 0;
+    for (int a = 0; a < 3; ++a) L.qf[a] = sk && a < g.D ? take(sizeof(double) * (size_t)h->gcap * NQ * g.nf[a]) : 0;
     L.status = take(256);
     L.inst = take(std::max(sizeof(Inst<float>), sizeof(Inst<double>)));
     L.total = off;
@@ -198,6 +206,10 @@ Bufs<T> bufs(const cdugks* h, int in) {
     b.vel = reinterpret_cast<const T*>(p + L.vel);
     b.refl = reinterpret_cast<const int*>(p + L.refl);
     b.status = reinterpret_cast<int*>(p + L.status);
+    const bool sk = h->collision == CDUGKS_COLLISION_SHAKHOV;
+    b.hq = sk ? reinterpret_cast<double*>(p + L.hq) : nullptr;
+    b.qs = sk ? reinterpret_cast<double*>(p + L.qs) : nullptr;
+    for (int a = 0; a < 3; ++a) b.qf[a] = sk && a < h->g.D ? reinterpret_cast<double*>(p + L.qf[a]) : nullptr;
     return b;
 }
 
@@ -257,7 +269,7 @@ int check_ready(const cdugks* h, bool need_init) {
 
 struct StateHeader {
     char magic[8];
-    int dim, prec, Nvp, pad;
+    int dim, prec, Nvp, collision;
     long long Nc, steps;
     double dt;
 };
@@ -447,6 +459,8 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
     const int mode = tile_mode(h->prec, h->g.D, tile_id);
     if (cdg::mode_r2(mode) != (h->recon == CDUGKS_RECON_FACE_GRADIENT))
         return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected reconstruction");
+    if (cdg::mode_sk(mode) != (h->collision == CDUGKS_COLLISION_SHAKHOV))
+        return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected collision model");
     if (cdg::mode_source(mode) == cdg::MODE_STORED)
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
@@ -485,9 +499,15 @@ int cdugks_set_reconstruction(cdugks_t* h, int recon) {
         return fail(CDUGKS_ERR_INVALID, "unknown reconstruction");
     if (h->bound) return fail(CDUGKS_ERR_INVALID, "select the reconstruction before cdugks_bind");
     int id = -1;
-    for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t)
-        if (cdg::mode_r2(tile_mode(h->prec, h->g.D, t)) == (recon == CDUGKS_RECON_FACE_GRADIENT)) id = t;
-    if (id < 0) return fail(CDUGKS_ERR_INVALID, "no tile shape implements this reconstruction for this dimension");
+    for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t) {
+        const int m = tile_mode(h->prec, h->g.D, t);
+        if (cdg::mode_r2(m) == (recon == CDUGKS_RECON_FACE_GRADIENT) &&
+            cdg::mode_sk(m) == (h->collision == CDUGKS_COLLISION_SHAKHOV))
+            id = t;
+    }
+    if (id < 0)
+        return fail(CDUGKS_ERR_INVALID,
+                    "no tile shape implements this reconstruction with this collision model for this dimension");
     if (recon == CDUGKS_RECON_FACE_GRADIENT)   // a mirror image three cells deep
         for (int a = 0; a < h->g.D; ++a)
             for (int s2 = 0; s2 < 2; ++s2)
@@ -495,6 +515,37 @@ int cdugks_set_reconstruction(cdugks_t* h, int recon) {
                     return fail(CDUGKS_ERR_INVALID, "the face-gradient reconstruction needs 3 cells next to a specular wall");
     h->recon = recon;
     return cdugks_set_tile(h, id);
+}
+
+int cdugks_set_collision(cdugks_t* h, int model) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    if (model != CDUGKS_COLLISION_TEDDF && model != CDUGKS_COLLISION_SHAKHOV)
+        return fail(CDUGKS_ERR_INVALID, "unknown collision model");
+    if (h->bound) return fail(CDUGKS_ERR_INVALID, "select the collision model before cdugks_bind");
+    int id = -1;
+    for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t) {
+        const int m = tile_mode(h->prec, h->g.D, t);
+        if (cdg::mode_sk(m) == (model == CDUGKS_COLLISION_SHAKHOV) &&
+            cdg::mode_r2(m) == (h->recon == CDUGKS_RECON_FACE_GRADIENT))
+            id = t;
+    }
+    if (id < 0)
+        return fail(CDUGKS_ERR_INVALID, "no tile shape implements this collision model with this reconstruction");
+    if (model == CDUGKS_COLLISION_SHAKHOV && cdg::mode_source(tile_mode(h->prec, h->g.D, id)) == cdg::MODE_STORED)
+        for (int a = 0; a < h->g.D; ++a)
+            if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
+                return fail(CDUGKS_ERR_INVALID, "the Shakhov shapes of this dimension support periodic and specular boundaries only");
+    const int old = h->collision;
+    h->collision = model;
+    h->g.shakhov = model == CDUGKS_COLLISION_SHAKHOV;
+    make_layout(h);
+    const int rc = cdugks_set_tile(h, id);
+    if (rc) {
+        h->collision = old;
+        h->g.shakhov = old == CDUGKS_COLLISION_SHAKHOV;
+        make_layout(h);
+    }
+    return rc;
 }
 
 int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) {
@@ -773,7 +824,8 @@ int cdugks_cell_distributions(cdugks_t* h, const long long* cells, int n, double
 int cdugks_state_bytes(const cdugks_t* h, size_t* bytes) {
     if (!h || !bytes) return fail(CDUGKS_ERR_INVALID, "null argument");
     const Geo& g = h->g;
-    *bytes = sizeof(StateHeader) + (size_t)g.Nvp * g.Nc * 2 * h->elt + sizeof(double) * (2 + g.D) * g.Nc;
+    const size_t nq = h->collision == CDUGKS_COLLISION_SHAKHOV ? (size_t)g.D : 0;   // the tracked heat flux
+    *bytes = sizeof(StateHeader) + (size_t)g.Nvp * g.Nc * 2 * h->elt + sizeof(double) * (2 + g.D + nq) * g.Nc;
     return CDUGKS_OK;
 }
 
@@ -793,6 +845,7 @@ int cdugks_get_state(cdugks_t* h, void* host, size_t bytes) {
     hd.Nc = g.Nc;
     hd.steps = h->steps;
     hd.dt = g.dt;
+    hd.collision = h->collision;
     unsigned char* p = static_cast<unsigned char*>(host);
     std::memcpy(p, &hd, sizeof(hd));
     const size_t sb = (size_t)g.Nvp * g.Nc * 2 * h->elt;
@@ -801,6 +854,10 @@ int cdugks_get_state(cdugks_t* h, void* host, size_t bytes) {
         (e = cudaMemcpyAsync(p + sizeof(hd) + sb, h->base + h->lay.W, sizeof(double) * (2 + g.D) * g.Nc,
                              cudaMemcpyDeviceToHost, h->stream)))
         return cuda_fail(e, "download state");
+    if (h->collision == CDUGKS_COLLISION_SHAKHOV &&
+        (e = cudaMemcpyAsync(p + sizeof(hd) + sb + sizeof(double) * (2 + g.D) * g.Nc, h->base + h->lay.hq,
+                             sizeof(double) * g.D * g.Nc, cudaMemcpyDeviceToHost, h->stream)))
+        return cuda_fail(e, "download heat flux");
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "get_state");
     return CDUGKS_OK;
 }
@@ -815,7 +872,7 @@ int cdugks_set_state(cdugks_t* h, const void* host, size_t bytes) {
     StateHeader hd;
     std::memcpy(&hd, host, sizeof(hd));
     if (std::memcmp(hd.magic, "CDUGKS1", 8) || hd.dim != g.D || hd.prec != h->prec || hd.Nvp != g.Nvp ||
-        hd.Nc != g.Nc || hd.dt != g.dt)
+        hd.Nc != g.Nc || hd.dt != g.dt || hd.collision != h->collision)
         return fail(CDUGKS_ERR_INVALID, "state image does not match this problem");
     const unsigned char* p = static_cast<const unsigned char*>(host);
     const size_t sb = (size_t)g.Nvp * g.Nc * 2 * h->elt;
@@ -824,6 +881,10 @@ int cdugks_set_state(cdugks_t* h, const void* host, size_t bytes) {
         (e = cudaMemcpyAsync(h->base + h->lay.W, p + sizeof(hd) + sb, sizeof(double) * (2 + g.D) * g.Nc,
                              cudaMemcpyHostToDevice, h->stream)))
         return cuda_fail(e, "upload state");
+    if (h->collision == CDUGKS_COLLISION_SHAKHOV &&
+        (e = cudaMemcpyAsync(h->base + h->lay.hq, p + sizeof(hd) + sb + sizeof(double) * (2 + g.D) * g.Nc,
+                             sizeof(double) * g.D * g.Nc, cudaMemcpyHostToDevice, h->stream)))
+        return cuda_fail(e, "upload heat flux");
     h->cur = 0;
     if (h->prec == CDUGKS_FP32) e = cdg::launch_cellc_f32(g, dinst<float>(h), 0, h->stream);
     else e = cdg::launch_cellc_f64(g, dinst<double>(h), 0, h->stream);
@@ -965,6 +1026,7 @@ int batch_member_ok(const cdugks* m, int prec, int D) {
     if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
     if (cdg::mode_source(tile_mode(m->prec, m->g.D, m->g.tile_id)) != cdg::MODE_FUSED)
         return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
+    if (m->collision != CDUGKS_COLLISION_TEDDF) return fail(CDUGKS_ERR_INVALID, "Shakhov instances are not batched");
     return CDUGKS_OK;
 }
 
@@ -1330,6 +1392,8 @@ extern "C" {
 int cdugks_step_noalloc(cdugks_t* h, const void* phi_in, void* phi_out, double* W, void* cuda_stream) {
     if (!h || !phi_in || !phi_out || !W) return fail(CDUGKS_ERR_INVALID, "null argument");
     if (phi_in == phi_out) return fail(CDUGKS_ERR_INVALID, "phi_in and phi_out must be different buffers");
+    if (h->collision != CDUGKS_COLLISION_TEDDF)
+        return fail(CDUGKS_ERR_INVALID, "the allocation-free step implements the two-time collision model only");
     for (int a = 0; a < h->g.D; ++a)
         if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
             return fail(CDUGKS_ERR_INVALID, "the allocation-free step supports periodic and specular boundaries only");

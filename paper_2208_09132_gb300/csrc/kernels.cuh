@@ -62,6 +62,7 @@ struct Geo {
     double idx[3];    // 1 / dx_a
     double dt, h;
     double K, R, mu_ref, T_ref, omega, Pr;
+    int shakhov;      // collision model: 0 the two relaxation times of Sec. 2, 1 the Shakhov S-model
 };
 
 template <typename T> struct CellC;
@@ -84,6 +85,10 @@ struct Bufs {
                           // 2h xi_2/dx_2 (w = 0 on padding)
     const int* refl;      // [8][Nvp] velocity index with the components of mask reversed
     int* status;
+    // Shakhov model only (null otherwise); NQ = D + D(D+1)/2 raw moments
+    double* hq;           // [D][Nc] heat flux of the current time level, tracked like W
+    double* qs;           // [G][NQ][Nc] raw velocity moments of phi* per velocity group
+    double* qf[3];        // [G][NQ][nf_a] raw velocity moments of the face values per group
 };
 
 // An instance as the kernels see it: geometry and both ping-pong orientations
@@ -116,6 +121,8 @@ template <> struct Num<float> {
         return y;
     }
     static __host__ __device__ __forceinline__ double cexp_scale() { return 1.4426950408889634; }
+    // 1/RT = cexp * irt_scale (cexp = -log2(e)/(2 RT))
+    static __host__ __device__ __forceinline__ float irt_scale() { return -1.3862943611198906f; }
     // half the van Leer slope: s1 s2 / (s1 + s2) (the factor 2 is folded into the
     // reconstruction coefficients)
     static __device__ __forceinline__ float vanleer(float s1, float s2) {
@@ -126,6 +133,7 @@ template <> struct Num<float> {
 template <> struct Num<double> {
     static __device__ __forceinline__ double expo(double x) { return exp(x); }
     static __host__ __device__ __forceinline__ double cexp_scale() { return 1.0; }
+    static __host__ __device__ __forceinline__ double irt_scale() { return -2.0; }
     static __device__ __forceinline__ double vanleer(double s1, double s2) {
         double p = s1 * s2;
         return p > 0.0 ? p / (s1 + s2) : 0.0;
@@ -143,13 +151,14 @@ struct CellC {
     T kp_g, kp_b, kp_s;         // phibar+ = eq + kp (phi* - eq) [+ kp_s Z (g* - g_eq)] (eq. phibarplus with
                                 //   phi - eq = fa (phi* - eq): kp = sa fa, kp_s = ssrc fa_g)
     T um_g, um_b, usrc;         // phi* = eq + um (phi - eq) [+ usrc Z (g - g_eq)] - dt dF (eq. phiupdate)
+    T sq[3], e2;                // Shakhov: sq = (1 - Pr) q / ((K + 5) p RT), e2 = (3 - D + K) D RT / 2 (else 0)
 };
 
 // The phibar+ constants of a cell as packed in shared memory: u (D), cexp,
-// pref, eb, hu2, kp_g, kp_b, kp_s.
-template <int D>
+// pref, eb, hu2, kp_g, kp_b, kp_s, and with the Shakhov model sq (D), e2.
+template <int D, bool SK = false>
 struct CellPack {
-    static constexpr int N = D + 7;
+    static constexpr int N = D + 7 + (SK ? D + 1 : 0);
     static constexpr int NV = (N + 3) / 4;
 };
 
@@ -159,6 +168,7 @@ struct FaceC {
     T u[3];
     T cexp, pref, eb, hu2;
     T al_g, al_b, gam_b;
+    T sq[3], e2;                // Shakhov constants of the face (as in CellC)
 };
 
 // Macroscopic state of a cell or face from its conserved variables (FP64).
@@ -236,9 +246,57 @@ __device__ __forceinline__ Relax<R> relax_of(const Geo& g, const Macro& m) {
     Relax<R> r;
     const R mu = A::mul((R)g.mu_ref, visc_power<R>(A::div((R)m.T, (R)g.T_ref), (R)g.omega));
     r.itg = A::div(A::mul((R)m.rho, (R)m.RT), mu);
-    r.itb = A::mul((R)g.Pr, r.itg);
-    r.itbg = A::mul(A::sub((R)g.Pr, R(1)), r.itg);
+    if (g.shakhov) {           // one relaxation time, no b-source
+        r.itb = r.itg;
+        r.itbg = R(0);
+    } else {
+        r.itb = A::mul((R)g.Pr, r.itg);
+        r.itbg = A::mul(A::sub((R)g.Pr, R(1)), r.itg);
+    }
     return r;
+}
+
+// The Shakhov S-model (the route to Pr != 1 that Sec. 1 names besides the
+// two-time model; its form is Shakhov's, for all N = 3 + K degrees of freedom,
+// integrated over the ones the velocity grid does not resolve):
+//   g_S = g_M (1 + cq (c^2/RT - D - 2)),
+//   b_S = g_M (|xi|^2/2 + eb + cq (|xi|^2/2 (c^2/RT - D - 2) + hL c^2 - e2)),
+// c = xi - u, cq = sq . c, hL = (3 - D + K)/2.  Per cell or face (FP64 here):
+// sq = (1 - Pr) q / ((K + 5) p RT) and e2 = hL D RT; q is the heat flux.
+template <typename T>
+__device__ __forceinline__ void shakhov_consts(const Geo& g, const Macro& m, const double* q, T sq[3], T& e2) {
+    for (int a = 0; a < 3; ++a) sq[a] = T(0);
+    e2 = T(0);
+    if (!g.shakhov) return;
+    const double A = ddiv(1.0 - g.Pr, dmul(dmul(g.K + 5.0, m.rho), dmul(m.RT, m.RT)));
+    for (int a = 0; a < g.D; ++a) sq[a] = q ? (T)dmul(A, q[a]) : T(0);
+    e2 = (T)dmul(dmul(0.5 * (3.0 - g.D + g.K), (double)g.D), m.RT);
+}
+
+// One velocity: the Shakhov equilibrium from the Maxwellian value gM.
+template <typename T, int D>
+__device__ __forceinline__ void shakhov_point(T gM, T c2, T cq, T irt, T hx, T eb, T hL, T e2, T& ge, T& be) {
+    const T P1 = fma(c2, irt, T(-(D + 2)));
+    ge = fma(gM * cq, P1, gM);
+    be = gM * (hx + eb + cq * fma(hx, P1, fma(hL, c2, -e2)));
+}
+
+// Heat flux at a cell or face from the raw moments s = (sum w xi_a b [D],
+// sum w xi_a xi_b g [a <= b]) of its distributions, relative to its conserved
+// variables W (rho, u, E from W):
+//   q_a = sum w xi_a b - u_a rho E - sum_b u_b (sum w xi_a xi_b g - rho u_a u_b).
+template <int D>
+__device__ __forceinline__ void heat_flux_raw(const Macro& m, const double* W, const double* s, double q[3]) {
+    double Pi[3][3];
+    int k = D;
+    for (int a = 0; a < D; ++a)
+        for (int b = a; b < D; ++b) Pi[a][b] = Pi[b][a] = s[k++];
+    for (int a = 0; a < 3; ++a) q[a] = 0.0;
+    for (int a = 0; a < D; ++a) {
+        double v = dsub(s[a], dmul(m.u[a], W[1 + D]));
+        for (int b = 0; b < D; ++b) v = dsub(v, dmul(m.u[b], dsub(Pi[a][b], dmul(m.rho, dmul(m.u[a], m.u[b])))));
+        q[a] = v;
+    }
 }
 
 template <typename T>
@@ -260,11 +318,12 @@ __device__ __forceinline__ void eq_consts(const Geo& g, const Macro& m, T u[3], 
 // fa = 1/(1 + x), fb = x fa (phi = fa phi* + fb phi_eq), kp = (1 - h/(2 tau)) fa,
 // kp_s = (h/2)(1/tau_b - 1/tau_g) fa_g, um = 1 - x, usrc = dt (1/tau_b - 1/tau_g).
 template <typename T>
-__device__ __forceinline__ void make_cell(const Geo& g, const double* W, CellC<T>& c) {
+__device__ __forceinline__ void make_cell(const Geo& g, const double* W, const double* q, CellC<T>& c) {
     using A = Ar<T>;
     const Macro m = macro_of(g, W);
     const Relax<T> r = relax_of<T>(g, m);
     eq_consts<T>(g, m, c.u, c.cexp, c.pref, c.eb, c.hu2);
+    shakhov_consts<T>(g, m, q, c.sq, c.e2);
     const T dt = (T)g.dt, hh = (T)(0.5 * g.h), hdt = (T)(0.5 * g.dt);
     const T xg = A::mul(hdt, r.itg), xb = A::mul(hdt, r.itb);
     const T fa_g = A::div(T(1), A::add(T(1), xg)), fa_b = A::div(T(1), A::add(T(1), xb));
@@ -283,11 +342,12 @@ __device__ __forceinline__ void make_cell(const Geo& g, const double* W, CellC<T
 // Face constants from the face W: equilibrium parameters, alpha = 1/(1 + h/(2 tau))
 // (the inverse of eq. phibar) and gamma_b = (h/2)(1/tau_b - 1/tau_g) alpha_b.
 template <typename T>
-__device__ __forceinline__ void make_face(const Geo& g, const double* W, FaceC<T>& f) {
+__device__ __forceinline__ void make_face(const Geo& g, const double* W, const double* q, FaceC<T>& f) {
     using A = Ar<T>;
     const Macro m = macro_of(g, W);
     const Relax<T> r = relax_of<T>(g, m);
     eq_consts<T>(g, m, f.u, f.cexp, f.pref, f.eb, f.hu2);
+    shakhov_consts<T>(g, m, q, f.sq, f.e2);
     const T hh = (T)(0.5 * g.h);
     f.al_g = A::div(T(1), A::add(T(1), A::mul(hh, r.itg)));
     f.al_b = A::div(T(1), A::add(T(1), A::mul(hh, r.itb)));
@@ -316,16 +376,24 @@ __device__ __forceinline__ Vel<T, D> load_vel(const Geo& g, const Bufs<T>& bf, i
     return v;
 }
 
+// The equilibria of the collision model at one velocity (cell or face constants c).
 template <typename T, int D, typename C>
-__device__ __forceinline__ void equilibrium(const C& c, const Vel<T, D>& v, T& geq, T& beq) {
-    T c2 = T(0);
+__device__ __forceinline__ void equilibrium(const Geo& g, const C& c, const Vel<T, D>& v, T& geq, T& beq) {
+    T c2 = T(0), cq = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         T d = v.xi[a] - c.u[a];
         c2 = fma(d, d, c2);
+        cq = fma(c.sq[a], d, cq);
     }
-    geq = c.pref * Num<T>::expo(c.cexp * c2);
-    beq = (v.hxi2 + c.eb) * geq;
+    const T gM = c.pref * Num<T>::expo(c.cexp * c2);
+    if (g.shakhov) {
+        shakhov_point<T, D>(gM, c2, cq, c.cexp * Num<T>::irt_scale(), v.hxi2, c.eb, (T)(0.5 * (3.0 - D + g.K)), c.e2,
+                            geq, beq);
+    } else {
+        geq = gM;
+        beq = (v.hxi2 + c.eb) * geq;
+    }
 }
 
 
@@ -533,16 +601,20 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Bit 3 (face gradient): the paper's variant of the reconstruction, which also
 // carries the slopes to the face with their own limited derivatives (three
 // halo layers; fused face-store shapes only).
-enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8 };
+// Bit 4 (Shakhov): the sweeps and k_flux evaluate the Shakhov equilibria
+// (face-store shapes only); k_faceq and k_cellq add the raw moments the heat
+// flux needs.
+enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16 };
 __host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
 __host__ __device__ constexpr bool mode_r2(int mode) { return (mode & MODE_R2) != 0; }
+__host__ __device__ constexpr bool mode_sk(int mode) { return (mode & MODE_SK) != 0; }
 __host__ __device__ constexpr int mode_halo(int mode) { return mode_r2(mode) ? 3 : 2; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
     using TL = Tile<D, T0, T1, T2, mode_halo(MODE)>;
-    static constexpr int NCCV = CellPack<D>::NV;  // phase-1 constants per box cell, packed in V4
+    static constexpr int NCCV = CellPack<D, mode_sk(MODE)>::NV;  // phase-1 constants per box cell, packed in V4
     static constexpr int NFC = D + 7;            // face constants
     static constexpr int NFCV = (NFC + 3) / 4;
     static constexpr int PN = mode_source(MODE) == MODE_STORED ? TL::SB : TL::BOX;   // cells of the phibar+ array
@@ -596,11 +668,12 @@ __device__ __forceinline__ void phibar_plus(T ge, T be, T gs, T bs, T z, T kp_g,
     pb = fma(kp_s * z, dg, fma(kp_b, bs - be, be));
 }
 
-// Pack a cell's phibar+ constants (CellPack order; u with the components of a
-// mirror image reversed) into V4 slots dst[j * stride].
-template <typename T, int D>
+// Pack a cell's phibar+ constants (CellPack order; u and the heat flux with
+// the components of a mirror image reversed) into V4 slots dst[j * stride].
+template <typename T, int D, bool SK = false>
 __device__ __forceinline__ void pack_cell(const CellC<T>& cs, int refl, V4<T>* dst, int stride) {
-    T cst[4 * CellPack<D>::NV];
+    using CP = CellPack<D, SK>;
+    T cst[4 * CP::NV];
 #pragma unroll
     for (int a = 0; a < D; ++a) cst[a] = (refl & (1 << a)) ? -cs.u[a] : cs.u[a];
     cst[D + 0] = cs.cexp;
@@ -610,14 +683,42 @@ __device__ __forceinline__ void pack_cell(const CellC<T>& cs, int refl, V4<T>* d
     cst[D + 4] = cs.kp_g;
     cst[D + 5] = cs.kp_b;
     cst[D + 6] = cs.kp_s;
+    if constexpr (SK) {
 #pragma unroll
-    for (int j = D + 7; j < 4 * CellPack<D>::NV; ++j) cst[j] = T(0);
+        for (int a = 0; a < D; ++a) cst[D + 7 + a] = (refl & (1 << a)) ? -cs.sq[a] : cs.sq[a];
+        cst[2 * D + 7] = cs.e2;
+    }
 #pragma unroll
-    for (int j = 0; j < CellPack<D>::NV; ++j) {
+    for (int j = CP::N; j < 4 * CP::NV; ++j) cst[j] = T(0);
+#pragma unroll
+    for (int j = 0; j < CP::NV; ++j) {
         V4<T> qv;
 #pragma unroll
         for (int e = 0; e < 4; ++e) qv.v[e] = cst[4 * j + e];
         dst[j * stride] = qv;
+    }
+}
+
+// The equilibria at one velocity from packed constants cst (CellPack or
+// FacePack order: u at 0, cexp at D, pref at D+1, eb at D+2, and with SK sq at
+// D+7 and e2 at 2D+7) and the velocity xi (hx = |xi|^2/2); also Z = xi.u - hu2.
+template <typename T, int D, bool SK>
+__device__ __forceinline__ void packed_eq(const T* cst, const T (&xi)[D], T hx, T hL, T& ge, T& be, T& z) {
+    T c2 = T(0), cq = T(0);
+    z = -cst[D + 3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const T d = xi[a] - cst[a];
+        c2 = fma(d, d, c2);
+        z = fma(xi[a], cst[a], z);
+        if constexpr (SK) cq = fma(cst[D + 7 + a], d, cq);
+    }
+    const T gM = cst[D + 1] * Num<T>::expo(cst[D + 0] * c2);
+    if constexpr (SK) {
+        shakhov_point<T, D>(gM, c2, cq, cst[D + 0] * Num<T>::irt_scale(), hx, cst[D + 2], hL, cst[2 * D + 7], ge, be);
+    } else {
+        ge = gM;
+        be = (hx + cst[D + 2]) * ge;
     }
 }
 
@@ -659,17 +760,17 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
 // CTA per tile of cells and group of velocity chunks, phibar+ formed on the
 // tile and a one-cell halo in shared memory, slopes of the tile's own cells,
 // both written in their layouts.
-template <typename T, int D, int T0_, int T1_, int T2_>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 __host__ __device__ constexpr size_t shslope_smem_bytes() {
     using TL = Tile<D, T0_, T1_, T2_>;
-    return ((size_t)2 * TL::SB + (size_t)CellPack<D>::NV * TL::SB) * sizeof(V4<T>) + sizeof(int) * 2 * TL::SB;
+    return ((size_t)2 * TL::SB + (size_t)CellPack<D, SK>::NV * TL::SB) * sizeof(V4<T>) + sizeof(int) * 2 * TL::SB;
 }
 
-template <typename T, int D, int T0_, int T1_, int T2_>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const Inst<T>* __restrict__ in, int cur) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using Q = V4<T>;
-    constexpr int SB = TL::SB, NCCV = CellPack<D>::NV;
+    constexpr int SB = TL::SB, NCCV = CellPack<D, SK>::NV;
     extern __shared__ __align__(32) unsigned char smem[];
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
@@ -698,7 +799,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
         bool dir;
         resolve<D>(g, q, refl, dir);
         const long long c = cell_index(g, q);
-        pack_cell<T, D>(bf.cellc[c], refl, CC + s2, SB);
+        pack_cell<T, D, SK>(bf.cellc[c], refl, CC + s2, SB);
         csrc[s2] = (int)c;
         cfl[s2] = refl;
     }
@@ -710,6 +811,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
     for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
     const int sc = TL::sbox_of(la[0], la[1], la[2]);
     const long long own = valid ? cell_index(g, qa) : 0;
+    const T hL = (T)(0.5 * (3.0 - D + g.K));
     for (int vt = vt0; vt < vt1; ++vt) {
         T xi[VC][D], hx[VC];
 #pragma unroll
@@ -745,15 +847,8 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
             Q qg, qb;
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
-                T c2 = T(0), z = -cst[D + 3];
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const T d = xi[v][a] - cst[a];
-                    c2 = fma(d, d, c2);
-                    z = fma(xi[v][a], cst[a], z);
-                }
-                const T ge = cst[D + 1] * Num<T>::expo(cst[D + 0] * c2);
-                const T be = (hx[v] + cst[D + 2]) * ge;
+                T ge, be, z;
+                packed_eq<T, D, SK>(cst, xi[v], hx[v], hL, ge, be, z);
                 phibar_plus<T>(ge, be, gs[v], bs[v], z, cst[D + 4], cst[D + 5], cst[D + 6], qg.v[v], qb.v[v]);
             }
             P[0 * SB + s2] = qg;
@@ -796,18 +891,19 @@ __device__ __forceinline__ void tile_origin(const Geo& g, int tile, int org[3]) 
     if (D >= 3) org[2] = tb * TL::T2;
 }
 
-// Face constants packed per face: u (D), cexp, pref, eb, hu2, alpha_g, alpha_b, gamma_b.
-template <int D>
+// Face constants packed per face: u (D), cexp, pref, eb, hu2, alpha_g, alpha_b,
+// gamma_b, and with the Shakhov model sq (D), e2.
+template <int D, bool SK = false>
 struct FacePack {
-    static constexpr int N = D + 7;
+    static constexpr int N = D + 7 + (SK ? D + 1 : 0);
     static constexpr int NV = (N + 3) / 4;   // V4 units
 };
 
 // The packed constants of every face of the tile (both ends of each axis)
 // into shared memory, FC[j * NFT + local face].
-template <typename T, int D, typename TL>
+template <typename T, int D, typename TL, bool SK = false>
 __device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& bf, const int org[3], V4<T>* FC) {
-    constexpr int NFCV = FacePack<D>::NV, NFT = TL::NFT;
+    constexpr int NFCV = FacePack<D, SK>::NV, NFT = TL::NFT;
 #pragma unroll
     for (int a = 0; a < D; ++a)
     for (int r = threadIdx.x; r < TL::foff(a + 1) - TL::foff(a); r += TL::NT) {
@@ -829,8 +925,13 @@ __device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& b
         cst[D + 4] = fs.al_g;
         cst[D + 5] = fs.al_b;
         cst[D + 6] = fs.gam_b;
+        if constexpr (SK) {
 #pragma unroll
-        for (int j = D + 7; j < 4 * NFCV; ++j) cst[j] = T(0);
+            for (int b = 0; b < D; ++b) cst[D + 7 + b] = fs.sq[b];
+            cst[2 * D + 7] = fs.e2;
+        }
+#pragma unroll
+        for (int j = FacePack<D, SK>::N; j < 4 * NFCV; ++j) cst[j] = T(0);
 #pragma unroll
         for (int j = 0; j < NFCV; ++j) {
             V4<T> qv;
@@ -845,25 +946,17 @@ __device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& b
 // constants fc, the inverse of eq. phibar applied to the reconstructed values
 // (gb, bb), the microflux xi_a phi (eq. flux) into (fg, fb), and its moments
 // with the quadrature weights added to sm.
-template <typename T, int D>
+template <typename T, int D, bool SK = false>
 __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], const T (&w)[VC], const T (&hx)[VC],
                                           int a, const T (&gb)[VC], const T (&bb)[VC], V4<T>& fg, V4<T>& fb,
-                                          T* sm) {
-    const T fcexp = fc[D + 0], fpref = fc[D + 1], feb = fc[D + 2], fhu2 = fc[D + 3];
+                                          T* sm, T hL = T(0)) {
     const T alg = fc[D + 4], alb = fc[D + 5], gmb = fc[D + 6];
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
-        T c2 = T(0), z = -fhu2;
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-            const T d = xi[v][b] - fc[b];
-            c2 = fma(d, d, c2);
-            z = fma(xi[v][b], fc[b], z);
-        }
-        const T ge = fpref * Num<T>::expo(fcexp * c2);
-        const T be = (hx[v] + feb) * ge;
+        T ge, be, z;
+        packed_eq<T, D, SK>(fc, xi[v], hx[v], hL, ge, be, z);
         const T gf = fma(alg, gb[v] - ge, ge);
-        const T bfv = fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+        const T bfv = SK ? fma(alb, bb[v] - be, be) : fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
         const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
         fg.v[v] = Fg;
         fb.v[v] = Fb;
@@ -877,20 +970,26 @@ __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], con
 
 // phi^n and phi_eq^n of one cell chunk: the deferred last factor of eq.
 // phiupdate applied to the stored phi* (gs, bs) with the cell constants.
-template <typename T, int D>
+template <typename T, int D, bool SK = false>
 __device__ __forceinline__ void own_state(const CellC<T>& own, const T (&xi)[VC][D], const T (&hx)[VC],
                                           const T (&gs)[VC], const T (&bs)[VC], T (&og)[VC], T (&ob)[VC],
-                                          T (&oge)[VC], T (&obe)[VC]) {
+                                          T (&oge)[VC], T (&obe)[VC], T hL = T(0)) {
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
-        T c2 = T(0);
+        T c2 = T(0), cq = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             const T d = xi[v][a] - own.u[a];
             c2 = fma(d, d, c2);
+            if constexpr (SK) cq = fma(own.sq[a], d, cq);
         }
-        oge[v] = own.pref * Num<T>::expo(own.cexp * c2);
-        obe[v] = (hx[v] + own.eb) * oge[v];
+        const T gM = own.pref * Num<T>::expo(own.cexp * c2);
+        if constexpr (SK) {
+            shakhov_point<T, D>(gM, c2, cq, own.cexp * Num<T>::irt_scale(), hx[v], own.eb, hL, own.e2, oge[v], obe[v]);
+        } else {
+            oge[v] = gM;
+            obe[v] = (hx[v] + own.eb) * oge[v];
+        }
         og[v] = fma(own.fa_g, gs[v], own.fb_g * oge[v]);
         ob[v] = fma(own.fa_b, bs[v], own.fb_b * obe[v]);
     }
@@ -972,7 +1071,9 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr bool STORED = mode_source(MODE) == MODE_STORED;   // ... and so do the slopes
     constexpr bool FACES = mode_faces(MODE);                     // sweep A stores the face values
     constexpr bool R2 = mode_r2(MODE);                           // face-gradient reconstruction
+    constexpr bool SK = mode_sk(MODE);                           // Shakhov equilibria
     static_assert(!(SWEEP_B && FACES), "sweep B of the face-store shapes is k_flux");
+    static_assert(!SK || (FACES && !R2 && mode_source(MODE) != MODE_PREP), "Shakhov shapes are fused or stored face-store shapes");
     static_assert(!R2 || (FACES && !PREP), "the face-gradient reconstruction is built for fused face-store shapes");
     constexpr int PN = SM::PN;
     using Q = V4<T>;
@@ -997,6 +1098,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = TL::NT / 32;
+    const T hL = (T)(0.5 * (3.0 - D + g.K));     // Shakhov: half the unresolved degrees of freedom
     int org[3];
     tile_origin<TL, D>(g, tile, org);
     const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
@@ -1037,7 +1139,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         csrc[k] = (int)c;
         cfl[k] = refl | (dir ? 8 : 0);
         if (PREP) continue;
-        pack_cell<T, D>(dir ? bf.cellc0[c] : bf.cellc[c], refl, CC + k, BOX);
+        pack_cell<T, D, SK>(dir ? bf.cellc0[c] : bf.cellc[c], refl, CC + k, BOX);
     }
     {   // halo list in box order (warp ballots), so neighbouring threads touch neighbouring cells
         constexpr int PER = ((BOX + NW - 1) / NW + 31) / 32 * 32;
@@ -1181,20 +1283,12 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 Chunk<T>::load(bf.phi_in + ad, gs);
                 Chunk<T>::load(bf.phi_in + ad + VC, bs);
             }
-            const T cexp = cst[D + 0], pref = cst[D + 1], eb = cst[D + 2], hu2 = cst[D + 3];
             const T kp_g = cst[D + 4], kp_b = cst[D + 5], kp_s = cst[D + 6];
             Q qg, qb;
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
-                T c2 = T(0), z = -hu2;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const T d = xi[v][a] - cst[a];
-                    c2 = fma(d, d, c2);
-                    z = fma(xi[v][a], cst[a], z);
-                }
-                const T ge = pref * Num<T>::expo(cexp * c2);
-                const T be = (hx[v] + eb) * ge;
+                T ge, be, z;
+                packed_eq<T, D, SK>(cst, xi[v], hx[v], hL, ge, be, z);
                 if (fl & 8) {
                     qg.v[v] = ge;
                     qb.v[v] = be;
@@ -1553,23 +1647,23 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 // moments are summed by its owner (the cell on its right; the last cell for
 // the domain's right end), in chunk order.
 
-template <typename T, int D, int T0_, int T1_, int T2_>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 struct FluxSmem {
     using TL = Tile<D, T0_, T1_, T2_>;
     static constexpr int NPL = TL::NPL;
     __host__ __device__ static constexpr int plane(int a) { return TL::plane(a); }
     __host__ __device__ static constexpr int poff(int a) { return TL::poff(a); }
     static_assert(TL::poff(D) == TL::NPL, "one slot per cell of each tile face");
-    static constexpr size_t nV4 = (size_t)FacePack<D>::NV * TL::NFT;
+    static constexpr size_t nV4 = (size_t)FacePack<D, SK>::NV * TL::NFT;
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
-    using FS = FluxSmem<T, D, T0_, T1_, T2_>;
+    using FS = FluxSmem<T, D, T0_, T1_, T2_, SK>;
     using Q = V4<T>;
-    constexpr int NM = 2 + D, NFT = TL::NFT, NFCV = FacePack<D>::NV;
+    constexpr int NM = 2 + D, NFT = TL::NFT, NFCV = FacePack<D, SK>::NV;
     Q* const FC = reinterpret_cast<Q*>(smem);     // [NFCV][NFT] packed face constants
     // running sums of the faces at the domain's right end, [NM][plane cell] per axis
     Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + FS::nV4 * sizeof(Q));
@@ -1582,12 +1676,13 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     bool valid = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) valid = valid && qa[a] < g.n[a];
-    stage_face_consts<T, D, TL>(g, bf, org, FC);
+    stage_face_consts<T, D, TL, SK>(g, bf, org, FC);
     for (int k = t; k < FS::NPL * NM; k += TL::NT) RS[k].zero();
     __syncthreads();
     if (!valid) return;          // no barrier below
 
     const CellC<T> own = bf.cellc[cell_index(g, qa)];
+    const T hL = (T)(0.5 * (3.0 - D + g.K));
     const size_t cell_ad = phi_addr(g, cell_index(g, qa), 0, 0);
     const size_t chunk_stride = (size_t)g.Nc * (2 * VC);
     bool own_right[3] = {false, false, false};
@@ -1644,7 +1739,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                 T sm[NM];
 #pragma unroll
                 for (int m = 0; m < NM; ++m) sm[m] = T(0);
-                face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm);
+                face_flux<T, D, SK>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL);
                 if (side == 0) {
 #pragma unroll
                     for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
@@ -1666,7 +1761,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
             }
         }
         T og[VC], ob[VC], oge[VC], obe[VC];
-        own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
+        own_state<T, D, SK>(own, xi, hx, gs, bs, og, ob, oge, obe, hL);
         T u[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = own.u[a];
@@ -1688,9 +1783,9 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 }
 
 // CTAs per SM for k_flux: shared memory and threads, keeping >= 80 registers.
-template <typename T, int D, int T0_, int T1_, int T2_>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 struct FluxOcc {
-    static constexpr size_t per = FluxSmem<T, D, T0_, T1_, T2_>::bytes + 1024;
+    static constexpr size_t per = FluxSmem<T, D, T0_, T1_, T2_, SK>::bytes + 1024;
     static constexpr int by_smem = (int)((228 * 1024) / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
     static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 128);
@@ -1699,11 +1794,11 @@ struct FluxOcc {
     static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(32) unsigned char smem[];
-    flux_body<T, D, T0_, T1_, T2_>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    flux_body<T, D, T0_, T1_, T2_, SK>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list
@@ -1728,6 +1823,99 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_
     flux_body<T, D, T0_, T1_, T2_>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
+// ---- Shakhov model: raw velocity moments for the heat flux
+//
+// Per item (a face of one axis, or a cell) of a [chunk][item][g|b][VC] array
+// and velocity group: s = (sum w xi_a b [D], sum w xi_a xi_b g [a <= b]) over
+// the group's chunks, in chunk order (per-chunk sums folded into Kahan pairs
+// in FP32), into dst[(grp * NQ + m) * n + item].  k_faceq reads the stored
+// face values (phibar at the faces), k_cellq the phi* just written (the
+// explicit part of eq. phiupdate).
+template <int D>
+struct NQ {
+    static constexpr int value = D + D * (D + 1) / 2;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void raw_moments(const Geo& g, const T* __restrict__ vel, const T* __restrict__ src,
+                                            long long n, long long item, int grp, double* __restrict__ dst) {
+    constexpr int M = NQ<D>::value;
+    Kahan<T> acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m].zero();
+    const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
+    for (int vt = vt0; vt < vt1; ++vt) {
+        T gv[VC], bv[VC];
+        const T* p = src + ((size_t)vt * (size_t)n + (size_t)item) * (2 * VC);
+        Chunk<T>::load(p, gv);
+        Chunk<T>::load(p + VC, bv);
+        T sm[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) sm[m] = T(0);
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const T* rec = vel + (size_t)(vt * VC + v) * 8;
+            T xi[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) xi[a] = rec[a];
+            const T wg = rec[3] * gv[v], wb = rec[3] * bv[v];
+            int k = D;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                sm[a] = fma(xi[a], wb, sm[a]);
+#pragma unroll
+                for (int b = a; b < D; ++b, ++k) sm[k] = fma(xi[a] * xi[b], wg, sm[k]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m].add(sm[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) dst[((size_t)grp * M + m) * (size_t)n + item] = acc[m].value();
+}
+
+// grid (faces / blockDim, velocity groups, axes)
+template <typename T, int D>
+__global__ void k_faceq(const Inst<T>* __restrict__ in, int cur) {
+    // the axis is a launch index: read what it selects from the record, copy nothing
+    const Geo& g = in->g;
+    const Bufs<T>& bf = in->b[cur];
+    const int a = blockIdx.z;
+    if (a >= D) return;
+    const long long nf = g.nf[a];
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < nf) raw_moments<T, D>(g, bf.vel, bf.face[a], nf, f, blockIdx.y, bf.qf[a]);
+}
+
+// grid (cells / blockDim, velocity groups)
+template <typename T, int D>
+__global__ void k_cellq(const Inst<T>* __restrict__ in, int cur) {
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < g.Nc) raw_moments<T, D>(g, bf.vel, bf.phi_out, g.Nc, c, blockIdx.y, bf.qs);
+}
+
+// Group sums of the raw moments of one item (fixed order), then its heat flux
+// relative to W divided by 1 + x Pr/tau: x = h/2 at a face (phibar relaxes the
+// heat flux by that factor), dt/2 at a cell (phi* against phi^{n+1}).
+template <typename T, int D>
+__device__ __forceinline__ void shakhov_heat_flux(const Geo& g, const double* src, long long n, long long item,
+                                                  const double* W, double x, double q[3]) {
+    constexpr int M = NQ<D>::value;
+    double s[M];
+    for (int m = 0; m < M; ++m) {
+        double v = 0.0;
+        for (int gg = 0; gg < g.G; ++gg) v = dadd(v, src[((size_t)gg * M + m) * (size_t)n + item]);
+        s[m] = v;
+    }
+    const Macro mc = macro_of(g, W);
+    heat_flux_raw<D>(mc, W, s, q);
+    const Relax<double> r = relax_of<double>(g, mc);
+    const double div = dadd(1.0, dmul(dmul(x, g.Pr), r.itg));
+    for (int a = 0; a < D; ++a) q[a] = ddiv(q[a], div);
+}
+
 // Face constants from the group-summed face W (fixed summation order).
 template <typename T, int D>
 __device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a, long long f) {
@@ -1738,7 +1926,9 @@ __device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a,
         for (int gg = 0; gg < g.G; ++gg) s += bf.wf[a][((size_t)gg * NM + m) * g.nf[a] + f];
         W[m] = s;
     }
-    make_face<T>(g, W, bf.facec[a][f]);
+    double q[3] = {0.0, 0.0, 0.0};
+    if (g.shakhov) shakhov_heat_flux<T, D>(g, bf.qf[a], g.nf[a], f, W, 0.5 * g.h, q);
+    make_face<T>(g, W, q, bf.facec[a][f]);
 }
 
 template <typename T, int D>
@@ -1792,7 +1982,12 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
     if (!finite) st |= ST_NONFINITE;
     else if (!(W[0] > 0.0) || !(2.0 * W[0] * W[1 + D] > m2)) st |= ST_NEGATIVE;
     if (st) atomicOr(bf.status, st);
-    make_cell<T>(g, W, bf.cellc[c]);
+    double hq[3] = {0.0, 0.0, 0.0};      // Shakhov: the heat flux of t_{n+1}
+    if (g.shakhov) {
+        shakhov_heat_flux<T, D>(g, bf.qs, g.Nc, c, W, 0.5 * g.dt, hq);
+        for (int a = 0; a < D; ++a) bf.hq[(size_t)a * g.Nc + c] = hq[a];
+    }
+    make_cell<T>(g, W, hq, bf.cellc[c]);
 }
 
 template <typename T, int D>
@@ -1825,7 +2020,10 @@ __global__ void k_cellc(const Inst<T>* __restrict__ in, int cur) {
     if (c >= g.Nc) return;
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int m = 0; m < 2 + D; ++m) W[m] = bf.W[(size_t)m * g.Nc + c];
-    make_cell<T>(g, W, bf.cellc[c]);
+    double q[3] = {0.0, 0.0, 0.0};
+    if (g.shakhov)
+        for (int a = 0; a < D; ++a) q[a] = bf.hq[(size_t)a * g.Nc + c];
+    make_cell<T>(g, W, q, bf.cellc[c]);
 }
 
 // Maxwell-Boltzmann initial state: W^0 from (rho, u, T), its constants (also
@@ -1848,9 +2046,10 @@ __global__ void k_init(const Inst<T>* __restrict__ in, int cur, const double* __
     }
     Wc[1 + D] = f[0] * (0.5 * u2 + cv * f[1 + D]);
     if (threadIdx.x < NM) bf.W[(size_t)threadIdx.x * g.Nc + c] = Wc[threadIdx.x];
+    if (g.shakhov && threadIdx.x < D) bf.hq[(size_t)threadIdx.x * g.Nc + c] = 0.0;   // a Maxwellian: q = 0
     __shared__ CellC<T> shc;
     if (threadIdx.x == 0) {       // the FP64 constants once per cell, not once per thread
-        make_cell<T>(g, Wc, shc);
+        make_cell<T>(g, Wc, nullptr, shc);
         bf.cellc[c] = shc;
         bf.cellc0[c] = shc;
     }
@@ -1859,7 +2058,7 @@ __global__ void k_init(const Inst<T>* __restrict__ in, int cur, const double* __
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(cc, v, ge, be);
+        equilibrium<T, D>(g, cc, v, ge, be);
         const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = ge;
         bf.phi_out[ad + VC] = be;
@@ -1908,7 +2107,7 @@ __global__ void __launch_bounds__(kStressThreads) k_stress(const Inst<T>* __rest
     for (int i = t; i < g.Nvp; i += kStressThreads) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(cc, v, ge, be);
+        equilibrium<T, D>(g, cc, v, ge, be);
         const size_t ad = phi_addr(g, c, i, 0);
         const double gv = (double)fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
         const double bv = (double)fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);
@@ -1971,7 +2170,7 @@ __global__ void k_finalise(const Inst<T>* __restrict__ in, int cur) {
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(cc, v, ge, be);
+        equilibrium<T, D>(g, cc, v, ge, be);
         const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
         bf.phi_out[ad + VC] = fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);

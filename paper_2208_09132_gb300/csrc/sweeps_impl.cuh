@@ -8,21 +8,26 @@ namespace cdg {
 // Block size of the per-face and per-cell kernels: small, so that the FP64
 // constant computations of a small problem spread over many SMs.
 constexpr int kSmallBlock = 64;
+// Block size of the raw-moment reductions (one thread per face or cell and group).
+constexpr int kMomBlock = 128;
 
 // One instantiated tile shape of the sweeps and its launches.  Prepared
 // shapes (MODE_PREP) form phibar+ of every point once per step (k_prep);
 // stored shapes (MODE_STORED) form phibar+ and the slopes (k_shslope); the
 // sweeps of both load what was formed instead of recomputing it on the halo.
 // Face-store shapes (MODE_FACES bit) have sweep A keep the reconstructed
-// face values and run k_flux as sweep B.
+// face values and run k_flux as sweep B.  Shakhov shapes (MODE_SK, face-store
+// only) add k_faceq before the face constants and k_cellq before the W update.
 template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED>
 struct Shape {
+    static constexpr bool SK = mode_sk(MODE);
     using SM = Smem<T, D, TX, TY, TZ, MODE>;
-    using FS = FluxSmem<T, D, TX, TY, TZ>;
+    using FS = FluxSmem<T, D, TX, TY, TZ, SK>;
     using TL = Tile<D, TX, TY, TZ>;
     static constexpr int mode = MODE;
     static constexpr int SRC = mode_source(MODE);
     static constexpr bool FACES = mode_faces(MODE);
+    static_assert(!SK || FACES, "Shakhov shapes are face-store shapes");
 
     // dynamic shared memory of the larger of the two sweeps
     static size_t smem_bytes() {
@@ -38,7 +43,7 @@ struct Shape {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
             return e;
         if constexpr (FACES) {
-            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)FS::bytes)))
                 return e;
         } else {
@@ -47,11 +52,11 @@ struct Shape {
                 return e;
         }
         if constexpr (SRC == MODE_STORED) {
-            if ((e = cudaFuncSetAttribute(k_shslope<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)shslope_smem_bytes<T, D, TX, TY, TZ>())))
+            if ((e = cudaFuncSetAttribute(k_shslope<T, D, TX, TY, TZ, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shslope_smem_bytes<T, D, TX, TY, TZ, SK>())))
                 return e;
         }
-        if constexpr (SRC == MODE_FUSED) {
+        if constexpr (SRC == MODE_FUSED && !SK) {
             if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false, MODE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
                 return e;
@@ -79,18 +84,28 @@ struct Shape {
             const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
             k_prep<T, D><<<pg, 128, 0, s>>>(in, cur, kChunks);
         } else if constexpr (SRC == MODE_STORED) {
-            k_shslope<T, D, TX, TY, TZ><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ>(), s>>>(in, cur);
+            k_shslope<T, D, TX, TY, TZ, SK><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s>>>(in, cur);
         }
         k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[1], s);
+        if constexpr (SK) {
+            long long nf = 0;
+            for (int a = 0; a < D; ++a) nf = g.nf[a] > nf ? g.nf[a] : nf;
+            const dim3 qg((unsigned)((nf + kMomBlock - 1) / kMomBlock), (unsigned)g.G, (unsigned)D);
+            k_faceq<T, D><<<qg, kMomBlock, 0, s>>>(in, cur);
+        }
         for (int a = 0; a < D; ++a) {
             const unsigned blocks = (unsigned)((g.nf[a] + kSmallBlock - 1) / kSmallBlock);
             k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
         }
         if (ev) cudaEventRecord(ev[2], s);
-        if constexpr (FACES) k_flux<T, D, TX, TY, TZ><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
+        if constexpr (FACES) k_flux<T, D, TX, TY, TZ, SK><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
         else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[3], s);
+        if constexpr (SK) {
+            const dim3 cg((unsigned)((g.Nc + kMomBlock - 1) / kMomBlock), (unsigned)g.G);
+            k_cellq<T, D><<<cg, kMomBlock, 0, s>>>(in, cur);
+        }
         k_wupdate<T, D><<<(unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock), kSmallBlock, 0, s>>>(in, cur);
         if (ev) cudaEventRecord(ev[4], s);
         return cudaGetLastError();
@@ -98,7 +113,7 @@ struct Shape {
 
     static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
                                    cudaStream_t s) {
-        if constexpr (SRC != MODE_FUSED) {
+        if constexpr (SRC != MODE_FUSED || SK) {
             return cudaErrorNotSupported;
         } else {
             cudaError_t e = configure();

@@ -69,6 +69,8 @@ def footprint_bytes(req: Request) -> int:
     h = ctypes.c_void_p()
     cdugks._check(lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)))
     try:
+        if req.cfg.get("collision", 0):
+            cdugks._check(lib.cdugks_set_collision(h, int(req.cfg["collision"])))
         if req.cfg.get("recon", 0):
             cdugks._check(lib.cdugks_set_reconstruction(h, int(req.cfg["recon"])))
         if req.tile_id:

@@ -55,7 +55,9 @@ def size_key(cfg, precision, context):
     cells = wl.ncells(cfg)
     bucket = 2 ** int(round(math.log2(max(cells, 1))))
     recon = ":faces-gradient" if cfg.get("recon", 0) else ""
-    return f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}{recon}"
+    coll = ":shakhov" if cfg.get("collision", 0) else ""
+    return (f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}"
+            f"{recon}{coll}")
 
 
 def candidates(cfg, precision, context="alone"):
@@ -64,11 +66,14 @@ def candidates(cfg, precision, context="alone"):
     groups = [g for g in (1, 2, 4, 8, 16, 32) if g <= nvt]
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     r2 = bool(cfg.get("recon", 0))
+    sk = bool(cfg.get("collision", 0))
     tiles = []
     for t in range(nt):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
-        if bool(mode & 8) != r2:
-            continue                      # shapes of the other reconstruction compute another scheme
+        if bool(mode & 8) != r2 or bool(mode & 16) != sk:
+            continue                      # shapes of the other reconstruction or collision compute another scheme
+        if context != "alone" and sk:
+            continue                      # Shakhov instances are not batched
         if context != "alone" and mode & 3 != 0:
             continue                      # only shapes that form phibar+ themselves are batched
         if mode & 3 == 2 and dirichlet:

@@ -115,3 +115,48 @@ def test_reconstruction_selection_rules():
     assert lib.cdugks_set_reconstruction(h, 1) != 0          # a wall needs 3 cells
     assert lib.cdugks_set_reconstruction(h, 0) == 0
     lib.cdugks_destroy(h)
+
+
+def test_collision_selection_rules():
+    """Shakhov collision: a face-store Shakhov shape in every dimension and
+    precision, selected before binding; the other shapes are refused while it
+    is selected, and so are the face-gradient reconstruction (no shape
+    implements both), Dirichlet walls with the stored-slope 3D shape and the
+    batch (host-side checks, no device)."""
+    lib = cdugks.load()
+
+    def handle(cfg, prec=cdugks.FP32):
+        g, v, p = cdugks.describe(cfg, prec)
+        h = ctypes.c_void_p()
+        assert lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)) == 0
+        return h
+
+    for prec in (cdugks.FP32, cdugks.FP64):
+        for dim in (1, 2, 3):
+            cfg, _ = wl.random_smooth(dim=dim, n=(8, 8, 8), nv=(4, 4, 4), seed=1)
+            h = handle(cfg, prec)
+            n0 = ctypes.c_size_t()
+            assert lib.cdugks_workspace_bytes(h, ctypes.byref(n0)) == 0
+            assert lib.cdugks_set_collision(h, wl.COLLISION_SHAKHOV) == 0, lib.cdugks_last_error()
+            info = cdugks.Info()
+            assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+            mode = cdugks.tile_shape(prec, dim, info.tile_id)[1]
+            assert mode & 16 and mode & 4                  # a Shakhov face-store shape
+            n1 = ctypes.c_size_t()
+            assert lib.cdugks_workspace_bytes(h, ctypes.byref(n1)) == 0
+            assert n1.value > n0.value                     # heat flux and raw-moment sums
+            assert lib.cdugks_set_tile(h, 0) != 0          # a two-time shape is refused now
+            assert lib.cdugks_set_reconstruction(h, 1) != 0
+            assert lib.cdugks_set_collision(h, 5) != 0
+            assert lib.cdugks_set_collision(h, wl.COLLISION_TEDDF) == 0
+            assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+            assert not cdugks.tile_shape(prec, dim, info.tile_id)[1] & 16
+            lib.cdugks_destroy(h)
+    cfg, _ = wl.random_smooth(dim=3, n=(8, 8, 8), nv=(4, 4, 4), seed=1)
+    cfg["bc"] = [[wl.BC_DIRICHLET] * 2] * 3
+    h = handle(cfg)
+    assert lib.cdugks_set_collision(h, wl.COLLISION_SHAKHOV) != 0
+    lib.cdugks_destroy(h)
+    for t in range(lib.cdugks_tile_count(cdugks.FP32, 2)):
+        m = cdugks.tile_shape(cdugks.FP32, 2, t)[1]
+        assert not (m & 16) or (m & 4 and not m & 8 and m & 3 != 1)

@@ -273,22 +273,25 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     (cfg, f), steps = case(name)
     refs = {}
 
-    def ref_of(recon):       # the oracle's result with the reconstruction a shape implements
-        if recon not in refs:
-            o = oracle_mod.Oracle(dict(cfg, recon=recon))
+    def ref_of(recon, coll):   # the oracle's result with the scheme a shape implements
+        if (recon, coll) not in refs:
+            o = oracle_mod.Oracle(dict(cfg, recon=recon, collision=coll))
             o.init(f)
             o.step(steps)
-            refs[recon] = o.moments()
-        return refs[recon]
+            refs[recon, coll] = o.moments()
+        return refs[recon, coll]
 
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
         if mode & 3 == 2 and dirichlet:
             continue      # stored-slope shapes take periodic and specular boundaries only
-        recon = 1 if mode & 8 else 0
-        ref = ref_of(recon)
-        s = cdugks.Solver(dict(cfg, recon=recon), precision=precision, tile_id=t, velocity_groups=2)
+        recon, coll = (1 if mode & 8 else 0), (1 if mode & 16 else 0)
+        if coll and min(cfg["nv"][:cfg["dim"]]) < 5:
+            continue      # the S-model blows up where 4 nodes per axis cannot carry a heat flux
+        ref = ref_of(recon, coll)
+        s = cdugks.Solver(dict(cfg, recon=recon, collision=coll), precision=precision, tile_id=t,
+                          velocity_groups=2)
         s.init(f)
         s.step(steps)
         assert s.sync_status() == 0
