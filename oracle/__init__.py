@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("recon", ctypes.c_int),
         ("collision", ctypes.c_int),
+        ("accel", ctypes.c_double * 3),
     ]
 
 
@@ -86,6 +87,7 @@ def _load():
         lib.oracle_cell_heat_flux.argtypes = [ctypes.c_void_p, dp]
         lib.oracle_set_state.argtypes = [ctypes.c_void_p, dp, dp, dp]
         lib.oracle_face_W.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+        lib.oracle_face_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
         lib.oracle_velocities.argtypes = [ctypes.c_void_p, dp, dp]
         lib.oracle_dt.restype = d
         lib.oracle_dt.argtypes = [ctypes.c_void_p]
@@ -122,7 +124,8 @@ class Oracle:
     ``cfg`` is a problem description dict (see ``paper_2208_09132_gb300.workloads``):
     keys dim, n, lo, hi, bc, nv, vlo, vhi, rule, K, R, mu_ref, T_ref, omega,
     Pr, dt, cfl; optional recon (0 upwind cell, 1 face gradient) and
-    collision (0 the paper's two relaxation times, 1 Shakhov S-model).
+    collision (0 the paper's two relaxation times, 1 Shakhov S-model) and
+    accel (a uniform external acceleration, 3 components).
     """
 
     def __init__(self, cfg: dict):
@@ -150,6 +153,9 @@ class Oracle:
         p.cfl = float(cfg.get("cfl", 0.5))
         p.recon = int(cfg.get("recon", 0))
         p.collision = int(cfg.get("collision", 0))
+        acc = list(cfg.get("accel", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+        for a in range(3):
+            p.accel[a] = float(acc[a])
         h = lib.oracle_create(ctypes.byref(p))
         if not h:
             raise ValueError("oracle_create rejected the problem description")
@@ -246,4 +252,13 @@ class Oracle:
             cnt *= (n[a] + 1) if a == axis else n[a]
         out = np.zeros((cnt, 2 + self.D))
         self._lib.oracle_face_W(self._h, int(axis), _ptr(out))
+        return out
+
+    def face_moments(self, axis: int, n: tuple) -> np.ndarray:
+        """Moments of the face distributions of the last step, ordered as face_W."""
+        cnt = 1
+        for a in range(self.D):
+            cnt *= (n[a] + 1) if a == axis else n[a]
+        out = np.zeros((cnt, 2 + self.D))
+        self._lib.oracle_face_moments(self._h, int(axis), _ptr(out))
         return out

@@ -10,7 +10,8 @@
  * Unified Gas Kinetic Scheme") and Sec. 2.1 ("The Algorithm"), for the reduced
  * distributions g (VDF, eq. g) and b (TEDF, eq. b) on a uniform Cartesian grid
  * in D = 1, 2 or 3 dimensions with a tensor-product discrete velocity grid.
- * External acceleration a = 0 throughout.
+ * External acceleration: none by default; a uniform vector a (accel) turns
+ * on the force terms of eqs. gsource/bsource (readings R-v below).
  *
  * Style: plain nested loops in the order the paper gives the steps, every
  * intermediate kept in a full array, std libm exp/pow, compensated
@@ -65,6 +66,26 @@
  *        At a face likewise q = q(phibar)/(1 + h Pr/(2 tau)).  The heat flux
  *        is tracked per cell like W; the initial Maxwellian state has q = 0,
  *        and so have Dirichlet ghosts.
+ *   R-v  (accel != 0) The force terms of eqs. gsource/bsource, S_g = -a.grad_xi g
+ *        and a.xi g - a.grad_xi b in S_b, with the velocity gradient by central
+ *        differences on the velocity grid, the distribution taken as zero beyond
+ *        its ends.  The source enters phibar+ with h/2 (eq. phibarplus) and the
+ *        update with dt at t_n (the rectangle rule of Sec. 2).  The W update
+ *        adds dt times the integrals of the sources taken analytically
+ *        (eqs. rhoupdate-rhoEupdate): 0 for rho, rho^n a for rho u and
+ *        (rho u)^n . a for rho E, as reading R-f takes the b-source's.
+ *   R-v1 At a face, eqs. rhoubar/rhoEbar: rho u = sum w xi gbar + (h/2) rho a,
+ *        then rho E = sum w bbar + (h/2) (rho u) . a with that rho u; the
+ *        inverse of eq. phibar takes the velocity gradients of the force terms
+ *        from phibar at the face and a.xi g with the face g (as R-i), so the
+ *        face distributions carry exactly the face conserved variables.
+ *   R-v3 At a specular wall face the wall takes the normal component of the
+ *        force: it is left out of that face's W corrections and inversion, so
+ *        the mirrored phibar and the face equilibrium stay symmetric and the
+ *        wall passes no mass and no energy.
+ *   R-v2 Ghost cells take phibar+ by the ghost rule itself: periodic copies,
+ *        specular mirror images (the force mirrored with the cell: the image
+ *        domain) and the Dirichlet equilibrium without a force term.
  *
  * Pinning (tests/test_oracle_pins.py): every step above is checked against a
  * closed form, an invariant or a textbook limit.  The S_b term of the
@@ -92,6 +113,9 @@ struct oracle {
     long Nc, Ne;        /* interior, extended cell counts */
     int Nv;
     double dx[3];
+    int nv1[3];         /* velocity nodes per axis (1 for unused axes) */
+    double dxi[3];      /* velocity grid spacing per axis */
+    int accel;          /* a != 0 */
     double gam;         /* adiabatic index */
     double *xi;         /* [Nv][3] discrete velocities */
     double *w;          /* [Nv] quadrature weights */
@@ -111,6 +135,7 @@ struct oracle {
     double *gf, *bf;            /* [3][Ne][Nv] phi at faces, t + h (inverse of eq. phibar) */
     double *dFg, *dFb;          /* [Ne][Nv] net microflux per cell volume (eq. flux) */
     double *Wn;                 /* [Ne][NW] updated conserved variables */
+    double *Fg, *Fb;            /* [Ne][Nv] force terms of the sources at t_n (accel, R-v) */
     double *qn;                 /* [Ne][3] heat flux at t_{n+1} (collision = 1) */
     long steps;
 };
@@ -286,6 +311,39 @@ static void heat_flux(const struct oracle *o, const double *g, const double *b, 
     }
 }
 
+/* The velocity-gradient parts of the force terms of eqs. gsource/bsource at
+ * one place from its distributions (g, b) [Nv] (R-v): sg = -a.grad_xi g and
+ * sb = -a.grad_xi b, the derivatives by central differences
+ * (g(k+1) - g(k-1))/(2 dxi) with g = 0 beyond the ends of the velocity grid.
+ * The whole force terms are S_g = sg and a.xi g + sb in S_b. */
+static void force_gradients(const struct oracle *o, const double *acc, const double *g, const double *b, double *sg,
+                            double *sb) {
+    const int D = o->D;
+    const long s1 = o->nv1[0], s2 = (long)o->nv1[0] * o->nv1[1];
+    for (long i = 0; i < o->Nv; ++i) {
+        const long k[3] = { i % o->nv1[0], (i / s1) % o->nv1[1], i / s2 };
+        const long st[3] = { 1, s1, s2 };
+        double G = 0.0, B = 0.0;
+        for (int a = 0; a < D; ++a) {
+            if (acc[a] == 0.0) continue;
+            double gp = 0.0, gm = 0.0, bp = 0.0, bm = 0.0;
+            if (k[a] + 1 < o->nv1[a]) { gp = g[i + st[a]]; bp = b[i + st[a]]; }
+            if (k[a] - 1 >= 0) { gm = g[i - st[a]]; bm = b[i - st[a]]; }
+            G += acc[a] * (gp - gm) / (2.0 * o->dxi[a]);
+            B += acc[a] * (bp - bm) / (2.0 * o->dxi[a]);
+        }
+        sg[i] = -G;
+        sb[i] = -B;
+    }
+}
+
+/* acc . xi_i */
+static double a_dot_xi(const struct oracle *o, const double *acc, long i) {
+    double s = 0.0;
+    for (int a = 0; a < o->D; ++a) s += acc[a] * o->xi[3 * i + a];
+    return s;
+}
+
 /* ------------------------------------------------------------- ghost layers */
 
 /* Fill the ghost cells of axis a over the full extent of the other axes
@@ -334,6 +392,37 @@ static void fill_ghosts(struct oracle *o) {
     for (int a = 0; a < o->D; ++a) fill_axis(o, a);
 }
 
+/* R-v2: phibar+ of the ghost cells of axis a by the ghost rule (the order
+ * of fill_axis, so corners agree): periodic copy, specular mirror image,
+ * Dirichlet equilibrium. */
+static void fill_axis_phibar(struct oracle *o, int a) {
+    long Nv = o->Nv;
+    int na = o->n[a];
+    for (long c = 0; c < o->Ne; ++c) {
+        int q[3];
+        ccoord(o, c, q);
+        int k = q[a];
+        if (k >= NG && k < NG + na) continue;
+        int side = (k < NG) ? 0 : 1;
+        int bc = o->p.bc[a][side];
+        int src[3] = { q[0], q[1], q[2] };
+        if (bc == ORACLE_BC_DIRICHLET) {
+            memcpy(&o->gp[c * Nv], &o->geq[c * Nv], sizeof(double) * Nv);
+            memcpy(&o->bp[c * Nv], &o->beq[c * Nv], sizeof(double) * Nv);
+            continue;
+        }
+        int mirror = bc == ORACLE_BC_SPECULAR;
+        if (mirror) src[a] = (k < NG) ? (2 * NG - 1 - k) : (2 * (NG + na) - 1 - k);
+        else src[a] = NG + (((k - NG) % na) + na) % na;
+        long s = cidx(o, src[0], src[1], src[2]);
+        for (long i = 0; i < Nv; ++i) {
+            long si = mirror ? o->refl[a][i] : i;
+            o->gp[c * Nv + i] = o->gp[s * Nv + si];
+            o->bp[c * Nv + i] = o->bp[s * Nv + si];
+        }
+    }
+}
+
 /* ----------------------------------------------------------------- create */
 
 static void *xalloc(size_t n) { void *p = calloc(n ? n : 1, 1); return p; }
@@ -344,6 +433,11 @@ oracle_t *oracle_create(const oracle_params *p) {
     if (!o) return NULL;
     o->p = *p;
     o->ng = p->recon ? 3 : 2;
+    o->accel = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(p->accel[a]) || (a >= p->D && p->accel[a] != 0.0)) { free(o); return NULL; }
+        if (p->accel[a] != 0.0) o->accel = 1;
+    }
     o->D = p->D;
     o->gam = (p->K + 5.0) / (p->K + 3.0);
     o->Nc = 1; o->Ne = 1; o->Nv = 1;
@@ -353,13 +447,15 @@ oracle_t *oracle_create(const oracle_params *p) {
             o->n[a] = p->n[a];
             o->ne[a] = p->n[a] + 2 * NG;
             o->dx[a] = (p->hi[a] - p->lo[a]) / p->n[a];
+            o->nv1[a] = p->nv[a];
+            o->dxi[a] = (p->vhi[a] - p->vlo[a]) / (p->nv[a] - 1);
             o->Nv *= p->nv[a];
             for (int s = 0; s < 2; ++s) {
                 if (p->bc[a][s] == ORACLE_BC_SPECULAR && (p->vlo[a] != -p->vhi[a] || p->n[a] < NG)) { free(o); return NULL; }
             }
             if ((p->bc[a][0] == ORACLE_BC_PERIODIC) != (p->bc[a][1] == ORACLE_BC_PERIODIC)) { free(o); return NULL; }
         } else {
-            o->n[a] = 1; o->ne[a] = 1; o->dx[a] = 1.0;
+            o->n[a] = 1; o->ne[a] = 1; o->dx[a] = 1.0; o->nv1[a] = 1; o->dxi[a] = 1.0;
         }
         o->Nc *= o->n[a];
         o->Ne *= o->ne[a];
@@ -407,11 +503,12 @@ oracle_t *oracle_create(const oracle_params *p) {
     o->Wn = xalloc(sizeof(double) * NW * Ne);
     o->q = xalloc(sizeof(double) * 3 * Ne);
     o->qn = xalloc(sizeof(double) * 3 * Ne);
+    o->Fg = xalloc(F); o->Fb = xalloc(F);
     o->Wdir = xalloc(sizeof(double) * NW * Ne);
     o->Wf = xalloc(sizeof(double) * 3 * NW * Ne);
     if (!o->g || !o->b || !o->geq || !o->beq || !o->Sb || !o->gp || !o->bp || !o->sg || !o->sb ||
         (p->recon && (!o->s2g || !o->s2b)) ||
-        !o->gfb || !o->bfb || !o->gf || !o->bf || !o->dFg || !o->dFb || !o->W || !o->Wn || !o->q || !o->qn ||
+        !o->gfb || !o->bfb || !o->gf || !o->bf || !o->dFg || !o->dFb || !o->W || !o->Wn || !o->q || !o->qn || !o->Fg || !o->Fb ||
         !o->Wdir || !o->Wf || !o->xi || !o->w) {
         oracle_destroy(o);
         return NULL;
@@ -441,7 +538,7 @@ void oracle_destroy(oracle_t *o) {
     free(o->gp); free(o->bp); free(o->sg); free(o->sb); free(o->s2g); free(o->s2b);
     free(o->gfb); free(o->bfb); free(o->gf); free(o->bf);
     free(o->dFg); free(o->dFb);
-    free(o->W); free(o->Wn); free(o->Wdir); free(o->Wf); free(o->q); free(o->qn);
+    free(o->W); free(o->Wn); free(o->Wdir); free(o->Wf); free(o->q); free(o->qn); free(o->Fg); free(o->Fb);
     free(o);
 }
 
@@ -529,7 +626,17 @@ static void one_step(struct oracle *o) {
             o->gp[k] = (2.0 * tg - h) / (2.0 * tg) * o->g[k] + h / (2.0 * tg) * o->geq[k];
             o->bp[k] = (2.0 * tb - h) / (2.0 * tb) * o->b[k] + h / (2.0 * tb) * o->beq[k] + 0.5 * h * o->Sb[k];
         }
+        if (o->accel) {   /* R-v: the force terms, h/2 of them in phibar+ */
+            force_gradients(o, o->p.accel, &o->g[c * Nv], &o->b[c * Nv], &o->Fg[c * Nv], &o->Fb[c * Nv]);
+            for (long i = 0; i < Nv; ++i) o->Fb[c * Nv + i] += a_dot_xi(o, o->p.accel, i) * o->g[c * Nv + i];
+            for (long i = 0; i < Nv; ++i) {
+                o->gp[c * Nv + i] += 0.5 * h * o->Fg[c * Nv + i];
+                o->bp[c * Nv + i] += 0.5 * h * o->Fb[c * Nv + i];
+            }
+        }
     }
+    if (o->accel)
+        for (int a = 0; a < D; ++a) fill_axis_phibar(o, a);   /* R-v2 */
 
     /* (2) van Leer limited slopes of phibar+ along every axis (eq. VanLeer),
      *     for every cell whose two neighbours exist in the extended grid. */
@@ -646,6 +753,15 @@ static void one_step(struct oracle *o) {
             double *Wf = &o->Wf[fo * NW];
             for (int k = 0; k < NW; ++k) Wf[k] = 0.0;
             for (int k = 0; k < 2 + D; ++k) Wf[k] = nsum_val(&m[k]);
+            /* R-v3: the force at this face; a specular wall takes its normal component */
+            double fa[3] = { o->p.accel[0], o->p.accel[1], o->p.accel[2] };
+            if ((q[a] == NG && o->p.bc[a][0] == ORACLE_BC_SPECULAR) ||
+                (q[a] == NG + o->n[a] && o->p.bc[a][1] == ORACLE_BC_SPECULAR))
+                fa[a] = 0.0;
+            if (o->accel) {   /* R-v1: eqs. rhoubar, rhoEbar */
+                for (int bax = 0; bax < D; ++bax) Wf[1 + bax] += 0.5 * h * Wf[0] * fa[bax];
+                for (int bax = 0; bax < D; ++bax) Wf[1 + D] += 0.5 * h * Wf[1 + bax] * fa[bax];
+            }
             double qf[3] = {0.0, 0.0, 0.0};   /* Shakhov: the face heat flux (R-s1, R-s2) */
             if (o->p.collision) heat_flux(o, &o->gfb[fo * Nv], &o->bfb[fo * Nv], Wf, qf);
 
@@ -656,16 +772,31 @@ static void one_step(struct oracle *o) {
             macro_from_W(o, Wf, &rho, u, &T);
             relax_times(o, rho, T, &tg, &tb, &itbg);
             for (int d = 0; d < 3; ++d) qf[d] /= 1.0 + h * o->p.Pr / (2.0 * tg);
+            double *fsg = NULL, *fsb = NULL;   /* R-v1: force gradients of phibar at the face */
+            if (o->accel) {
+                fsg = (double *)calloc((size_t)2 * Nv, sizeof(double));
+                fsb = fsg + Nv;
+                force_gradients(o, fa, &o->gfb[fo * Nv], &o->bfb[fo * Nv], fsg, fsb);
+            }
             for (long i = 0; i < Nv; ++i) {
                 const double *xi = &o->xi[3 * i];
                 double ge, be;
                 model_equilibrium(o, rho, u, T, qf, xi, &ge, &be);
                 double G = o->gfb[fo * Nv + i], B = o->bfb[fo * Nv + i];
-                double gfv = (2.0 * tg * G + h * ge) / (2.0 * tg + h);
-                double bfv = (2.0 * tb * B + h * be + h * tb * zeta(o, xi, u) * itbg * (gfv - ge)) / (2.0 * tb + h);
+                double gfv, bfv;
+                if (!o->accel) {
+                    gfv = (2.0 * tg * G + h * ge) / (2.0 * tg + h);
+                    bfv = (2.0 * tb * B + h * be + h * tb * zeta(o, xi, u) * itbg * (gfv - ge)) / (2.0 * tb + h);
+                } else {   /* the inverse of eq. phibar with the whole source S; a.xi g with the face g (R-i) */
+                    gfv = (2.0 * tg * G + h * ge + h * tg * fsg[i]) / (2.0 * tg + h);
+                    bfv = (2.0 * tb * B + h * be +
+                           h * tb * (zeta(o, xi, u) * itbg * (gfv - ge) + a_dot_xi(o, fa, i) * gfv + fsb[i])) /
+                          (2.0 * tb + h);
+                }
                 o->gf[fo * Nv + i] = gfv;
                 o->bf[fo * Nv + i] = bfv;
             }
+            free(fsg);
         }
     }
 
@@ -699,6 +830,12 @@ static void one_step(struct oracle *o) {
         }
         for (int k = 0; k < NW; ++k) o->Wn[c * NW + k] = 0.0;
         for (int k = 0; k < 2 + D; ++k) o->Wn[c * NW + k] = o->W[c * NW + k] - dt * nsum_val(&m[k]);
+        if (o->accel) {   /* R-v: dt times the integrals of the sources at t_n */
+            for (int a = 0; a < D; ++a) {
+                o->Wn[c * NW + 1 + a] += dt * o->W[c * NW] * o->p.accel[a];
+                o->Wn[c * NW + 1 + D] += dt * o->W[c * NW + 1 + a] * o->p.accel[a];
+            }
+        }
 
         double rho0, u0[3], T0, tg0, tb0, itbg0;
         macro_from_W(o, &o->W[c * NW], &rho0, u0, &T0);
@@ -715,6 +852,10 @@ static void one_step(struct oracle *o) {
                 long k = c * Nv + i;
                 eg[i] = o->g[k] + 0.5 * dt * (o->geq[k] - o->g[k]) / tg0 - dt * o->dFg[k];
                 eb[i] = o->b[k] + 0.5 * dt * (o->beq[k] - o->b[k]) / tb0 - dt * o->dFb[k];
+                if (o->accel) {
+                    eg[i] += dt * o->Fg[k];
+                    eb[i] += dt * o->Fb[k];
+                }
             }
             heat_flux(o, eg, eb, &o->Wn[c * NW], q1);
             free(eg);
@@ -724,10 +865,18 @@ static void one_step(struct oracle *o) {
             long k = c * Nv + i;
             double ge1, be1;
             model_equilibrium(o, rho1, u1, T1, q1, &o->xi[3 * i], &ge1, &be1);
-            double gnew = (o->g[k] + 0.5 * dt * (ge1 / tg1 + (o->geq[k] - o->g[k]) / tg0)
-                           - dt * o->dFg[k]) / (1.0 + dt / (2.0 * tg1));
-            double bnew = (o->b[k] + 0.5 * dt * (be1 / tb1 + (o->beq[k] - o->b[k]) / tb0)
-                           - dt * o->dFb[k] + dt * o->Sb[k]) / (1.0 + dt / (2.0 * tb1));
+            double gnew, bnew;
+            if (!o->accel) {
+                gnew = (o->g[k] + 0.5 * dt * (ge1 / tg1 + (o->geq[k] - o->g[k]) / tg0)
+                        - dt * o->dFg[k]) / (1.0 + dt / (2.0 * tg1));
+                bnew = (o->b[k] + 0.5 * dt * (be1 / tb1 + (o->beq[k] - o->b[k]) / tb0)
+                        - dt * o->dFb[k] + dt * o->Sb[k]) / (1.0 + dt / (2.0 * tb1));
+            } else {   /* eq. phiupdate with S^n = the b-source + the force terms */
+                gnew = (o->g[k] + 0.5 * dt * (ge1 / tg1 + (o->geq[k] - o->g[k]) / tg0)
+                        - dt * o->dFg[k] + dt * o->Fg[k]) / (1.0 + dt / (2.0 * tg1));
+                bnew = (o->b[k] + 0.5 * dt * (be1 / tb1 + (o->beq[k] - o->b[k]) / tb0)
+                        - dt * o->dFb[k] + dt * (o->Sb[k] + o->Fb[k])) / (1.0 + dt / (2.0 * tb1));
+            }
             o->g[k] = gnew;
             o->b[k] = bnew;
         }
@@ -891,6 +1040,33 @@ void oracle_cell_heat_flux(const oracle_t *o, double *out) {
         long c = interior_ext(o, ic);
         for (int a = 0; a < o->D; ++a) out[ic * o->D + a] = o->q[c * 3 + a];
     }
+}
+
+/* Moments (rho, rho u, rho E) of the face distributions phi of the last step
+ * (the inverse of eq. phibar), axis a, in the order of oracle_face_W. */
+void oracle_face_moments(const oracle_t *o, int a, double *out) {
+    int D = o->D;
+    long k = 0, Nv = o->Nv;
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = (d < D) ? NG : 0;
+        hi[d] = (d < D) ? NG + o->n[d] : 1;
+    }
+    hi[a] += 1;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x, ++k) {
+                long fo = (long)a * o->Ne + cidx(o, x, y, z);
+                nsum m[NW];
+                memset(m, 0, sizeof(m));
+                for (long i = 0; i < Nv; ++i) {
+                    double G = o->gf[fo * Nv + i];
+                    nsum_add(&m[0], o->w[i] * G);
+                    for (int b = 0; b < D; ++b) nsum_add(&m[1 + b], o->w[i] * o->xi[3 * i + b] * G);
+                    nsum_add(&m[1 + D], o->w[i] * o->bf[fo * Nv + i]);
+                }
+                for (int m2 = 0; m2 < 2 + D; ++m2) out[k * (2 + D) + m2] = nsum_val(&m[m2]);
+            }
 }
 
 /* Face conserved variables of the last step, axis a, [Nfaces_a][2+D] in the

@@ -33,6 +33,7 @@ typedef struct {
     double cfl;
     int recon;             /* 0: reconstruction R-c; 1: the face-gradient variant R-c2 */
     int collision;         /* 0: the paper's two relaxation times (TEDDF); 1: Shakhov S-model */
+    double accel[3];       /* uniform external acceleration a (eqs. gsource, bsource); 0 = none */
 } oracle_params;
 
 typedef struct oracle oracle_t;
@@ -52,6 +53,7 @@ void oracle_shakhov_equilibrium(const oracle_t *o, double rho, const double *u, 
 void oracle_cell_heat_flux(const oracle_t *o, double *out);   /* [Nc][D] tracked q (collision = 1) */
 int oracle_set_state(oracle_t *o, const double *g, const double *b, const double *W);
 void oracle_face_W(const oracle_t *o, int a, double *out);
+void oracle_face_moments(const oracle_t *o, int a, double *out);   /* moments of the face phi, as oracle_face_W */
 void oracle_velocities(const oracle_t *o, double *xi, double *w);     /* [Nv][3], [Nv] */
 double oracle_dt(const oracle_t *o);
 int oracle_nv(const oracle_t *o);

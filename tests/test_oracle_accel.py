@@ -1,0 +1,161 @@
+"""Pins of the oracle's external-acceleration source terms (eqs. gsource,
+bsource with a != 0; readings R-v to R-v2 of the oracle).
+
+  uniform acceleration     a uniform gas gains u = u0 + a t exactly (the W
+                           source), its energy follows the rectangle rule of
+                           Sec. 2 step by step, and its distribution stays the
+                           Maxwellian of its moments to second order in the
+                           velocity spacing (the central differences)
+  face inversion           the face distributions carry exactly the face
+                           conserved variables of eqs. rhoubar/rhoEbar, in the
+                           collisional and the collisionless regime
+  balance                  periodic domains: mass conserved, momentum and
+                           energy change by dt sum rho a and dt sum rho u . a
+  hydrostatics             an isothermal atmosphere between specular walls
+                           stays at rest, at second order away from the walls
+  free fall                a collisionless gas converges to the exact solution
+                           f0(x - xi t + a t^2/2, xi - a t) of the Vlasov equation
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2208_09132_gb300 import workloads as wl
+
+R = 0.5
+
+
+def cplx_amp(f, x, k):
+    return 2.0 * np.sum((f - f.mean()) * np.exp(-1j * k * x)) / f.size
+
+
+@pytest.mark.parametrize("D,a", [(1, (0.8, 0.0)), (2, (0.8, -0.5))])
+def test_uniform_gas_accelerates_exactly(oracle_mod, D, a):
+    dev = []
+    for nv in (24, 48, 96) if D == 1 else (32, 64, 128):
+        cfg = wl._base(D, [3] * D, [0] * D, [1] * D, [[0, 0]] * D, [nv] * D, [-8.0] * D, [8.0] * D, K=2.0,
+                       mu_ref=1e-2, T_ref=1.0, omega=0.5, Pr=2.0 / 3.0, cfl=0.5)
+        cfg["accel"] = list(a) + [0.0]
+        cfg["dt"] = 1e-3
+        o = oracle_mod.Oracle(cfg)
+        u0 = np.array([0.3, -0.1])[:D]
+        o.init(np.tile([1.0] + list(u0) + [1.0], (o.Nc, 1)))
+        W = o.conserved()[0].copy()
+        n = 150 if D == 1 else 60
+        av = np.array(a[:D])
+        for _ in range(n):                       # the rectangle rule, step by step
+            W[1 + D] += o.dt * W[1:1 + D] @ av
+            W[1:1 + D] += o.dt * W[0] * av
+        o.step(n - 1)
+        Wl = o.conserved()[0].copy()
+        o.step(1)
+        Wo = o.conserved()
+        assert np.abs(Wo - W).max() <= 1e-13 * np.abs(W).max(), (Wo[0], W)
+        # the face conserved variables (eqs. rhobar-rhoEbar) are the gas half a
+        # step h later: rho u + h rho a and rho E + h rho u.a + h^2 rho a^2 / 2
+        h = 0.5 * o.dt
+        Wh = Wl.copy()
+        Wh[1:1 + D] += h * Wl[0] * av
+        Wh[1 + D] += h * Wl[1:1 + D] @ av + 0.5 * h * h * Wl[0] * (av @ av)
+        for ax in range(D):
+            Wf = o.face_W(ax, [3] * D)
+            assert np.abs(Wf - Wh).max() <= 1e-7 * np.abs(Wh).max(), (ax, Wf[0], Wh)   # quadrature of tails
+        m = o.moments()[0]
+        assert np.abs(m[1:1 + D] - (u0 + n * o.dt * np.array(a[:D]))).max() < 1e-13
+        g, _ = o.distributions()
+        ge, _ = o.equilibrium(m[0], m[1:1 + D], m[1 + D])
+        dev.append(np.abs(g[0] - ge).max() / ge.max())
+    orders = [math.log2(dev[i] / dev[i + 1]) for i in range(2)]
+    assert min(orders) > 1.8, (dev, orders)
+
+
+@pytest.mark.parametrize("mu", [1e-2, 1e250])
+def test_face_distributions_carry_the_face_conserved_variables(oracle_mod, mu):
+    """Inverting eq. phibar with the whole source (force gradients from phibar,
+    a.xi g with the face g) gives face distributions whose moments are the face
+    W of eqs. rhobar-rhoEbar with their (h/2) rho a corrections."""
+    n = (10, 8)
+    cfg, f = wl.random_smooth(dim=2, n=n, nv=(40, 40), seed=3, amp=0.3, kn=1e-2, vmax=9.0)
+    cfg["mu_ref"], cfg["omega"] = mu, (0.5 if mu < 1 else 0.0)
+    cfg["accel"] = [0.7, -0.4, 0.0]
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(3)
+    for a in (0, 1):
+        Wf, Mf = o.face_W(a, n), o.face_moments(a, n)
+        assert np.all(np.abs(Mf - Wf).max(0) <= 1e-13 * np.abs(Wf).max(0)), np.abs(Mf - Wf).max(0)
+
+
+def test_momentum_and_energy_balance_periodic(oracle_mod):
+    cfg, f = wl.random_smooth(dim=2, n=(12, 10), nv=(14, 14), seed=6, amp=0.3, kn=3e-3, vmax=8.0)
+    a = np.array([0.7, -0.4])
+    cfg["accel"] = list(a) + [0.0]
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    for _ in range(6):
+        W0 = o.conserved()
+        o.step(1)
+        W1 = o.conserved()
+        S0, S1 = W0.sum(0), W1.sum(0)
+        assert abs(S1[0] - S0[0]) <= 1e-13 * S0[0]
+        assert np.abs(S1[1:3] - S0[1:3] - o.dt * S0[0] * a).max() <= 1e-13 * S0[0]
+        assert abs(S1[3] - S0[3] - o.dt * (W0[:, 1:3] @ a).sum()) <= 1e-13 * S0[3]
+
+
+def test_hydrostatic_atmosphere_stays_at_rest(oracle_mod):
+    """rho = exp(a x / RT) under a = -1 between specular walls: mass is
+    conserved exactly (the mirror image of phibar+ reflects the wall flux) and
+    the spurious velocity vanishes with the grid.  The wall cells converge at
+    first order, where the mirror image puts a kink into the hydrostatic
+    density gradient; the interior faster, until the waves the walls radiate
+    reach it (orders 1.5 and 1.7 on these grids)."""
+    a, RT = -1.0, 0.5
+    inner, wall = [], []
+    for nx in (32, 64, 128):
+        cfg = wl._base(1, [nx], [0], [1], [[wl.BC_SPECULAR] * 2], [48], [-8.0], [8.0], K=2.0, mu_ref=1e-3,
+                       T_ref=1.0, omega=0.5, Pr=2.0 / 3.0, cfl=0.5)
+        cfg["accel"] = [a, 0.0, 0.0]
+        _, (x,) = wl.cell_centres(cfg)
+        o = oracle_mod.Oracle(cfg)
+        o.init(wl._fields(np.exp(a * x / RT), [np.zeros_like(x)], np.full_like(x, RT / R)))
+        m0 = o.conserved()[:, 0].sum()
+        o.step(int(round(0.5 / o.dt)))
+        assert abs(o.conserved()[:, 0].sum() - m0) <= 1e-13 * m0
+        u = np.abs(o.moments()[:, 1])
+        inner.append(u[nx // 4: 3 * nx // 4].max())
+        wall.append(u.max())
+    assert wall[-1] < 3e-3 and inner[-1] < 2e-4, (wall, inner)
+    assert min(math.log2(inner[i] / inner[i + 1]) for i in range(2)) > 1.4, inner
+    assert min(math.log2(wall[i] / wall[i + 1]) for i in range(2)) > 0.9, wall
+
+
+def test_collisionless_free_fall_converges_to_the_exact_solution(oracle_mod):
+    """Collisionless, periodic: f(x, xi, t) = f0(x - xi t + a t^2/2, xi - a t)
+    for f0 = a Maxwellian with a density wave.  The source enters the update by
+    the rectangle rule (first order in time), the stencils are second order."""
+    a, t_end, k = 0.5, 0.25, 2 * math.pi
+    errs = []
+    for nx, nv in ((32, 32), (64, 64), (128, 128)):
+        cfg = wl._base(1, [nx], [0], [1], [[0, 0]], [nv], [-7.0], [7.0], K=0.0, mu_ref=1e250, T_ref=1.0,
+                       omega=0.0, Pr=1.0, cfl=0.5)
+        cfg["accel"] = [a, 0.0, 0.0]
+        _, (x,) = wl.cell_centres(cfg)
+        o = oracle_mod.Oracle(cfg)
+        cfg["dt"] = t_end / math.ceil(t_end / o.dt)
+        o = oracle_mod.Oracle(cfg)
+        o.init(wl._fields(1 + 0.2 * np.sin(k * x), [np.zeros_like(x)], np.full_like(x, 1.0)))
+        o.step(int(round(t_end / o.dt)))
+        xi, _ = o.velocities()
+        xi = xi[:, 0]
+        g, _ = o.distributions()
+        # exact, averaged over each cell: the density factor integrates in closed form
+        RT = R * 1.0
+        dx = 1.0 / nx
+        shift = x[:, None] - xi[None, :] * t_end + 0.5 * a * t_end ** 2
+        avg = 1 + 0.2 * np.sin(k * shift) * np.sin(k * dx / 2) / (k * dx / 2)
+        v = xi[None, :] - a * t_end
+        exact = avg * np.exp(-v * v / (2 * RT)) / math.sqrt(2 * math.pi * RT)
+        errs.append(np.abs(g - exact).max() / exact.max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 2e-2 and min(orders) > 0.9, (errs, orders)
