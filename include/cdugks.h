@@ -230,6 +230,8 @@ CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
  * (cdugks_set_reconstruction); the others the upwind-cell one.
  * Bit 4 (value 16): the shape implements the Shakhov collision model
  * (cdugks_set_collision); the others the two-time model.
+ * Bit 5 (value 32): the shape implements the external acceleration
+ * (cdugks_set_acceleration); the others none.
  * Every mode but 0 must be selected before cdugks_bind; modes with bits 0-1
  * nonzero are not batched (modes 0 and 4 are). */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
@@ -281,6 +283,25 @@ CDUGKS_API int cdugks_set_reconstruction(cdugks_t *h, int recon);
 #define CDUGKS_COLLISION_TEDDF 0
 #define CDUGKS_COLLISION_SHAKHOV 1
 CDUGKS_API int cdugks_set_collision(cdugks_t *h, int model);
+
+/* Uniform external acceleration a (host double[3], components beyond dim 0;
+ * NULL or all zero turns it off; call before cdugks_bind).  It switches on
+ * the force terms of eqs. gsource/bsource: S_g = -a.grad_xi g and
+ * a.xi g - a.grad_xi b in S_b, the velocity gradients by central differences
+ * on the velocity grid (the distribution taken as 0 beyond its ends).  The
+ * sources enter phibar+ with h/2 (eq. phibarplus) and phi* with dt at t_n
+ * (the rectangle rule of Sec. 2); W gains dt (0, rho^n a, (rho u)^n . a); the
+ * face W gains (h/2) rho a and then (h/2) (rho u) . a (eqs. rhoubar,
+ * rhoEbar); the inverse of eq. phibar at a face takes the force gradients of
+ * phibar there and a.xi g with the face g.  A specular wall face leaves out
+ * the normal component of the force (the wall takes it), so walls pass no
+ * mass.  Ghost cells take phibar+ by their rule (copy, mirror image,
+ * Dirichlet equilibrium).  Selects the first tile shape that implements it
+ * (prepared face-store shapes, mode bit 5); the upwind-cell reconstruction
+ * and the two-time collision model only; not batched, not in
+ * cdugks_step_noalloc.  Errors: INVALID (non-finite, nonzero beyond dim,
+ * already bound, no shape). */
+CDUGKS_API int cdugks_set_acceleration(cdugks_t *h, const double *a);
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances stepped together: every kernel of a time step

@@ -24,7 +24,8 @@ EXPORTS = [
     "cdugks_profile_step",
     "cdugks_sync_status", "cdugks_moments", "cdugks_stress_heat_flux", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
-    "cdugks_set_velocity_groups", "cdugks_set_reconstruction", "cdugks_set_collision", "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
+    "cdugks_set_velocity_groups", "cdugks_set_reconstruction", "cdugks_set_collision", "cdugks_set_acceleration",
+    "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
     "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
     "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy", "cdugks_batch_admit", "cdugks_batch_retire",
@@ -99,6 +100,7 @@ def load(build_if_needed: bool = True):
         "cdugks_set_velocity_groups": (i, [vp, i]),
         "cdugks_set_reconstruction": (i, [vp, i]),
         "cdugks_set_collision": (i, [vp, i]),
+        "cdugks_set_acceleration": (i, [vp, dp]),
         "cdugks_destroy": (None, [vp]),
         "cdugks_strerror": (ctypes.c_char_p, [i]),
         "cdugks_last_error": (ctypes.c_char_p, []),
@@ -183,6 +185,10 @@ class Solver:
         self._h = h
         if cfg.get("collision", 0):          # the Shakhov model (and its default shape)
             _check(self._lib.cdugks_set_collision(h, int(cfg["collision"])))
+        if any(cfg.get("accel", (0.0, 0.0, 0.0))):   # the external acceleration (and its default shape)
+            acc = np.zeros(3)
+            acc[: len(cfg["accel"])] = cfg["accel"]
+            _check(self._lib.cdugks_set_acceleration(h, _dptr(acc)))
         if cfg.get("recon", 0):              # the face-gradient reconstruction (and its default shape)
             _check(self._lib.cdugks_set_reconstruction(h, int(cfg["recon"])))
         if tile_id:
@@ -351,7 +357,8 @@ def tile_shape(precision: int, dim: int, tile_id: int):
     0-1: 0 fused, 1 prepared phibar+, 2 stored phibar+ and slopes; bit 2 (4):
     face store (sweep A keeps the face values, sweep B only forms fluxes);
     bit 3 (8): the face-gradient reconstruction (cfg["recon"] = 1);
-    bit 4 (16): the Shakhov collision model (cfg["collision"] = 1)."""
+    bit 4 (16): the Shakhov collision model (cfg["collision"] = 1);
+    bit 5 (32): the external acceleration (cfg["accel"] nonzero)."""
     out = (ctypes.c_int * 4)()
     _check(load().cdugks_tile_shape(int(precision), int(dim), int(tile_id), out))
     return tuple(out[:3]), int(out[3])

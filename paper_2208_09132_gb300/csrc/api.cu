@@ -45,13 +45,15 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     size_t phi[2], pb, sg, fv[3], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst;
     size_t hq, qs, qf[3];     // Shakhov model only
+    size_t force;             // acceleration only
     size_t total;
 };
 
 // Optional workspace buffers, by the sweep modes that need them.
-enum { BUF_PHIBAR = 1, BUF_SLOPES = 2, BUF_FACES = 4 };
+enum { BUF_PHIBAR = 1, BUF_SLOPES = 2, BUF_FACES = 4, BUF_FORCE = 8 };
 int buffers_of(int mode) {
     int b = 0;
+    if (cdg::mode_acc(mode)) b |= BUF_FORCE;
     if (cdg::mode_source(mode) != cdg::MODE_FUSED) b |= BUF_PHIBAR;
     if (cdg::mode_source(mode) == cdg::MODE_STORED) b |= BUF_SLOPES;
     if (cdg::mode_faces(mode)) b |= BUF_FACES;
@@ -159,6 +161,7 @@ void make_layout(cdugks* h) {
     L.phi[0] = take(state);
     L.phi[1] = take(state);
     L.pb = (h->bufs_cap & BUF_PHIBAR) ? take(state) : 0;
+    L.force = (h->bufs_cap & BUF_FORCE) ? take(state) : 0;
     L.sg = (h->bufs_cap & BUF_SLOPES) ? take(state * g.D) : 0;
     for (int a = 0; a < 3; ++a)
         L.fv[a] = (h->bufs_cap & BUF_FACES) && a < g.D ? take((size_t)g.Nvp * (size_t)g.nf[a] * 2 * h->elt) : 0;
@@ -192,6 +195,7 @@ Bufs<T> bufs(const cdugks* h, int in) {
     b.phi_in = reinterpret_cast<const T*>(p + L.phi[in]);
     b.phi_out = reinterpret_cast<T*>(p + L.phi[1 - in]);
     b.phibar = (h->bufs_cap & BUF_PHIBAR) ? reinterpret_cast<T*>(p + L.pb) : nullptr;
+    b.force = (h->bufs_cap & BUF_FORCE) ? reinterpret_cast<T*>(p + L.force) : nullptr;
     b.sigma = (h->bufs_cap & BUF_SLOPES) ? reinterpret_cast<T*>(p + L.sg) : nullptr;
     for (int a = 0; a < 3; ++a)
         b.face[a] = (h->bufs_cap & BUF_FACES) && a < h->g.D ? reinterpret_cast<T*>(p + L.fv[a]) : nullptr;
@@ -330,6 +334,8 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
                 return fail(CDUGKS_ERR_INVALID, "bad velocity grid (n >= 2, hi > lo, Boole needs n = 4m+1)");
             }
             nv[a] = vgrid->n[a];
+            g.nv1[a] = vgrid->n[a];
+            g.dxi[a] = (vgrid->hi[a] - vgrid->lo[a]) / (vgrid->n[a] - 1);
             g.n[a] = grid->n[a];
             g.bc[a][0] = grid->bc[a][0];
             g.bc[a][1] = grid->bc[a][1];
@@ -337,6 +343,8 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
         } else {
             nodes[a].assign(1, 0.0);
             wts[a].assign(1, 1.0);
+            g.nv1[a] = 1;
+            g.dxi[a] = 1.0;
             g.n[a] = 1;
             g.dx[a] = 1.0;
         }
@@ -461,6 +469,8 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
         return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected reconstruction");
     if (cdg::mode_sk(mode) != (h->collision == CDUGKS_COLLISION_SHAKHOV))
         return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected collision model");
+    if (cdg::mode_acc(mode) != (h->g.accel != 0))
+        return fail(CDUGKS_ERR_INVALID, "tile shape does not implement the selected external acceleration");
     if (cdg::mode_source(mode) == cdg::MODE_STORED)
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
@@ -502,7 +512,7 @@ int cdugks_set_reconstruction(cdugks_t* h, int recon) {
     for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t) {
         const int m = tile_mode(h->prec, h->g.D, t);
         if (cdg::mode_r2(m) == (recon == CDUGKS_RECON_FACE_GRADIENT) &&
-            cdg::mode_sk(m) == (h->collision == CDUGKS_COLLISION_SHAKHOV))
+            cdg::mode_sk(m) == (h->collision == CDUGKS_COLLISION_SHAKHOV) && cdg::mode_acc(m) == (h->g.accel != 0))
             id = t;
     }
     if (id < 0)
@@ -526,7 +536,7 @@ int cdugks_set_collision(cdugks_t* h, int model) {
     for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t) {
         const int m = tile_mode(h->prec, h->g.D, t);
         if (cdg::mode_sk(m) == (model == CDUGKS_COLLISION_SHAKHOV) &&
-            cdg::mode_r2(m) == (h->recon == CDUGKS_RECON_FACE_GRADIENT))
+            cdg::mode_r2(m) == (h->recon == CDUGKS_RECON_FACE_GRADIENT) && cdg::mode_acc(m) == (h->g.accel != 0))
             id = t;
     }
     if (id < 0)
@@ -545,6 +555,34 @@ int cdugks_set_collision(cdugks_t* h, int model) {
         h->g.shakhov = old == CDUGKS_COLLISION_SHAKHOV;
         make_layout(h);
     }
+    return rc;
+}
+
+int cdugks_set_acceleration(cdugks_t* h, const double* a) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    if (h->bound) return fail(CDUGKS_ERR_INVALID, "set the acceleration before cdugks_bind");
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 3 && a; ++b) {
+        if (!std::isfinite(a[b]) || (b >= h->g.D && a[b] != 0.0))
+            return fail(CDUGKS_ERR_INVALID, "acceleration components must be finite, and 0 beyond dim");
+        acc[b] = a[b];
+    }
+    const int on = acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0;
+    int id = -1;
+    for (int t = 0; t < tile_count(h->prec, h->g.D) && id < 0; ++t) {
+        const int m = tile_mode(h->prec, h->g.D, t);
+        if (cdg::mode_acc(m) == (on != 0) && cdg::mode_sk(m) == (h->collision == CDUGKS_COLLISION_SHAKHOV) &&
+            cdg::mode_r2(m) == (h->recon == CDUGKS_RECON_FACE_GRADIENT))
+            id = t;
+    }
+    if (id < 0)
+        return fail(CDUGKS_ERR_INVALID,
+                    "no tile shape implements the acceleration with this collision model and reconstruction");
+    const Geo old = h->g;
+    for (int b = 0; b < 3; ++b) h->g.acc[b] = acc[b];
+    h->g.accel = on;
+    const int rc = cdugks_set_tile(h, id);
+    if (rc) h->g = old;
     return rc;
 }
 
@@ -1392,8 +1430,9 @@ extern "C" {
 int cdugks_step_noalloc(cdugks_t* h, const void* phi_in, void* phi_out, double* W, void* cuda_stream) {
     if (!h || !phi_in || !phi_out || !W) return fail(CDUGKS_ERR_INVALID, "null argument");
     if (phi_in == phi_out) return fail(CDUGKS_ERR_INVALID, "phi_in and phi_out must be different buffers");
-    if (h->collision != CDUGKS_COLLISION_TEDDF)
-        return fail(CDUGKS_ERR_INVALID, "the allocation-free step implements the two-time collision model only");
+    if (h->collision != CDUGKS_COLLISION_TEDDF || h->g.accel)
+        return fail(CDUGKS_ERR_INVALID,
+                    "the allocation-free step implements the two-time collision model without acceleration only");
     for (int a = 0; a < h->g.D; ++a)
         if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
             return fail(CDUGKS_ERR_INVALID, "the allocation-free step supports periodic and specular boundaries only");

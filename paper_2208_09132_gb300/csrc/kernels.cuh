@@ -63,6 +63,10 @@ struct Geo {
     double dt, h;
     double K, R, mu_ref, T_ref, omega, Pr;
     int shakhov;      // collision model: 0 the two relaxation times of Sec. 2, 1 the Shakhov S-model
+    int accel;        // a uniform external acceleration is on (eqs. gsource, bsource)
+    double acc[3];    // its components a_b (0 beyond D)
+    int nv1[3];       // velocity nodes per axis (velocity i = k0 + nv1_0 (k1 + nv1_1 k2))
+    double dxi[3];    // velocity spacing per axis
 };
 
 template <typename T> struct CellC;
@@ -89,6 +93,7 @@ struct Bufs {
     double* hq;           // [D][Nc] heat flux of the current time level, tracked like W
     double* qs;           // [G][NQ][Nc] raw velocity moments of phi* per velocity group
     double* qf[3];        // [G][NQ][nf_a] raw velocity moments of the face values per group
+    T* force;             // acceleration only: force terms of the sources at t_n, state layout
 };
 
 // An instance as the kernels see it: geometry and both ping-pong orientations
@@ -604,11 +609,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Bit 4 (Shakhov): the sweeps and k_flux evaluate the Shakhov equilibria
 // (face-store shapes only); k_faceq and k_cellq add the raw moments the heat
 // flux needs.
-enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16 };
+// Bit 5 (acceleration): k_prep adds the force terms of the sources (prepared
+// face-store shapes only) and k_flux takes them at the faces and in phi*.
+enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16, MODE_ACC = 32 };
 __host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
 __host__ __device__ constexpr bool mode_r2(int mode) { return (mode & MODE_R2) != 0; }
 __host__ __device__ constexpr bool mode_sk(int mode) { return (mode & MODE_SK) != 0; }
+__host__ __device__ constexpr bool mode_acc(int mode) { return (mode & MODE_ACC) != 0; }
 __host__ __device__ constexpr int mode_halo(int mode) { return mode_r2(mode) ? 3 : 2; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
@@ -722,9 +730,40 @@ __device__ __forceinline__ void packed_eq(const T* cst, const T (&xi)[D], T hx, 
     }
 }
 
+// ---- external acceleration (eqs. gsource, bsource)
+//
+// The velocity-gradient parts of the force terms at velocity i of one place:
+// fg = -sum_b a_b (g(i + s_b) - g(i - s_b)) / (2 dxi_b), fb likewise from b,
+// central differences on the velocity grid with the distribution taken as 0
+// beyond its ends (s_b the index stride of axis b).  val(j, g, b) supplies
+// the distributions at velocity j; acc the force to use (a face at a
+// specular wall leaves out its normal component).
+template <typename T, int D, typename F>
+__device__ __forceinline__ void force_gradient(const Geo& g, const double* acc, int i, F&& val, T& fg, T& fb) {
+    fg = T(0);
+    fb = T(0);
+    int stride = 1;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const int k = (i / stride) % g.nv1[b];
+        if (acc[b] != 0.0) {
+            T gp = T(0), gm = T(0), bp = T(0), bm = T(0);
+            if (k + 1 < g.nv1[b]) val(i + stride, gp, bp);
+            if (k >= 1) val(i - stride, gm, bm);
+            const T c = (T)(acc[b] / (2.0 * g.dxi[b]));
+            fg = fma(-c, gp - gm, fg);
+            fb = fma(-c, bp - bm, fb);
+        }
+        stride *= g.nv1[b];
+    }
+}
+
 // phibar+ (eq. phibarplus) of every point, for the prepared-shift shapes:
 // one thread per cell over a run of velocity chunks, constants read once.
-template <typename T, int D>
+// With the acceleration (ACC) it also forms the force terms F^n of the
+// sources from phi^n (= fa phi* + fb phi_eq) at the neighbouring velocities,
+// adds h/2 of them to phibar+ and stores them for the update.
+template <typename T, int D, bool ACC = false>
 __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_thread) {
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
@@ -732,9 +771,23 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
     if (c >= g.Nc) return;
     const CellC<T> cs = bf.cellc[c];
     const int vt0 = blockIdx.y * chunks_per_thread, vt1 = min(g.NVT, vt0 + chunks_per_thread);
+    // phi^n of this cell at velocity j (the deferred end of eq. phiupdate)
+    auto phin = [&](int j, T& gv, T& bv) {
+        const T* rec = bf.vel + (size_t)j * 8;
+        T c2 = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const T d = rec[a] - cs.u[a];
+            c2 = fma(d, d, c2);
+        }
+        const T ge = cs.pref * Num<T>::expo(cs.cexp * c2);
+        const T be = (rec[4] + cs.eb) * ge;
+        gv = fma(cs.fa_g, bf.phi_in[phi_addr(g, c, j, 0)], cs.fb_g * ge);
+        bv = fma(cs.fa_b, bf.phi_in[phi_addr(g, c, j, 1)], cs.fb_b * be);
+    };
     for (int vt = vt0; vt < vt1; ++vt) {
         const size_t ad = phi_addr(g, c, vt * VC, 0);
-        T gs[VC], bs[VC], pg[VC], pb[VC];
+        T gs[VC], bs[VC], pg[VC], pb[VC], fg[VC], fb[VC];
         Chunk<T>::load(bf.phi_in + ad, gs);
         Chunk<T>::load(bf.phi_in + ad + VC, bs);
 #pragma unroll
@@ -750,9 +803,28 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
             const T ge = cs.pref * Num<T>::expo(cs.cexp * c2);
             const T be = (rec[4] + cs.eb) * ge;
             phibar_plus<T>(ge, be, gs[v], bs[v], z, cs.kp_g, cs.kp_b, cs.kp_s, pg[v], pb[v]);
+            if constexpr (ACC) {
+                const int i = vt * VC + v;
+                fg[v] = fb[v] = T(0);
+                if (i < g.nv1[0] * g.nv1[1] * g.nv1[2]) {
+                    force_gradient<T, D>(g, g.acc, i, phin, fg[v], fb[v]);
+                    T ax = T(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) ax = fma((T)g.acc[a], rec[a], ax);
+                    const T gn = fma(cs.fa_g, gs[v], cs.fb_g * ge);      // phi^n at i
+                    fb[v] = fma(ax, gn, fb[v]);
+                }
+                const T hh = (T)(0.5 * g.h);
+                pg[v] = fma(hh, fg[v], pg[v]);
+                pb[v] = fma(hh, fb[v], pb[v]);
+            }
         }
         Chunk<T>::store(bf.phibar + ad, pg);
         Chunk<T>::store(bf.phibar + ad + VC, pb);
+        if constexpr (ACC) {
+            Chunk<T>::store(bf.force + ad, fg);
+            Chunk<T>::store(bf.force + ad + VC, fb);
+        }
     }
 }
 
@@ -946,17 +1018,23 @@ __device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& b
 // constants fc, the inverse of eq. phibar applied to the reconstructed values
 // (gb, bb), the microflux xi_a phi (eq. flux) into (fg, fb), and its moments
 // with the quadrature weights added to sm.
-template <typename T, int D, bool SK = false>
+// With the acceleration (ACC), the inverse of eq. phibar takes the whole
+// source: alpha (h/2) fgg for g, and alpha_b (h/2) (a.xi g_f + fgb) for b, fgg
+// and fgb the force gradients of phibar at the face, axi = a . xi.
+template <typename T, int D, bool SK = false, bool ACC = false>
 __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], const T (&w)[VC], const T (&hx)[VC],
                                           int a, const T (&gb)[VC], const T (&bb)[VC], V4<T>& fg, V4<T>& fb,
-                                          T* sm, T hL = T(0)) {
+                                          T* sm, T hL = T(0), const T* fgg = nullptr, const T* fgb = nullptr,
+                                          const T* axi = nullptr, T hh = T(0)) {
     const T alg = fc[D + 4], alb = fc[D + 5], gmb = fc[D + 6];
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
         T ge, be, z;
         packed_eq<T, D, SK>(fc, xi[v], hx[v], hL, ge, be, z);
-        const T gf = fma(alg, gb[v] - ge, ge);
-        const T bfv = SK ? fma(alb, bb[v] - be, be) : fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+        T gf = fma(alg, gb[v] - ge, ge);
+        if constexpr (ACC) gf = fma(alg * hh, fgg[v], gf);
+        T bfv = SK ? fma(alb, bb[v] - be, be) : fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+        if constexpr (ACC) bfv = fma(alb * hh, fma(axi[v], gf, fgb[v]), bfv);
         const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
         fg.v[v] = Fg;
         fb.v[v] = Fb;
@@ -1658,7 +1736,7 @@ struct FluxSmem {
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
 __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using FS = FluxSmem<T, D, T0_, T1_, T2_, SK>;
@@ -1739,7 +1817,34 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                 T sm[NM];
 #pragma unroll
                 for (int m = 0; m < NM; ++m) sm[m] = T(0);
-                face_flux<T, D, SK>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL);
+                if constexpr (ACC) {
+                    // the force at this face (a specular wall takes the normal component),
+                    // its gradients from the face values at the neighbouring velocities
+                    double fac[3] = {g.acc[0], g.acc[1], g.acc[2]};
+                    if ((side == 0 && qa[a] == 0 && g.bc[a][0] == BC_SPECULAR) ||
+                        (side == 1 && own_right[a] && g.bc[a][1] == BC_SPECULAR))
+                        fac[a] = 0.0;
+                    const long long fidx = (long long)ff[a] + side * fs;
+                    const T* fbase = bf.face[a];
+                    auto val = [&](int j, T& gv, T& bv) {
+                        const size_t fa0 = face_addr(g, a, fidx, j / VC) + (j % VC);
+                        gv = fbase[fa0];
+                        bv = fbase[fa0 + VC];
+                    };
+                    T fgg[VC], fgb[VC], axi[VC];
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        const int i = vt * VC + v;
+                        fgg[v] = fgb[v] = axi[v] = T(0);
+                        if (i < g.nv1[0] * g.nv1[1] * g.nv1[2]) force_gradient<T, D>(g, fac, i, val, fgg[v], fgb[v]);
+#pragma unroll
+                        for (int b = 0; b < D; ++b) axi[v] = fma((T)fac[b], xi[v][b], axi[v]);
+                    }
+                    face_flux<T, D, SK, true>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL, fgg, fgb,
+                                              axi, (T)(0.5 * g.h));
+                } else {
+                    face_flux<T, D, SK>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL);
+                }
                 if (side == 0) {
 #pragma unroll
                     for (int m = 0; m < NM; ++m) acc[a][m].add(sm[m]);
@@ -1758,6 +1863,16 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
             for (int v = 0; v < VC; ++v) {
                 dFg[v] = fma(idx, F[1][0].v[v] - F[0][0].v[v], dFg[v]);
                 dFb[v] = fma(idx, F[1][1].v[v] - F[0][1].v[v], dFb[v]);
+            }
+        }
+        if constexpr (ACC) {     // + dt F^n of the own cell (eq. phiupdate's source, rectangle rule)
+            T fgo[VC], fbo[VC];
+            Chunk<T>::load(bf.force + ad, fgo);
+            Chunk<T>::load(bf.force + ad + VC, fbo);
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                dFg[v] -= fgo[v];
+                dFb[v] -= fbo[v];
             }
         }
         T og[VC], ob[VC], oge[VC], obe[VC];
@@ -1794,11 +1909,11 @@ struct FluxOcc {
     static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(32) unsigned char smem[];
-    flux_body<T, D, T0_, T1_, T2_, SK>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    flux_body<T, D, T0_, T1_, T2_, SK, ACC>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list
@@ -1926,6 +2041,16 @@ __device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a,
         for (int gg = 0; gg < g.G; ++gg) s += bf.wf[a][((size_t)gg * NM + m) * g.nf[a] + f];
         W[m] = s;
     }
+    if (g.accel) {   // eqs. rhoubar, rhoEbar: + (h/2) rho a, then + (h/2) (rho u) . a
+        double fac[3] = {g.acc[0], g.acc[1], g.acc[2]};
+        const long long st = a == 0 ? 1 : (a == 1 ? (long long)g.fn[a][0] : (long long)g.fn[a][0] * g.fn[a][1]);
+        const int qn = (int)((f / st) % g.fn[a][a]);
+        if ((qn == 0 && g.bc[a][0] == BC_SPECULAR) || (qn == g.n[a] && g.bc[a][1] == BC_SPECULAR))
+            fac[a] = 0.0;    // a specular wall takes the normal component of the force
+        const double hh = 0.5 * g.h;
+        for (int b = 0; b < D; ++b) W[1 + b] = dadd(W[1 + b], dmul(dmul(hh, W[0]), fac[b]));
+        for (int b = 0; b < D; ++b) W[1 + D] = dadd(W[1 + D], dmul(dmul(hh, W[1 + b]), fac[b]));
+    }
     double q[3] = {0.0, 0.0, 0.0};
     if (g.shakhov) shakhov_heat_flux<T, D>(g, bf.qf[a], g.nf[a], f, W, 0.5 * g.h, q);
     make_face<T>(g, W, q, bf.facec[a][f]);
@@ -1969,9 +2094,16 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
         }
     }
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < NM; ++m) W[m] = __fma_rn(-g.dt, dW[m], bf.W[(size_t)m * g.Nc + c]);
+    if (g.accel) {   // + dt times the source integrals at t_n: rho^n a, (rho u)^n . a
+        const double rho0 = bf.W[c];
+        for (int b = 0; b < D; ++b) {
+            W[1 + b] = dadd(W[1 + b], dmul(dmul(g.dt, rho0), g.acc[b]));
+            W[1 + D] = dadd(W[1 + D], dmul(dmul(g.dt, bf.W[(size_t)(1 + b) * g.Nc + c]), g.acc[b]));
+        }
+    }
     bool finite = true;
     for (int m = 0; m < NM; ++m) {
-        W[m] = __fma_rn(-g.dt, dW[m], bf.W[(size_t)m * g.Nc + c]);
         finite = finite && isfinite(W[m]);
         bf.W[(size_t)m * g.Nc + c] = W[m];
     }

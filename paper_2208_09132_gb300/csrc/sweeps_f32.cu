@@ -6,17 +6,20 @@ namespace cdg {
 namespace {
 constexpr int FF = MODE_FUSED | MODE_FACES, SF = MODE_STORED | MODE_FACES, FG = MODE_FUSED | MODE_FACES | MODE_R2;
 constexpr int FFS = FF | MODE_SK, SFS = SF | MODE_SK;   // Shakhov collision
+constexpr int PFA = MODE_PREP | MODE_FACES | MODE_ACC;   // external acceleration
 using Table32 = ShapeTable<
     float,
     ShapeList<Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>,
-              Shape<float, 1, 256, 1, 1, FF>, Shape<float, 1, 256, 1, 1, FG>, Shape<float, 1, 256, 1, 1, FFS>>,
+              Shape<float, 1, 256, 1, 1, FF>, Shape<float, 1, 256, 1, 1, FG>, Shape<float, 1, 256, 1, 1, FFS>,
+              Shape<float, 1, 256, 1, 1, PFA>>,
     ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, MODE_PREP>,
               Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>,
               Shape<float, 2, 32, 16, 1>, Shape<float, 2, 32, 8, 1, FF>, Shape<float, 2, 32, 16, 1, FF>,
-              Shape<float, 2, 32, 8, 1, SF>, Shape<float, 2, 16, 8, 1, FG>, Shape<float, 2, 32, 8, 1, FFS>>,
+              Shape<float, 2, 32, 8, 1, SF>, Shape<float, 2, 16, 8, 1, FG>, Shape<float, 2, 32, 8, 1, FFS>,
+              Shape<float, 2, 32, 8, 1, PFA>>,
     ShapeList<Shape<float, 3, 8, 4, 4>, Shape<float, 3, 8, 8, 4, MODE_PREP>, Shape<float, 3, 8, 8, 4, MODE_STORED>,
               Shape<float, 3, 8, 4, 4, MODE_STORED>, Shape<float, 3, 8, 8, 4, SF>, Shape<float, 3, 8, 4, 4, SF>,
-              Shape<float, 3, 8, 8, 4, SFS>>>;
+              Shape<float, 3, 8, 8, 4, SFS>, Shape<float, 3, 8, 4, 4, PFA>>>;
 }
 
 int tile_count_f32(int D) { return Table32::count(D); }

@@ -7,14 +7,17 @@ namespace cdg {
 namespace {
 constexpr int FF = MODE_FUSED | MODE_FACES, SF = MODE_STORED | MODE_FACES, FG = MODE_FUSED | MODE_FACES | MODE_R2;
 constexpr int FFS = FF | MODE_SK, SFS = SF | MODE_SK;   // Shakhov collision
+constexpr int PFA = MODE_PREP | MODE_FACES | MODE_ACC;   // external acceleration
 using Table64 = ShapeTable<
     double,
     ShapeList<Shape<double, 1, 256, 1, 1>, Shape<double, 1, 128, 1, 1>, Shape<double, 1, 64, 1, 1>,
-              Shape<double, 1, 128, 1, 1, FF>, Shape<double, 1, 128, 1, 1, FG>, Shape<double, 1, 128, 1, 1, FFS>>,
+              Shape<double, 1, 128, 1, 1, FF>, Shape<double, 1, 128, 1, 1, FG>, Shape<double, 1, 128, 1, 1, FFS>,
+              Shape<double, 1, 128, 1, 1, PFA>>,
     ShapeList<Shape<double, 2, 16, 8, 1>, Shape<double, 2, 8, 8, 1>, Shape<double, 2, 16, 8, 1, MODE_STORED>,
-              Shape<double, 2, 16, 8, 1, FF>, Shape<double, 2, 8, 8, 1, FG>, Shape<double, 2, 16, 8, 1, FFS>>,
+              Shape<double, 2, 16, 8, 1, FF>, Shape<double, 2, 8, 8, 1, FG>, Shape<double, 2, 16, 8, 1, FFS>,
+              Shape<double, 2, 16, 8, 1, PFA>>,
     ShapeList<Shape<double, 3, 4, 4, 4>, Shape<double, 3, 8, 4, 4, MODE_PREP>, Shape<double, 3, 8, 4, 4, MODE_STORED>,
-              Shape<double, 3, 8, 4, 4, SF>, Shape<double, 3, 8, 4, 4, SFS>>>;
+              Shape<double, 3, 8, 4, 4, SF>, Shape<double, 3, 8, 4, 4, SFS>, Shape<double, 3, 8, 4, 4, PFA>>>;
 }
 
 int tile_count_f64(int D) { return Table64::count(D); }

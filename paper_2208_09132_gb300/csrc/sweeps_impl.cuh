@@ -18,6 +18,8 @@ constexpr int kMomBlock = 128;
 // Face-store shapes (MODE_FACES bit) have sweep A keep the reconstructed
 // face values and run k_flux as sweep B.  Shakhov shapes (MODE_SK, face-store
 // only) add k_faceq before the face constants and k_cellq before the W update.
+// Acceleration shapes (MODE_ACC, prepared face-store only) form the force
+// terms in k_prep and take them in k_flux.
 template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED>
 struct Shape {
     static constexpr bool SK = mode_sk(MODE);
@@ -28,6 +30,9 @@ struct Shape {
     static constexpr int SRC = mode_source(MODE);
     static constexpr bool FACES = mode_faces(MODE);
     static_assert(!SK || FACES, "Shakhov shapes are face-store shapes");
+    static constexpr bool ACC = mode_acc(MODE);
+    static_assert(!ACC || (SRC == MODE_PREP && FACES && !SK && !mode_r2(MODE)),
+                  "acceleration shapes are prepared face-store shapes");
 
     // dynamic shared memory of the larger of the two sweeps
     static size_t smem_bytes() {
@@ -43,7 +48,7 @@ struct Shape {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
             return e;
         if constexpr (FACES) {
-            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, SK, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)FS::bytes)))
                 return e;
         } else {
@@ -82,7 +87,7 @@ struct Shape {
         if constexpr (SRC == MODE_PREP) {
             constexpr int kChunks = 8;
             const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
-            k_prep<T, D><<<pg, 128, 0, s>>>(in, cur, kChunks);
+            k_prep<T, D, ACC><<<pg, 128, 0, s>>>(in, cur, kChunks);
         } else if constexpr (SRC == MODE_STORED) {
             k_shslope<T, D, TX, TY, TZ, SK><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s>>>(in, cur);
         }
@@ -99,7 +104,7 @@ struct Shape {
             k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
         }
         if (ev) cudaEventRecord(ev[2], s);
-        if constexpr (FACES) k_flux<T, D, TX, TY, TZ, SK><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
+        if constexpr (FACES) k_flux<T, D, TX, TY, TZ, SK, ACC><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
         else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
         if (ev) cudaEventRecord(ev[3], s);
         if constexpr (SK) {

@@ -71,6 +71,10 @@ def footprint_bytes(req: Request) -> int:
     try:
         if req.cfg.get("collision", 0):
             cdugks._check(lib.cdugks_set_collision(h, int(req.cfg["collision"])))
+        if any(req.cfg.get("accel", (0.0, 0.0, 0.0))):
+            acc = np.zeros(3)
+            acc[: len(req.cfg["accel"])] = req.cfg["accel"]
+            cdugks._check(lib.cdugks_set_acceleration(h, cdugks._dptr(acc)))
         if req.cfg.get("recon", 0):
             cdugks._check(lib.cdugks_set_reconstruction(h, int(req.cfg["recon"])))
         if req.tile_id:

@@ -55,7 +55,7 @@ def size_key(cfg, precision, context):
     cells = wl.ncells(cfg)
     bucket = 2 ** int(round(math.log2(max(cells, 1))))
     recon = ":faces-gradient" if cfg.get("recon", 0) else ""
-    coll = ":shakhov" if cfg.get("collision", 0) else ""
+    coll = (":shakhov" if cfg.get("collision", 0) else "") + (":accel" if any(cfg.get("accel", (0, 0, 0))) else "")
     return (f"{'fp32' if precision == cdugks.FP32 else 'fp64'}:{context}:D{D}:cells~{bucket}:nv{wl.nvel(cfg)}"
             f"{recon}{coll}")
 
@@ -67,11 +67,12 @@ def candidates(cfg, precision, context="alone"):
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     r2 = bool(cfg.get("recon", 0))
     sk = bool(cfg.get("collision", 0))
+    ac = any(cfg.get("accel", (0.0, 0.0, 0.0)))
     tiles = []
     for t in range(nt):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
-        if bool(mode & 8) != r2 or bool(mode & 16) != sk:
-            continue                      # shapes of the other reconstruction or collision compute another scheme
+        if bool(mode & 8) != r2 or bool(mode & 16) != sk or bool(mode & 32) != ac:
+            continue                      # shapes of another reconstruction, collision or force compute another scheme
         if context != "alone" and sk:
             continue                      # Shakhov instances are not batched
         if context != "alone" and mode & 3 != 0:

@@ -160,3 +160,43 @@ def test_collision_selection_rules():
     for t in range(lib.cdugks_tile_count(cdugks.FP32, 2)):
         m = cdugks.tile_shape(cdugks.FP32, 2, t)[1]
         assert not (m & 16) or (m & 4 and not m & 8 and m & 3 != 1)
+
+
+def test_acceleration_selection_rules():
+    """External acceleration: a prepared face-store shape with the force in every
+    dimension and precision, chosen before binding; components beyond dim and
+    non-finite values are refused, and so are the Shakhov model and the
+    face-gradient reconstruction with it (host-side checks, no device)."""
+    lib = cdugks.load()
+
+    def handle(cfg, prec=cdugks.FP32):
+        g, v, p = cdugks.describe(cfg, prec)
+        h = ctypes.c_void_p()
+        assert lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)) == 0
+        return h
+
+    def vec(*a):
+        return (ctypes.c_double * 3)(*a)
+
+    for prec in (cdugks.FP32, cdugks.FP64):
+        for dim in (1, 2, 3):
+            cfg, _ = wl.random_smooth(dim=dim, n=(8, 8, 8), nv=(4, 4, 4), seed=1)
+            h = handle(cfg, prec)
+            a = [0.5, -0.2, 0.1][:dim] + [0.0] * (3 - dim)
+            assert lib.cdugks_set_acceleration(h, vec(*a)) == 0, lib.cdugks_last_error()
+            info = cdugks.Info()
+            assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+            mode = cdugks.tile_shape(prec, dim, info.tile_id)[1]
+            assert mode & 32 and mode & 4 and mode & 3 == 1
+            assert lib.cdugks_set_tile(h, 0) != 0
+            assert lib.cdugks_set_collision(h, wl.COLLISION_SHAKHOV) != 0
+            if dim < 3:
+                assert lib.cdugks_set_reconstruction(h, 1) != 0
+                bad = [0.0] * 3
+                bad[dim] = 1.0
+                assert lib.cdugks_set_acceleration(h, vec(*bad)) != 0        # beyond dim
+            assert lib.cdugks_set_acceleration(h, vec(float("nan"), 0.0, 0.0)) != 0
+            assert lib.cdugks_set_acceleration(h, None) == 0                 # off again
+            assert lib.cdugks_info(h, ctypes.byref(info)) == 0
+            assert not cdugks.tile_shape(prec, dim, info.tile_id)[1] & 32
+            lib.cdugks_destroy(h)

@@ -35,7 +35,7 @@ def _solo(cfg, f, prec, steps, tile=0, groups=0):
 def test_batch_equals_members_alone(prec, graph):
     steps = 7
     batched = [t for t in range(cdugks.load().cdugks_tile_count(prec, 1))
-               if not cdugks.tile_shape(prec, 1, t)[1] & 16]          # Shakhov shapes are not batched
+               if not cdugks.tile_shape(prec, 1, t)[1] & 19]          # prepared, stored and Shakhov shapes are not
     tiles = [batched[k % len(batched)] for k in range(len(_members_1d()))]
     # every shape, a member of a face-gradient shape with that reconstruction
     probs = [(dict(cfg, recon=1 if cdugks.tile_shape(prec, 1, t)[1] & 8 else 0), f)
@@ -76,7 +76,8 @@ def test_tile_shapes_agree_with_the_oracle(oracle_mod):
     cfg, f = wl.random_smooth(dim=1, n=(300,), nv=(16,), seed=3, amp=0.3, kn=3e-3)
     for t in range(cdugks.load().cdugks_tile_count(cdugks.FP64, 1)):
         mode = cdugks.tile_shape(cdugks.FP64, 1, t)[1]
-        c = dict(cfg, recon=1 if mode & 8 else 0, collision=1 if mode & 16 else 0)
+        c = dict(cfg, recon=1 if mode & 8 else 0, collision=1 if mode & 16 else 0,
+                 accel=[0.4, 0.0, 0.0] if mode & 32 else [0.0, 0.0, 0.0])
         o = oracle_mod.Oracle(c)
         o.init(f)
         o.step(20)

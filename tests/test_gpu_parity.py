@@ -273,13 +273,13 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
     (cfg, f), steps = case(name)
     refs = {}
 
-    def ref_of(recon, coll):   # the oracle's result with the scheme a shape implements
-        if (recon, coll) not in refs:
-            o = oracle_mod.Oracle(dict(cfg, recon=recon, collision=coll))
+    def ref_of(recon, coll, acc):   # the oracle's result with the scheme a shape implements
+        if (recon, coll, acc) not in refs:
+            o = oracle_mod.Oracle(dict(cfg, recon=recon, collision=coll, accel=list(acc)))
             o.init(f)
             o.step(steps)
-            refs[recon, coll] = o.moments()
-        return refs[recon, coll]
+            refs[recon, coll, acc] = o.moments()
+        return refs[recon, coll, acc]
 
     dirichlet = any(wl.BC_DIRICHLET in cfg["bc"][a] for a in range(cfg["dim"]))
     for t in range(cdugks.load().cdugks_tile_count(precision, cfg["dim"])):
@@ -287,10 +287,11 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
         if mode & 3 == 2 and dirichlet:
             continue      # stored-slope shapes take periodic and specular boundaries only
         recon, coll = (1 if mode & 8 else 0), (1 if mode & 16 else 0)
+        acc = tuple([0.4, -0.3, 0.2][:cfg["dim"]] + [0.0] * (3 - cfg["dim"])) if mode & 32 else (0.0, 0.0, 0.0)
         if coll and min(cfg["nv"][:cfg["dim"]]) < 5:
             continue      # the S-model blows up where 4 nodes per axis cannot carry a heat flux
-        ref = ref_of(recon, coll)
-        s = cdugks.Solver(dict(cfg, recon=recon, collision=coll), precision=precision, tile_id=t,
+        ref = ref_of(recon, coll, acc)
+        s = cdugks.Solver(dict(cfg, recon=recon, collision=coll, accel=list(acc)), precision=precision, tile_id=t,
                           velocity_groups=2)
         s.init(f)
         s.step(steps)
