@@ -60,6 +60,9 @@ def design_bytes(mode, D, elt):
     if mode & 16:                                             # Shakhov: raw moments of the faces and of phi*
         d["face_moments"] = 2 * D * elt
         d["cell_moments"] = 2 * elt
+    if mode & 32:                                             # acceleration: the force terms, written and read
+        d["prep"] += 2 * elt
+        d["sweep_b"] += 2 * elt
     return d
 
 
@@ -401,6 +404,8 @@ def run_ours(args, ws, rank, local):
         cfg["recon"] = args.recon
     if args.collision:
         cfg["collision"] = args.collision
+    if args.accel:
+        cfg["accel"] = ([float(v) for v in args.accel.split(",")] + [0.0, 0.0])[:3]
     prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
@@ -522,6 +527,7 @@ def run_ours(args, ws, rank, local):
                        "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode & 7, str(mode)),
                        "reconstruction": "face gradient" if mode & 8 else "upwind cell",
                        "collision": "Shakhov" if mode & 16 else "two relaxation times (Sec. 2)",
+                       "acceleration": list(cfg.get("accel", [0.0, 0.0, 0.0]))[:cfg["dim"]],
                        "launch": f"CUDA graphs of {gsteps} steps" if gsteps > 1 else "one launch per kernel",
                        "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
                              else "state fits in L2",
@@ -552,6 +558,8 @@ def run_reference(args, ws, rank):
         cfg["recon"] = args.recon
     if args.collision:
         cfg["collision"] = args.collision
+    if args.accel:
+        cfg["accel"] = ([float(v) for v in args.accel.split(",")] + [0.0, 0.0])[:3]
     D = cfg["dim"]
     sample = dict(cfg)
     side = {1: 256, 2: 32, 3: 4}[D]
@@ -593,6 +601,7 @@ def main():
     ap.add_argument("--graph", type=int, default=10, help="steps per captured CUDA graph (1: plain launches)")
     ap.add_argument("--recon", type=int, default=0, help="1: the face-gradient reconstruction (1D/2D workloads)")
     ap.add_argument("--collision", type=int, default=0, help="1: the Shakhov collision model")
+    ap.add_argument("--accel", default="", help="uniform external acceleration, e.g. 0,-0.5")
     ap.add_argument("--groups", type=int, default=None, help="with --tile: velocity groups")
     ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
     ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")
