@@ -758,6 +758,59 @@ __device__ __forceinline__ void force_gradient(const Geo& g, const double* acc, 
     }
 }
 
+// The same for the four velocities of chunk vt at once, when every row of
+// the velocity grid is whole chunks (nv1_0 a multiple of VC): the neighbour
+// of a lane along axis b > 0 is the same lane of chunk vt +- s_b/VC, along
+// axis 0 the next lane (or the end lane of chunk vt +- 1).  chunk(vn, gv, bv)
+// loads the distributions of chunk vn; (gc, bc) are those of chunk vt.  Whole
+// chunks are vector loads, coalesced across the cells (or faces) of a warp.
+template <typename T, int D, typename F>
+__device__ __forceinline__ void force_gradient_chunk(const Geo& g, const double* acc, int vt, F&& chunk,
+                                                     const T (&gc)[VC], const T (&bc)[VC], T (&fg)[VC],
+                                                     T (&fb)[VC]) {
+#pragma unroll
+    for (int v = 0; v < VC; ++v) fg[v] = fb[v] = T(0);
+    int stride = 1;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        if (acc[b] != 0.0) {
+            const T c = (T)(acc[b] / (2.0 * g.dxi[b]));
+            T gp[VC], gm[VC], bp[VC], bm[VC];
+            const int k0 = ((vt * VC) / stride) % g.nv1[b];      // lane 0's index along b
+            if (b == 0) {
+                T gn[VC], bn[VC];
+                const bool up = k0 + VC < g.nv1[0], dn = k0 >= 1;
+                if (up) chunk(vt + 1, gn, bn);
+#pragma unroll
+                for (int v = 0; v < VC - 1; ++v) { gp[v] = gc[v + 1]; bp[v] = bc[v + 1]; }
+                gp[VC - 1] = up ? gn[0] : T(0);
+                bp[VC - 1] = up ? bn[0] : T(0);
+                if (dn) chunk(vt - 1, gn, bn);
+#pragma unroll
+                for (int v = 1; v < VC; ++v) { gm[v] = gc[v - 1]; bm[v] = bc[v - 1]; }
+                gm[0] = dn ? gn[VC - 1] : T(0);
+                bm[0] = dn ? bn[VC - 1] : T(0);
+            } else {                                          // the four lanes share their index along b
+                const int sc = stride / VC;
+                if (k0 + 1 < g.nv1[b]) chunk(vt + sc, gp, bp);
+                else
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) gp[v] = bp[v] = T(0);
+                if (k0 >= 1) chunk(vt - sc, gm, bm);
+                else
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) gm[v] = bm[v] = T(0);
+            }
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                fg[v] = fma(-c, gp[v] - gm[v], fg[v]);
+                fb[v] = fma(-c, bp[v] - bm[v], fb[v]);
+            }
+        }
+        stride *= g.nv1[b];
+    }
+}
+
 // phibar+ (eq. phibarplus) of every point, for the prepared-shift shapes:
 // one thread per cell over a run of velocity chunks, constants read once.
 // With the acceleration (ACC) it also forms the force terms F^n of the
@@ -785,11 +838,39 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
         gv = fma(cs.fa_g, bf.phi_in[phi_addr(g, c, j, 0)], cs.fb_g * ge);
         bv = fma(cs.fa_b, bf.phi_in[phi_addr(g, c, j, 1)], cs.fb_b * be);
     };
+    // phi^n of this cell for the four velocities of chunk vn
+    auto phin_chunk = [&](int vn, T (&gv)[VC], T (&bv)[VC]) {
+        const size_t an = phi_addr(g, c, vn * VC, 0);
+        T gsn[VC], bsn[VC];
+        Chunk<T>::load(bf.phi_in + an, gsn);
+        Chunk<T>::load(bf.phi_in + an + VC, bsn);
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const T* rec = bf.vel + (size_t)(vn * VC + v) * 8;
+            T c2 = T(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const T d = rec[a] - cs.u[a];
+                c2 = fma(d, d, c2);
+            }
+            const T ge = cs.pref * Num<T>::expo(cs.cexp * c2);
+            const T be = (rec[4] + cs.eb) * ge;
+            gv[v] = fma(cs.fa_g, gsn[v], cs.fb_g * ge);
+            bv[v] = fma(cs.fa_b, bsn[v], cs.fb_b * be);
+        }
+    };
+    const bool rows = g.nv1[0] % VC == 0;      // velocity rows are whole chunks
     for (int vt = vt0; vt < vt1; ++vt) {
         const size_t ad = phi_addr(g, c, vt * VC, 0);
-        T gs[VC], bs[VC], pg[VC], pb[VC], fg[VC], fb[VC];
+        T gs[VC], bs[VC], pg[VC], pb[VC], fg[VC], fb[VC], gn0[VC], bn0[VC];
         Chunk<T>::load(bf.phi_in + ad, gs);
         Chunk<T>::load(bf.phi_in + ad + VC, bs);
+        if constexpr (ACC) {
+            if (rows) {
+                phin_chunk(vt, gn0, bn0);
+                force_gradient_chunk<T, D>(g, g.acc, vt, phin_chunk, gn0, bn0, fg, fb);
+            }
+        }
 #pragma unroll
         for (int v = 0; v < VC; ++v) {
             const T* rec = bf.vel + (size_t)(vt * VC + v) * 8;
@@ -805,9 +886,9 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
             phibar_plus<T>(ge, be, gs[v], bs[v], z, cs.kp_g, cs.kp_b, cs.kp_s, pg[v], pb[v]);
             if constexpr (ACC) {
                 const int i = vt * VC + v;
-                fg[v] = fb[v] = T(0);
+                if (!rows) fg[v] = fb[v] = T(0);
                 if (i < g.nv1[0] * g.nv1[1] * g.nv1[2]) {
-                    force_gradient<T, D>(g, g.acc, i, phin, fg[v], fb[v]);
+                    if (!rows) force_gradient<T, D>(g, g.acc, i, phin, fg[v], fb[v]);
                     T ax = T(0);
 #pragma unroll
                     for (int a = 0; a < D; ++a) ax = fma((T)g.acc[a], rec[a], ax);
@@ -1832,11 +1913,23 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                         bv = fbase[fa0 + VC];
                     };
                     T fgg[VC], fgb[VC], axi[VC];
+                    if (g.nv1[0] % VC == 0) {        // velocity rows are whole chunks: vector loads
+                        auto chunk = [&](int vn, T (&gv)[VC], T (&bv)[VC]) {
+                            const T* p = fbase + face_addr(g, a, fidx, vn);
+                            Chunk<T>::load(p, gv);
+                            Chunk<T>::load(p + VC, bv);
+                        };
+                        force_gradient_chunk<T, D>(g, fac, vt, chunk, gb, bb, fgg, fgb);
+                    }
 #pragma unroll
                     for (int v = 0; v < VC; ++v) {
                         const int i = vt * VC + v;
-                        fgg[v] = fgb[v] = axi[v] = T(0);
-                        if (i < g.nv1[0] * g.nv1[1] * g.nv1[2]) force_gradient<T, D>(g, fac, i, val, fgg[v], fgb[v]);
+                        if (g.nv1[0] % VC != 0) {
+                            fgg[v] = fgb[v] = T(0);
+                            if (i < g.nv1[0] * g.nv1[1] * g.nv1[2])
+                                force_gradient<T, D>(g, fac, i, val, fgg[v], fgb[v]);
+                        }
+                        axi[v] = T(0);
 #pragma unroll
                         for (int b = 0; b < D; ++b) axi[v] = fma((T)fac[b], xi[v][b], axi[v]);
                     }
