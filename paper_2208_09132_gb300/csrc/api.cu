@@ -651,8 +651,9 @@ int cdugks_init(cdugks_t* h, const double* rho_u_T) {
 
 namespace {
 cudaError_t launch_one_step(cdugks* h) {
-    if (h->prec == CDUGKS_FP32) return cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream);
-    return cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream);
+    const void* phi_in = h->base + h->lay.phi[h->cur];
+    if (h->prec == CDUGKS_FP32) return cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream, nullptr, phi_in);
+    return cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream, nullptr, phi_in);
 }
 }  // namespace
 
@@ -721,8 +722,9 @@ int cdugks_profile_step(cdugks_t* h, int nsteps, double* ms_out) {
         if ((e = cudaEventCreate(&ev[made]))) break;
     for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
         cudaEvent_t* es = &ev[(size_t)s * 5];
-        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream, es);
-        else e = cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream, es);
+        const void* phi_in = h->base + h->lay.phi[h->cur];
+        if (h->prec == CDUGKS_FP32) e = cdg::launch_step_f32(h->g, dinst<float>(h), h->cur, h->stream, es, phi_in);
+        else e = cdg::launch_step_f64(h->g, dinst<double>(h), h->cur, h->stream, es, phi_in);
         if (e) break;
         h->cur = 1 - h->cur;
         h->steps += 1;

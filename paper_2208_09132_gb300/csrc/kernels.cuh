@@ -32,6 +32,7 @@
 // equilibrium), not by ghost copies.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -41,7 +42,15 @@ namespace cdg {
 constexpr int VC = 4;             // velocities per chunk: the innermost run of the state layout
 
 enum { BC_PERIODIC = 0, BC_SPECULAR = 1, BC_DIRICHLET = 2 };
-enum { ST_NONFINITE = 1, ST_NEGATIVE = 2 };
+enum { ST_NONFINITE = 1, ST_NEGATIVE = 2, ST_TIMEOUT = 4 };
+
+// Tensor maps of the g and b halves of the input state buffer for the TMA
+// staging of sweep A (one box of tile + halo cells per chunk), passed by value
+// as a kernel parameter; on = 0 when the launch has none.
+struct TmaPair {
+    CUtensorMap g, b;
+    int on;
+};
 
 // Problem geometry and physics, passed by value to every kernel.
 struct Geo {
@@ -596,6 +605,41 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---- TMA (cp.async.bulk.tensor) and mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// generic-proxy accesses of shared memory before async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n" ::
+            "r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::
+            "r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
 
 // Sweep modes.  The low two bits say where sweep A (and a recomputing sweep
 // B) takes phibar+ and the slopes from: 0 forms both on the halo box itself;
@@ -639,7 +683,10 @@ struct Smem {
     // CTAs per SM that a dynamic shared-memory size allows, and the limit of threads and >= 80 registers
     __host__ __device__ static constexpr int fit(size_t b) { return (int)((size_t)(228 * 1024) / (b + 1024)); }
     static constexpr int lim = (2048 / TL::NT) < (65536 / (TL::NT * 80)) ? (2048 / TL::NT) : (65536 / (TL::NT * 80));
-    static constexpr size_t nST = (size_t)2 * TL::BOX;      // staged phi* chunk (g, b) per box cell
+    // staged phi* chunk per box cell: g at [0, BOXP), b at [BOXP, 2 BOXP) (BOXP: BOX rounded to 128 B
+    // for TMA), then slack for the 128-byte alignment of TMA destinations and the mbarrier
+    static constexpr int BOXP = (TL::BOX * (int)sizeof(V4<T>) + 127) / 128 * 128 / (int)sizeof(V4<T>);
+    static constexpr size_t nST = (size_t)2 * BOXP + 256 / sizeof(V4<T>);
     static constexpr size_t a1 = (nP + nS + nS2 + nCC) * sizeof(V4<T>) + rs_bytes + sizeof(int) * nInt;   // sweep A
     static constexpr bool st_fits = fit(a1 + nST * sizeof(V4<T>)) >= (fit(a1) < lim ? fit(a1) : lim);
     // Sweep A of the fused shapes stages the next chunk's phi* of its halo box in
@@ -924,7 +971,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const In
     using TL = Tile<D, T0_, T1_, T2_>;
     using Q = V4<T>;
     constexpr int SB = TL::SB, NCCV = CellPack<D, SK>::NV;
-    extern __shared__ __align__(32) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][SB]
@@ -1223,7 +1270,8 @@ __device__ __forceinline__ void write_face_sums(const Geo& g, double* const* dst
 }
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
-__device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
+__device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem,
+                                           const TmaPair* tm = nullptr) {
     using TL = Tile<D, T0_, T1_, T2_, mode_halo(MODE)>;
     using SM = Smem<T, D, T0_, T1_, T2_, MODE>;
     constexpr bool PREP = mode_source(MODE) != MODE_FUSED;      // phibar+ comes from a prepared buffer
@@ -1247,7 +1295,11 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     Q* const CC = S2 + SM::nS2;                   // [NCCV][BOX] packed cell constants
     Q* const FF = CC + SM::nCC;                   // [2][NFT] face fluxes (sweep B)
     Q* const FC = FF + SM::nFF;                   // [NFCV][NFT] packed face constants (sweep B)
-    Q* const ST = CC + SM::nCC + (SWEEP_B ? SM::nFF + SM::nFC : 0);   // [2][BOX] staged phi* (STAGE)
+    // [2][BOXP] staged phi* (STAGE), 128-byte aligned for TMA, then the mbarrier of the TMA copies
+    Q* const STraw = CC + SM::nCC + (SWEEP_B ? SM::nFF + SM::nFC : 0);
+    Q* const ST = STraw + ((128u - (smem_u32(STraw) & 127u)) & 127u) / sizeof(Q);
+    uint64_t* const tbar = reinterpret_cast<uint64_t*>(ST + 2 * SM::BOXP);
+    constexpr int BOXP = SM::BOXP;
     constexpr int SB2 = TL::SB2;
     Kahan<T>* const RS = reinterpret_cast<Kahan<T>*>(smem + sizeof(Q) * SM::vcount(SWEEP_B));
     int* const csrc = reinterpret_cast<int*>(smem + sizeof(Q) * SM::vcount(SWEEP_B) + SM::rs_bytes);
@@ -1347,6 +1399,30 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 #pragma unroll
     for (int a = 0; a < D; ++a) pl[a] = TL::poff(a) * NM + TL::plane_pos(a, la);
     for (int k = t; k < (int)SM::nRS; k += TL::NT) RS[k].zero();
+    // TMA staging (1D/2D): for a tile whose halo box lies inside the domain the
+    // box of every chunk is one tensor copy of g and one of b, issued by thread 0
+    // and completed on an mbarrier; the other tiles copy per cell (boundary
+    // mapping).  Boxes are at most 256 cells per axis.
+    bool tma = false;
+    if constexpr (STAGE && D <= 2 && TL::E0 <= 256 && TL::E1 <= 256) {
+        tma = tm != nullptr && tm->on;
+#pragma unroll
+        for (int a = 0; a < D; ++a) tma = tma && org[a] - TL::HALO >= 0 && org[a] + TL::tdim(a) + TL::HALO <= g.n[a];
+        if (tma && t == 0) mbar_init(tbar, 1);
+    }
+    unsigned tphase = 0;
+    auto fetch_tma = [&](int vt) {      // thread 0: both halves of chunk vt's box
+        constexpr unsigned bytes = 2u * TL::BOX * sizeof(Q);
+        mbar_expect_tx(tbar, bytes);
+        if constexpr (D == 1) {
+            tma_load_3d(ST, &tm->g, tbar, 0, org[0] - TL::HALO, vt);
+            tma_load_3d(ST + BOXP, &tm->b, tbar, 0, org[0] - TL::HALO, vt);
+        } else {
+            tma_load_4d(ST, &tm->g, tbar, 0, org[0] - TL::HALO, org[1] - TL::HALO, vt);
+            tma_load_4d(ST + BOXP, &tm->b, tbar, 0, org[0] - TL::HALO, org[1] - TL::HALO, vt);
+        }
+    };
+    bool tma_late = false;              // a bounded wait gave up (then the CTA reports and stops)
     __syncthreads();
     constexpr int NH = TL::NH;
 
@@ -1364,22 +1440,38 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 for (int v = 0; v < VC; ++v) {
                     const int is = bf.refl[(fl & 7) * g.Nvp + vt * VC + v];
                     cp_async_elem(&ST[k].v[v], bf.phi_in + phi_addr(g, c, is, 0));
-                    cp_async_elem(&ST[BOX + k].v[v], bf.phi_in + phi_addr(g, c, is, 1));
+                    cp_async_elem(&ST[BOXP + k].v[v], bf.phi_in + phi_addr(g, c, is, 1));
                 }
             } else {
                 const size_t ad = phi_addr(g, c, vt * VC, 0);
                 cp_async_chunk(&ST[k], bf.phi_in + ad);
-                cp_async_chunk(&ST[BOX + k], bf.phi_in + ad + VC);
+                cp_async_chunk(&ST[BOXP + k], bf.phi_in + ad + VC);
             }
         };
         one(kc);
         for (int h = t; h < NH; h += TL::NT) one(halo[h]);
         cp_async_commit();
     };
-    if (STAGE && vt0 < vt1) fetch(vt0);
+    __syncthreads();                    // the mbarrier's initialisation is visible
+    if (STAGE && vt0 < vt1) {
+        if (tma) {
+            if (t == 0) fetch_tma(vt0);
+        } else {
+            fetch(vt0);
+        }
+    }
 
     for (int vt = vt0; vt < vt1; ++vt) {
-        if (STAGE) cp_async_wait_all();            // this thread's copies of chunk vt have landed
+        if (STAGE) {
+            if (tma) {                                 // the box of chunk vt has landed
+                bool done = false;
+                for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(tbar, tphase);
+                tma_late = tma_late || !done;
+                tphase ^= 1u;
+            } else {
+                cp_async_wait_all();                   // this thread's copies of chunk vt have landed
+            }
+        }
         // velocity records of the chunk (same for every thread); nu = 2 h xi / dx
         T xi[VC][D], nu[VC][D], w[VC], hx[VC];
 #pragma unroll
@@ -1424,7 +1516,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 #pragma unroll
                 for (int v = 0; v < VC; ++v) gs[v] = bs[v] = T(0);
             } else if (STAGE) {
-                const Q sg = ST[k], sb = ST[BOX + k];
+                const Q sg = ST[k], sb = ST[BOXP + k];
 #pragma unroll
                 for (int v = 0; v < VC; ++v) {
                     gs[v] = sg.v[v];
@@ -1546,9 +1638,21 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         } else {
             cell(kc, valid);
             for (int h = t; h < NH; h += TL::NT) cell(halo[h], false);
-            if (STAGE && vt + 1 < vt1) fetch(vt + 1);    // this thread's slots are read: refill them
+            if (STAGE && !tma && vt + 1 < vt1) fetch(vt + 1);    // this thread's slots are read: refill them
         }
-        __syncthreads();
+        if (tma) {
+            // every thread has read the box: the next chunk's copies may overwrite it
+            if (__syncthreads_or(tma_late)) {
+                if (t == 0) atomicOr(bf.status, ST_TIMEOUT);
+                return;
+            }
+            if (t == 0 && vt + 1 < vt1) {
+                fence_proxy_async_smem();
+                fetch_tma(vt + 1);
+            }
+        } else {
+            __syncthreads();
+        }
 
         // ---- phase 2: half van Leer slopes (times dx) of the cells [-1, T] around the tile
         for (int s = t; s < (STORED ? 0 : SB); s += TL::NT) {
@@ -1790,9 +1894,9 @@ struct Occ {
 // One problem instance: grid (tiles, velocity groups).
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
-    k_sweep(const Inst<T>* __restrict__ in, int cur) {
-    extern __shared__ __align__(32) unsigned char smem[];
-    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    k_sweep(const Inst<T>* __restrict__ in, int cur, const __grid_constant__ TmaPair tm) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem, &tm);
 }
 
 // ---- sweep B of the face-store shapes
@@ -2005,7 +2109,7 @@ struct FluxOcc {
 template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux(const Inst<T>* __restrict__ in, int cur) {
-    extern __shared__ __align__(32) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     flux_body<T, D, T0_, T1_, T2_, SK, ACC>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
@@ -2016,7 +2120,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_
 template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE = MODE_FUSED>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
     k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
-    extern __shared__ __align__(32) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
@@ -2025,7 +2129,7 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
 template <typename T, int D, int T0_, int T1_, int T2_>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
     k_flux_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
-    extern __shared__ __align__(32) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     flux_body<T, D, T0_, T1_, T2_>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);

@@ -42,8 +42,12 @@ int tile_mode_f64(int D, int id);
 // and use orientation `cur` (read state buffer cur, write the other).
 // One time step: sweep A, face constants, sweep B, W update (+ cell constants of W^{n+1}).
 // ev: null, or five events recorded before, between and after the four phases.
-cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr);
-cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// phi_in: the device address of the state buffer the step reads (the tensor
+// maps of sweep A's TMA staging), or null (per-cell staging only).
+cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                            const void* phi_in = nullptr);
+cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                            const void* phi_in = nullptr);
 // One time step of every instance of a batch.
 cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s);
 cudaError_t launch_batch_step_f64(const BatchPlan& p, const Inst<double>* insts, int* cur, cudaStream_t s);

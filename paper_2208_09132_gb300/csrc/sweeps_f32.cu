@@ -27,8 +27,9 @@ TileShape tile_shape_f32(int D, int id) { return Table32::shape(D, id); }
 size_t sweep_smem_f32(int D, int id) { return Table32::smem(D, id); }
 int tile_mode_f32(int D, int id) { return Table32::mode(D, id); }
 
-cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
-    return Table32::step(g, in, cur, s, ev);
+cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
+                            const void* phi_in) {
+    return Table32::step(g, in, cur, s, ev, phi_in);
 }
 cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s) {
     return run_batch_step<Table32, float>(p, insts, cur, s);

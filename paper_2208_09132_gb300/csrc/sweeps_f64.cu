@@ -25,8 +25,9 @@ TileShape tile_shape_f64(int D, int id) { return Table64::shape(D, id); }
 size_t sweep_smem_f64(int D, int id) { return Table64::smem(D, id); }
 int tile_mode_f64(int D, int id) { return Table64::mode(D, id); }
 
-cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
-    return Table64::step(g, in, cur, s, ev);
+cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
+                            const void* phi_in) {
+    return Table64::step(g, in, cur, s, ev, phi_in);
 }
 cudaError_t launch_batch_step_f64(const BatchPlan& p, const Inst<double>* insts, int* cur, cudaStream_t s) {
     return run_batch_step<Table64, double>(p, insts, cur, s);

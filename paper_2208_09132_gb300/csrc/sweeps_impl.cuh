@@ -1,6 +1,8 @@
 // sweeps_impl.cuh -- launch helpers shared by the two precision translation units.
 #pragma once
 
+#include <cstring>
+
 #include "launch.cuh"
 
 namespace cdg {
@@ -10,6 +12,59 @@ namespace cdg {
 constexpr int kSmallBlock = 64;
 // Block size of the raw-moment reductions (one thread per face or cell and group).
 constexpr int kMomBlock = 128;
+
+// Tensor maps for the TMA staging of sweep A: the g and b halves of the state
+// buffer phi_in ([chunk][cell][g|b][VC]) as tensors (VC, n0[, n1], chunks)
+// whose boxes are the tile's halo box of one chunk (the kernel uses them for
+// 1D and 2D tiles whose box lies inside the domain).  The encoder is the
+// driver's, reached through the runtime; without it the launch stages per cell.
+using TensorMapEncode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline TensorMapEncode tensor_map_encoder() {
+    static const TensorMapEncode enc = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<TensorMapEncode>(fn);
+    }();
+    return enc;
+}
+template <typename T, int D, typename TL>
+TmaPair make_tma(const Geo& g, const void* phi_in) {
+    TmaPair tp;
+    std::memset(&tp, 0, sizeof(tp));
+    const TensorMapEncode enc = tensor_map_encoder();
+    if (!enc || !phi_in || D > 2 || TL::E0 > 256 || TL::E1 > 256) return tp;
+    const cuuint64_t cs = 2 * VC * sizeof(T);                  // bytes per cell and chunk
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+    const cuuint32_t rank = D + 2;
+    dims[0] = VC;
+    box[0] = VC;
+    dims[1] = (cuuint64_t)g.n[0];
+    box[1] = TL::E0;
+    strides[0] = cs;
+    if (D == 2) {
+        dims[2] = (cuuint64_t)g.n[1];
+        box[2] = TL::E1;
+        strides[1] = cs * (cuuint64_t)g.n[0];
+    }
+    dims[rank - 1] = (cuuint64_t)g.NVT;
+    box[rank - 1] = 1;
+    strides[rank - 2] = cs * (cuuint64_t)g.Nc;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    char* base = static_cast<char*>(const_cast<void*>(phi_in));
+    const CUresult rg = enc(&tp.g, dt, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult rb = enc(&tp.b, dt, rank, base + VC * sizeof(T), dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    tp.on = rg == CUDA_SUCCESS && rb == CUDA_SUCCESS;
+    return tp;
+}
 
 // One instantiated tile shape of the sweeps and its launches.  Prepared
 // shapes (MODE_PREP) form phibar+ of every point once per step (k_prep);
@@ -79,7 +134,8 @@ struct Shape {
         return cudaSuccess;
     }
 
-    static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
+    static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
+                            const void* phi_in) {
         cudaError_t e = configure();
         if (e) return e;
         const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
@@ -91,7 +147,8 @@ struct Shape {
         } else if constexpr (SRC == MODE_STORED) {
             k_shslope<T, D, TX, TY, TZ, SK><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s>>>(in, cur);
         }
-        k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur);
+        const TmaPair tma = make_tma<T, D, typename SM::TL>(g, SM::stage(false) ? phi_in : nullptr);
+        k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur, tma);
         if (ev) cudaEventRecord(ev[1], s);
         if constexpr (SK) {
             long long nf = 0;
@@ -105,7 +162,7 @@ struct Shape {
         }
         if (ev) cudaEventRecord(ev[2], s);
         if constexpr (FACES) k_flux<T, D, TX, TY, TZ, SK, ACC><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
-        else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur);
+        else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur, make_tma<T, D, TL>(g, nullptr));
         if (ev) cudaEventRecord(ev[3], s);
         if constexpr (SK) {
             const dim3 cg((unsigned)((g.Nc + kMomBlock - 1) / kMomBlock), (unsigned)g.G);
@@ -141,7 +198,7 @@ template <>
 struct ShapeList<> {
     static constexpr int count = 0;
     template <typename T>
-    static cudaError_t step(int, const Geo&, const Inst<T>*, int, cudaStream_t, cudaEvent_t*) {
+    static cudaError_t step(int, const Geo&, const Inst<T>*, int, cudaStream_t, cudaEvent_t*, const void*) {
         return cudaErrorInvalidValue;
     }
     template <typename T>
@@ -157,8 +214,10 @@ struct ShapeList<H, R...> {
     using Rest = ShapeList<R...>;
     static constexpr int count = 1 + Rest::count;
     template <typename T>
-    static cudaError_t step(int id, const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
-        return id == 0 ? H::step(g, in, cur, s, ev) : Rest::template step<T>(id - 1, g, in, cur, s, ev);
+    static cudaError_t step(int id, const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
+                            const void* phi_in) {
+        return id == 0 ? H::step(g, in, cur, s, ev, phi_in)
+                       : Rest::template step<T>(id - 1, g, in, cur, s, ev, phi_in);
     }
     template <typename T>
     static cudaError_t sweep_batch(int id, bool B, const Item* it, int n, const Inst<T>* in, const int* cur,
@@ -177,10 +236,11 @@ struct ShapeTable {
     static TileShape shape(int D, int id) { return D == 1 ? L1::shape(id) : (D == 2 ? L2::shape(id) : L3::shape(id)); }
     static size_t smem(int D, int id) { return D == 1 ? L1::smem(id) : (D == 2 ? L2::smem(id) : L3::smem(id)); }
     static int mode(int D, int id) { return D == 1 ? L1::mode(id) : (D == 2 ? L2::mode(id) : L3::mode(id)); }
-    static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev) {
-        if (g.D == 1) return L1::template step<T>(g.tile_id, g, in, cur, s, ev);
-        if (g.D == 2) return L2::template step<T>(g.tile_id, g, in, cur, s, ev);
-        return L3::template step<T>(g.tile_id, g, in, cur, s, ev);
+    static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
+                            const void* phi_in) {
+        if (g.D == 1) return L1::template step<T>(g.tile_id, g, in, cur, s, ev, phi_in);
+        if (g.D == 2) return L2::template step<T>(g.tile_id, g, in, cur, s, ev, phi_in);
+        return L3::template step<T>(g.tile_id, g, in, cur, s, ev, phi_in);
     }
     static cudaError_t sweep_batch(int D, int id, bool B, const Item* it, int n, const Inst<T>* in, const int* cur,
                                    cudaStream_t s) {

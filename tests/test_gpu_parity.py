@@ -298,3 +298,36 @@ def test_every_tile_shape_matches_oracle(oracle_mod, name, precision, tol):
         assert s.sync_status() == 0
         err = rel_linf(s.moments(), ref)
         assert np.all(err <= tol), (name, t, err)
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_tma_staged_interior_tiles_match_oracle(oracle_mod, dim, precision, tol):
+    """Domains large enough for interior tiles, whose halo boxes sweep A stages
+    with tensor copies (TMA), beside edge tiles that stage per cell (periodic
+    wrap on one axis, specular walls on the other), for every fused shape."""
+    if dim == 1:
+        cfg, f = wl.random_smooth(dim=1, n=(600,), nv=(12,), seed=21, amp=0.3, kn=3e-3)
+    else:
+        cfg, f = wl.random_smooth(dim=2, n=(100, 44), nv=(8, 6), seed=22, amp=0.3, kn=3e-3)
+        cfg = _bc(cfg, [(P, P), (S, S)])
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(8)
+    ref = o.moments()
+    go, bo = o.distributions()
+    tested = 0
+    for t in range(cdugks.load().cdugks_tile_count(precision, dim)):
+        mode = cdugks.tile_shape(precision, dim, t)[1]
+        if mode & ~4:
+            continue          # fused shapes (with or without the face store) of the default scheme
+        s = cdugks.Solver(cfg, precision=precision, tile_id=t, velocity_groups=3)
+        s.init(f)
+        s.step(8)
+        assert s.sync_status() == 0
+        assert np.all(rel_linf(s.moments(), ref) <= tol), (t, rel_linf(s.moments(), ref))
+        g, b = s.distributions()
+        assert np.abs(g - go).max() <= tol * np.abs(go).max()
+        assert np.abs(b - bo).max() <= tol * np.abs(bo).max()
+        tested += 1
+    assert tested >= 2
