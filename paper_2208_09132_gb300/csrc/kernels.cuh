@@ -605,6 +605,12 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---- programmatic dependent launch: the kernels of a step are launched so
+// that the next one may be scheduled while the previous one drains; each
+// waits here, before it reads anything its predecessor wrote (a no-op when
+// launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---- TMA (cp.async.bulk.tensor) and mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -865,6 +871,7 @@ __device__ __forceinline__ void force_gradient_chunk(const Geo& g, const double*
 // adds h/2 of them to phibar+ and stores them for the update.
 template <typename T, int D, bool ACC = false>
 __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_thread) {
+    pdl_wait();
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -968,6 +975,7 @@ __host__ __device__ constexpr size_t shslope_smem_bytes() {
 
 template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT) k_shslope(const Inst<T>* __restrict__ in, int cur) {
+    pdl_wait();
     using TL = Tile<D, T0_, T1_, T2_>;
     using Q = V4<T>;
     constexpr int SB = TL::SB, NCCV = CellPack<D, SK>::NV;
@@ -1896,6 +1904,7 @@ template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
     k_sweep(const Inst<T>* __restrict__ in, int cur, const __grid_constant__ TmaPair tm) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
     sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem, &tm);
 }
 
@@ -2110,6 +2119,7 @@ template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool AC
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
     flux_body<T, D, T0_, T1_, T2_, SK, ACC>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
@@ -2121,6 +2131,7 @@ template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE =
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1_, T2_, SWEEP_B, MODE>::value))
     k_sweep_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
@@ -2130,6 +2141,7 @@ template <typename T, int D, int T0_, int T1_, int T2_>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
     k_flux_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     flux_body<T, D, T0_, T1_, T2_>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
@@ -2189,6 +2201,7 @@ __device__ __forceinline__ void raw_moments(const Geo& g, const T* __restrict__ 
 // grid (faces / blockDim, velocity groups, axes)
 template <typename T, int D>
 __global__ void k_faceq(const Inst<T>* __restrict__ in, int cur) {
+    pdl_wait();
     // the axis is a launch index: read what it selects from the record, copy nothing
     const Geo& g = in->g;
     const Bufs<T>& bf = in->b[cur];
@@ -2202,6 +2215,7 @@ __global__ void k_faceq(const Inst<T>* __restrict__ in, int cur) {
 // grid (cells / blockDim, velocity groups)
 template <typename T, int D>
 __global__ void k_cellq(const Inst<T>* __restrict__ in, int cur) {
+    pdl_wait();
     const Geo g = in->g;
     const Bufs<T> bf = in->b[cur];
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2255,6 +2269,7 @@ __device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a,
 
 template <typename T, int D>
 __global__ void k_facec(const Inst<T>* __restrict__ in, int cur, int a) {
+    pdl_wait();
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f < in->g.nf[a]) facec_body<T, D>(in->g, in->b[cur], a, f);
 }
@@ -2262,6 +2277,7 @@ __global__ void k_facec(const Inst<T>* __restrict__ in, int cur, int a) {
 template <typename T, int D>
 __global__ void k_facec_batch(const RItem* __restrict__ items, const Inst<T>* __restrict__ insts,
                               const int* __restrict__ cur) {
+    pdl_wait();
     const RItem it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     for (long long k = threadIdx.x; k < it.count; k += blockDim.x)
@@ -2321,6 +2337,7 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
 
 template <typename T, int D>
 __global__ void k_wupdate(const Inst<T>* __restrict__ in, int cur) {
+    pdl_wait();
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < in->g.Nc) wupdate_body<T, D>(in->g, in->b[cur], c);
 }
@@ -2330,6 +2347,7 @@ __global__ void k_wupdate(const Inst<T>* __restrict__ in, int cur) {
 template <typename T, int D>
 __global__ void k_wupdate_batch(const RItem* __restrict__ items, const Inst<T>* __restrict__ insts,
                                 int* __restrict__ cur) {
+    pdl_wait();
     const RItem it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
     const int c0 = cur[it.inst] & 1;

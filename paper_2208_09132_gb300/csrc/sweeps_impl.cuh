@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstring>
+#include <utility>
 
 #include "launch.cuh"
 
@@ -12,6 +13,24 @@ namespace cdg {
 constexpr int kSmallBlock = 64;
 // Block size of the raw-moment reductions (one thread per face or cell and group).
 constexpr int kMomBlock = 128;
+
+// A launch of a step kernel with programmatic stream serialisation: it may be
+// scheduled while the previous kernel on the stream drains, and waits in
+// pdl_wait() before it reads that kernel's results.
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // Tensor maps for the TMA staging of sweep A: the g and b halves of the state
 // buffer phi_in ([chunk][cell][g|b][VC]) as tensors (VC, n0[, n1], chunks)
@@ -143,32 +162,40 @@ struct Shape {
         if constexpr (SRC == MODE_PREP) {
             constexpr int kChunks = 8;
             const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
-            k_prep<T, D, ACC><<<pg, 128, 0, s>>>(in, cur, kChunks);
+            if ((e = launch_pdl(k_prep<T, D, ACC>, pg, dim3(128), 0, s, in, cur, kChunks))) return e;
         } else if constexpr (SRC == MODE_STORED) {
-            k_shslope<T, D, TX, TY, TZ, SK><<<grid, TL::NT, shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s>>>(in, cur);
+            if ((e = launch_pdl(k_shslope<T, D, TX, TY, TZ, SK>, grid, dim3(TL::NT),
+                                shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s, in, cur)))
+                return e;
         }
         const TmaPair tma = make_tma<T, D, typename SM::TL>(g, SM::stage(false) ? phi_in : nullptr);
-        k_sweep<T, D, TX, TY, TZ, false, MODE><<<grid, TL::NT, SM::bytes(false), s>>>(in, cur, tma);
+        if ((e = launch_pdl(k_sweep<T, D, TX, TY, TZ, false, MODE>, grid, dim3(TL::NT), SM::bytes(false), s, in, cur,
+                            tma)))
+            return e;
         if (ev) cudaEventRecord(ev[1], s);
         if constexpr (SK) {
             long long nf = 0;
             for (int a = 0; a < D; ++a) nf = g.nf[a] > nf ? g.nf[a] : nf;
             const dim3 qg((unsigned)((nf + kMomBlock - 1) / kMomBlock), (unsigned)g.G, (unsigned)D);
-            k_faceq<T, D><<<qg, kMomBlock, 0, s>>>(in, cur);
+            if ((e = launch_pdl(k_faceq<T, D>, qg, dim3(kMomBlock), 0, s, in, cur))) return e;
         }
         for (int a = 0; a < D; ++a) {
             const unsigned blocks = (unsigned)((g.nf[a] + kSmallBlock - 1) / kSmallBlock);
-            k_facec<T, D><<<blocks, kSmallBlock, 0, s>>>(in, cur, a);
+            if ((e = launch_pdl(k_facec<T, D>, dim3(blocks), dim3(kSmallBlock), 0, s, in, cur, a))) return e;
         }
         if (ev) cudaEventRecord(ev[2], s);
-        if constexpr (FACES) k_flux<T, D, TX, TY, TZ, SK, ACC><<<grid, TL::NT, FS::bytes, s>>>(in, cur);
-        else k_sweep<T, D, TX, TY, TZ, true, MODE><<<grid, TL::NT, SM::bytes(true), s>>>(in, cur, make_tma<T, D, TL>(g, nullptr));
+        if constexpr (FACES) e = launch_pdl(k_flux<T, D, TX, TY, TZ, SK, ACC>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+        else e = launch_pdl(k_sweep<T, D, TX, TY, TZ, true, MODE>, grid, dim3(TL::NT), SM::bytes(true), s, in, cur,
+                            make_tma<T, D, TL>(g, nullptr));
+        if (e) return e;
         if (ev) cudaEventRecord(ev[3], s);
         if constexpr (SK) {
             const dim3 cg((unsigned)((g.Nc + kMomBlock - 1) / kMomBlock), (unsigned)g.G);
-            k_cellq<T, D><<<cg, kMomBlock, 0, s>>>(in, cur);
+            if ((e = launch_pdl(k_cellq<T, D>, cg, dim3(kMomBlock), 0, s, in, cur))) return e;
         }
-        k_wupdate<T, D><<<(unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock), kSmallBlock, 0, s>>>(in, cur);
+        if ((e = launch_pdl(k_wupdate<T, D>, dim3((unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock)), dim3(kSmallBlock),
+                            0, s, in, cur)))
+            return e;
         if (ev) cudaEventRecord(ev[4], s);
         return cudaGetLastError();
     }
@@ -181,10 +208,14 @@ struct Shape {
             cudaError_t e = configure();
             if (e) return e;
             if (n <= 0) return cudaSuccess;
-            if (!B) k_sweep_batch<T, D, TX, TY, TZ, false, MODE><<<n, TL::NT, SM::bytes(false), s>>>(items, insts, cur);
-            else if constexpr (FACES) k_flux_batch<T, D, TX, TY, TZ><<<n, TL::NT, FS::bytes, s>>>(items, insts, cur);
-            else k_sweep_batch<T, D, TX, TY, TZ, true, MODE><<<n, TL::NT, SM::bytes(true), s>>>(items, insts, cur);
-            return cudaGetLastError();
+            if (!B)
+                return launch_pdl(k_sweep_batch<T, D, TX, TY, TZ, false, MODE>, dim3(n), dim3(TL::NT), SM::bytes(false),
+                                  s, items, insts, cur);
+            if constexpr (FACES)
+                return launch_pdl(k_flux_batch<T, D, TX, TY, TZ>, dim3(n), dim3(TL::NT), FS::bytes, s, items, insts, cur);
+            else
+                return launch_pdl(k_sweep_batch<T, D, TX, TY, TZ, true, MODE>, dim3(n), dim3(TL::NT), SM::bytes(true), s,
+                                  items, insts, cur);
         }
     }
 
@@ -258,20 +289,22 @@ cudaError_t run_batch_step(const BatchPlan& p, const Inst<T>* insts, int* cur, c
             return e;
     if (p.n_face > 0) {
         switch (p.D) {
-            case 1: k_facec_batch<T, 1><<<p.n_face, kSmallBlock, 0, s>>>(p.face_items, insts, cur); break;
-            case 2: k_facec_batch<T, 2><<<p.n_face, kSmallBlock, 0, s>>>(p.face_items, insts, cur); break;
-            default: k_facec_batch<T, 3><<<p.n_face, kSmallBlock, 0, s>>>(p.face_items, insts, cur); break;
+            case 1: e = launch_pdl(k_facec_batch<T, 1>, dim3(p.n_face), dim3(kSmallBlock), 0, s, p.face_items, insts, cur); break;
+            case 2: e = launch_pdl(k_facec_batch<T, 2>, dim3(p.n_face), dim3(kSmallBlock), 0, s, p.face_items, insts, cur); break;
+            default: e = launch_pdl(k_facec_batch<T, 3>, dim3(p.n_face), dim3(kSmallBlock), 0, s, p.face_items, insts, cur); break;
         }
+        if (e) return e;
     }
     for (int k = 0; k < p.ntile; ++k)
         if ((e = Table::sweep_batch(p.D, p.tile_id[k], true, p.sweep_items[k], p.n_sweep[k], insts, cur, s)))
             return e;
     if (p.n_cell > 0) {
         switch (p.D) {
-            case 1: k_wupdate_batch<T, 1><<<p.n_cell, kSmallBlock, 0, s>>>(p.cell_items, insts, cur); break;
-            case 2: k_wupdate_batch<T, 2><<<p.n_cell, kSmallBlock, 0, s>>>(p.cell_items, insts, cur); break;
-            default: k_wupdate_batch<T, 3><<<p.n_cell, kSmallBlock, 0, s>>>(p.cell_items, insts, cur); break;
+            case 1: e = launch_pdl(k_wupdate_batch<T, 1>, dim3(p.n_cell), dim3(kSmallBlock), 0, s, p.cell_items, insts, cur); break;
+            case 2: e = launch_pdl(k_wupdate_batch<T, 2>, dim3(p.n_cell), dim3(kSmallBlock), 0, s, p.cell_items, insts, cur); break;
+            default: e = launch_pdl(k_wupdate_batch<T, 3>, dim3(p.n_cell), dim3(kSmallBlock), 0, s, p.cell_items, insts, cur); break;
         }
+        if (e) return e;
     }
     return cudaGetLastError();
 }
