@@ -513,7 +513,7 @@ def run_ours(args, ws, rank, local):
     result = None
     if rank == 0:
         cpu = cpu_baseline(cfg) if (ws == 1 and not args.skip_cpu) else None
-        launches_per_step = 3 + cfg["dim"] + (1 if mode & 3 else 0) + (2 if mode & 16 else 0)
+        launches_per_step = 4 + (1 if mode & 3 else 0) + (2 if mode & 16 else 0)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

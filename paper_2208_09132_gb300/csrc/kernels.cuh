@@ -2267,11 +2267,13 @@ __device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a,
     make_face<T>(g, W, q, bf.facec[a][f]);
 }
 
+// grid (faces / blockDim, axes): every axis in one launch
 template <typename T, int D>
-__global__ void k_facec(const Inst<T>* __restrict__ in, int cur, int a) {
+__global__ void k_facec(const Inst<T>* __restrict__ in, int cur) {
     pdl_wait();
+    const int a = blockIdx.y;
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f < in->g.nf[a]) facec_body<T, D>(in->g, in->b[cur], a, f);
+    if (a < D && f < in->g.nf[a]) facec_body<T, D>(in->g, in->b[cur], a, f);
 }
 
 template <typename T, int D>

@@ -179,9 +179,11 @@ struct Shape {
             const dim3 qg((unsigned)((nf + kMomBlock - 1) / kMomBlock), (unsigned)g.G, (unsigned)D);
             if ((e = launch_pdl(k_faceq<T, D>, qg, dim3(kMomBlock), 0, s, in, cur))) return e;
         }
-        for (int a = 0; a < D; ++a) {
-            const unsigned blocks = (unsigned)((g.nf[a] + kSmallBlock - 1) / kSmallBlock);
-            if ((e = launch_pdl(k_facec<T, D>, dim3(blocks), dim3(kSmallBlock), 0, s, in, cur, a))) return e;
+        {
+            long long nf = 0;
+            for (int a = 0; a < D; ++a) nf = g.nf[a] > nf ? g.nf[a] : nf;
+            const dim3 fgrid((unsigned)((nf + kSmallBlock - 1) / kSmallBlock), (unsigned)D);
+            if ((e = launch_pdl(k_facec<T, D>, fgrid, dim3(kSmallBlock), 0, s, in, cur))) return e;
         }
         if (ev) cudaEventRecord(ev[2], s);
         if constexpr (FACES) e = launch_pdl(k_flux<T, D, TX, TY, TZ, SK, ACC>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
