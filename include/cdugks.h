@@ -151,7 +151,9 @@ CDUGKS_API int cdugks_profile_step(cdugks_t *h, int nsteps, double *ms_out);
 
 /* Synchronise the stream and report the device status word: OK, or
  * NONFINITE / NEGATIVE if any step since the last check produced a
- * non-finite conserved variable or rho <= 0 or T <= 0.  Clears the word. */
+ * non-finite conserved variable or rho <= 0 or T <= 0, or TIMEOUT if a
+ * kernel's bounded wait for its tensor copies gave up (the kernel then stops
+ * and that step's result is incomplete).  Clears the word. */
 CDUGKS_API int cdugks_sync_status(cdugks_t *h);
 
 /* Macroscopic fields from the tracked W: host out[Nc][2+D] = rho, u[D], T.

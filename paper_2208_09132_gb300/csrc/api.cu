@@ -752,6 +752,8 @@ int cdugks_sync_status(cdugks_t* h) {
         return cuda_fail(e, "read status");
     if ((e = cudaMemsetAsync(h->base + h->lay.status, 0, 256, h->stream))) return cuda_fail(e, "clear status");
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "cudaStreamSynchronize");
+    if (st & cdg::ST_TIMEOUT)
+        return fail(CDUGKS_ERR_TIMEOUT, "a bounded device wait (tensor-copy barrier) gave up; that step is incomplete");
     if (st & cdg::ST_NONFINITE) return fail(CDUGKS_ERR_NONFINITE, "a conserved variable became non-finite");
     if (st & cdg::ST_NEGATIVE) return fail(CDUGKS_ERR_NEGATIVE, "density or internal energy became <= 0");
     return CDUGKS_OK;
