@@ -305,6 +305,17 @@ CDUGKS_API int cdugks_set_collision(cdugks_t *h, int model);
  * already bound, no shape). */
 CDUGKS_API int cdugks_set_acceleration(cdugks_t *h, const double *a);
 
+/* Testing hook for the failure path of the bounded device waits (on = 1;
+ * 0 restores normal operation).  While on, sweep A issues none of its tensor
+ * copies and its wait gives up after 2^10 tries instead of 2^22: a step on a
+ * tile shape that stages with tensor copies (the fused shapes of 1D/2D
+ * problems large enough for interior tiles) stops its sweep and the next
+ * cdugks_sync_status reports CDUGKS_ERR_TIMEOUT.  Nothing faults or hangs;
+ * that step's results are incomplete (cdugks_init or cdugks_set_state
+ * restores a valid state) and the handle stays usable.  Drops captured
+ * graphs. */
+CDUGKS_API int cdugks_test_wait_timeout(cdugks_t *h, int on);
+
 /* ---------------------------------------------------------------- batches
  * Many independent instances stepped together: every kernel of a time step
  * is one launch over a device work list of all members' (tile, velocity

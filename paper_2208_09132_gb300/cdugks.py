@@ -24,7 +24,7 @@ EXPORTS = [
     "cdugks_profile_step",
     "cdugks_sync_status", "cdugks_moments", "cdugks_stress_heat_flux", "cdugks_conserved", "cdugks_distributions",
     "cdugks_state_bytes", "cdugks_get_state", "cdugks_set_state", "cdugks_info",
-    "cdugks_set_velocity_groups", "cdugks_set_reconstruction", "cdugks_set_collision", "cdugks_set_acceleration",
+    "cdugks_set_velocity_groups", "cdugks_set_reconstruction", "cdugks_set_collision", "cdugks_set_acceleration", "cdugks_test_wait_timeout",
     "cdugks_destroy", "cdugks_strerror", "cdugks_last_error",
     "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
         "cdugks_set_reconstruction": (i, [vp, i]),
         "cdugks_set_collision": (i, [vp, i]),
         "cdugks_set_acceleration": (i, [vp, dp]),
+        "cdugks_test_wait_timeout": (i, [vp, i]),
         "cdugks_destroy": (None, [vp]),
         "cdugks_strerror": (ctypes.c_char_p, [i]),
         "cdugks_last_error": (ctypes.c_char_p, []),

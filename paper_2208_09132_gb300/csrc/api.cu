@@ -412,6 +412,7 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     // reconstruction coefficients 2 h xi_a / dx_a in the velocity records
     for (long long i = 0; i < Nv; ++i)
         for (int a = 0; a < D; ++a) h->vel[(size_t)i * 8 + 5 + a] = 2.0 * g.hdx[a] * h->vel[(size_t)i * 8 + a];
+    g.wait_log2 = 22;
     g.K = phys->K;
     g.R = phys->R;
     g.mu_ref = phys->mu_ref;
@@ -584,6 +585,15 @@ int cdugks_set_acceleration(cdugks_t* h, const double* a) {
     const int rc = cdugks_set_tile(h, id);
     if (rc) h->g = old;
     return rc;
+}
+
+int cdugks_test_wait_timeout(cdugks_t* h, int on) {
+    if (!h) return fail(CDUGKS_ERR_INVALID, "null handle");
+    drop_graphs(h);
+    h->g.wait_test = on ? 1 : 0;
+    h->g.wait_log2 = on ? 10 : 22;
+    if (h->bound) return upload_inst(h);
+    return CDUGKS_OK;
 }
 
 int cdugks_bind(cdugks_t* h, void* device_ptr, size_t bytes, void* cuda_stream) {

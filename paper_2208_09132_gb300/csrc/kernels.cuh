@@ -76,6 +76,8 @@ struct Geo {
     double acc[3];    // its components a_b (0 beyond D)
     int nv1[3];       // velocity nodes per axis (velocity i = k0 + nv1_0 (k1 + nv1_1 k2))
     double dxi[3];    // velocity spacing per axis
+    int wait_log2;    // bounded waits give up after 2^wait_log2 tries
+    int wait_test;    // test hook: sweep A issues no tensor copies, so its bounded wait runs out
 };
 
 template <typename T> struct CellC;
@@ -1420,6 +1422,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     }
     unsigned tphase = 0;
     auto fetch_tma = [&](int vt) {      // thread 0: both halves of chunk vt's box
+        if (g.wait_test) return;        // (test hook) nothing arrives: the wait below runs out
         constexpr unsigned bytes = 2u * TL::BOX * sizeof(Q);
         mbar_expect_tx(tbar, bytes);
         if constexpr (D == 1) {
@@ -1473,7 +1476,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         if (STAGE) {
             if (tma) {                                 // the box of chunk vt has landed
                 bool done = false;
-                for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(tbar, tphase);
+                for (int it = 0; it < (1 << g.wait_log2) && !done; ++it) done = mbar_try_wait(tbar, tphase);
                 tma_late = tma_late || !done;
                 tphase ^= 1u;
             } else {

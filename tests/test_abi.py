@@ -200,3 +200,15 @@ def test_acceleration_selection_rules():
             assert lib.cdugks_info(h, ctypes.byref(info)) == 0
             assert not cdugks.tile_shape(prec, dim, info.tile_id)[1] & 32
             lib.cdugks_destroy(h)
+
+
+def test_wait_timeout_hook_needs_no_device():
+    cfg, _ = wl.random_smooth(dim=2, n=(8, 8), nv=(4, 4), seed=1)
+    lib = cdugks.load()
+    g, v, p = cdugks.describe(cfg, cdugks.FP32)
+    h = ctypes.c_void_p()
+    assert lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)) == 0
+    assert lib.cdugks_test_wait_timeout(h, 1) == 0          # unbound: host state only
+    assert lib.cdugks_test_wait_timeout(h, 0) == 0
+    assert lib.cdugks_test_wait_timeout(None, 1) != 0
+    lib.cdugks_destroy(h)
