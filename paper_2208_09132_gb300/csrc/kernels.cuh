@@ -17,19 +17,26 @@
 //             reconstructed face values and sweep B is k_flux, which reads them;
 //             otherwise sweep B reconstructs them again.
 //
-// Sweep modes (the mode of a tile shape) choose where the stencil work is done:
-// on the halo box by the sweeps, once per point by a pre-pass (k_prep,
-// k_shslope), and whether face values are stored; bit 3 selects the paper's
-// face-gradient variant of the reconstruction (a three-cell halo).
 //   W update  W^{n+1} = W^n - dt sum_faces (M_right - M_left)/dx (eqs.
 //             rhoupdate-rhoEupdate, outward normals), the status check and the
 //             cell constants of W^{n+1}.
+//
+// Sweep modes (the mode of a tile shape) choose where the stencil work is done:
+// on the halo box by the sweeps, once per point by a pre-pass (k_prep,
+// k_shslope), and whether face values are stored; bit 3 selects the paper's
+// face-gradient variant of the reconstruction (a three-cell halo), bit 4 the
+// Shakhov collision model (with k_faceq and k_cellq for the heat flux), bit 5
+// the external acceleration (force terms formed by k_prep).
 //
 // Layout in HBM: phi*[velocity chunk][cell][field g|b][VC], VC = 4 velocities,
 // so one cell's chunk of g and b is one 32-byte sector (FP32) read with two
 // 16-byte vector loads.  Boundaries are applied by index mapping while the
 // halo is loaded (periodic wrap, mirror with reflected velocity, fixed
-// equilibrium), not by ghost copies.
+// equilibrium), not by ghost copies.  Sweep A stages the next chunk's halo box
+// ahead of use: with tensor copies (TMA, completed on an mbarrier with a
+// bounded wait) on 1D/2D tiles whose box lies inside the domain, per cell with
+// cp.async elsewhere.  The kernels of a step are chained by programmatic
+// dependent launch (pdl_wait before the first dependent read).
 #pragma once
 
 #include <cuda.h>
