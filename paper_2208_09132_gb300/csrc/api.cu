@@ -419,6 +419,8 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     g.T_ref = phys->T_ref;
     g.omega = phys->omega;
     g.Pr = phys->Pr;
+    // with Pr = 1 the TEDDF b-source coefficient (Pr - 1)/tau vanishes exactly
+    g.nosrc = phys->Pr == 1.0;
     set_tiles(h, 0);
     h->vel32 = cast_vec<float>(h->vel);
     h->gsel = 0;

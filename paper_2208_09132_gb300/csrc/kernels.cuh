@@ -85,6 +85,7 @@ struct Geo {
     double dxi[3];    // velocity spacing per axis
     int wait_log2;    // bounded waits give up after 2^wait_log2 tries
     int wait_test;    // test hook: sweep A issues no tensor copies, so its bounded wait runs out
+    int nosrc;        // the b-source Z/tau_bg (g - g_eq) vanishes (Pr = 1, or the Shakhov model)
 };
 
 template <typename T> struct CellC;
@@ -670,12 +671,19 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 // flux needs.
 // Bit 5 (acceleration): k_prep adds the force terms of the sources (prepared
 // face-store shapes only) and k_flux takes them at the faces and in phi*.
-enum { MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16, MODE_ACC = 32 };
+// Bit 6 (launch-time, not a tile shape): the instance has no b-source, so
+// sweep A and k_flux leave out Z = xi.u - u^2/2 and its terms (whose
+// coefficients are then exactly 0: the same results, fewer instructions).
+enum {
+    MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16, MODE_ACC = 32,
+    MODE_NOSRC = 64
+};
 __host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
 __host__ __device__ constexpr bool mode_r2(int mode) { return (mode & MODE_R2) != 0; }
 __host__ __device__ constexpr bool mode_sk(int mode) { return (mode & MODE_SK) != 0; }
 __host__ __device__ constexpr bool mode_acc(int mode) { return (mode & MODE_ACC) != 0; }
+__host__ __device__ constexpr bool mode_nosrc(int mode) { return (mode & (MODE_NOSRC | MODE_SK)) != 0; }
 __host__ __device__ constexpr int mode_halo(int mode) { return mode_r2(mode) ? 3 : 2; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
@@ -731,11 +739,13 @@ __device__ __forceinline__ size_t sig_addr(const Geo& g, long long cell, int i, 
 
 // phibar+ of one point (eq. phibarplus) from the stored phi* (gs, bs), the
 // equilibrium (ge, be), Z = xi.u - |u|^2/2 and the cell constants.
-template <typename T>
+// (NOSRC: kp_s = 0, the source term is left out.)
+template <typename T, bool NOSRC = false>
 __device__ __forceinline__ void phibar_plus(T ge, T be, T gs, T bs, T z, T kp_g, T kp_b, T kp_s, T& pg, T& pb) {
     const T dg = gs - ge;
     pg = fma(kp_g, dg, ge);
-    pb = fma(kp_s * z, dg, fma(kp_b, bs - be, be));
+    if constexpr (NOSRC) pb = fma(kp_b, bs - be, be);
+    else pb = fma(kp_s * z, dg, fma(kp_b, bs - be, be));
 }
 
 // Pack a cell's phibar+ constants (CellPack order; u and the heat flux with
@@ -772,15 +782,15 @@ __device__ __forceinline__ void pack_cell(const CellC<T>& cs, int refl, V4<T>* d
 // The equilibria at one velocity from packed constants cst (CellPack or
 // FacePack order: u at 0, cexp at D, pref at D+1, eb at D+2, and with SK sq at
 // D+7 and e2 at 2D+7) and the velocity xi (hx = |xi|^2/2); also Z = xi.u - hu2.
-template <typename T, int D, bool SK>
+template <typename T, int D, bool SK, bool NOZ = false>
 __device__ __forceinline__ void packed_eq(const T* cst, const T (&xi)[D], T hx, T hL, T& ge, T& be, T& z) {
     T c2 = T(0), cq = T(0);
-    z = -cst[D + 3];
+    z = NOZ ? T(0) : -cst[D + 3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T d = xi[a] - cst[a];
         c2 = fma(d, d, c2);
-        z = fma(xi[a], cst[a], z);
+        if constexpr (!NOZ) z = fma(xi[a], cst[a], z);
         if constexpr (SK) cq = fma(cst[D + 7 + a], d, cq);
     }
     const T gM = cst[D + 1] * Num<T>::expo(cst[D + 0] * c2);
@@ -1166,7 +1176,7 @@ __device__ __forceinline__ void stage_face_consts(const Geo& g, const Bufs<T>& b
 // With the acceleration (ACC), the inverse of eq. phibar takes the whole
 // source: alpha (h/2) fgg for g, and alpha_b (h/2) (a.xi g_f + fgb) for b, fgg
 // and fgb the force gradients of phibar at the face, axi = a . xi.
-template <typename T, int D, bool SK = false, bool ACC = false>
+template <typename T, int D, bool SK = false, bool ACC = false, bool NOSRC = false>
 __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], const T (&w)[VC], const T (&hx)[VC],
                                           int a, const T (&gb)[VC], const T (&bb)[VC], V4<T>& fg, V4<T>& fb,
                                           T* sm, T hL = T(0), const T* fgg = nullptr, const T* fgb = nullptr,
@@ -1175,10 +1185,12 @@ __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], con
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
         T ge, be, z;
-        packed_eq<T, D, SK>(fc, xi[v], hx[v], hL, ge, be, z);
+        packed_eq<T, D, SK, SK || NOSRC>(fc, xi[v], hx[v], hL, ge, be, z);
         T gf = fma(alg, gb[v] - ge, ge);
         if constexpr (ACC) gf = fma(alg * hh, fgg[v], gf);
-        T bfv = SK ? fma(alb, bb[v] - be, be) : fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
+        T bfv;
+        if constexpr (SK || NOSRC) bfv = fma(alb, bb[v] - be, be);
+        else bfv = fma(gmb * z, gf - ge, fma(alb, bb[v] - be, be));
         if constexpr (ACC) bfv = fma(alb * hh, fma(axi[v], gf, fgb[v]), bfv);
         const T Fg = xi[v][a] * gf, Fb = xi[v][a] * bfv;
         fg.v[v] = Fg;
@@ -1242,7 +1254,7 @@ __device__ __forceinline__ void net_flux(const Geo& g, const V4<T>* FF, const in
 
 // phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
 // (eq. phiupdate, the last factor deferred) of one cell chunk, stored at dst.
-template <typename T, int D>
+template <typename T, int D, bool NOSRC = false>
 __device__ __forceinline__ void store_phi_star(const Geo& g, const T (&xi)[VC][D], const T (&u)[D], T hu2, T um_g,
                                                T um_b, T usrc, const T (&og)[VC], const T (&ob)[VC],
                                                const T (&oge)[VC], const T (&obe)[VC], const T (&dFg)[VC],
@@ -1251,12 +1263,16 @@ __device__ __forceinline__ void store_phi_star(const Geo& g, const T (&xi)[VC][D
     const T dt = (T)g.dt;
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
-        T z = -hu2;
-#pragma unroll
-        for (int a = 0; a < D; ++a) z = fma(xi[v][a], u[a], z);
         const T dg = og[v] - oge[v];
         ng[v] = fma(-dt, dFg[v], fma(um_g, dg, oge[v]));
-        nb[v] = fma(-dt, dFb[v], fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
+        if constexpr (NOSRC) {
+            nb[v] = fma(-dt, dFb[v], fma(um_b, ob[v] - obe[v], obe[v]));
+        } else {
+            T z = -hu2;
+#pragma unroll
+            for (int a = 0; a < D; ++a) z = fma(xi[v][a], u[a], z);
+            nb[v] = fma(-dt, dFb[v], fma(usrc * z, dg, fma(um_b, ob[v] - obe[v], obe[v])));
+        }
     }
     Chunk<T>::store(dst, ng);
     Chunk<T>::store(dst + VC, nb);
@@ -1296,6 +1312,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr bool FACES = mode_faces(MODE);                     // sweep A stores the face values
     constexpr bool R2 = mode_r2(MODE);                           // face-gradient reconstruction
     constexpr bool SK = mode_sk(MODE);                           // Shakhov equilibria
+    constexpr bool NOSRC = mode_nosrc(MODE);                     // no b-source (its terms left out)
     static_assert(!(SWEEP_B && FACES), "sweep B of the face-store shapes is k_flux");
     static_assert(!SK || (FACES && !R2 && mode_source(MODE) != MODE_PREP), "Shakhov shapes are fused or stored face-store shapes");
     static_assert(!R2 || (FACES && !PREP), "the face-gradient reconstruction is built for fused face-store shapes");
@@ -1557,12 +1574,12 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
                 T ge, be, z;
-                packed_eq<T, D, SK>(cst, xi[v], hx[v], hL, ge, be, z);
+                packed_eq<T, D, SK, NOSRC>(cst, xi[v], hx[v], hL, ge, be, z);
                 if (fl & 8) {
                     qg.v[v] = ge;
                     qb.v[v] = be;
                 } else {
-                    phibar_plus<T>(ge, be, gs[v], bs[v], z, kp_g, kp_b, kp_s, qg.v[v], qb.v[v]);
+                    phibar_plus<T, NOSRC>(ge, be, gs[v], bs[v], z, kp_g, kp_b, kp_s, qg.v[v], qb.v[v]);
                     if (SWEEP_B && keep) {   // phi^n of the owned cell (the deferred end of eq. phiupdate)
                         og[v] = fma(own.fa_g, gs[v], own.fb_g * ge);
                         ob[v] = fma(own.fa_b, bs[v], own.fb_b * be);
@@ -1843,7 +1860,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                             for (int e = 0; e < 4; ++e) fcst[4 * j + e] = qv.v[e];
                         }
                         Q fg, fb;
-                        face_flux<T, D>(fcst, xi, w, hx, a, gb, bb, fg, fb, sm);
+                        face_flux<T, D, false, false, NOSRC>(fcst, xi, w, hx, a, gb, bb, fg, fb, sm);
                         FF[0 * NFT + fl] = fg;
                         FF[1 * NFT + fl] = fb;
                     }
@@ -1884,7 +1901,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
                     hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
                 }
-                store_phi_star<T, D>(g, xi, u, hu2, um_g, um_b, usrc, og, ob, oge, obe, dFg, dFb,
+                store_phi_star<T, D, NOSRC>(g, xi, u, hu2, um_g, um_b, usrc, og, ob, oge, obe, dFg, dFb,
                                      bf.phi_out + phi_addr(g, cell_index(g, qa), vt * VC, 0));
             }
         }
@@ -1940,7 +1957,7 @@ struct FluxSmem {
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false, bool NOSRC = false>
 __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
     using TL = Tile<D, T0_, T1_, T2_>;
     using FS = FluxSmem<T, D, T0_, T1_, T2_, SK>;
@@ -2056,10 +2073,10 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 #pragma unroll
                         for (int b = 0; b < D; ++b) axi[v] = fma((T)fac[b], xi[v][b], axi[v]);
                     }
-                    face_flux<T, D, SK, true>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL, fgg, fgb,
-                                              axi, (T)(0.5 * g.h));
+                    face_flux<T, D, SK, true, NOSRC>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL, fgg,
+                                                     fgb, axi, (T)(0.5 * g.h));
                 } else {
-                    face_flux<T, D, SK>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL);
+                    face_flux<T, D, SK, false, NOSRC>(fcst, xi, w, hx, a, gb, bb, F[side][0], F[side][1], sm, hL);
                 }
                 if (side == 0) {
 #pragma unroll
@@ -2096,7 +2113,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
         T u[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = own.u[a];
-        store_phi_star<T, D>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
+        store_phi_star<T, D, SK || NOSRC>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
                              bf.phi_out + ad);
     }
 #pragma unroll
@@ -2125,12 +2142,12 @@ struct FluxOcc {
     static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false, bool NOSRC = false>
 __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux(const Inst<T>* __restrict__ in, int cur) {
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_wait();
-    flux_body<T, D, T0_, T1_, T2_, SK, ACC>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
+    flux_body<T, D, T0_, T1_, T2_, SK, ACC, NOSRC>(in->g, in->b[cur], blockIdx.x, blockIdx.y, smem);
 }
 
 // Many instances in one launch: the device table of instances and a work list

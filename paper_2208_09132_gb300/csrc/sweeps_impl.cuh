@@ -107,6 +107,11 @@ struct Shape {
     static constexpr bool ACC = mode_acc(MODE);
     static_assert(!ACC || (SRC == MODE_PREP && FACES && !SK && !mode_r2(MODE)),
                   "acceleration shapes are prepared face-store shapes");
+    static_assert((MODE & MODE_NOSRC) == 0, "the no-b-source bit is chosen at launch");
+    // Face-store TEDDF shapes carry a second pair of sweeps for instances with
+    // no b-source (Pr = 1), chosen per launch; the Shakhov shapes have none.
+    static constexpr bool NS = FACES && !SK;
+    static constexpr int MODE_NS = MODE | MODE_NOSRC;
 
     // dynamic shared memory of the larger of the two sweeps
     static size_t smem_bytes() {
@@ -128,6 +133,14 @@ struct Shape {
         } else {
             if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, true, MODE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(true))))
+                return e;
+        }
+        if constexpr (NS) {
+            if ((e = cudaFuncSetAttribute(k_sweep<T, D, TX, TY, TZ, false, MODE_NS>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
+                return e;
+            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, false, ACC, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::bytes)))
                 return e;
         }
         if constexpr (SRC == MODE_STORED) {
@@ -169,9 +182,14 @@ struct Shape {
                 return e;
         }
         const TmaPair tma = make_tma<T, D, typename SM::TL>(g, SM::stage(false) ? phi_in : nullptr);
-        if ((e = launch_pdl(k_sweep<T, D, TX, TY, TZ, false, MODE>, grid, dim3(TL::NT), SM::bytes(false), s, in, cur,
-                            tma)))
-            return e;
+        const bool ns = NS && g.nosrc;
+        if constexpr (NS) {
+            if (ns)
+                e = launch_pdl(k_sweep<T, D, TX, TY, TZ, false, MODE_NS>, grid, dim3(TL::NT), SM::bytes(false), s, in,
+                               cur, tma);
+        }
+        if (!ns) e = launch_pdl(k_sweep<T, D, TX, TY, TZ, false, MODE>, grid, dim3(TL::NT), SM::bytes(false), s, in, cur, tma);
+        if (e) return e;
         if (ev) cudaEventRecord(ev[1], s);
         if constexpr (SK) {
             long long nf = 0;
@@ -186,7 +204,11 @@ struct Shape {
             if ((e = launch_pdl(k_facec<T, D>, fgrid, dim3(kSmallBlock), 0, s, in, cur))) return e;
         }
         if (ev) cudaEventRecord(ev[2], s);
-        if constexpr (FACES) e = launch_pdl(k_flux<T, D, TX, TY, TZ, SK, ACC>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+        if constexpr (NS) {
+            if (ns) e = launch_pdl(k_flux<T, D, TX, TY, TZ, false, ACC, true>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+            else e = launch_pdl(k_flux<T, D, TX, TY, TZ, false, ACC>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+        } else if constexpr (FACES)
+            e = launch_pdl(k_flux<T, D, TX, TY, TZ, SK, ACC>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
         else e = launch_pdl(k_sweep<T, D, TX, TY, TZ, true, MODE>, grid, dim3(TL::NT), SM::bytes(true), s, in, cur,
                             make_tma<T, D, TL>(g, nullptr));
         if (e) return e;
