@@ -235,7 +235,10 @@ CDUGKS_API int cdugks_set_tile(cdugks_t *h, int tile_id);
  * Bit 5 (value 32): the shape implements the external acceleration
  * (cdugks_set_acceleration); the others none.
  * Every mode but 0 must be selected before cdugks_bind; modes with bits 0-1
- * nonzero are not batched (modes 0 and 4 are). */
+ * nonzero are not batched (modes 0 and 4 are).  A face-store shape of the
+ * two-time model steps a handle created with Pr = 1 (no b-source, Sec. 2)
+ * with sweeps compiled without the b-source terms; the mode reported here
+ * does not change. */
 CDUGKS_API int cdugks_tile_shape(int precision, int dim, int tile_id, int *out);
 
 /* The reconstruction of phibar at a face (Sec. 2.1).
