@@ -485,6 +485,12 @@ __device__ __forceinline__ size_t phi_addr(const Geo& g, long long cell, int i, 
     return ((size_t)(i / VC) * (size_t)g.Nc + (size_t)cell) * (2 * VC) + (size_t)field * VC + (i % VC);
 }
 
+// A hint: fetch `bytes` (a multiple of 16, p 16-byte aligned, all inside one
+// allocation) from global memory into L2.  No completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes));
+}
+
 // VC consecutive values as vector loads / stores (16-byte aligned by layout).
 template <typename T> struct Chunk;
 template <> struct Chunk<float> {
@@ -1996,8 +2002,28 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int m = 0; m < NM; ++m) acc[a][m].zero();
+    // The first thread of each x-row of the tile asks L2 for the row's data of
+    // the next chunk while this one is formed: its cells' phi*, its left faces
+    // along every axis (along x the row's right end too), and along y / z the
+    // faces above the tile's last row.  Rows are contiguous in every layout.
+    const bool row_lead = la[0] == 0;
+    const int nrow = min(TL::T0, g.n[0] - org[0]);
+    constexpr int RB = 2 * VC * (int)sizeof(T);     // bytes per cell or face and chunk
+    const int tdim[3] = {TL::T0, TL::T1, TL::T2};
 
     for (int vt = vt0; vt < vt1; ++vt) {
+        if (row_lead && vt + 1 < vt1) {
+            prefetch_l2(bf.phi_in + cell_ad + (size_t)(vt + 1) * chunk_stride, nrow * RB);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const T* fb = bf.face[a] + face_addr(g, a, ff[a], vt + 1);
+                prefetch_l2(fb, (nrow + (a == 0 ? 1 : 0)) * RB);
+                if (a > 0 && (la[a] == tdim[a] - 1 || own_right[a])) {
+                    const int fs = a == 1 ? g.fn[1][0] : g.fn[2][0] * g.fn[2][1];
+                    prefetch_l2(fb + (size_t)fs * (2 * VC), nrow * RB);
+                }
+            }
+        }
         T xi[VC][D], w[VC], hx[VC];
 #pragma unroll
         for (int v = 0; v < VC; ++v) {
