@@ -1369,14 +1369,60 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         l[1] = D >= 2 ? (k / TL::E0) % TL::E1 - TL::HALO : 0;
         l[2] = D >= 3 ? k / (TL::E0 * TL::E1) - TL::HALO : 0;
     };
+    // The cells the tile's faces read: upwind of a face are the owned cells and
+    // one layer below each axis, and one layer above an axis only where faces on
+    // the tile's upper side are formed (the domain's end in sweep A, every tile
+    // edge in sweep B); phibar+ is needed on those and on their neighbours
+    // along every axis (the slopes).  Corners beyond that are never read.  The
+    // shapes that load phibar+ (and the slopes) skip the rest; the fused ones
+    // form the whole box (measured faster: fixed trip counts, no spills).
+    constexpr bool PRUNE = PREP && !R2;
+    bool rext[3] = {true, true, true};
+#pragma unroll
+    for (int a = 0; a < D; ++a) rext[a] = SWEEP_B || org[a] + TL::tdim(a) >= g.n[a];
+    auto upwind_cell = [&](const int (&l)[3]) {
+        int out = 0;
+        bool ok = true;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            if (l[b] < -1 || l[b] > TL::tdim(b)) ok = false;
+            else if (l[b] == -1) ++out;
+            else if (l[b] == TL::tdim(b)) {
+                ++out;
+                ok = ok && rext[b];
+            }
+        }
+        return ok && out <= 1;
+    };
+    auto needed_box = [&](const int (&l)[3]) {
+        if (upwind_cell(l)) return true;
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            int m[3] = {l[0], l[1], l[2]};
+            m[b] = l[b] - 1;
+            any = any || upwind_cell(m);
+            m[b] = l[b] + 1;
+            any = any || upwind_cell(m);
+        }
+        return any;
+    };
     auto is_halo = [&](int k) {
         int l[3];
         box_local(k, l);
         bool inner = true;
 #pragma unroll
         for (int a = 0; a < D; ++a) inner = inner && l[a] >= 0 && l[a] < TL::tdim(a);
-        return !inner;
+        return !inner && (!PRUNE || needed_box(l));
     };
+    // bit j: slope-box cell t + j NT is upwind of a face (its slopes are formed or loaded)
+    static_assert((SB + TL::NT - 1) / TL::NT <= 32, "one mask bit per slope-box cell of a thread");
+    unsigned smask = 0;
+    for (int s2 = t, j = 0; s2 < SB; s2 += TL::NT, ++j) {
+        int l[3];
+        TL::sbox_local(s2, l);
+        if (!PRUNE || upwind_cell(l)) smask |= 1u << j;
+    }
 
     // ---- prologue: halo box (boundary mapping, packed constants), ordered halo list, face constants
     for (int k = t; k < BOX; k += TL::NT) {
@@ -1392,6 +1438,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         if (PREP) continue;
         pack_cell<T, D, SK>(dir ? bf.cellc0[c] : bf.cellc[c], refl, CC + k, BOX);
     }
+    int nhalo = 0;      // length of the halo list
     {   // halo list in box order (warp ballots), so neighbouring threads touch neighbouring cells
         constexpr int PER = ((BOX + NW - 1) / NW + 31) / 32 * 32;
         const int k0 = warp * PER, k1 = min(BOX, k0 + PER);
@@ -1404,6 +1451,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         __syncthreads();
         int base = 0;
         for (int w2 = 0; w2 < warp; ++w2) base += wcount[w2];
+        for (int w2 = 0; w2 < NW; ++w2) nhalo += wcount[w2];
         for (int kb = k0; kb < k1; kb += 32) {
             const int k = kb + lane;
             const bool hk = k < k1 && is_halo(k);
@@ -1465,7 +1513,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     };
     bool tma_late = false;              // a bounded wait gave up (then the CTA reports and stops)
     __syncthreads();
-    constexpr int NH = TL::NH;
+    const int NH = PRUNE ? nhalo : TL::NH;
 
     // Asynchronous copies of chunk vt's phi* for the box cells this thread forms
     // in phase 1 (its own cell and its halo cells), into its own ST slots: a
@@ -1634,7 +1682,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         if (STORED) {
             // phibar+ and slopes of the cells [-1, T] around the tile from the stored arrays;
             // a mirrored cell takes the reflected velocity and flips the mirrored slope components
-            for (int s2 = t; s2 < SB; s2 += TL::NT) {
+            for (int s2 = t, j = 0; s2 < SB; s2 += TL::NT, ++j) {
+                if (PRUNE && !((smask >> j) & 1u)) continue;
                 int sl[3];
                 TL::sbox_local(s2, sl);
                 const int k = TL::box_of(sl[0], sl[1], sl[2]);
@@ -1696,7 +1745,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
         }
 
         // ---- phase 2: half van Leer slopes (times dx) of the cells [-1, T] around the tile
-        for (int s = t; s < (STORED ? 0 : SB); s += TL::NT) {
+        for (int s = t, j = 0; s < (STORED ? 0 : SB); s += TL::NT, ++j) {
+            if (PRUNE && !((smask >> j) & 1u)) continue;
             int sl[3];
             TL::sbox_local(s, sl);
             const int k = TL::box_of(sl[0], sl[1], sl[2]);
@@ -2006,7 +2056,9 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
     // the next chunk while this one is formed: its cells' phi*, its left faces
     // along every axis (along x the row's right end too), and along y / z the
     // faces above the tile's last row.  Rows are contiguous in every layout.
-    const bool row_lead = la[0] == 0;
+    // (Not with the force terms, whose reads of neighbouring velocity chunks
+    // measured slower with it.)
+    const bool row_lead = !ACC && la[0] == 0;
     const int nrow = min(TL::T0, g.n[0] - org[0]);
     constexpr int RB = 2 * VC * (int)sizeof(T);     // bytes per cell or face and chunk
     const int tdim[3] = {TL::T0, TL::T1, TL::T2};
