@@ -2,6 +2,8 @@
 design-byte accounting of the bench, and the serving step count."""
 import math
 
+import pytest
+
 import numpy as np
 
 from paper_2208_09132_gb300 import cdugks, serving, tune
@@ -88,3 +90,67 @@ def test_sine_wave_reaches_its_end_time_within_the_cfl_bound():
         _, (x,) = wl.cell_centres(cfg)
         assert (f[:, 0] == 1.0).all() and (f[:, 2] == 1.0).all()
         assert abs(f[:, 1] - np.sin(2 * np.pi * x)).max() < 1e-15
+
+
+def _upwind_cell(l, T, D, rext):
+    """Slope-box cell l (tile-local) is upwind of a face the tile forms; the
+    rule sweep A uses to skip unread cells of shapes that load phibar+."""
+    out, ok = 0, True
+    for b in range(D):
+        if l[b] < -1 or l[b] > T[b]:
+            ok = False
+        elif l[b] == -1:
+            out += 1
+        elif l[b] == T[b]:
+            out += 1
+            ok = ok and rext[b]
+    return ok and out <= 1
+
+
+def _needed_box_cell(l, T, D, rext):
+    if _upwind_cell(l, T, D, rext):
+        return True
+    for b in range(D):
+        for d in (-1, 1):
+            m = list(l)
+            m[b] += d
+            if _upwind_cell(m, T, D, rext):
+                return True
+    return False
+
+
+@pytest.mark.parametrize("D,T", [(1, (256,)), (2, (32, 8)), (2, (16, 8)), (3, (8, 4, 4)), (3, (8, 8, 4))])
+def test_pruned_halo_covers_every_read_of_the_faces(D, T):
+    """Every cell a face of the tile reads (both candidate upwind cells of each
+    face formed, their phibar+ and the neighbours their slopes use) is in the
+    set the sweeps keep, for interior, edge and ragged tiles, sweeps A and B."""
+    import itertools
+    import random
+    rng = random.Random(1)
+    T3 = list(T) + [1] * (3 - D)
+    for _ in range(12):
+        n = [rng.randint(1, 3 * T3[a] + 5) if a < D else 1 for a in range(3)]
+        org = [rng.randint(0, (n[a] - 1) // T3[a]) * T3[a] if a < D else 0 for a in range(3)]
+        for sweep_b in (False, True):
+            rext = [sweep_b or org[a] + T3[a] >= n[a] for a in range(3)]
+            ups = set()
+            for la in itertools.product(*[range(T3[b]) for b in range(3)]):
+                qa = [org[b] + la[b] for b in range(3)]
+                if any(qa[b] >= n[b] for b in range(D)):
+                    continue
+                for a in range(D):
+                    own_right = qa[a] == n[a] - 1
+                    right = (la[a] == T3[a] - 1 or own_right) if sweep_b else own_right
+                    for side in ([0, 1] if right else [0]):
+                        left = list(la)
+                        left[a] += side - 1
+                        rgt = list(left)
+                        rgt[a] += 1
+                        ups.update([tuple(left), tuple(rgt)])
+            assert all(_upwind_cell(u, T3, D, rext) for u in ups)
+            for u in ups:
+                for b in range(D):
+                    for d in (-1, 1):
+                        m = list(u)
+                        m[b] += d
+                        assert _needed_box_cell(m, T3, D, rext), (D, T, n, org, sweep_b, m)
