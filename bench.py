@@ -205,10 +205,16 @@ def cpu_baseline(cfg, budget_s=12.0):
     rng_fields = np.column_stack([np.ones(nc)] + [0.1 * np.sin(2 * math.pi * X[0])] * D + [np.full(nc, cfg["T_ref"])])
     o = oracle.Oracle(sample)
     o.init(rng_fields)
-    t0 = time.perf_counter()
-    o.step(1)
-    t1 = time.perf_counter() - t0
-    n = max(1, min(100000, int(budget_s / max(t1, 1e-6))))
+    k, el0 = 1, 0.0               # per-step time from a calibration run of at least 0.25 s
+    while True:
+        t0 = time.perf_counter()
+        o.step(k)
+        el0 = time.perf_counter() - t0
+        if el0 >= 0.25 or k >= 4096:
+            break
+        k *= 4
+    t1 = el0 / k
+    n = max(1, min(200000, int(budget_s / max(t1, 1e-7))))
     t0 = time.perf_counter()
     o.step(n)
     el = time.perf_counter() - t0
