@@ -2327,6 +2327,32 @@ __global__ void k_cellq(const Inst<T>* __restrict__ in, int cur) {
     if (c < g.Nc) raw_moments<T, D>(g, bf.vel, bf.phi_out, g.Nc, c, blockIdx.y, bf.qs);
 }
 
+// Sums over the velocity groups of M per-group partial sums of one item
+// (src[(gg M + m) n], src at the item), added in group order; the loads of
+// four groups are issued before their additions, so a thread waits for one
+// memory round trip per four groups, not per group.
+template <int M>
+__device__ __forceinline__ void group_sums(const double* __restrict__ src, size_t n, int G, double (&s)[M]) {
+    constexpr int UG = 4;
+#pragma unroll
+    for (int m = 0; m < M; ++m) s[m] = 0.0;
+    int gg = 0;
+    for (; gg + UG <= G; gg += UG) {
+        double v[UG][M];
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+            for (int m = 0; m < M; ++m) v[u][m] = src[((size_t)(gg + u) * M + m) * n];
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+            for (int m = 0; m < M; ++m) s[m] = dadd(s[m], v[u][m]);
+    }
+    for (; gg < G; ++gg)
+#pragma unroll
+        for (int m = 0; m < M; ++m) s[m] = dadd(s[m], src[((size_t)gg * M + m) * n]);
+}
+
 // Group sums of the raw moments of one item (fixed order), then its heat flux
 // relative to W divided by 1 + x Pr/tau: x = h/2 at a face (phibar relaxes the
 // heat flux by that factor), dt/2 at a cell (phi* against phi^{n+1}).
@@ -2335,11 +2361,7 @@ __device__ __forceinline__ void shakhov_heat_flux(const Geo& g, const double* sr
                                                   const double* W, double x, double q[3]) {
     constexpr int M = NQ<D>::value;
     double s[M];
-    for (int m = 0; m < M; ++m) {
-        double v = 0.0;
-        for (int gg = 0; gg < g.G; ++gg) v = dadd(v, src[((size_t)gg * M + m) * (size_t)n + item]);
-        s[m] = v;
-    }
+    group_sums<M>(src + item, (size_t)n, g.G, s);
     const Macro mc = macro_of(g, W);
     heat_flux_raw<D>(mc, W, s, q);
     const Relax<double> r = relax_of<double>(g, mc);
@@ -2349,13 +2371,13 @@ __device__ __forceinline__ void shakhov_heat_flux(const Geo& g, const double* sr
 
 // Face constants from the group-summed face W (fixed summation order).
 template <typename T, int D>
-__device__ __forceinline__ void facec_body(const Geo g, const Bufs<T> bf, int a, long long f) {
+__device__ __forceinline__ void facec_body(const Geo& g, const Bufs<T>& bf, int a, long long f) {
     constexpr int NM = 2 + D;
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int m = 0; m < NM; ++m) {
-        double s = 0.0;
-        for (int gg = 0; gg < g.G; ++gg) s += bf.wf[a][((size_t)gg * NM + m) * g.nf[a] + f];
-        W[m] = s;
+    {
+        double s[NM];
+        group_sums<NM>(bf.wf[a] + f, (size_t)g.nf[a], g.G, s);
+        for (int m = 0; m < NM; ++m) W[m] = s[m];
     }
     if (g.accel) {   // eqs. rhoubar, rhoEbar: + (h/2) rho a, then + (h/2) (rho u) . a
         double fac[3] = {g.acc[0], g.acc[1], g.acc[2]};
@@ -2394,7 +2416,7 @@ __global__ void k_facec_batch(const RItem* __restrict__ items, const Inst<T>* __
 // W^{n+1} = W^n - dt sum_a (M_a(right face) - M_a(left face)) / dx_a (outward
 // normals), the status check, and the cell constants of W^{n+1}.
 template <typename T, int D>
-__device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long long c) {
+__device__ __forceinline__ void wupdate_body(const Geo& g, const Bufs<T>& bf, long long c) {
     constexpr int NM = 2 + D;
     int q[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long long)g.n[0] * g.n[1]))};
     double dW[NM];
@@ -2404,14 +2426,10 @@ __device__ __forceinline__ void wupdate_body(const Geo g, const Bufs<T> bf, long
         int qr[3] = {q[0], q[1], q[2]};
         qr[a] += 1;
         const long long fr = face_index(g, a, qr);
-        for (int m = 0; m < NM; ++m) {
-            double sr = 0.0, sl = 0.0;
-            for (int gg = 0; gg < g.G; ++gg) {
-                sr = dadd(sr, bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fr]);
-                sl = dadd(sl, bf.mf[a][((size_t)gg * NM + m) * g.nf[a] + fl]);
-            }
-            dW[m] = __fma_rn(dsub(sr, sl), g.idx[a], dW[m]);
-        }
+        double sr[NM], sl[NM];
+        group_sums<NM>(bf.mf[a] + fr, (size_t)g.nf[a], g.G, sr);
+        group_sums<NM>(bf.mf[a] + fl, (size_t)g.nf[a], g.G, sl);
+        for (int m = 0; m < NM; ++m) dW[m] = __fma_rn(dsub(sr[m], sl[m]), g.idx[a], dW[m]);
     }
     double W[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int m = 0; m < NM; ++m) W[m] = __fma_rn(-g.dt, dW[m], bf.W[(size_t)m * g.Nc + c]);

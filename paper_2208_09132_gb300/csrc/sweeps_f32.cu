@@ -11,7 +11,7 @@ using Table32 = ShapeTable<
     float,
     ShapeList<Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>,
               Shape<float, 1, 256, 1, 1, FF>, Shape<float, 1, 256, 1, 1, FG>, Shape<float, 1, 256, 1, 1, FFS>,
-              Shape<float, 1, 256, 1, 1, PFA>>,
+              Shape<float, 1, 256, 1, 1, PFA>, Shape<float, 1, 128, 1, 1, FF>, Shape<float, 1, 64, 1, 1, FF>>,
     ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, MODE_PREP>,
               Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>,
               Shape<float, 2, 32, 16, 1>, Shape<float, 2, 32, 8, 1, FF>, Shape<float, 2, 32, 16, 1, FF>,

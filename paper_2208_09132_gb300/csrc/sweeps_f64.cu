@@ -12,7 +12,7 @@ using Table64 = ShapeTable<
     double,
     ShapeList<Shape<double, 1, 256, 1, 1>, Shape<double, 1, 128, 1, 1>, Shape<double, 1, 64, 1, 1>,
               Shape<double, 1, 128, 1, 1, FF>, Shape<double, 1, 128, 1, 1, FG>, Shape<double, 1, 128, 1, 1, FFS>,
-              Shape<double, 1, 128, 1, 1, PFA>>,
+              Shape<double, 1, 128, 1, 1, PFA>, Shape<double, 1, 64, 1, 1, FF>, Shape<double, 1, 32, 1, 1, FF>>,
     ShapeList<Shape<double, 2, 16, 8, 1>, Shape<double, 2, 8, 8, 1>, Shape<double, 2, 16, 8, 1, MODE_STORED>,
               Shape<double, 2, 16, 8, 1, FF>, Shape<double, 2, 8, 8, 1, FG>, Shape<double, 2, 16, 8, 1, FFS>,
               Shape<double, 2, 16, 8, 1, PFA>>,
