@@ -2477,6 +2477,9 @@ __global__ void k_wupdate_batch(const RItem* __restrict__ items, const Inst<T>* 
                                 int* __restrict__ cur) {
     pdl_wait();
     const RItem it = items[blockIdx.x];
+    // The member's first block flips its buffer index when done, so a later
+    // block of the same member may read either value: the two records differ
+    // only in the phi buffers, which the W update does not touch.
     const int c0 = cur[it.inst] & 1;
     const Geo g = insts[it.inst].g;
     const Bufs<T> bf = insts[it.inst].b[c0];
