@@ -169,10 +169,11 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, kernel, precision, tile_id=None, groups=None):
-    """DRAM bytes per point for a kernel from the committed ncu summary, if it
-    was taken on the current kernel source in the same launch configuration;
-    else None."""
+def ncu_traffic(workload, kernel, precision, tile_id=None, groups=None, field="dram_bytes_per_point"):
+    """DRAM bytes (or, with field="thread_instructions_per_point", executed
+    thread instructions) per point for a kernel from the committed ncu
+    summary, if it was taken on the current kernel source in the same launch
+    configuration; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
@@ -185,7 +186,17 @@ def ncu_traffic(workload, kernel, precision, tile_id=None, groups=None):
         return None
     if (tile_id is not None and e.get("tile_id") != tile_id) or (groups is not None and e.get("velocity_groups") != groups):
         return None
-    return float(e["dram_bytes_per_point"])
+    return float(e[field]) if field in e else None
+
+
+def issue_roofline(ipp, points_per_launch, seconds, sms, sm_mhz):
+    """A kernel against the instruction-issue ceiling: ipp thread instructions
+    per point over a launch of points_per_launch points taking seconds, against
+    sms x 128 thread instructions per clock (4 schedulers x 32 lanes) at sm_mhz."""
+    rate = ipp * points_per_launch / seconds
+    peak = sms * 128 * sm_mhz * 1e6
+    return {"thread_instructions_per_point": ipp, "achieved": round(rate / 1e12, 3), "peak": round(peak / 1e12, 3),
+            "unit": "T thread-instructions/s", "frac": round(rate / peak, 4)}
 
 
 def cpu_baseline(cfg, budget_s=12.0):
@@ -479,6 +490,14 @@ def run_ours(args, ws, rank, local):
                 "step_bytes_per_point": ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname],
                 "step_hbm_frac": round((ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname]) * P
                                        / (total_ms / args.steps / 1e3) / 1e9 / peak, 4)}
+    # The sweeps are bound by instruction issue rather than HBM: the same kernel
+    # against the issue ceiling, SMs x 128 thread instructions per clock at the
+    # maximum SM clock, from the executed instructions of the ncu capture.
+    ipp = ncu_traffic(args.workload, dom, pname, s.info().tile_id, s.info().velocity_groups,
+                      field="thread_instructions_per_point")
+    if ipp is not None:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        roofline["issue"] = issue_roofline(ipp, P, t_dom, sms, (clk or {}).get("sm_max_mhz") or 2070.0)
 
     # ---- end to end through the C ABI with pinned host buffers
     NM = 2 + cfg["dim"]
