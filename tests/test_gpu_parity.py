@@ -335,15 +335,18 @@ def test_face_store_shapes_without_b_source_match_oracle(oracle_mod, name, preci
 
 @pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
 @pytest.mark.parametrize("dim", [1, 2])
-def test_tma_staged_interior_tiles_match_oracle(oracle_mod, dim, precision, tol):
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.0])
+def test_tma_staged_interior_tiles_match_oracle(oracle_mod, dim, precision, tol, Pr):
     """Domains large enough for interior tiles, whose halo boxes sweep A stages
     with tensor copies (TMA), beside edge tiles that stage per cell (periodic
-    wrap on one axis, specular walls on the other), for every fused shape."""
+    wrap on one axis, specular walls on the other), for every fused shape; at
+    Pr = 1 the face-store shapes take the sweeps without the b-source terms."""
     if dim == 1:
         cfg, f = wl.random_smooth(dim=1, n=(600,), nv=(12,), seed=21, amp=0.3, kn=3e-3)
     else:
         cfg, f = wl.random_smooth(dim=2, n=(100, 44), nv=(8, 6), seed=22, amp=0.3, kn=3e-3)
         cfg = _bc(cfg, [(P, P), (S, S)])
+    cfg = dict(cfg, Pr=Pr)
     o = oracle_mod.Oracle(cfg)
     o.init(f)
     o.step(8)
