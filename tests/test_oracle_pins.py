@@ -281,6 +281,47 @@ def test_specular_walls_along_any_axis_equal_the_mirror_image(oracle_mod, dim, a
     assert np.abs(m1[:, 1 + axis]).max() > 1e-3      # the wall-normal flow is not trivial
 
 
+
+
+def _free_stream_error(oracle_mod, dim, N, axes, t_end):
+    """L1 error of the collisionless scheme against the exact translation
+    g(x - xi t) of a smooth product profile in the two axes, g = b/(|xi|^2/2 + 1)."""
+    n = [N, N] if dim == 2 else [4, N, N]
+    nv = (4, 4) if dim == 2 else (2, 4, 4)
+    cfg, f = wl.random_smooth(dim=dim, n=n, nv=nv, seed=0, amp=0.0, mu_ref=1e250, omega=0.0, vmax=1.0, cfl=0.4)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    xi, w = o.velocities()
+    _, X = wl.cell_centres(cfg)
+    a, c = axes
+
+    def prof(p, q):
+        return 1.0 + 0.3 * np.sin(2 * np.pi * p) * np.sin(2 * np.pi * q)
+
+    g0 = np.stack([prof(X[a], X[c]) for _ in range(len(w))], axis=1)
+    b0 = g0 * (0.5 * (xi ** 2).sum(1) + 1.0)[None, :]
+    W = np.column_stack([g0 @ w] + [g0 @ (w * xi[:, k]) for k in range(dim)] + [b0 @ w])
+    o.set_state(g0, b0, W)
+    nsteps = int(round(t_end / o.dt))
+    o.step(nsteps)
+    t = nsteps * o.dt
+    g, _ = o.distributions()
+    ex = np.stack([prof(X[a] - xi[i, a] * t, X[c] - xi[i, c] * t) for i in range(len(w))], axis=1)
+    return np.abs(g - ex).mean()
+
+
+@pytest.mark.parametrize("dim,axes,N", [(2, (0, 1), 32), (3, (1, 2), 16)])
+def test_free_streaming_of_a_product_profile_is_second_order(oracle_mod, dim, axes, N):
+    """Collisionless transport of a profile that varies along two axes at once,
+    against its exact translation: the error falls at second order under grid
+    refinement at fixed CFL.  The tangential part of the reconstruction along
+    the characteristic (the -h xi_b sigma_b terms, b other than the face
+    normal) carries the cross term of that order; without it the observed
+    order drops to about 1.2 - 1.4."""
+    e1 = _free_stream_error(oracle_mod, dim, N, axes, 0.2)
+    e2 = _free_stream_error(oracle_mod, dim, 2 * N, axes, 0.2)
+    assert math.log2(e1 / e2) >= 1.75, (e1, e2)
+
 # -------------------------------------------------------------- free streaming
 
 def test_free_streaming_is_muscl_hancock_advection(oracle_mod):
