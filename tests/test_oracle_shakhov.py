@@ -119,6 +119,28 @@ def test_unit_prandtl_is_the_bgk_scheme_bit_for_bit(oracle_mod):
 
 
 @pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.5])
+def test_tracked_heat_flux_in_a_sheared_2d_flow(oracle_mod, Pr):
+    """The same identity in 2D, where the flow carries shear stress: the heat
+    flux relative to W takes the pressure work of the off-diagonal stress
+    components (sum over b of u_b P_ab, b other than a)."""
+    n = 12       # 48 nodes per axis on [-11, 11]: the quadrature error is below the tolerance
+    cfg = wl._base(2, [n, n], [0, 0], [1, 1], [[0, 0], [0, 0]], [48, 48], [-11.0, -11.0], [11.0, 11.0], K=2.0,
+                   mu_ref=2e-2, T_ref=1.0, omega=0.5, Pr=Pr, cfl=0.5)
+    cfg["collision"] = SHAKHOV
+    _, (x, y) = wl.cell_centres(cfg)
+    T = 1.0 + 0.3 * np.sin(2 * math.pi * x)
+    f = wl._fields(1.0 / T, [0.3 + 0.2 * np.cos(2 * math.pi * y), 0.25 * np.sin(2 * math.pi * x)], T)
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(20)
+    P, qd = o.stress_heat_flux()
+    qt = o.cell_heat_flux()
+    assert np.abs(P[:, 0, 1]).max() > 1e-3            # shear stress is present
+    assert np.abs(qd).max() > 1e-3
+    assert np.abs(qt - qd).max() < 1e-9 * np.abs(qd).max(), np.abs(qt - qd).max()
+
+
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 1.5])
 def test_tracked_heat_flux_is_that_of_the_distributions(oracle_mod, Pr):
     """The heat flux the next equilibrium uses (from the update's explicit part,
     divided by 1 + dt Pr/(2 tau)) is the heat flux of the updated distributions."""
