@@ -558,9 +558,11 @@ def test_euler_limit_sod_against_exact_riemann(oracle_mod):
 
 # --------------------------------------------------------- Navier-Stokes rates
 
-def _shear_rate(oracle_mod, mu, Pr, nx=32, nv=24, vmax=6.0):
+def _shear_rate(oracle_mod, mu, Pr, nx=32, nv=24, vmax=6.0, T_ref=2.0, omega=0.0):
+    """Decay rate of a shear wave in a gas at T = 2 (R = 1/2, so p = rho = 1),
+    and its Navier-Stokes value k^2 mu(T)/rho with mu(T) = mu (T/T_ref)^omega."""
     cfg = wl._base(2, [nx, 1], [0, 0], [1, 1], [[0, 0], [0, 0]], [nv, nv], [-vmax] * 2, [vmax] * 2,
-                   K=0.0, mu_ref=mu, T_ref=2.0, omega=0.0, Pr=Pr, cfl=0.5)
+                   K=0.0, mu_ref=mu, T_ref=T_ref, omega=omega, Pr=Pr, cfl=0.5)
     _, (x, y) = wl.cell_centres(cfg)
     f = wl._fields(np.ones_like(x), [np.zeros_like(x), 1e-3 * np.sin(2 * math.pi * x)],
                    np.full_like(x, 2.0))
@@ -573,7 +575,15 @@ def _shear_rate(oracle_mod, mu, Pr, nx=32, nv=24, vmax=6.0):
     a1 = abs(cplx_amp(o.moments()[:, 2], x, k))
     o.step(n2 - n1)
     a2 = abs(cplx_amp(o.moments()[:, 2], x, k))
-    return math.log(a1 / a2) / ((n2 - n1) * o.dt), k * k * mu
+    return math.log(a1 / a2) / ((n2 - n1) * o.dt), k * k * mu * (2.0 / T_ref) ** omega
+
+
+def test_ns_shear_wave_decay_follows_the_viscosity_law(oracle_mod):
+    """eq. visc: with the gas at T = 2 and T_ref = 0.5, omega = 0.5, the
+    viscosity is mu_ref (T/T_ref)^omega = 2 mu_ref (and mu_ref / 2 if the law
+    were inverted)."""
+    rate, pred = _shear_rate(oracle_mod, mu=0.0025, Pr=2.0 / 3.0, nx=48, T_ref=0.5, omega=0.5)
+    assert abs(rate / pred - 1.0) < 0.02, (rate, pred)
 
 
 @pytest.mark.slow
