@@ -97,6 +97,33 @@ def test_uniform_gas_accelerates_exactly_in_3d_on_unequal_velocity_grids(oracle_
     assert np.abs(o.discrete_moments() - Wo).max() <= 2e-5, np.abs(o.discrete_moments() - Wo).max(axis=0)
 
 
+def test_one_step_of_the_force_terms_moves_the_first_moments_exactly(oracle_mod):
+    """A uniform collisionless gas advances by the rectangle rule, so one step
+    adds dt S to g and b.  With central differences in velocity (zero beyond
+    the grid) summation by parts gives the moments of S exactly, up to the
+    grid's tails: sum w xi_c S_g = a_c rho, and for the energy flux
+    sum w xi_c S_b = a_c rho E + sum_d a_d sum w xi_d xi_c g.  On a grid whose
+    spacing differs per axis this holds only if each axis's difference takes
+    its own spacing, for g and for b."""
+    a = np.array([0.4, -0.3, 0.6])
+    cfg = wl._base(3, [2, 2, 2], [0] * 3, [1] * 3, [[0, 0]] * 3, [20, 24, 28], [-8.0] * 3, [8.0] * 3, K=2.0,
+                   mu_ref=1e250, T_ref=1.0, omega=0.0, Pr=1.0, cfl=0.5)
+    cfg["accel"] = list(a)
+    cfg["dt"] = 1e-3
+    o = oracle_mod.Oracle(cfg)
+    o.init(np.tile([1.0, 0.3, -0.1, 0.2, 1.0], (o.Nc, 1)))
+    xi, w = o.velocities()
+    g0, b0 = o.distributions()
+    o.step(1)
+    g1, b1 = o.distributions()
+    for c in range(3):
+        dP = (w * xi[:, c]) @ (g1[0] - g0[0])
+        assert abs(dP - o.dt * a[c] * (w @ g0[0])) <= 1e-12 * abs(dP), c
+        dF = (w * xi[:, c]) @ (b1[0] - b0[0])
+        pred = o.dt * (a[c] * (w @ b0[0]) + sum(a[d] * ((w * xi[:, d] * xi[:, c]) @ g0[0]) for d in range(3)))
+        assert abs(dF - pred) <= 1e-12 * abs(pred), (c, dF, pred)
+
+
 @pytest.mark.parametrize("mu", [1e-2, 1e250])
 def test_face_distributions_carry_the_face_conserved_variables(oracle_mod, mu):
     """Inverting eq. phibar with the whole source (force gradients from phibar,
