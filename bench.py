@@ -5,12 +5,16 @@ Metric: phase-space point-updates per second (one point-update = g and b
 advanced one time step at one (cell, discrete velocity) point, the "phase space
 cell update" of the paper's scaling study).
 
-Default workload: the 2D Kelvin-Helmholtz problem with FP32 storage, 256^2
-periodic cells x 32^2 velocities on [-6,6]^2, Kn = 1e-3, Pr = 1 (synthetic
-initial fields).  One bench step = one full time step of the scheme.
+Default workload: the 3D shear-wave problem with FP32 storage, 64^3 periodic
+cells x 24^3 velocities on [-6,6]^3, Kn = 1e-4, Pr = 2/3 (synthetic initial
+fields; 3.6e9 phase-space points, 29 GB per state buffer).  One bench step =
+one full time step of the scheme.  The same line carries, as sub-objects, the
+plain FP64 path on the same workload and the batched form (256 uneven 1D
+thermoacoustic instances in FP32) with its FP64 one-instance-at-a-time
+comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c3|c3s|c4|c5|einfeldt] [--no-tune]
+                  [--workload c1|c2|c3|c3s|c4|c5|einfeldt] [--tune]
 
 N > 1 runs independent replicas (the path does not shard across GPUs on this
 build), one per rank under torch.distributed.run; value = all points / max time.
@@ -84,11 +88,6 @@ def pick_workload(name):
 
 def points(cfg):
     return wl.ncells(cfg) * wl.nvel(cfg)
-
-
-def default_tile_1d(nx):
-    """Tile shape for a 1D instance: fewer, fuller CTAs for long grids."""
-    return 0 if nx > 1536 else (1 if nx > 384 else 2)
 
 
 # --------------------------------------------------------------------- clocks
@@ -271,9 +270,11 @@ def max_over_ranks(x, ws):
 
 # ---------------------------------------------------------------- our arm
 
-def run_batched(args, ws, rank, local):
+def run_batched(args, ws, rank, local, sub=False):
     """Many uneven 1D instances (the batched thermoacoustic workload) stepped
-    together: one launch per kernel for all members, replayed from a CUDA graph."""
+    together: one launch per kernel for all members, replayed from a CUDA graph.
+    With sub=True it is the "batched" part of the default line (200 timed
+    steps) and returns the sub-object."""
     import torch
 
     from paper_2208_09132_gb300 import cdugks
@@ -285,11 +286,8 @@ def run_batched(args, ws, rank, local):
     members = []
     choices = {}
     for cfg, f in probs:
-        if args.tune:
-            from paper_2208_09132_gb300 import tune
-            tile, groups = tune.tune(cfg, cdugks.FP32, context="batch", device=dev)
-        else:
-            tile, groups = default_tile_1d(cfg["n"][0]), 1
+        from paper_2208_09132_gb300 import tune
+        tile, groups = tune.choose(cfg, cdugks.FP32, context="batch", device=dev, allow_tuning=args.tune)
         choices[(tile, groups)] = choices.get((tile, groups), 0) + 1
         s = cdugks.Solver(cfg, precision=cdugks.FP32, device=dev, tile_id=tile, velocity_groups=groups)
         s.init(f)
@@ -301,7 +299,7 @@ def run_batched(args, ws, rank, local):
     batch.step(max(args.warmup, 3))
     if batch.sync() != 0:
         raise RuntimeError("a member's status flagged a broken state during warm-up")
-    K = max(gsteps, args.steps // gsteps * gsteps)
+    K = 200 if sub else max(gsteps, args.steps // gsteps * gsteps)
     clocks = ClockSampler(local)
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K // gsteps + 1)]
@@ -314,9 +312,20 @@ def run_batched(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
-    per_step = [ev[k].elapsed_time(ev[k + 1]) / gsteps for k in range(K // gsteps)]
     total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), ws)
     status = batch.sync()
+    # step latency: single-step graph replays, each between two events
+    batch.capture(1)
+    nlat = 500
+    lev = [torch.cuda.Event(enable_timing=True) for _ in range(nlat + 1)]
+    torch.cuda.synchronize()
+    lev[0].record(stream)
+    for k in range(nlat):
+        batch.step(1)
+        lev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per_step = [lev[k].elapsed_time(lev[k + 1]) for k in range(nlat)]
+    status = status or batch.sync()
     value = ws * P * K / (total_ms / 1e3)
     peak, peak_kind = measured_peak_hbm()
     step_bytes = 24 * P
@@ -343,8 +352,19 @@ def run_batched(args, ws, rank, local):
         fp64 = {"value": P * n64 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n64, "steps": n64,
                 "what": "each instance stepped alone in FP64, one after another"}
         del plain
+    del batch, members
+    torch.cuda.empty_cache()
     if rank != 0:
         return None
+    lat = {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
+           "samples": nlat, "what": "per batched step, single-step graph replays between two CUDA events"}
+    if sub:
+        return {"workload": "batched_thermoacoustic_1d_256_instances", "value": value, "unit": UNIT,
+                "ms_per_step": total_ms / K, "steps": K, "instances": len(probs), "points": P,
+                "launch": f"one launch per kernel for all members, CUDA graph of {gsteps} steps",
+                "latency_ms": lat, "fp64_plain": fp64,
+                "vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
+                "step_hbm_frac": round(achieved / peak, 4), "status_ok": status == 0}
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -353,7 +373,7 @@ def run_batched(args, ws, rank, local):
                    "launch": f"one launch per kernel for all members, CUDA graph of {gsteps} steps",
                    "tile_groups_counts": {f"tile{t}_g{g}": n for (t, g), n in sorted(choices.items())},
                    "l2": "inputs larger than L2" if P * 8 > 129e6 else "state fits in L2"},
-        "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
+        "latency_ms": lat,
         "roofline": {"bound": "hbm", "kernel": "batched step (all kernels)", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                      "algorithmic_bytes_per_point": 24, "traffic": None},
@@ -409,6 +429,38 @@ def run_served(args, ws, rank, local):
     }
 
 
+def time_fp64_plain(cfg, fields, dev, budget_s=20.0):
+    """The plain FP64 path on the same workload, one instance: a warm-up step,
+    then as many timed steps (at least 2, at most 20) as fit the time budget."""
+    import torch
+
+    from paper_2208_09132_gb300 import cdugks
+
+    s64 = cdugks.Solver(cfg, precision=cdugks.FP64, device=dev)
+    s64.init(fields)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s64.stream)
+    s64.step(1)
+    e1.record(s64.stream)
+    torch.cuda.synchronize()
+    one = e0.elapsed_time(e1) / 1e3
+    n64 = int(max(2, min(20, budget_s / max(one, 1e-6))))
+    e0.record(s64.stream)
+    s64.step(n64)
+    e1.record(s64.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    P = points(cfg)
+    info = s64.info()
+    out = {"value": P * n64 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n64, "steps": n64,
+           "tile": list(info.tile)[:cfg["dim"]], "tile_id": info.tile_id,
+           "velocity_groups": info.velocity_groups, "status_ok": s64.sync_status() == 0}
+    del s64
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -429,22 +481,28 @@ def run_ours(args, ws, rank, local):
     tile, groups = 0, 0
     if args.tile is not None:
         tile, groups = args.tile, args.groups or 0
-    elif args.tune:
+    else:
         from paper_2208_09132_gb300 import tune
-        tile, groups = tune.tune(cfg, prec, context="alone", device=dev)
+        tile, groups = tune.choose(cfg, prec, context="alone", device=dev, allow_tuning=args.tune)
     s = cdugks.Solver(cfg, precision=prec, device=dev, stream=torch.cuda.Stream(device=dev), tile_id=tile,
                       velocity_groups=groups)
     stream = s.stream
     s.init(fields)
-    for _ in range(args.warmup):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup):
+        if k == args.warmup - 1:
+            e0.record(stream)
         s.step(1)
+    e1.record(stream)
     torch.cuda.synchronize()
     if s.sync_status() != 0:
         raise RuntimeError("device status flagged a broken state during warm-up")
+    step_est = e0.elapsed_time(e1) / 1e3
 
-    # steps replayed from CUDA graphs of gsteps steps when the count allows (one
-    # launch per gsteps steps; the same kernels and results)
-    gsteps = args.graph if args.graph > 1 and args.steps % args.graph == 0 else 1
+    # steps replayed from CUDA graphs of gsteps steps when the count allows and
+    # the step is short enough for launch overhead to matter (one launch per
+    # gsteps steps; the same kernels and results)
+    gsteps = args.graph if (args.graph > 1 and args.steps % args.graph == 0 and step_est < 5e-3) else 1
     if gsteps > 1:
         s.capture(gsteps)
         s.step(gsteps)              # first replay, untimed
@@ -470,8 +528,25 @@ def run_ours(args, ws, rank, local):
     status = s.sync_status()
     value = ws * P * args.steps / (total_ms / 1e3)
 
+    # ---- step latency: every step on its own between two events, as many steps
+    # as about 10 s allow (at least the timed count, at most 500)
+    nlat = int(max(nwin if gsteps == 1 else 0, min(500, 10.0 / max(step_est, 1e-6))))
+    if gsteps == 1 and nlat <= nwin:
+        lat = per_step
+    else:
+        if gsteps > 1:
+            s.capture(1)
+        lev = [torch.cuda.Event(enable_timing=True) for _ in range(nlat + 1)]
+        torch.cuda.synchronize()
+        lev[0].record(stream)
+        for k in range(nlat):
+            s.step(1)
+            lev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        lat = [lev[k].elapsed_time(lev[k + 1]) for k in range(nlat)]
+
     # ---- per-kernel durations of the same launches (CUDA events on the bound stream)
-    nprof = max(3, min(args.steps, 50))
+    nprof = int(max(3, min(args.steps, 50, 5.0 / max(step_est, 1e-6))))
     ph = s.profile_step(nprof)
     names = ["sweep_a", "face_constants", "sweep_b", "w_update"]
     dom = max(("sweep_a", "sweep_b"), key=lambda k: ph[names.index(k)])
@@ -481,15 +556,17 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = measured_peak_hbm()
     achieved = abytes / t_dom / 1e9
     traffic_pp = ncu_traffic(args.workload, dom, pname, s.info().tile_id, s.info().velocity_groups)
+    step_bytes = ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname]
+    step_ms = total_ms / args.steps
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "algorithmic_bytes_per_point": ALGO_BYTES[dom][pname],
                 "traffic": None if traffic_pp is None else traffic_pp * P,
                 "phase_ms": {n: round(float(v), 4) for n, v in zip(names, ph)},
                 "design_bytes_per_point": design_bytes(mode, cfg["dim"], 4 if pname == "fp32" else 8),
-                "step_bytes_per_point": ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname],
-                "step_hbm_frac": round((ALGO_BYTES["sweep_a"][pname] + ALGO_BYTES["sweep_b"][pname]) * P
-                                       / (total_ms / args.steps / 1e3) / 1e9 / peak, 4)}
+                "step_bytes_per_point": step_bytes,
+                "step_achieved": round(step_bytes * P / (step_ms / 1e3) / 1e9, 1),
+                "step_hbm_frac": round(step_bytes * P / (step_ms / 1e3) / 1e9 / peak, 4)}
     # The sweeps are bound by instruction issue rather than HBM: the same kernel
     # against the issue ceiling, SMs x 128 thread instructions per clock at the
     # maximum SM clock, from the executed instructions of the ncu capture.
@@ -517,52 +594,50 @@ def run_ours(args, ws, rank, local):
            "h2d_bytes_per_step": host_in.numel() * 8 / e2e_steps,
            "d2h_bytes_per_step": host_out.numel() * 8 / e2e_steps,
            "what": "cdugks_init from pinned host fields + cdugks_step(K) + cdugks_moments to pinned host"}
+    info = s.info()
+    dt_used = s.dt
+    launches_per_step = 4 + (1 if mode & 3 else 0) + (2 if mode & 16 else 0)
+    del s
+    torch.cuda.empty_cache()
+
+    # ---- the batched form (C4) with its own FP64 one-at-a-time comparison
+    batched = None
+    if args.workload == "c3" and not args.skip_batched:
+        batched = run_batched(args, ws, rank, local, sub=True)
 
     # ---- the plain FP64 path on the same workload (the one-instance comparison)
     fp64 = None
     if prec == cdugks.FP32 and not args.skip_fp64:
-        s64 = cdugks.Solver(cfg, precision=cdugks.FP64, device=dev)
-        s64.init(fields)
-        s64.step(2)
-        n64 = max(3, min(20, args.steps))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s64.stream)
-        s64.step(n64)
-        e1.record(s64.stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        fp64 = {"value": P * n64 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n64, "steps": n64}
-        del s64
+        fp64 = time_fp64_plain(cfg, fields, dev)
 
     result = None
     if rank == 0:
         cpu = cpu_baseline(cfg) if (ws == 1 and not args.skip_cpu) else None
-        launches_per_step = 4 + (1 if mode & 3 else 0) + (2 if mode & 16 else 0)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "time_to_solution_s": (total_ms / args.steps * cfg["steps"] / 1e3) if args.workload == "einfeldt" else None,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "time_to_solution_s": (step_ms * cfg["steps"] / 1e3) if args.workload == "einfeldt" else None,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if pname == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": cfg["name"], "precision": pname, "cells": wl.ncells(cfg),
-                       "velocities": wl.nvel(cfg), "points": P, "dt": s.dt,
-                       "state_bytes": s.info().state_bytes,
-                       "tile": list(s.info().tile)[:cfg["dim"]], "velocity_groups": s.info().velocity_groups,
-                       "tile_id": s.info().tile_id, "sweep_mode": MODE_NAMES.get(mode & 7, str(mode)),
+                       "velocities": wl.nvel(cfg), "points": P, "dt": dt_used,
+                       "state_bytes": info.state_bytes,
+                       "tile": list(info.tile)[:cfg["dim"]], "velocity_groups": info.velocity_groups,
+                       "tile_id": info.tile_id, "sweep_mode": MODE_NAMES.get(mode & 7, str(mode)),
                        "reconstruction": "face gradient" if mode & 8 else "upwind cell",
                        "collision": "Shakhov" if mode & 16 else "two relaxation times (Sec. 2)",
                        "acceleration": list(cfg.get("accel", [0.0, 0.0, 0.0]))[:cfg["dim"]],
                        "launch": f"CUDA graphs of {gsteps} steps" if gsteps > 1 else "one launch per kernel",
-                       "l2": "inputs larger than L2 (state > 129 MB)" if s.info().state_bytes > 129e6
+                       "l2": "inputs larger than L2 (state > 129 MB)" if info.state_bytes > 129e6
                              else "state fits in L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
-                           "what": f"per step, over {gsteps}-step graph replays" if gsteps > 1 else "per step"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "samples": len(lat), "what": "per step, each step between two CUDA events"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_plain": fp64,
+            "batched": batched,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "status_ok": status == 0,
@@ -618,10 +693,12 @@ def main():
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 1000; einfeldt: to t_end)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c3")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 plain comparison")
-    ap.add_argument("--no-tune", dest="tune", action="store_false", help="default tile / group choice")
+    ap.add_argument("--skip-batched", action="store_true", help="omit the batched sub-object of the 3D workload")
+    ap.add_argument("--tune", dest="tune", action="store_true",
+                    help="tune sizes missing from the tuner cache (default: cached choice, else a default shape)")
     ap.add_argument("--tile", type=int, default=None, help="pin the tile shape id (skips tuning)")
     ap.add_argument("--graph", type=int, default=10, help="steps per captured CUDA graph (1: plain launches)")
     ap.add_argument("--recon", type=int, default=0, help="1: the face-gradient reconstruction (1D/2D workloads)")
@@ -633,8 +710,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.steps is None:   # the einfeldt workload runs its whole solve; the others 1000 steps
-        args.steps = pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt" else 1000
+    if args.steps is None:   # the einfeldt workload runs its whole solve; the 3D workload 20 steps, others 1000
+        args.steps = (pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt"
+                      else (20 if args.workload in ("c3", "c3s") else 1000))
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, ws, rank)

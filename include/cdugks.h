@@ -54,7 +54,13 @@ extern "C" {
 #define CDUGKS_ERR_OOM (-2)         /* bound workspace too small */
 #define CDUGKS_ERR_CUDA (-3)        /* a CUDA runtime call failed */
 #define CDUGKS_ERR_NONFINITE (-4)   /* a conserved variable became NaN/Inf */
-#define CDUGKS_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define CDUGKS_ERR_TIMEOUT (-5)     /* a bounded device wait gave up: the launch that
+                                       reported it stopped early, so its results are
+                                       incomplete; a wait that runs out for a real
+                                       reason (not the test hook) may leave tensor
+                                       copies in flight, so treat every later result
+                                       in that CUDA context as untrusted and destroy
+                                       the handle rather than re-initialise it */
 #define CDUGKS_ERR_UNBOUND (-6)     /* no workspace bound / state not initialised */
 #define CDUGKS_ERR_NEGATIVE (-7)    /* density or temperature became <= 0 */
 
@@ -67,8 +73,14 @@ extern "C" {
 #define CDUGKS_RULE_BOOLE 1         /* composite Boole (4th-order Newton-Cotes), n = 4m+1 */
 
 #define CDUGKS_FP64 0               /* g, b stored and computed in double */
-#define CDUGKS_FP32 1               /* g, b stored and computed in float; W, T and all
-                                       velocity-space sums accumulated in double */
+#define CDUGKS_FP32 1               /* g, b stored in float and the per-point arithmetic
+                                       in float; W, rho, u, T (T from E - u^2/2) in
+                                       double.  The velocity-space sums of a velocity
+                                       group are summed per chunk of 4 velocities in
+                                       float and the chunk sums folded into float
+                                       Kahan pairs (compensated summation); the
+                                       groups' partial sums are added in double, in
+                                       a fixed order. */
 
 /* Spatial grid: dim = D in {1,2,3}; n[a] cells on [lo[a], hi[a]] along axis
  * a < D (entries a >= D ignored); bc[a][0] / bc[a][1] the low / high side.
@@ -371,7 +383,9 @@ CDUGKS_API const char *cdugks_last_error(void);
  *   phi_out  device buffer of the same size for t_{n+1} (not phi_in)
  *   W        device conserved variables [2+D][Nc] doubles, updated in place
  *   stream   cudaStream_t as void* (NULL = legacy default stream)
- * Asynchronous; no device status word is reported (inspect W).  Every other
+ * Asynchronous.  No device status word is reported: after synchronising the
+ * stream the caller must check W itself (every entry finite, rho > 0 and
+ * rho E > |rho u|^2 / (2 rho) in every cell) before trusting the state.  Every other
  * piece of device scratch lives in one fixed 32 MiB array in this library
  * (held by every GPU that loads it until the process exits): problems whose
  * cell/face tables and face-moment sums exceed it are rejected with

@@ -13,7 +13,11 @@ for its shape (how many CTAs a launch has against the SM count decides how
 full its last wave is).  The fastest candidate is cached in a JSON file
 (``CDUGKS_TUNE_CACHE`` or
 ``~/.cache/cdugks_tune.json``) keyed by the size bucket, so a later process
-reuses it.  Choices never change results beyond rounding order: every tile and
+reuses it.  Choices this tuner made on a GB300 for the benchmark sizes ship
+beside it (``tune_cache.json``, same format, each entry tagged with the shape
+table it was tuned on); ``choose`` takes a cached choice, else tunes when
+asked to, else a default shape.  ``python -m paper_2208_09132_gb300.tune``
+tunes the benchmark sizes into the cache.  Choices never change results beyond rounding order: every tile and
 group split computes the same scheme.
 """
 from __future__ import annotations
@@ -32,6 +36,54 @@ SMS = 152
 
 def cache_path() -> str:
     return os.environ.get("CDUGKS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cdugks_tune.json"))
+
+
+PACKAGED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+
+
+def source_tag() -> str:
+    """Hash of the library's shape tables (every tile shape and sweep mode of
+    both precisions, as the library reports them): a cached choice names a
+    tile id, which means nothing in another table."""
+    import hashlib
+    h = hashlib.sha256()
+    for prec in (cdugks.FP32, cdugks.FP64):
+        for D in (1, 2, 3):
+            for t in range(cdugks.load().cdugks_tile_count(prec, D)):
+                h.update(repr((prec, D, t, cdugks.tile_shape(prec, D, t))).encode())
+    return h.hexdigest()[:16]
+
+
+def default_choice(cfg, precision):
+    """Launch shape without tuning: the face-store shape of the default scheme
+    with the most cells per tile that fits the problem, velocity groups chosen
+    by the library (enough CTAs for a few waves)."""
+    D = cfg["dim"]
+    best = None
+    for t, _ in candidates(cfg, precision, "alone"):
+        dims, mode = cdugks.tile_shape(precision, D, t)
+        if not mode & 4:
+            continue
+        cells = int(np.prod(dims[:D]))
+        pref = (mode & 3 == 0, cells if cells <= wl.ncells(cfg) else -cells)
+        if best is None or pref > best[0]:
+            best = (pref, t)
+    return (best[1] if best else 0), 0
+
+
+def choose(cfg, precision, context="alone", device="cuda:0", allow_tuning=False):
+    """The cached tuned shape (this machine's cache, then the one shipped
+    beside the tuner) when it was tuned on the same shape table; else tune
+    (allow_tuning) or take default_choice()."""
+    key = size_key(cfg, precision, context)
+    tag = source_tag()
+    for path in (cache_path(), PACKAGED):
+        d = _load_cache(path)
+        if key in d and d[key].get("source") == tag:
+            return tuple(d[key]["choice"])
+    if allow_tuning:
+        return tune(cfg, precision, context=context, device=device)
+    return default_choice(cfg, precision)
 
 
 def _load_cache(path):
@@ -136,7 +188,8 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
     path = cache or cache_path()
     d = _load_cache(path)
     key = size_key(cfg, precision, context)
-    if key in d and not refresh:
+    tag = source_tag()
+    if key in d and not refresh and d[key].get("source") == tag:
         return tuple(d[key]["choice"])
     import torch
 
@@ -165,7 +218,28 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
     results.sort()
     best = results[0]
     d = _load_cache(path)
-    d[key] = {"choice": [best[1], best[2]], "ms_per_point": best[0],
+    d[key] = {"choice": [best[1], best[2]], "ms_per_point": best[0], "source": tag,
               "tried": [[t, g, ms] for ms, t, g in results]}
     _save_cache(path, d)
     return best[1], best[2]
+
+
+def bench_sizes():
+    """(cfg, precision, context) of every instance size the benchmark runs."""
+    out = [(wl.workload_c3(kn=1e-4)[0], cdugks.FP32, "alone"), (wl.workload_c3(kn=1e-4, scale=2, nv=12)[0],
+                                                              cdugks.FP32, "alone"),
+           (wl.workload_c2()[0], cdugks.FP32, "alone"), (wl.workload_c1()[0], cdugks.FP64, "alone")]
+    seen = set()
+    for cfg, _ in wl.workload_c4():
+        k = size_key(cfg, cdugks.FP32, "batch")
+        if k not in seen:
+            seen.add(k)
+            out.append((cfg, cdugks.FP32, "batch"))
+    return out
+
+
+if __name__ == "__main__":
+    import sys
+    dev = sys.argv[1] if len(sys.argv) > 1 else "cuda:0"
+    for cfg, prec, ctx in bench_sizes():
+        print(size_key(cfg, prec, ctx), tune(cfg, prec, context=ctx, device=dev, refresh=True), flush=True)

@@ -1,0 +1,175 @@
+"""FP32 storage against the FP64 oracle over each workload's own step count,
+on grids the oracle finishes in about a minute, and FP32 parity at high Mach
+number.
+
+The workloads fix the precision target of the FP32 path: relative L-infinity
+<= 1e-5 on rho, u, T against the FP64 oracle, and conservation drift <= 1e-6
+relative.  The short parity cases run <= 60 steps; these run the workloads'
+own counts, where rounding accumulates:
+
+* the 2D Kelvin-Helmholtz physics (32^2 velocities on [-6,6]^2, Kn = 1e-3,
+  Pr = 1, CFL 0.8) at 64^2 cells for its 1000 steps;
+* the 3D shear wave (24^3 velocities on [-6,6]^3, Pr = 2/3, CFL 0.7) for its
+  100 steps at Kn = 1e-4 (8^3 cells), 1e-2 and 1 (6^3 cells);
+* three members of the batched thermoacoustic workload for their 2000 steps,
+  stepped inside one batch as the bench steps them.
+
+Each runs in the default launch shape and in the one the bench times.  The
+high-Mach cases put the flow at Mach 3 on a wide velocity grid, where the
+Maxwellian exponent c^2/(2RT) spans hundreds.  Every test prints its errors
+(run with -s to see them).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2208_09132_gb300 import cdugks, workloads as wl
+from test_gpu_parity import rel_linf
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5         # relative L-infinity on rho, u, T
+DRIFT = 1e-6       # conservation drift, relative
+
+
+def drift(c0, c1):
+    """Relative drift of the domain totals of W (mass, momentum, energy):
+    momentum is scaled by the total mass times the largest speed scale
+    sqrt(sum E / sum rho) so that a zero mean momentum has a scale."""
+    s0, s1 = c0.sum(0), c1.sum(0)
+    mass, energy = s0[0], s0[-1]
+    scale = np.full_like(s0, mass)
+    scale[1:-1] = mass * math.sqrt(energy / mass)
+    scale[-1] = energy
+    return np.abs(s1 - s0) / scale
+
+
+def solve(cfg, f, steps, precision, tile=None, groups=0):
+    s = cdugks.Solver(cfg, precision=precision, tile_id=tile if tile is not None else 0, velocity_groups=groups)
+    s.init(f)
+    c0 = s.conserved()
+    s.step(steps)
+    assert s.sync_status() == 0
+    return s, c0
+
+
+def bench_tile(precision, D):
+    """The sweep mode the bench's tuned 2D and 3D launches use: fused face store
+    in 2D, stored slopes with face store in 3D (and any lean shape present)."""
+    mode = 4 if D == 2 else 6
+    nt = cdugks.load().cdugks_tile_count(precision, D)
+    return [t for t in range(nt) if cdugks.tile_shape(precision, D, t)[1] == mode][:1]
+
+
+def check_against(oracle_mod, name, cfg, f, steps, tiles):
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    ref = o.moments()
+    for t in tiles:
+        s, c0 = solve(cfg, f, steps, cdugks.FP32, tile=t)
+        err = rel_linf(s.moments(), ref)
+        dr = drift(c0, s.conserved())
+        print(f"\n[longrun] {name} tile {t} ({steps} steps): rel Linf rho,u,T = "
+              f"{', '.join(f'{e:.2e}' for e in err)}; drift = {', '.join(f'{d:.1e}' for d in dr)}")
+        assert np.all(err <= TOL), (name, t, err)
+        if all(cfg["bc"][a] == [wl.BC_PERIODIC] * 2 for a in range(cfg["dim"])):
+            assert np.all(dr <= DRIFT), (name, t, dr)
+
+
+def test_kh_physics_1000_steps(oracle_mod):
+    cfg, f = wl.kelvin_helmholtz(n=64, nv=32, kn=1e-3)
+    check_against(oracle_mod, "kh 64^2 x 32^2", cfg, f, cfg["steps"], [0] + bench_tile(cdugks.FP32, 2))
+
+
+@pytest.mark.parametrize("kn,n", [(1e-4, 8), (1e-2, 6), (1.0, 6)])
+def test_shear3d_physics_100_steps(oracle_mod, kn, n):
+    cfg, f = wl.shear3d(n=n, nv=24, kn=kn)
+    check_against(oracle_mod, f"shear3d {n}^3 x 24^3 Kn={kn:g}", cfg, f, cfg["steps"],
+                  [0] + bench_tile(cdugks.FP32, 3))
+
+
+def test_batched_members_2000_steps(oracle_mod):
+    """Three members of the batched workload (one per velocity count, the
+    smallest grids of each) stepped together in one batch for 2000 steps."""
+    probs = wl.workload_c4()
+    pick = {}
+    for cfg, f in probs:
+        nv = cfg["nv"][0]
+        if nv not in pick or cfg["n"][0] < pick[nv][0]["n"][0]:
+            pick[nv] = (cfg, f)
+    chosen = [pick[nv] for nv in sorted(pick)]
+    steps = chosen[0][0]["steps"]
+    members = []
+    for cfg, f in chosen:
+        tile = cdugks.find_tile(cdugks.FP32, 1, (64,), 4)
+        s = cdugks.Solver(cfg, precision=cdugks.FP32, tile_id=tile)
+        s.init(f)
+        members.append((s, s.conserved()))
+    b = cdugks.Batch([m for m, _ in members])
+    b.capture(10)
+    b.step(steps)
+    assert b.sync() == 0
+    for (cfg, f), (s, c0) in zip(chosen, members):
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        o.step(steps)
+        err = rel_linf(s.moments(), o.moments())
+        dr = drift(c0, s.conserved())
+        print(f"\n[longrun] batched member {cfg['name']} Kn-mu {cfg['mu_ref']:.2e} Pr {cfg['Pr']:.3f} "
+              f"({steps} steps): rel Linf rho,u,T = {', '.join(f'{e:.2e}' for e in err)}; "
+              f"drift = {', '.join(f'{d:.1e}' for d in dr)}")
+        assert np.all(err <= TOL), (cfg["name"], err)
+        assert np.all(dr <= DRIFT), (cfg["name"], dr)
+
+
+# ---------------------------------------------------------------- high Mach
+
+def drifting(cfg, f, U):
+    """The same problem seen from a frame moving at -U: every cell's velocity
+    gains U (the fields are (rho, u..., T))."""
+    f = f.copy()
+    for a, ua in enumerate(U):
+        f[:, 1 + a] += ua
+    return cfg, f
+
+
+def mach_of(f, cfg):
+    D = cfg["dim"]
+    gamma = (cfg["K"] + 5.0) / (cfg["K"] + 3.0)
+    u2 = (f[:, 1:1 + D] ** 2).sum(1)
+    return float(np.sqrt(u2 / (gamma * cfg["R"] * f[:, 1 + D])).max())
+
+
+def high_mach_cases():
+    # 1D Sod at Mach 3 (both states drifting at 3 sound speeds of the left
+    # state), periodic (two Riemann problems), velocities on [-14, 14]
+    cfg, f = wl.sod(nx=128, nv=96, kn=1e-4, bc=wl.BC_PERIODIC)
+    cfg["vlo"][0], cfg["vhi"][0] = -14.0, 14.0
+    U = 3.0 * math.sqrt(1.4 * 0.5 * f[0, 2])
+    yield "1d_sod_mach3", drifting(cfg, f, [U]), 60
+    # 2D Kelvin-Helmholtz drifting diagonally, velocities on [-12, 12]^2
+    cfg, f = wl.kelvin_helmholtz(n=24, nv=28, kn=1e-3, vmax=12.0)
+    yield "2d_kh_drift", drifting(cfg, f, [3.0, 2.0]), 20
+    # 3D shear wave drifting along x, velocities on [-9, 9]^3
+    cfg, f = wl.shear3d(n=6, nv=20, kn=1e-2, vmax=9.0)
+    yield "3d_shear_drift", drifting(cfg, f, [2.2, 0.0, 0.0]), 10
+
+
+@pytest.mark.parametrize("name,case,steps", list(high_mach_cases()), ids=[c[0] for c in high_mach_cases()])
+def test_fp32_high_mach_matches_oracle(oracle_mod, name, case, steps):
+    cfg, f = case
+    assert mach_of(f, cfg) >= 2.5
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    ref = o.moments()
+    D = cfg["dim"]
+    tiles = [0] + (bench_tile(cdugks.FP32, D) if D > 1 else [cdugks.find_tile(cdugks.FP32, 1, (64,), 4)])
+    for t in tiles:
+        s, c0 = solve(cfg, f, steps, cdugks.FP32, tile=t)
+        err = rel_linf(s.moments(), ref)
+        print(f"\n[highmach] {name} Mach {mach_of(f, cfg):.2f} tile {t}: rel Linf rho,u,T = "
+              f"{', '.join(f'{e:.2e}' for e in err)}")
+        assert np.all(err <= TOL), (name, t, err)

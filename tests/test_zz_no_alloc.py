@@ -28,12 +28,12 @@ def _state_parts(solver, blob, elt):
     return blob[hdr:hdr + nphi], blob[hdr + nphi:]
 
 
-@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
-def test_noalloc_step_matches_the_workspace_step_on_two_calls(precision, tol):
+def _two_calls_against_workspace_step(cfg, f, precision, tol, setup=None):
+    """Two allocation-free calls in a row from the state of a regular solver,
+    each compared with one regular step; setup(lib, handle) configures the
+    allocation-free handle first (tile shape, velocity groups)."""
     import torch
 
-    cfg, f = wl.random_smooth(dim=2, n=(40, 24), nv=(8, 12), seed=21, amp=0.3, kn=3e-3)
-    cfg["bc"][0] = [wl.BC_SPECULAR, wl.BC_SPECULAR]
     elt = 8 if precision == cdugks.FP64 else 4
     ref = cdugks.Solver(cfg, precision=precision)
     ref.init(f)
@@ -50,7 +50,9 @@ def test_noalloc_step_matches_the_workspace_step_on_two_calls(precision, tol):
     h = ctypes.c_void_p()
     assert lib.cdugks_create(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p), ctypes.byref(h)) == 0
     try:
-        D, Nc = 2, ref.Nc
+        if setup is not None:
+            setup(lib, h)
+        D, Nc = cfg["dim"], ref.Nc
         for call in range(2):
             rc = lib.cdugks_step_noalloc(h, ctypes.c_void_p(buf[call % 2].data_ptr()),
                                          ctypes.c_void_p(buf[(call + 1) % 2].data_ptr()),
@@ -69,6 +71,40 @@ def test_noalloc_step_matches_the_workspace_step_on_two_calls(precision, tol):
             assert np.abs(b - a).max() <= tol * np.abs(a).max(), call
     finally:
         lib.cdugks_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+def test_noalloc_step_matches_the_workspace_step_on_two_calls(precision, tol):
+    cfg, f = wl.random_smooth(dim=2, n=(40, 24), nv=(8, 12), seed=21, amp=0.3, kn=3e-3)
+    cfg["bc"][0] = [wl.BC_SPECULAR, wl.BC_SPECULAR]
+    _two_calls_against_workspace_step(cfg, f, precision, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(cdugks.FP64, 1e-12), (cdugks.FP32, 1e-5)])
+def test_noalloc_with_a_face_store_shape_selected(precision, tol):
+    """A handle whose selected shape stores face values (a buffer the fixed
+    array has no room for) steps in the plain fused shape instead."""
+    cfg, f = wl.random_smooth(dim=2, n=(40, 24), nv=(8, 12), seed=23, amp=0.3, kn=3e-3)
+    nt = cdugks.load().cdugks_tile_count(precision, 2)
+    faces = [t for t in range(nt) if cdugks.tile_shape(precision, 2, t)[1] == 4]
+    assert faces
+
+    def setup(lib, h):
+        assert lib.cdugks_set_tile(h, faces[0]) == 0
+
+    _two_calls_against_workspace_step(cfg, f, precision, tol, setup)
+
+
+def test_noalloc_halves_the_velocity_groups_to_fit():
+    """64^2 cells and 16^2 velocities with 64 velocity groups need about 35 MB
+    of face-moment partial sums; the step halves the group count once (to 32)
+    and fits in the 32 MiB array."""
+    cfg, f = wl.random_smooth(dim=2, n=(64, 64), nv=(16, 16), seed=24, amp=0.3, kn=3e-3)
+
+    def setup(lib, h):
+        assert lib.cdugks_set_velocity_groups(h, 64) == 0
+
+    _two_calls_against_workspace_step(cfg, f, cdugks.FP32, 1e-5, setup)
 
 
 def test_noalloc_rejects_oversized_problems_and_dirichlet():
