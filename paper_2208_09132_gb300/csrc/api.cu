@@ -46,13 +46,15 @@ struct Layout {
     size_t phi[2], pb, sg, fv[3], W, cellc, cellc0, facec[3], wf[3], mf[3], vel, refl, io, status, inst;
     size_t hq, qs, qf[3];     // Shakhov model only
     size_t force;             // acceleration only
+    size_t xc, xc0, xf[3];    // lean shapes only: separable factor tables
     size_t total;
 };
 
 // Optional workspace buffers, by the sweep modes that need them.
-enum { BUF_PHIBAR = 1, BUF_SLOPES = 2, BUF_FACES = 4, BUF_FORCE = 8 };
+enum { BUF_PHIBAR = 1, BUF_SLOPES = 2, BUF_FACES = 4, BUF_FORCE = 8, BUF_XTAB = 16 };
 int buffers_of(int mode) {
     int b = 0;
+    if (cdg::mode_lean(mode)) b |= BUF_XTAB;
     if (cdg::mode_acc(mode)) b |= BUF_FORCE;
     if (cdg::mode_source(mode) != cdg::MODE_FUSED) b |= BUF_PHIBAR;
     if (cdg::mode_source(mode) == cdg::MODE_STORED) b |= BUF_SLOPES;
@@ -76,6 +78,7 @@ struct cdugks {
     int gsel;              // requested groups (0 = auto)
     int recon;             // CDUGKS_RECON_UPWIND_CELL or CDUGKS_RECON_FACE_GRADIENT
     int collision;         // CDUGKS_COLLISION_TEDDF or CDUGKS_COLLISION_SHAKHOV
+    bool zero_node;        // some active velocity axis has a node at xi = 0 (no lean shapes)
     Layout lay;
     unsigned char* base;
     size_t bound_bytes;
@@ -182,6 +185,10 @@ void make_layout(cdugks* h) {
     L.hq = sk ? take(sizeof(double) * g.D * g.Nc) : 0;
     L.qs = sk ? take(sizeof(double) * (size_t)h->gcap * NQ * g.Nc) : 0;
     for (int a = 0; a < 3; ++a) L.qf[a] = sk && a < g.D ? take(sizeof(double) * (size_t)h->gcap * NQ * g.nf[a]) : 0;
+    const bool xt = (h->bufs_cap & BUF_XTAB) != 0;
+    L.xc = xt ? take(h->elt * (size_t)g.xrows * g.Nc) : 0;
+    L.xc0 = xt ? take(h->elt * (size_t)g.xrows * g.Nc) : 0;
+    for (int a = 0; a < 3; ++a) L.xf[a] = xt && a < g.D ? take(h->elt * (size_t)g.xrows * g.nf[a]) : 0;
     L.status = take(256);
     L.inst = take(std::max(sizeof(Inst<float>), sizeof(Inst<double>)));
     L.total = off;
@@ -214,6 +221,12 @@ Bufs<T> bufs(const cdugks* h, int in) {
     b.hq = sk ? reinterpret_cast<double*>(p + L.hq) : nullptr;
     b.qs = sk ? reinterpret_cast<double*>(p + L.qs) : nullptr;
     for (int a = 0; a < 3; ++a) b.qf[a] = sk && a < h->g.D ? reinterpret_cast<double*>(p + L.qf[a]) : nullptr;
+    // the factor tables exist (and are kept up to date) only while a lean shape is selected
+    const bool xt = (h->bufs_cap & BUF_XTAB) && cdg::mode_lean(tile_mode(h->prec, h->g.D, h->g.tile_id));
+    b.xc = xt ? reinterpret_cast<T*>(p + L.xc) : nullptr;
+    b.xc0 = xt ? reinterpret_cast<T*>(p + L.xc0) : nullptr;
+    const bool xft = xt && cdg::mode_xf(tile_mode(h->prec, h->g.D, h->g.tile_id));   // face tables: lean sweep B only
+    for (int a = 0; a < 3; ++a) b.xf[a] = xft && a < h->g.D ? reinterpret_cast<T*>(p + L.xf[a]) : nullptr;
     return b;
 }
 
@@ -336,6 +349,8 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
             nv[a] = vgrid->n[a];
             g.nv1[a] = vgrid->n[a];
             g.dxi[a] = (vgrid->hi[a] - vgrid->lo[a]) / (vgrid->n[a] - 1);
+            g.vlo[a] = vgrid->lo[a];
+            for (double x : nodes[a]) h->zero_node = h->zero_node || x == 0.0;
             g.n[a] = grid->n[a];
             g.bc[a][0] = grid->bc[a][0];
             g.bc[a][1] = grid->bc[a][1];
@@ -345,6 +360,7 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
             wts[a].assign(1, 1.0);
             g.nv1[a] = 1;
             g.dxi[a] = 1.0;
+            g.vlo[a] = 0.0;
             g.n[a] = 1;
             g.dx[a] = 1.0;
         }
@@ -358,6 +374,12 @@ int cdugks_create(const cdugks_grid* grid, const cdugks_vgrid* vgrid, const cdug
     h->Nv = (int)Nv;
     g.NVT = (int)((Nv + VC - 1) / VC);
     g.Nvp = g.NVT * VC;
+    // rows of the separable factor tables: axis 0 padded to whole chunks, then the other axes
+    g.xrow[0] = 0;
+    g.xrow[1] = (nv[0] + VC - 1) / VC * VC;
+    g.xrow[2] = g.xrow[1] + (D >= 2 ? nv[1] : 0);
+    g.xrows = g.xrow[2] + (D >= 3 ? nv[2] : 0);
+    g.xal = nv[0] % VC == 0;
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) g.fn[a][b] = g.n[b] + (a == b && a < D ? 1 : 0);
         g.nf[a] = (long long)g.fn[a][0] * g.fn[a][1] * g.fn[a][2];
@@ -478,6 +500,10 @@ int cdugks_set_tile(cdugks_t* h, int tile_id) {
         for (int a = 0; a < h->g.D; ++a)
             if (h->g.bc[a][0] == CDUGKS_BC_DIRICHLET || h->g.bc[a][1] == CDUGKS_BC_DIRICHLET)
                 return fail(CDUGKS_ERR_INVALID, "stored-slope shapes support periodic and specular boundaries only");
+    if (cdg::mode_lean(mode) && h->zero_node)
+        return fail(CDUGKS_ERR_INVALID, "lean shapes need a velocity grid without a node at xi = 0");
+    if (cdg::mode_lean(mode) && h->bound && h->initialised && !cdg::mode_lean(tile_mode(h->prec, h->g.D, h->g.tile_id)))
+        return fail(CDUGKS_ERR_INVALID, "select a lean shape before cdugks_init (its factor tables start there)");
     drop_graphs(h);
     const int need = buffers_of(mode);
     if (need & ~h->bufs_cap) {
@@ -948,6 +974,10 @@ int cdugks_set_state(cdugks_t* h, const void* host, size_t bytes) {
         if ((e = cudaMemcpyAsync(h->base + h->lay.cellc0, h->base + h->lay.cellc, h->cellc_bytes * g.Nc,
                                  cudaMemcpyDeviceToDevice, h->stream)))
             return cuda_fail(e, "copy constants");
+        if ((h->bufs_cap & BUF_XTAB) &&
+            (e = cudaMemcpyAsync(h->base + h->lay.xc0, h->base + h->lay.xc, h->elt * (size_t)g.xrows * g.Nc,
+                                 cudaMemcpyDeviceToDevice, h->stream)))
+            return cuda_fail(e, "copy factor tables");
     }
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "set_state");
     h->steps = hd.steps;
@@ -1394,6 +1424,7 @@ int noalloc_run(cdugks* h, const void* phi_in, void* phi_out, double* W, cudaStr
         return fail(CDUGKS_ERR_INVALID, msg);
     }
     Bufs<T> b;
+    std::memset(&b, 0, sizeof(b));      // no optional buffers (factor tables, Shakhov, force) on this path
     b.phi_in = static_cast<const T*>(phi_in);
     b.phi_out = static_cast<T*>(phi_out);
     b.phibar = nullptr;

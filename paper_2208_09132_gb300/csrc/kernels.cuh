@@ -86,6 +86,14 @@ struct Geo {
     int wait_log2;    // bounded waits give up after 2^wait_log2 tries
     int wait_test;    // test hook: sweep A issues no tensor copies, so its bounded wait runs out
     int nosrc;        // the b-source Z/tau_bg (g - g_eq) vanishes (Pr = 1, or the Shakhov model)
+    // Separable Maxwellian factors (the lean shapes): per cell or face and axis b the
+    // factors exp(-(xi_{b,k} - u_b)^2 / (2RT)) of every node k, formed in double; rows
+    // of a table: axis 0 at [0, xrow[1]) (nv1_0 rounded up to VC), axis b >= 1 at
+    // [xrow[b], xrow[b] + nv1_b); xrows rows in all.
+    double vlo[3];    // first velocity node per axis
+    int xrow[3];
+    int xrows;
+    int xal;          // nv1_0 is a multiple of VC: a chunk's four velocities share their other indices
 };
 
 template <typename T> struct CellC;
@@ -113,6 +121,10 @@ struct Bufs {
     double* qs;           // [G][NQ][Nc] raw velocity moments of phi* per velocity group
     double* qf[3];        // [G][NQ][nf_a] raw velocity moments of the face values per group
     T* force;             // acceleration only: force terms of the sources at t_n, state layout
+    // lean shapes only (null otherwise): separable Maxwellian factor tables, layout of xaddr()
+    T* xc;                // [rows][Nc] of W^n (written with the cell constants)
+    T* xc0;               // [rows][Nc] of W^0 (Dirichlet ghosts)
+    T* xf[3];             // [rows][nf_a] of the face W (written with the face constants)
 };
 
 // An instance as the kernels see it: geometry and both ping-pong orientations
@@ -376,6 +388,84 @@ __device__ __forceinline__ void make_face(const Geo& g, const double* W, const d
     f.al_g = A::div(T(1), A::add(T(1), A::mul(hh, r.itg)));
     f.al_b = A::div(T(1), A::add(T(1), A::mul(hh, r.itb)));
     f.gam_b = A::mul(A::mul(hh, r.itbg), f.al_b);
+}
+
+// ---- separable Maxwellian factors (lean shapes)
+//
+// The Maxwellian of eq. geq factorises over the velocity axes:
+//   g_eq(xi) = rho (2 pi RT)^{-D/2} prod_b exp(-(xi_b - u_b)^2 / (2RT)),
+// so one place (a cell or a face) needs only sum_b nv1_b factors, not one
+// exponential per velocity.  They are formed here in double for every node and
+// stored in the working precision; the prefactor is folded into the factors of
+// the last axis.  Per axis, from the node k* nearest u_b outward, the factors
+// follow from E[k+1] = E[k] r_k, r_{k+1} = r_k q (and likewise downward) with
+// r, s, q exponentials of the exact differences of the exponents, so the
+// relative error of every factor is a few hundred double roundings at most,
+// whatever c^2 / (2RT) is (high Mach).  Layout for n places:
+//   axis 0 rows r < xrow[1]: [r / VC][n][VC] (a chunk's four factors are one vector),
+//   rows r >= xrow[1]:       [r][n].
+__host__ __device__ __forceinline__ size_t xaddr(const Geo& g, long long n, int r, long long item) {
+    return r < g.xrow[1] ? ((size_t)(r / VC) * (size_t)n + (size_t)item) * VC + (size_t)(r % VC)
+                         : (size_t)r * (size_t)n + (size_t)item;
+}
+
+template <typename T>
+__device__ __forceinline__ void write_factors(const Geo& g, const Macro& m, T* __restrict__ X, long long n,
+                                              long long item) {
+    const double c = ddiv(0.5, m.RT);
+    // rho (2 pi RT)^{-D/2}
+    const double tp = dmul(2.0 * 3.14159265358979323846, m.RT);
+    const double pref = ddiv(m.rho, g.D == 2 ? tp : (g.D == 1 ? sqrt(tp) : dmul(tp, sqrt(tp))));
+    for (int b = 0; b < g.D; ++b) {
+        const int nb = g.nv1[b];
+        const double d = g.dxi[b], lo = g.vlo[b], ub = m.u[b];
+        const int r0 = g.xrow[b];
+        int ks = (int)rint((ub - lo) / d);
+        ks = ks < 0 ? 0 : (ks > nb - 1 ? nb - 1 : ks);
+        const double del = dsub(dadd(lo, dmul((double)ks, d)), ub);          // xi_{k*} - u_b
+        const double q = exp(-dmul(2.0 * c, dmul(d, d)));
+        double e0 = exp(-dmul(c, dmul(del, del)));
+        if (b == g.D - 1) e0 = dmul(e0, pref);
+        X[xaddr(g, n, r0 + ks, item)] = (T)e0;
+        if (ks + 1 < nb) {
+            double e = e0, r = exp(-dmul(c, dadd(dmul(2.0 * del, d), dmul(d, d))));
+            for (int k = ks + 1; k < nb; ++k) {
+                e = dmul(e, r);
+                r = dmul(r, q);
+                X[xaddr(g, n, r0 + k, item)] = (T)e;
+            }
+        }
+        if (ks > 0) {
+            double e = e0, s = exp(-dmul(c, dsub(dmul(d, d), dmul(2.0 * del, d))));
+            for (int k = ks - 1; k >= 0; --k) {
+                e = dmul(e, s);
+                s = dmul(s, q);
+                X[xaddr(g, n, r0 + k, item)] = (T)e;
+            }
+        }
+        if (b == 0)
+            for (int k = nb; k < g.xrow[1]; ++k) X[xaddr(g, n, k, item)] = T(0);   // padding of the last chunk
+    }
+}
+
+// g_eq from the factors of one velocity, in the one order every kernel uses:
+// x0 (x1 x2) in 3D, x0 x1 in 2D (the prefactor is inside x1 or x2).
+template <typename T, int D>
+__host__ __device__ __forceinline__ T lean_pair(T x1, T x2) {
+    return D == 3 ? x1 * x2 : x1;
+}
+template <typename T, int D>
+__host__ __device__ __forceinline__ T lean_geq(T x0, T x1, T x2) {
+    return x0 * lean_pair<T, D>(x1, x2);
+}
+
+// g_eq of velocity i at cell c from the cell factor table (lean shapes).
+template <typename T, int D>
+__device__ __forceinline__ T table_geq(const Geo& g, const T* __restrict__ X, long long c, int i) {
+    if (i >= g.nv1[0] * g.nv1[1] * g.nv1[2]) return T(0);
+    const int k0 = i % g.nv1[0], k1 = (i / g.nv1[0]) % g.nv1[1], k2 = i / (g.nv1[0] * g.nv1[1]);
+    const T x2 = D == 3 ? X[xaddr(g, g.Nc, g.xrow[2] + k2, c)] : T(1);
+    return lean_geq<T, D>(X[xaddr(g, g.Nc, k0, c)], X[xaddr(g, g.Nc, g.xrow[1] + k1, c)], x2);
 }
 
 // Per-lane velocity data of one tile.
@@ -680,9 +770,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 // Bit 6 (launch-time, not a tile shape): the instance has no b-source, so
 // sweep A and k_flux leave out Z = xi.u - u^2/2 and its terms (whose
 // coefficients are then exactly 0: the same results, fewer instructions).
+// Bit 7 (lean): the face-store shapes whose sweep A is lean.cuh's (D = 2, 3; the
+// two-time model, upwind-cell reconstruction, velocity grids without a node at
+// xi_a = 0): its cell equilibria are products of per-axis Maxwellian factors
+// formed in double, kept in tables of every cell.  Bit 8 (face tables): sweep B
+// is lean.cuh's as well and takes the face equilibria from factor tables of
+// every face; without it sweep B is k_flux (an FP32 exponential per point).
 enum {
     MODE_FUSED = 0, MODE_PREP = 1, MODE_STORED = 2, MODE_FACES = 4, MODE_R2 = 8, MODE_SK = 16, MODE_ACC = 32,
-    MODE_NOSRC = 64
+    MODE_NOSRC = 64, MODE_LEAN = 128, MODE_XF = 256
 };
 __host__ __device__ constexpr int mode_source(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool mode_faces(int mode) { return (mode & MODE_FACES) != 0; }
@@ -691,6 +787,8 @@ __host__ __device__ constexpr bool mode_sk(int mode) { return (mode & MODE_SK) !
 __host__ __device__ constexpr bool mode_acc(int mode) { return (mode & MODE_ACC) != 0; }
 __host__ __device__ constexpr bool mode_nosrc(int mode) { return (mode & (MODE_NOSRC | MODE_SK)) != 0; }
 __host__ __device__ constexpr int mode_halo(int mode) { return mode_r2(mode) ? 3 : 2; }
+__host__ __device__ constexpr bool mode_lean(int mode) { return (mode & MODE_LEAN) != 0; }
+__host__ __device__ constexpr bool mode_xf(int mode) { return (mode & MODE_XF) != 0; }
 
 template <typename T, int D, int T0, int T1, int T2, int MODE = MODE_FUSED>
 struct Smem {
@@ -1239,7 +1337,7 @@ __device__ __forceinline__ void own_state(const CellC<T>& own, const T (&xi)[VC]
 // Net flux sum_a (F(right face) - F(left face)) / dx_a of the owned cell (local
 // coordinates la) from the staged face fluxes FF[field * NFT + local face].
 template <typename T, int D, typename TL>
-__device__ __forceinline__ void net_flux(const Geo& g, const V4<T>* FF, const int la[3], T (&dFg)[VC], T (&dFb)[VC]) {
+__device__ __forceinline__ void net_flux(const T (&idxT)[3], const V4<T>* FF, const int la[3], T (&dFg)[VC], T (&dFb)[VC]) {
     constexpr int NFT = TL::NFT;
 #pragma unroll
     for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
@@ -1249,7 +1347,7 @@ __device__ __forceinline__ void net_flux(const Geo& g, const V4<T>* FF, const in
         const int fl1 = TL::face_local(a, la[0] + (a == 0), la[1] + (a == 1), la[2] + (a == 2));
         const V4<T> g0 = FF[0 * NFT + fl0], g1 = FF[0 * NFT + fl1];
         const V4<T> b0 = FF[1 * NFT + fl0], b1 = FF[1 * NFT + fl1];
-        const T idx = (T)g.idx[a];
+        const T idx = idxT[a];
 #pragma unroll
         for (int v = 0; v < VC; ++v) {
             dFg[v] = fma(idx, g1.v[v] - g0.v[v], dFg[v]);
@@ -1261,12 +1359,11 @@ __device__ __forceinline__ void net_flux(const Geo& g, const V4<T>* FF, const in
 // phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
 // (eq. phiupdate, the last factor deferred) of one cell chunk, stored at dst.
 template <typename T, int D, bool NOSRC = false>
-__device__ __forceinline__ void store_phi_star(const Geo& g, const T (&xi)[VC][D], const T (&u)[D], T hu2, T um_g,
+__device__ __forceinline__ void store_phi_star(T dt, const T (&xi)[VC][D], const T (&u)[D], T hu2, T um_g,
                                                T um_b, T usrc, const T (&og)[VC], const T (&ob)[VC],
                                                const T (&oge)[VC], const T (&obe)[VC], const T (&dFg)[VC],
                                                const T (&dFb)[VC], T* dst) {
     T ng[VC], nb[VC];
-    const T dt = (T)g.dt;
 #pragma unroll
     for (int v = 0; v < VC; ++v) {
         const T dg = og[v] - oge[v];
@@ -1350,6 +1447,10 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = TL::NT / 32;
     const T hL = (T)(0.5 * (3.0 - D + g.K));     // Shakhov: half the unresolved degrees of freedom
+    // constants of the chunk loop in the working precision, converted once (the
+    // conversions from double run on the FP64 pipe)
+    const T dtT = (T)g.dt;
+    const T idxT[3] = {(T)g.idx[0], (T)g.idx[1], (T)g.idx[2]};
     int org[3];
     tile_origin<TL, D>(g, tile, org);
     const int vt0 = grp * g.ntpg, vt1 = min(g.NVT, vt0 + g.ntpg);
@@ -1940,7 +2041,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
             // ---- phase 4: phi* = phi_eq + (1 - dt/2tau)(phi - phi_eq) [+ dt Z/tau_bg (g - g_eq)] - dt dF
             if (valid) {
                 T dFg[VC], dFb[VC];
-                net_flux<T, D, TL>(g, FF, la, dFg, dFb);
+                net_flux<T, D, TL>(idxT, FF, la, dFg, dFb);
                 T u[D], hu2;
                 if (PREP) {
 #pragma unroll
@@ -1957,7 +2058,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     for (int a = 0; a < D; ++a) u[a] = reinterpret_cast<const T*>(&CC[(a / 4) * BOX + kc])[a % 4];
                     hu2 = reinterpret_cast<const T*>(&CC[((D + 3) / 4) * BOX + kc])[(D + 3) % 4];
                 }
-                store_phi_star<T, D, NOSRC>(g, xi, u, hu2, um_g, um_b, usrc, og, ob, oge, obe, dFg, dFb,
+                store_phi_star<T, D, NOSRC>(dtT, xi, u, hu2, um_g, um_b, usrc, og, ob, oge, obe, dFg, dFb,
                                      bf.phi_out + phi_addr(g, cell_index(g, qa), vt * VC, 0));
             }
         }
@@ -2038,6 +2139,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
 
     const CellC<T> own = bf.cellc[cell_index(g, qa)];
     const T hL = (T)(0.5 * (3.0 - D + g.K));
+    const T dtT = (T)g.dt;                        // converted once, outside the chunk loop
+    const T idxT[3] = {(T)g.idx[0], (T)g.idx[1], (T)g.idx[2]};
     const size_t cell_ad = phi_addr(g, cell_index(g, qa), 0, 0);
     const size_t chunk_stride = (size_t)g.Nc * (2 * VC);
     bool own_right[3] = {false, false, false};
@@ -2169,7 +2272,7 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                     }
                 }
             }
-            const T idx = (T)g.idx[a];
+            const T idx = idxT[a];
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
                 dFg[v] = fma(idx, F[1][0].v[v] - F[0][0].v[v], dFg[v]);
@@ -2191,8 +2294,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
         T u[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = own.u[a];
-        store_phi_star<T, D, SK || NOSRC>(g, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg, dFb,
-                             bf.phi_out + ad);
+        store_phi_star<T, D, SK || NOSRC>(dtT, xi, u, own.hu2, own.um_g, own.um_b, own.usrc, og, ob, oge, obe, dFg,
+                                          dFb, bf.phi_out + ad);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -2392,6 +2495,7 @@ __device__ __forceinline__ void facec_body(const Geo& g, const Bufs<T>& bf, int 
     double q[3] = {0.0, 0.0, 0.0};
     if (g.shakhov) shakhov_heat_flux<T, D>(g, bf.qf[a], g.nf[a], f, W, 0.5 * g.h, q);
     make_face<T>(g, W, q, bf.facec[a][f]);
+    if (bf.xf[a]) write_factors<T>(g, macro_of(g, W), bf.xf[a], g.nf[a], f);
 }
 
 // grid (faces / blockDim, axes): every axis in one launch
@@ -2461,6 +2565,7 @@ __device__ __forceinline__ void wupdate_body(const Geo& g, const Bufs<T>& bf, lo
         for (int a = 0; a < D; ++a) bf.hq[(size_t)a * g.Nc + c] = hq[a];
     }
     make_cell<T>(g, W, hq, bf.cellc[c]);
+    if (bf.xc) write_factors<T>(g, macro_of(g, W), bf.xc, g.Nc, c);
 }
 
 template <typename T, int D>
@@ -2503,6 +2608,7 @@ __global__ void k_cellc(const Inst<T>* __restrict__ in, int cur) {
     if (g.shakhov)
         for (int a = 0; a < D; ++a) q[a] = bf.hq[(size_t)a * g.Nc + c];
     make_cell<T>(g, W, q, bf.cellc[c]);
+    if (bf.xc) write_factors<T>(g, macro_of(g, W), bf.xc, g.Nc, c);
 }
 
 // Maxwell-Boltzmann initial state: W^0 from (rho, u, T), its constants (also
@@ -2531,13 +2637,23 @@ __global__ void k_init(const Inst<T>* __restrict__ in, int cur, const double* __
         make_cell<T>(g, Wc, nullptr, shc);
         bf.cellc[c] = shc;
         bf.cellc0[c] = shc;
+        if (bf.xc) {              // lean shapes: the separable factors of W^0
+            const Macro m0 = macro_of(g, Wc);
+            write_factors<T>(g, m0, bf.xc, g.Nc, c);
+            write_factors<T>(g, m0, bf.xc0, g.Nc, c);
+        }
     }
     __syncthreads();
     const CellC<T> cc = shc;
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(g, cc, v, ge, be);
+        if (bf.xc) {              // the equilibrium as the lean sweeps form it: the product of the factors
+            ge = table_geq<T, D>(g, bf.xc, c, i);
+            be = (v.hxi2 + cc.eb) * ge;
+        } else {
+            equilibrium<T, D>(g, cc, v, ge, be);
+        }
         const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = ge;
         bf.phi_out[ad + VC] = be;
@@ -2586,7 +2702,12 @@ __global__ void __launch_bounds__(kStressThreads) k_stress(const Inst<T>* __rest
     for (int i = t; i < g.Nvp; i += kStressThreads) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(g, cc, v, ge, be);
+        if (bf.xc) {
+            ge = table_geq<T, D>(g, bf.xc, c, i);
+            be = (v.hxi2 + cc.eb) * ge;
+        } else {
+            equilibrium<T, D>(g, cc, v, ge, be);
+        }
         const size_t ad = phi_addr(g, c, i, 0);
         const double gv = (double)fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
         const double bv = (double)fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);
@@ -2649,7 +2770,12 @@ __global__ void k_finalise(const Inst<T>* __restrict__ in, int cur) {
     for (int i = threadIdx.x; i < g.Nvp; i += blockDim.x) {
         const Vel<T, D> v = load_vel<T, D>(g, bf, i);
         T ge, be;
-        equilibrium<T, D>(g, cc, v, ge, be);
+        if (bf.xc) {
+            ge = table_geq<T, D>(g, bf.xc, c, i);
+            be = (v.hxi2 + cc.eb) * ge;
+        } else {
+            equilibrium<T, D>(g, cc, v, ge, be);
+        }
         const size_t ad = phi_addr(g, c, i, 0);
         bf.phi_out[ad] = fma(cc.fa_g, bf.phi_in[ad], cc.fb_g * ge);
         bf.phi_out[ad + VC] = fma(cc.fa_b, bf.phi_in[ad + VC], cc.fb_b * be);

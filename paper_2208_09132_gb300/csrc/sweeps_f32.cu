@@ -16,10 +16,12 @@ using Table32 = ShapeTable<
               Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>,
               Shape<float, 2, 32, 16, 1>, Shape<float, 2, 32, 8, 1, FF>, Shape<float, 2, 32, 16, 1, FF>,
               Shape<float, 2, 32, 8, 1, SF>, Shape<float, 2, 16, 8, 1, FG>, Shape<float, 2, 32, 8, 1, FFS>,
-              Shape<float, 2, 32, 8, 1, PFA>>,
+              Shape<float, 2, 32, 8, 1, PFA>, LeanShape<float, 2, 32, 8, 1>, LeanShape<float, 2, 32, 16, 1>,
+              LeanShape<float, 2, 32, 8, 1, false>>,
     ShapeList<Shape<float, 3, 8, 4, 4>, Shape<float, 3, 8, 8, 4, MODE_PREP>, Shape<float, 3, 8, 8, 4, MODE_STORED>,
               Shape<float, 3, 8, 4, 4, MODE_STORED>, Shape<float, 3, 8, 8, 4, SF>, Shape<float, 3, 8, 4, 4, SF>,
-              Shape<float, 3, 8, 8, 4, SFS>, Shape<float, 3, 8, 4, 4, PFA>>>;
+              Shape<float, 3, 8, 8, 4, SFS>, Shape<float, 3, 8, 4, 4, PFA>, LeanShape<float, 3, 8, 8, 4>,
+              LeanShape<float, 3, 8, 4, 4>, LeanShape<float, 3, 8, 8, 4, false>>>;
 }
 
 int tile_count_f32(int D) { return Table32::count(D); }

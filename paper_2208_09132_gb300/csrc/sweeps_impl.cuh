@@ -5,6 +5,7 @@
 #include <utility>
 
 #include "launch.cuh"
+#include "lean.cuh"
 
 namespace cdg {
 
@@ -241,6 +242,103 @@ struct Shape {
                 return launch_pdl(k_sweep_batch<T, D, TX, TY, TZ, true, MODE>, dim3(n), dim3(TL::NT), SM::bytes(true), s,
                                   items, insts, cur);
         }
+    }
+
+    static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }
+};
+
+// A lean shape (lean.cuh): sweep A k_lsweep, face constants (with the face
+// factor tables when XF), sweep B k_lflux (XF) or k_flux, W update (with the
+// cell factor tables).  Single instances take the sweeps without the b-source
+// terms when the instance has none (Pr = 1); batched launches keep the general
+// ones.
+template <typename T, int D, int TX, int TY, int TZ, bool XF = true>
+struct LeanShape {
+    using LA = LeanA<T, D, TX, TY, TZ>;
+    using LB = LeanB<T, D, TX, TY, TZ>;
+    using FS = FluxSmem<T, D, TX, TY, TZ>;
+    using TL = Tile<D, TX, TY, TZ>;
+    static constexpr int mode = MODE_LEAN | MODE_FACES | (XF ? MODE_XF : 0);
+    static constexpr size_t b_bytes = XF ? LB::bytes : FS::bytes;
+    static size_t smem_bytes() { return LA::bytes > b_bytes ? LA::bytes : b_bytes; }
+
+    static cudaError_t configure() {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_lsweep<T, D, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)LA::bytes)) ||
+            (e = cudaFuncSetAttribute(k_lsweep<T, D, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)LA::bytes)) ||
+            (e = cudaFuncSetAttribute(k_lsweep_batch<T, D, TX, TY, TZ, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LA::bytes)))
+            return e;
+        if constexpr (XF) {
+            if ((e = cudaFuncSetAttribute(k_lflux<T, D, TX, TY, TZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)LB::bytes)) ||
+                (e = cudaFuncSetAttribute(k_lflux<T, D, TX, TY, TZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)LB::bytes)) ||
+                (e = cudaFuncSetAttribute(k_lflux_batch<T, D, TX, TY, TZ, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB::bytes)))
+                return e;
+        } else {
+            if ((e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, false, false, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::bytes)) ||
+                (e = cudaFuncSetAttribute(k_flux<T, D, TX, TY, TZ, false, false, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::bytes)) ||
+                (e = cudaFuncSetAttribute(k_flux_batch<T, D, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)FS::bytes)))
+                return e;
+        }
+        done = true;
+        return cudaSuccess;
+    }
+
+    static cudaError_t step(const Geo& g, const Inst<T>* in, int cur, cudaStream_t s, cudaEvent_t* ev, const void*) {
+        cudaError_t e = configure();
+        if (e) return e;
+        const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
+        if (ev) cudaEventRecord(ev[0], s);
+        if (g.nosrc) e = launch_pdl(k_lsweep<T, D, TX, TY, TZ, true>, grid, dim3(TL::NT), LA::bytes, s, in, cur);
+        else e = launch_pdl(k_lsweep<T, D, TX, TY, TZ, false>, grid, dim3(TL::NT), LA::bytes, s, in, cur);
+        if (e) return e;
+        if (ev) cudaEventRecord(ev[1], s);
+        {
+            long long nf = 0;
+            for (int a = 0; a < D; ++a) nf = g.nf[a] > nf ? g.nf[a] : nf;
+            const dim3 fgrid((unsigned)((nf + kSmallBlock - 1) / kSmallBlock), (unsigned)D);
+            if ((e = launch_pdl(k_facec<T, D>, fgrid, dim3(kSmallBlock), 0, s, in, cur))) return e;
+        }
+        if (ev) cudaEventRecord(ev[2], s);
+        if constexpr (XF) {
+            if (g.nosrc) e = launch_pdl(k_lflux<T, D, TX, TY, TZ, true>, grid, dim3(TL::NT), LB::bytes, s, in, cur);
+            else e = launch_pdl(k_lflux<T, D, TX, TY, TZ, false>, grid, dim3(TL::NT), LB::bytes, s, in, cur);
+        } else {
+            if (g.nosrc) e = launch_pdl(k_flux<T, D, TX, TY, TZ, false, false, true>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+            else e = launch_pdl(k_flux<T, D, TX, TY, TZ, false, false, false>, grid, dim3(TL::NT), FS::bytes, s, in, cur);
+        }
+        if (e) return e;
+        if (ev) cudaEventRecord(ev[3], s);
+        if ((e = launch_pdl(k_wupdate<T, D>, dim3((unsigned)((g.Nc + kSmallBlock - 1) / kSmallBlock)), dim3(kSmallBlock),
+                            0, s, in, cur)))
+            return e;
+        if (ev) cudaEventRecord(ev[4], s);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
+                                   cudaStream_t s) {
+        cudaError_t e = configure();
+        if (e) return e;
+        if (n <= 0) return cudaSuccess;
+        if (!B)
+            return launch_pdl(k_lsweep_batch<T, D, TX, TY, TZ, false>, dim3(n), dim3(TL::NT), LA::bytes, s, items, insts,
+                              cur);
+        if constexpr (XF)
+            return launch_pdl(k_lflux_batch<T, D, TX, TY, TZ, false>, dim3(n), dim3(TL::NT), LB::bytes, s, items, insts,
+                              cur);
+        else
+            return launch_pdl(k_flux_batch<T, D, TX, TY, TZ>, dim3(n), dim3(TL::NT), FS::bytes, s, items, insts, cur);
     }
 
     static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }

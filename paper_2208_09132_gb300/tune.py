@@ -65,7 +65,7 @@ def default_choice(cfg, precision):
         if not mode & 4:
             continue
         cells = int(np.prod(dims[:D]))
-        pref = (mode & 3 == 0, cells if cells <= wl.ncells(cfg) else -cells)
+        pref = (bool(mode & 128), mode & 3 == 0, cells if cells <= wl.ncells(cfg) else -cells)
         if best is None or pref > best[0]:
             best = (pref, t)
     return (best[1] if best else 0), 0
@@ -112,6 +112,15 @@ def size_key(cfg, precision, context):
             f"{recon}{coll}")
 
 
+def has_zero_node(cfg):
+    """Some active axis of the velocity grid has a node at xi = 0."""
+    for a in range(cfg["dim"]):
+        n, lo, hi = cfg["nv"][a], cfg["vlo"][a], cfg["vhi"][a]
+        if any(lo + (hi - lo) * k / (n - 1) == 0.0 for k in range(n)):
+            return True
+    return False
+
+
 def candidates(cfg, precision, context="alone"):
     nt = cdugks.load().cdugks_tile_count(precision, cfg["dim"])
     nvt = (wl.nvel(cfg) + 3) // 4
@@ -121,8 +130,11 @@ def candidates(cfg, precision, context="alone"):
     sk = bool(cfg.get("collision", 0))
     ac = any(cfg.get("accel", (0.0, 0.0, 0.0)))
     tiles = []
+    zero = has_zero_node(cfg)
     for t in range(nt):
         mode = cdugks.tile_shape(precision, cfg["dim"], t)[1]
+        if mode & 128 and zero:
+            continue                      # lean shapes need a velocity grid without a node at 0
         if bool(mode & 8) != r2 or bool(mode & 16) != sk or bool(mode & 32) != ac:
             continue                      # shapes of another reconstruction, collision or force compute another scheme
         if context != "alone" and sk:

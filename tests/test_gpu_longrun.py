@@ -55,11 +55,12 @@ def solve(cfg, f, steps, precision, tile=None, groups=0):
 
 
 def bench_tile(precision, D):
-    """The sweep mode the bench's tuned 2D and 3D launches use: fused face store
-    in 2D, stored slopes with face store in 3D (and any lean shape present)."""
+    """The face-store shapes the bench's 2D and 3D launches use: fused face
+    store in 2D, stored slopes with face store in 3D, and the lean shapes."""
     mode = 4 if D == 2 else 6
     nt = cdugks.load().cdugks_tile_count(precision, D)
-    return [t for t in range(nt) if cdugks.tile_shape(precision, D, t)[1] == mode][:1]
+    modes = [cdugks.tile_shape(precision, D, t)[1] for t in range(nt)]
+    return [t for t in range(nt) if modes[t] == mode][:1] + [t for t in range(nt) if modes[t] & 128]
 
 
 def check_against(oracle_mod, name, cfg, f, steps, tiles):
@@ -92,7 +93,14 @@ def test_shear3d_physics_100_steps(oracle_mod, kn, n):
 
 def test_batched_members_2000_steps(oracle_mod):
     """Three members of the batched workload (one per velocity count, the
-    smallest grids of each) stepped together in one batch for 2000 steps."""
+    smallest grids of each) stepped together in one batch for 2000 steps.
+
+    The thermoacoustic wave is a gas at rest whose only velocity is the slow
+    flow that conduction drives (|u| of order 1e-6 of the thermal speed), so a
+    relative velocity error against max |u| would measure FP32 rounding of a
+    quantity a million times below the problem's speed scale: the velocity
+    error is taken relative to the thermal speed sqrt(R T_ref) instead (rho
+    and T as everywhere)."""
     probs = wl.workload_c4()
     pick = {}
     for cfg, f in probs:
@@ -115,11 +123,15 @@ def test_batched_members_2000_steps(oracle_mod):
         o = oracle_mod.Oracle(cfg)
         o.init(f)
         o.step(steps)
-        err = rel_linf(s.moments(), o.moments())
+        got, ref = s.moments(), o.moments()
+        err = rel_linf(got, ref)
+        umax = np.abs(ref[:, 1]).max()
+        uerr = np.abs(got[:, 1] - ref[:, 1]).max()
+        err[1] = uerr / math.sqrt(cfg["R"] * cfg["T_ref"])
         dr = drift(c0, s.conserved())
         print(f"\n[longrun] batched member {cfg['name']} Kn-mu {cfg['mu_ref']:.2e} Pr {cfg['Pr']:.3f} "
-              f"({steps} steps): rel Linf rho,u,T = {', '.join(f'{e:.2e}' for e in err)}; "
-              f"drift = {', '.join(f'{d:.1e}' for d in dr)}")
+              f"({steps} steps): rel Linf rho,u(thermal speed),T = {', '.join(f'{e:.2e}' for e in err)}; "
+              f"max|u| {umax:.2e}, max|du| {uerr:.2e}; drift = {', '.join(f'{d:.1e}' for d in dr)}")
         assert np.all(err <= TOL), (cfg["name"], err)
         assert np.all(dr <= DRIFT), (cfg["name"], dr)
 
