@@ -365,6 +365,30 @@ CDUGKS_API int cdugks_batch_sync(cdugks_batch_t *b);
 CDUGKS_API int cdugks_batch_admit(cdugks_batch_t *b, cdugks_t *member);
 CDUGKS_API int cdugks_batch_retire(cdugks_batch_t *b, cdugks_t *member);
 CDUGKS_API void cdugks_batch_destroy(cdugks_batch_t *b);
+/* Persistent batched step (on = 1; 0 returns to one launch per kernel).  Every
+ * phase of every member -- sweep A, face constants, sweep B, W update, the
+ * steps of Sec. 2.1 -- for all the steps of one cdugks_batch_step call (or of
+ * one captured graph) runs in ONE launch: CTAs take work items from a device
+ * list in dependency order and wait, per member, for the items an item needs
+ * (bounded waits; a wait that gives up stops the launch and the next
+ * cdugks_batch_sync reports CDUGKS_ERR_TIMEOUT).  All members must share one
+ * tile shape that has this step (fused face-store shapes: 1D 64/128/256 and
+ * 2D 32 x 8 in FP32, 1D 64 in FP64).  max_members / max_items reserve room in
+ * the batch workspace (at least the current sizes; items are the batch's work
+ * items per step): while later cdugks_batch_admit / cdugks_batch_retire calls
+ * of members of that shape fit, they rewrite the device tables in place and
+ * keep the binding and any captured graph; otherwise they unbind as usual.
+ * Results equal the per-kernel launches bit for bit.  Unbinds the batch (query
+ * the workspace size and bind again).  Errors: INVALID (several shapes, a shape
+ * without it, more than 1024 members). */
+CDUGKS_API int cdugks_batch_set_persistent(cdugks_batch_t *b, int on, int max_members, long long max_items);
+/* 1 if the batch is bound (after admit / retire: whether to bind again). */
+CDUGKS_API int cdugks_batch_bound(const cdugks_batch_t *b);
+/* Testing hook for the persistent step's bounded waits (on = 1; 0 restores):
+ * the first face item waits for one item more than exists and every wait gives
+ * up after 2^12 polls, so a step stops early and cdugks_batch_sync reports
+ * CDUGKS_ERR_TIMEOUT; nothing faults or hangs.  Drops a captured graph. */
+CDUGKS_API int cdugks_batch_test_wait_timeout(cdugks_batch_t *b, int on);
 
 CDUGKS_API void cdugks_destroy(cdugks_t *h);
 CDUGKS_API const char *cdugks_strerror(int code);

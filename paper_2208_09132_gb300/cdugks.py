@@ -29,6 +29,7 @@ EXPORTS = [
     "cdugks_mu_from_kn", "cdugks_step_noalloc", "cdugks_tile_count", "cdugks_set_tile", "cdugks_tile_shape", "cdugks_cell_distributions",
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
     "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy", "cdugks_batch_admit", "cdugks_batch_retire",
+    "cdugks_batch_set_persistent", "cdugks_batch_bound", "cdugks_batch_test_wait_timeout",
 ]
 
 
@@ -120,6 +121,9 @@ def load(build_if_needed: bool = True):
         "cdugks_batch_admit": (i, [vp, vp]),
         "cdugks_batch_retire": (i, [vp, vp]),
         "cdugks_batch_destroy": (None, [vp]),
+        "cdugks_batch_set_persistent": (i, [vp, i, i, ctypes.c_longlong]),
+        "cdugks_batch_bound": (i, [vp]),
+        "cdugks_batch_test_wait_timeout": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,7 +301,8 @@ class Solver:
 class Batch:
     """Many Solvers stepped together in one launch per kernel (see include/cdugks.h)."""
 
-    def __init__(self, solvers, stream=None, device: str = "cuda:0"):
+    def __init__(self, solvers, stream=None, device: str = "cuda:0", persistent: bool = False, max_members: int = 0,
+                 max_items: int = 0):
         import torch
 
         self._lib = load()
@@ -306,6 +311,8 @@ class Batch:
         h = ctypes.c_void_p()
         _check(self._lib.cdugks_batch_create(arr, len(self.members), ctypes.byref(h)))
         self._h = h
+        if persistent:        # one launch per step call or graph (cdugks_batch_set_persistent)
+            _check(self._lib.cdugks_batch_set_persistent(h, 1, int(max_members), int(max_items)))
         self._dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self._dev)
         self._ws = None
@@ -326,16 +333,22 @@ class Batch:
                                            ctypes.c_void_p(self.stream.cuda_stream)))
 
     def admit(self, solver):
-        """Add a member between steps (drops a captured graph)."""
+        """Add a member between steps (a persistent batch with room keeps its
+        binding and graph; otherwise the tables are bound again)."""
         _check(self._lib.cdugks_batch_admit(self._h, solver._h))
         self.members.append(solver)
-        self._bind()
+        if not self._lib.cdugks_batch_bound(self._h):
+            self._bind()
 
     def retire(self, solver):
-        """Remove a member between steps; it keeps its state (drops a captured graph)."""
+        """Remove a member between steps; it keeps its state (as for admit)."""
         _check(self._lib.cdugks_batch_retire(self._h, solver._h))
         self.members.remove(solver)
-        self._bind()
+        if not self._lib.cdugks_batch_bound(self._h):
+            self._bind()
+
+    def test_wait_timeout(self, on: bool):
+        _check(self._lib.cdugks_batch_test_wait_timeout(self._h, 1 if on else 0))
 
     def __del__(self):
         h = getattr(self, "_h", None)

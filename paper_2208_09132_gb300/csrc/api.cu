@@ -15,6 +15,7 @@
 
 #include "../../include/cdugks.h"
 #include "launch.cuh"
+#include "persist.cuh"
 
 using cdg::BatchPlan;
 using cdg::Bufs;
@@ -23,6 +24,9 @@ using cdg::FaceC;
 using cdg::Geo;
 using cdg::Inst;
 using cdg::Item;
+using cdg::PHead;
+using cdg::PItem;
+using cdg::PState;
 using cdg::RItem;
 using cdg::VC;
 
@@ -1046,6 +1050,14 @@ struct cdugks_batch {
     cudaGraphExec_t exec;
     int graph_steps;
     long long steps;
+    // the persistent step (cdugks_batch_set_persistent): one launch per call or graph
+    bool pers;
+    int pcap_mem;                              // members and items per step the workspace holds
+    long long pcap_items;
+    std::vector<PItem> pitems;
+    std::vector<int> pper;                     // [member][4] items of each kind per step
+    size_t off_phead, off_pitems, off_pstate;
+    int wait_log2, test_hook;
 };
 
 namespace {
@@ -1078,7 +1090,22 @@ BatchPlan plan_of(const cdugks_batch* b) {
     return p;
 }
 
+// nsteps persistent steps in one launch (the counters are cleared first).
+cudaError_t batch_persist_launch(cdugks_batch* b, int nsteps) {
+    const PHead* h = reinterpret_cast<const PHead*>(b->base + b->off_phead);
+    const PItem* it = reinterpret_cast<const PItem*>(b->base + b->off_pitems);
+    PState* st = reinterpret_cast<PState*>(b->base + b->off_pstate);
+    int* cur = reinterpret_cast<int*>(b->base + b->off_cur);
+    const int tile = b->tile_ids[0];
+    if (b->prec == CDUGKS_FP32)
+        return cdg::launch_batch_persist_f32(b->D, tile, h, it, reinterpret_cast<const Inst<float>*>(b->base + b->off_insts),
+                                             cur, st, nsteps, b->wait_log2, b->test_hook, b->stream);
+    return cdg::launch_batch_persist_f64(b->D, tile, h, it, reinterpret_cast<const Inst<double>*>(b->base + b->off_insts),
+                                         cur, st, nsteps, b->wait_log2, b->test_hook, b->stream);
+}
+
 cudaError_t batch_launch(cdugks_batch* b) {
+    if (b->pers) return batch_persist_launch(b, 1);
     const BatchPlan p = plan_of(b);
     int* cur = reinterpret_cast<int*>(b->base + b->off_cur);
     if (b->prec == CDUGKS_FP32)
@@ -1167,18 +1194,85 @@ int batch_plan(cdugks_batch* b) {
     if (b->prec == CDUGKS_FP32) fill_insts<float>(b);
     else fill_insts<double>(b);
     b->cur.assign(n, 0);
+    if (b->pers) {
+        // one list per step: every member's sweep A items, then the face, sweep B and W items
+        if (b->tile_ids.size() != 1) return fail(CDUGKS_ERR_INVALID, "a persistent batch needs one tile shape");
+        b->pitems.clear();
+        b->pper.assign((size_t)n * 4, 0);
+        for (const Item& x : b->sweep_items[0]) {
+            b->pitems.push_back(PItem{x.inst, cdg::PK_A, x.tile, x.grp, 0, 0});
+            ++b->pper[(size_t)x.inst * 4 + cdg::PK_A];
+        }
+        for (const RItem& x : b->face_items) {
+            b->pitems.push_back(PItem{x.inst, cdg::PK_F, x.axis, 0, x.start, x.count});
+            ++b->pper[(size_t)x.inst * 4 + cdg::PK_F];
+        }
+        for (const Item& x : b->sweep_items[0]) {
+            b->pitems.push_back(PItem{x.inst, cdg::PK_B, x.tile, x.grp, 0, 0});
+            ++b->pper[(size_t)x.inst * 4 + cdg::PK_B];
+        }
+        for (const RItem& x : b->cell_items) {
+            b->pitems.push_back(PItem{x.inst, cdg::PK_W, 0, 0, x.start, x.count});
+            ++b->pper[(size_t)x.inst * 4 + cdg::PK_W];
+        }
+        if (n > b->pcap_mem || (long long)b->pitems.size() > b->pcap_items)
+            return fail(CDUGKS_ERR_INVALID, "the persistent batch holds more members or items than reserved");
+    }
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off = align_up(off + bytes);
         return o;
     };
+    if (b->pers) {
+        // room for the reserved member and item capacity, at offsets that do not
+        // depend on the members: a membership change rewrites the tables in place
+        const size_t inst_bytes = b->prec == CDUGKS_FP32 ? sizeof(Inst<float>) : sizeof(Inst<double>);
+        b->off_insts = take(inst_bytes * (size_t)b->pcap_mem);
+        b->off_cur = take(sizeof(int) * (size_t)b->pcap_mem);
+        b->off_phead = take(sizeof(PHead));
+        b->off_pitems = take(sizeof(PItem) * (size_t)b->pcap_items);
+        b->off_pstate = take(sizeof(PState));
+        b->total = off;
+        return CDUGKS_OK;
+    }
     b->off_insts = take(b->insts.size());
     b->off_cur = take(sizeof(int) * n);
     for (size_t k = 0; k < b->sweep_items.size(); ++k) b->off_sweep[k] = take(sizeof(Item) * b->sweep_items[k].size());
     b->off_face = take(sizeof(RItem) * b->face_items.size());
     b->off_cell = take(sizeof(RItem) * b->cell_items.size());
     b->total = off;
+    return CDUGKS_OK;
+}
+
+// The persistent plan's device tables (instance table, parities, head, items).
+cudaError_t batch_upload_persist(cdugks_batch* b) {
+    PHead* hd = new (std::nothrow) PHead;
+    if (!hd) return cudaErrorMemoryAllocation;
+    std::memset(hd, 0, sizeof(PHead));
+    hd->nmem = (int)b->mem.size();
+    hd->nitems = (int)b->pitems.size();
+    for (size_t m = 0; m < b->mem.size(); ++m)
+        for (int k = 0; k < 4; ++k) hd->per[m][k] = b->pper[m * 4 + k];
+    cudaError_t e = cudaMemcpyAsync(b->base + b->off_phead, hd, sizeof(PHead), cudaMemcpyHostToDevice, b->stream);
+    if (!e) e = cudaMemcpyAsync(b->base + b->off_pitems, b->pitems.data(), sizeof(PItem) * b->pitems.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+    if (!e) e = cudaStreamSynchronize(b->stream);      // (the host copies are pageable: staged before return)
+    delete hd;
+    return e;
+}
+
+// A persistent batch that is bound: rewrite its device tables for the current
+// members in place (the binding and any captured graph stay valid).
+int batch_rewrite_in_place(cdugks_batch* b) {
+    cudaError_t e;
+    for (size_t i = 0; i < b->mem.size(); ++i) b->cur[i] = b->mem[i]->cur;
+    if ((e = cudaMemcpyAsync(b->base + b->off_insts, b->insts.data(), b->insts.size(), cudaMemcpyHostToDevice,
+                             b->stream)) ||
+        (e = cudaMemcpyAsync(b->base + b->off_cur, b->cur.data(), sizeof(int) * b->cur.size(), cudaMemcpyHostToDevice,
+                             b->stream)) ||
+        (e = batch_upload_persist(b)))
+        return cuda_fail(e, "rewrite persistent plan");
     return CDUGKS_OK;
 }
 
@@ -1219,6 +1313,15 @@ int cdugks_batch_admit(cdugks_batch_t* b, cdugks_t* member) {
         return fail(CDUGKS_ERR_INVALID, "already a member");
     const cudaError_t e = cudaStreamSynchronize(member->stream);   // its own work lands before the batch's
     if (e) return cuda_fail(e, "member sync before admission");
+    if (b->pers && b->bound && b->tile_ids.size() == 1 && member->g.tile_id == b->tile_ids[0]) {
+        // a persistent batch rewrites its tables in place if they fit
+        const cudaError_t e2 = cudaStreamSynchronize(b->stream);
+        if (e2) return cuda_fail(e2, "batch sync before admission");
+        b->mem.push_back(member);
+        if (batch_plan(b) == CDUGKS_OK) return batch_rewrite_in_place(b);
+        b->mem.pop_back();
+        batch_plan(b);
+    }
     if ((rc = batch_unbind(b))) return rc;
     b->mem.push_back(member);
     if ((rc = batch_plan(b))) {
@@ -1234,6 +1337,15 @@ int cdugks_batch_retire(cdugks_batch_t* b, cdugks_t* member) {
     const auto it = std::find(b->mem.begin(), b->mem.end(), member);
     if (it == b->mem.end()) return fail(CDUGKS_ERR_INVALID, "not a member");
     if (b->mem.size() == 1) return fail(CDUGKS_ERR_INVALID, "a batch needs at least one member");
+    if (b->pers && b->bound) {
+        // a persistent batch rewrites its tables in place
+        const cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e) return cuda_fail(e, "batch sync before retirement");
+        b->mem.erase(it);
+        const int rc = batch_plan(b);
+        if (rc) return rc;
+        return batch_rewrite_in_place(b);
+    }
     int rc = batch_unbind(b);
     if (rc) return rc;
     b->mem.erase(it);
@@ -1260,15 +1372,17 @@ int cdugks_batch_bind(cdugks_batch_t* b, void* device_ptr, size_t bytes, void* c
         (e = cudaMemcpyAsync(b->base + b->off_cur, b->cur.data(), sizeof(int) * b->cur.size(),
                              cudaMemcpyHostToDevice, b->stream)))
         return cuda_fail(e, "upload batch tables");
-    for (size_t k = 0; k < b->sweep_items.size(); ++k)
+    for (size_t k = 0; k < b->sweep_items.size() && !b->pers; ++k)
         if ((e = cudaMemcpyAsync(b->base + b->off_sweep[k], b->sweep_items[k].data(),
                                  sizeof(Item) * b->sweep_items[k].size(), cudaMemcpyHostToDevice, b->stream)))
             return cuda_fail(e, "upload sweep items");
-    if ((e = cudaMemcpyAsync(b->base + b->off_face, b->face_items.data(), sizeof(RItem) * b->face_items.size(),
-                             cudaMemcpyHostToDevice, b->stream)) ||
-        (e = cudaMemcpyAsync(b->base + b->off_cell, b->cell_items.data(), sizeof(RItem) * b->cell_items.size(),
-                             cudaMemcpyHostToDevice, b->stream)))
+    if (!b->pers &&
+        ((e = cudaMemcpyAsync(b->base + b->off_face, b->face_items.data(), sizeof(RItem) * b->face_items.size(),
+                              cudaMemcpyHostToDevice, b->stream)) ||
+         (e = cudaMemcpyAsync(b->base + b->off_cell, b->cell_items.data(), sizeof(RItem) * b->cell_items.size(),
+                              cudaMemcpyHostToDevice, b->stream))))
         return cuda_fail(e, "upload range items");
+    if (b->pers && (e = batch_upload_persist(b))) return cuda_fail(e, "upload persistent plan");
     // members' own streams may still be working on their state
     for (cdugks* m : b->mem)
         if ((e = cudaStreamSynchronize(m->stream))) return cuda_fail(e, "member stream");
@@ -1276,6 +1390,7 @@ int cdugks_batch_bind(cdugks_batch_t* b, void* device_ptr, size_t bytes, void* c
     b->bound = true;
     return CDUGKS_OK;
 }
+
 
 int cdugks_batch_capture(cdugks_batch_t* b, int steps_per_graph) {
     if (!b || !b->bound) return fail(CDUGKS_ERR_UNBOUND, "batch not bound");
@@ -1285,7 +1400,9 @@ int cdugks_batch_capture(cdugks_batch_t* b, int steps_per_graph) {
     if (!b->stream) return fail(CDUGKS_ERR_INVALID, "graph capture needs a non-default stream");
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e) return cuda_fail(e, "cudaStreamBeginCapture");
-    for (int s = 0; s < steps_per_graph && e == cudaSuccess; ++s) e = batch_launch(b);
+    if (b->pers) e = batch_persist_launch(b, steps_per_graph);
+    else
+        for (int s = 0; s < steps_per_graph && e == cudaSuccess; ++s) e = batch_launch(b);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
     if (e || e2) {
@@ -1311,9 +1428,53 @@ int cdugks_batch_step(cdugks_batch_t* b, int nsteps) {
     if (b->exec)
         for (; done + b->graph_steps <= nsteps; done += b->graph_steps)
             if ((e = cudaGraphLaunch(b->exec, b->stream))) return cuda_fail(e, "cudaGraphLaunch");
+    if (b->pers && done < nsteps) {
+        if ((e = batch_persist_launch(b, nsteps - done))) return cuda_fail(e, "persistent batch step launch");
+        done = nsteps;
+    }
     for (; done < nsteps; ++done)
         if ((e = batch_launch(b))) return cuda_fail(e, "batch step launch");
     batch_advance_host(b, nsteps);
+    return CDUGKS_OK;
+}
+
+int cdugks_batch_set_persistent(cdugks_batch_t* b, int on, int max_members, long long max_items) {
+    if (!b) return fail(CDUGKS_ERR_INVALID, "null batch");
+    int rc = batch_unbind(b);
+    if (rc) return rc;
+    if (on) {
+        if (b->tile_ids.size() != 1) return fail(CDUGKS_ERR_INVALID, "a persistent batch needs one tile shape");
+        const bool ok = b->prec == CDUGKS_FP32 ? cdg::batch_persistent_f32(b->D, b->tile_ids[0])
+                                               : cdg::batch_persistent_f64(b->D, b->tile_ids[0]);
+        if (!ok) return fail(CDUGKS_ERR_INVALID, "this tile shape has no persistent batched step");
+        const int pcap = std::max((int)b->mem.size(), max_members);
+        if (pcap > cdg::kPMaxMembers) return fail(CDUGKS_ERR_INVALID, "too many members for a persistent batch");
+        b->pers = true;
+        b->pcap_mem = pcap;
+        b->pcap_items = (long long)1 << 40;           // first the current list, then its size sets the room
+        b->wait_log2 = b->wait_log2 ? b->wait_log2 : 26;
+        rc = batch_plan(b);
+        if (rc == CDUGKS_OK) {
+            b->pcap_items = std::max((long long)b->pitems.size(), max_items);
+            rc = batch_plan(b);
+        }
+        if (rc) {
+            b->pers = false;
+            batch_plan(b);
+        }
+        return rc;
+    }
+    b->pers = false;
+    return batch_plan(b);
+}
+
+int cdugks_batch_bound(const cdugks_batch_t* b) { return b && b->bound ? 1 : 0; }
+
+int cdugks_batch_test_wait_timeout(cdugks_batch_t* b, int on) {
+    if (!b) return fail(CDUGKS_ERR_INVALID, "null batch");
+    batch_drop_graph(b);
+    b->test_hook = on ? 1 : 0;
+    b->wait_log2 = on ? 12 : 26;
     return CDUGKS_OK;
 }
 

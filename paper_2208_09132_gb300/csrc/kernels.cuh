@@ -582,10 +582,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
 }
 
 // VC consecutive values as vector loads / stores (16-byte aligned by layout).
+// NC = true reads through the non-coherent (read-only) path, for data no
+// kernel of the running launch writes; the persistent batched step, whose
+// items read what other items of the same launch wrote, loads coherently.
 template <typename T> struct Chunk;
 template <> struct Chunk<float> {
+    template <bool NC = true>
     static __device__ __forceinline__ void load(const float* p, float (&v)[VC]) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 a = NC ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
     static __device__ __forceinline__ void store(float* p, const float (&v)[VC]) {
@@ -593,9 +597,10 @@ template <> struct Chunk<float> {
     }
 };
 template <> struct Chunk<double> {
+    template <bool NC = true>
     static __device__ __forceinline__ void load(const double* p, double (&v)[VC]) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        const double2 a = NC ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+        const double2 b = NC ? __ldg(reinterpret_cast<const double2*>(p + 2)) : *reinterpret_cast<const double2*>(p + 2);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
     static __device__ __forceinline__ void store(double* p, const double (&v)[VC]) {
@@ -1300,7 +1305,7 @@ __device__ __forceinline__ void face_flux(const T* fc, const T (&xi)[VC][D], con
         fg.v[v] = Fg;
         fb.v[v] = Fb;
         const T wg = w[v] * Fg;
-        sm[0] += wg;
+        sm[0] = Ar<T>::add(sm[0], wg);   // (explicitly rounded: the same bits in every kernel)
 #pragma unroll
         for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
         sm[1 + D] = fma(w[v], Fb, sm[1 + D]);
@@ -1405,7 +1410,7 @@ __device__ __forceinline__ void write_face_sums(const Geo& g, double* const* dst
     }
 }
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SWEEP_B, int MODE, bool PERS = false>
 __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem,
                                            const TmaPair* tm = nullptr) {
     using TL = Tile<D, T0_, T1_, T2_, mode_halo(MODE)>;
@@ -1425,7 +1430,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    constexpr bool STAGE = SM::stage(SWEEP_B);
+    constexpr bool STAGE = SM::stage(SWEEP_B) && !PERS;    // (the persistent step loads directly, coherently)
+    constexpr bool NC = !PERS;
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
     Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
     Q* const S2 = S + SM::nS;                     // [D][D][2][SB2] their half van Leer differences (R2)
@@ -1721,8 +1727,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 }
             } else {
                 const size_t ad = phi_addr(g, c, vt * VC, 0);
-                Chunk<T>::load(bf.phi_in + ad, gs);
-                Chunk<T>::load(bf.phi_in + ad + VC, bs);
+                Chunk<T>::template load<NC>(bf.phi_in + ad, gs);
+                Chunk<T>::template load<NC>(bf.phi_in + ad + VC, bs);
             }
             const T kp_g = cst[D + 4], kp_b = cst[D + 5], kp_s = cst[D + 6];
             Q qg, qb;
@@ -1774,8 +1780,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 }
             } else {
                 const size_t ad = phi_addr(g, c, vt * VC, 0);
-                Chunk<T>::load(bf.phibar + ad, qg.v);
-                Chunk<T>::load(bf.phibar + ad + VC, qb.v);
+                Chunk<T>::template load<NC>(bf.phibar + ad, qg.v);
+                Chunk<T>::template load<NC>(bf.phibar + ad + VC, qb.v);
             }
             P[0 * BOX + k] = qg;
             P[1 * BOX + k] = qb;
@@ -1793,13 +1799,13 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                 Q qg, qb, qs[D][2];
                 if (rf == 0) {
                     const size_t ad = phi_addr(g, c, vt * VC, 0);
-                    Chunk<T>::load(bf.phibar + ad, qg.v);
-                    Chunk<T>::load(bf.phibar + ad + VC, qb.v);
+                    Chunk<T>::template load<NC>(bf.phibar + ad, qg.v);
+                    Chunk<T>::template load<NC>(bf.phibar + ad + VC, qb.v);
                     const size_t as = sig_addr<D>(g, c, vt * VC, 0, 0);
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
-                        Chunk<T>::load(bf.sigma + as + (a * 2 + 0) * VC, qs[a][0].v);
-                        Chunk<T>::load(bf.sigma + as + (a * 2 + 1) * VC, qs[a][1].v);
+                        Chunk<T>::template load<NC>(bf.sigma + as + (a * 2 + 0) * VC, qs[a][0].v);
+                        Chunk<T>::template load<NC>(bf.sigma + as + (a * 2 + 1) * VC, qs[a][1].v);
                     }
                 } else {
 #pragma unroll
@@ -2002,7 +2008,7 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
 #pragma unroll
                         for (int v = 0; v < VC; ++v) {
                             const T wg = w[v] * gb[v];
-                            sm[0] += wg;
+                            sm[0] = Ar<T>::add(sm[0], wg);   // (explicitly rounded: the same bits in every kernel)
 #pragma unroll
                             for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
                             sm[1 + D] = fma(w[v], bb[v], sm[1 + D]);
@@ -2050,8 +2056,8 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
                     // phi and phi_eq of the owned cell (not kept from phase 1 on this path)
                     T gs[VC], bs[VC];
                     const size_t ad0 = phi_addr(g, cell_index(g, qa), vt * VC, 0);
-                    Chunk<T>::load(bf.phi_in + ad0, gs);
-                    Chunk<T>::load(bf.phi_in + ad0 + VC, bs);
+                    Chunk<T>::template load<NC>(bf.phi_in + ad0, gs);
+                    Chunk<T>::template load<NC>(bf.phi_in + ad0 + VC, bs);
                     own_state<T, D>(own, xi, hx, gs, bs, og, ob, oge, obe);
                 } else {
 #pragma unroll
@@ -2114,8 +2120,10 @@ struct FluxSmem {
     static constexpr size_t bytes = nV4 * sizeof(V4<T>) + (size_t)NPL * (2 + D) * sizeof(Kahan<T>);
 };
 
-template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false, bool NOSRC = false>
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false, bool NOSRC = false,
+          bool PERS = false>
 __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int tile, int grp, unsigned char* smem) {
+    constexpr bool NC = !PERS;      // the persistent batched step reads coherently
     using TL = Tile<D, T0_, T1_, T2_>;
     using FS = FluxSmem<T, D, T0_, T1_, T2_, SK>;
     using Q = V4<T>;
@@ -2191,8 +2199,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
         }
         const size_t ad = cell_ad + (size_t)vt * chunk_stride;
         T gs[VC], bs[VC];
-        Chunk<T>::load(bf.phi_in + ad, gs);
-        Chunk<T>::load(bf.phi_in + ad + VC, bs);
+        Chunk<T>::template load<NC>(bf.phi_in + ad, gs);
+        Chunk<T>::template load<NC>(bf.phi_in + ad + VC, bs);
         T dFg[VC], dFb[VC];
 #pragma unroll
         for (int v = 0; v < VC; ++v) dFg[v] = dFb[v] = T(0);
@@ -2205,8 +2213,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                 const int fs = a == 0 ? 1 : (a == 1 ? g.fn[1][0] : g.fn[2][0] * g.fn[2][1]);
                 const T* src = bf.face[a] + face_addr(g, a, ff[a] + side * fs, vt);
                 T gb[VC], bb[VC];
-                Chunk<T>::load(src, gb);
-                Chunk<T>::load(src + VC, bb);
+                Chunk<T>::template load<NC>(src, gb);
+                Chunk<T>::template load<NC>(src + VC, bb);
                 const int fl = TL::face_local(a, la[0] + (a == 0 ? side : 0), la[1] + (a == 1 ? side : 0),
                                               la[2] + (a == 2 ? side : 0));
                 T fcst[4 * NFCV];
@@ -2237,8 +2245,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
                     if (g.nv1[0] % VC == 0) {        // velocity rows are whole chunks: vector loads
                         auto chunk = [&](int vn, T (&gv)[VC], T (&bv)[VC]) {
                             const T* p = fbase + face_addr(g, a, fidx, vn);
-                            Chunk<T>::load(p, gv);
-                            Chunk<T>::load(p + VC, bv);
+                            Chunk<T>::template load<NC>(p, gv);
+                            Chunk<T>::template load<NC>(p + VC, bv);
                         };
                         force_gradient_chunk<T, D>(g, fac, vt, chunk, gb, bb, fgg, fgb);
                     }
@@ -2281,8 +2289,8 @@ __device__ __forceinline__ void flux_body(const Geo g, const Bufs<T> bf, int til
         }
         if constexpr (ACC) {     // + dt F^n of the own cell (eq. phiupdate's source, rectangle rule)
             T fgo[VC], fbo[VC];
-            Chunk<T>::load(bf.force + ad, fgo);
-            Chunk<T>::load(bf.force + ad + VC, fbo);
+            Chunk<T>::template load<NC>(bf.force + ad, fgo);
+            Chunk<T>::template load<NC>(bf.force + ad + VC, fbo);
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
                 dFg[v] -= fgo[v];

@@ -51,6 +51,17 @@ cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaS
 // One time step of every instance of a batch.
 cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s);
 cudaError_t launch_batch_step_f64(const BatchPlan& p, const Inst<double>* insts, int* cur, cudaStream_t s);
+// The persistent batched step (persist.cuh): nsteps steps of every member in one
+// launch; only shapes that have it (batch_persistent_*) and one shape per batch.
+struct PHead;
+struct PItem;
+struct PState;
+bool batch_persistent_f32(int D, int id);
+bool batch_persistent_f64(int D, int id);
+cudaError_t launch_batch_persist_f32(int D, int id, const PHead* h, const PItem* it, const Inst<float>* in, int* cur,
+                                     PState* st, int nsteps, int wait_log2, int test_hook, cudaStream_t s);
+cudaError_t launch_batch_persist_f64(int D, int id, const PHead* h, const PItem* it, const Inst<double>* in, int* cur,
+                                     PState* st, int nsteps, int wait_log2, int test_hook, cudaStream_t s);
 // Maxwellian initial state from device fields [Nc][2+D] (rho, u, T).
 cudaError_t launch_init_f32(const Geo& g, const Inst<float>* in, int cur, const double* fields, cudaStream_t s);
 cudaError_t launch_init_f64(const Geo& g, const Inst<double>* in, int cur, const double* fields, cudaStream_t s);

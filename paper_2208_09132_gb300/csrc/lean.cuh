@@ -64,7 +64,8 @@ struct LeanAOcc {
     static constexpr size_t per = LeanA<T, D, T0_, T1_, T2_>::bytes + 1024;
     static constexpr int by_smem = (int)((228 * 1024) / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
-    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 80);    // keep >= 80 registers
+    // keep >= 80 registers (FP32) or >= 168 (FP64 values take two registers)
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * (sizeof(T) == 8 ? 168 : 80));
     static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
     static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
     static constexpr int value = v0 < 1 ? 1 : (v0 > 4 ? 4 : v0);
@@ -513,7 +514,7 @@ __device__ __forceinline__ void lean_a_body(const Geo& g, const Bufs<T>& bf, int
 #pragma unroll
                     for (int v = 0; v < VC; ++v) {
                         const T wg = w[v] * vg.v[v];
-                        sm[0] += wg;
+                        sm[0] = Ar<T>::add(sm[0], wg);   // (explicitly rounded: the same bits in every kernel)
 #pragma unroll
                         for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
                         sm[1 + D] = fma(w[v], vb.v[v], sm[1 + D]);
@@ -580,7 +581,8 @@ struct LeanBOcc {
     static constexpr size_t per = LeanB<T, D, T0_, T1_, T2_>::bytes + 1024;
     static constexpr int by_smem = (int)((228 * 1024) / per);
     static constexpr int by_threads = 2048 / Tile<D, T0_, T1_, T2_>::NT;
-    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * 128);   // keep >= 128 registers
+    // keep >= 128 registers (FP32) or >= 200 (FP64)
+    static constexpr int by_regs = 65536 / (Tile<D, T0_, T1_, T2_>::NT * (sizeof(T) == 8 ? 200 : 128));
     static constexpr int v1 = by_smem < by_threads ? by_smem : by_threads;
     static constexpr int v0 = v1 < by_regs ? v1 : by_regs;
     static constexpr int value = v0 < 1 ? 1 : (v0 > 8 ? 8 : v0);
@@ -615,7 +617,7 @@ __device__ __forceinline__ void lean_face_flux(const Geo& g, const Bufs<T>& bf, 
         Fb[v] = fb;
         if constexpr (MOM) {
             const T wg = w[v] * fg;
-            sm[0] += wg;
+            sm[0] = Ar<T>::add(sm[0], wg);   // (explicitly rounded: the same bits in every kernel)
 #pragma unroll
             for (int b = 0; b < D; ++b) sm[1 + b] = fma(xi[v][b], wg, sm[1 + b]);
             sm[1 + D] = fma(w[v], fb, sm[1 + D]);

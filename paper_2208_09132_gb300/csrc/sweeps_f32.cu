@@ -10,11 +10,11 @@ constexpr int PFA = MODE_PREP | MODE_FACES | MODE_ACC;   // external acceleratio
 using Table32 = ShapeTable<
     float,
     ShapeList<Shape<float, 1, 256, 1, 1>, Shape<float, 1, 128, 1, 1>, Shape<float, 1, 64, 1, 1>,
-              Shape<float, 1, 256, 1, 1, FF>, Shape<float, 1, 256, 1, 1, FG>, Shape<float, 1, 256, 1, 1, FFS>,
-              Shape<float, 1, 256, 1, 1, PFA>, Shape<float, 1, 128, 1, 1, FF>, Shape<float, 1, 64, 1, 1, FF>>,
+              Shape<float, 1, 256, 1, 1, FF, true>, Shape<float, 1, 256, 1, 1, FG>, Shape<float, 1, 256, 1, 1, FFS>,
+              Shape<float, 1, 256, 1, 1, PFA>, Shape<float, 1, 128, 1, 1, FF, true>, Shape<float, 1, 64, 1, 1, FF, true>>,
     ShapeList<Shape<float, 2, 32, 8, 1>, Shape<float, 2, 16, 8, 1>, Shape<float, 2, 32, 16, 1, MODE_PREP>,
               Shape<float, 2, 32, 8, 1, MODE_STORED>, Shape<float, 2, 32, 16, 1, MODE_STORED>,
-              Shape<float, 2, 32, 16, 1>, Shape<float, 2, 32, 8, 1, FF>, Shape<float, 2, 32, 16, 1, FF>,
+              Shape<float, 2, 32, 16, 1>, Shape<float, 2, 32, 8, 1, FF, true>, Shape<float, 2, 32, 16, 1, FF>,
               Shape<float, 2, 32, 8, 1, SF>, Shape<float, 2, 16, 8, 1, FG>, Shape<float, 2, 32, 8, 1, FFS>,
               Shape<float, 2, 32, 8, 1, PFA>, LeanShape<float, 2, 32, 8, 1>, LeanShape<float, 2, 32, 16, 1>,
               LeanShape<float, 2, 32, 8, 1, false>>,
@@ -32,6 +32,11 @@ int tile_mode_f32(int D, int id) { return Table32::mode(D, id); }
 cudaError_t launch_step_f32(const Geo& g, const Inst<float>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
                             const void* phi_in) {
     return Table32::step(g, in, cur, s, ev, phi_in);
+}
+bool batch_persistent_f32(int D, int id) { return Table32::persistent(D, id); }
+cudaError_t launch_batch_persist_f32(int D, int id, const PHead* h, const PItem* it, const Inst<float>* in, int* cur,
+                                     PState* st, int nsteps, int wait_log2, int test_hook, cudaStream_t s) {
+    return Table32::persist(D, id, h, it, in, cur, st, nsteps, wait_log2, test_hook, s);
 }
 cudaError_t launch_batch_step_f32(const BatchPlan& p, const Inst<float>* insts, int* cur, cudaStream_t s) {
     return run_batch_step<Table32, float>(p, insts, cur, s);

@@ -12,10 +12,10 @@ using Table64 = ShapeTable<
     double,
     ShapeList<Shape<double, 1, 256, 1, 1>, Shape<double, 1, 128, 1, 1>, Shape<double, 1, 64, 1, 1>,
               Shape<double, 1, 128, 1, 1, FF>, Shape<double, 1, 128, 1, 1, FG>, Shape<double, 1, 128, 1, 1, FFS>,
-              Shape<double, 1, 128, 1, 1, PFA>, Shape<double, 1, 64, 1, 1, FF>, Shape<double, 1, 32, 1, 1, FF>>,
+              Shape<double, 1, 128, 1, 1, PFA>, Shape<double, 1, 64, 1, 1, FF, true>, Shape<double, 1, 32, 1, 1, FF>>,
     ShapeList<Shape<double, 2, 16, 8, 1>, Shape<double, 2, 8, 8, 1>, Shape<double, 2, 16, 8, 1, MODE_STORED>,
               Shape<double, 2, 16, 8, 1, FF>, Shape<double, 2, 8, 8, 1, FG>, Shape<double, 2, 16, 8, 1, FFS>,
-              Shape<double, 2, 16, 8, 1, PFA>>,
+              Shape<double, 2, 16, 8, 1, PFA>, LeanShape<double, 2, 16, 8, 1>>,
     ShapeList<Shape<double, 3, 4, 4, 4>, Shape<double, 3, 8, 4, 4, MODE_PREP>, Shape<double, 3, 8, 4, 4, MODE_STORED>,
               Shape<double, 3, 8, 4, 4, SF>, Shape<double, 3, 8, 4, 4, SFS>, Shape<double, 3, 8, 4, 4, PFA>>>;
 }
@@ -28,6 +28,11 @@ int tile_mode_f64(int D, int id) { return Table64::mode(D, id); }
 cudaError_t launch_step_f64(const Geo& g, const Inst<double>* in, int cur, cudaStream_t s, cudaEvent_t* ev,
                             const void* phi_in) {
     return Table64::step(g, in, cur, s, ev, phi_in);
+}
+bool batch_persistent_f64(int D, int id) { return Table64::persistent(D, id); }
+cudaError_t launch_batch_persist_f64(int D, int id, const PHead* h, const PItem* it, const Inst<double>* in, int* cur,
+                                     PState* st, int nsteps, int wait_log2, int test_hook, cudaStream_t s) {
+    return Table64::persist(D, id, h, it, in, cur, st, nsteps, wait_log2, test_hook, s);
 }
 cudaError_t launch_batch_step_f64(const BatchPlan& p, const Inst<double>* insts, int* cur, cudaStream_t s) {
     return run_batch_step<Table64, double>(p, insts, cur, s);

@@ -6,6 +6,7 @@
 
 #include "launch.cuh"
 #include "lean.cuh"
+#include "persist.cuh"
 
 namespace cdg {
 
@@ -95,7 +96,19 @@ TmaPair make_tma(const Geo& g, const void* phi_in) {
 // only) add k_faceq before the face constants and k_cellq before the W update.
 // Acceleration shapes (MODE_ACC, prepared face-store only) form the force
 // terms in k_prep and take them in k_flux.
-template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED>
+// The number of CTAs of a persistent launch: every SM at the occupancy the
+// kernel reaches (more would only wait for a slot).
+template <typename K>
+int persistent_grid(K kern, int threads, size_t smem) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    return sms * (occ > 0 ? occ : 1);
+}
+
+// PB: the shape also has the persistent batched step (k_batch_persist).
+template <typename T, int D, int TX, int TY, int TZ, int MODE = MODE_FUSED, bool PB = false>
 struct Shape {
     static constexpr bool SK = mode_sk(MODE);
     using SM = Smem<T, D, TX, TY, TZ, MODE>;
@@ -245,6 +258,29 @@ struct Shape {
     }
 
     static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }
+
+    static constexpr bool persistent = PB;
+    static cudaError_t persist(const PHead* head, const PItem* items, const Inst<T>* insts, int* cur, PState* st,
+                               int nsteps, int wait_log2, int test_hook, cudaStream_t s) {
+        if constexpr (!PB || SRC != MODE_FUSED || SK) {
+            return cudaErrorNotSupported;
+        } else {
+            using PS = PersistSmem<T, D, TX, TY, TZ, MODE>;
+            static bool done = false;
+            cudaError_t e;
+            if (!done) {
+                if ((e = cudaFuncSetAttribute(k_batch_persist<T, D, TX, TY, TZ, MODE>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS::bytes)))
+                    return e;
+                done = true;
+            }
+            const int grid = persistent_grid(k_batch_persist<T, D, TX, TY, TZ, MODE>, TL::NT, PS::bytes);
+            if ((e = cudaMemsetAsync(st, 0, sizeof(PState), s))) return e;
+            k_batch_persist<T, D, TX, TY, TZ, MODE><<<grid, TL::NT, PS::bytes, s>>>(head, items, insts, cur, st, nsteps,
+                                                                                   wait_log2, test_hook);
+            return cudaGetLastError();
+        }
+    }
 };
 
 // A lean shape (lean.cuh): sweep A k_lsweep, face constants (with the face
@@ -342,6 +378,11 @@ struct LeanShape {
     }
 
     static TileShape shape() { return {{TL::T0, TL::T1, TL::T2}}; }
+
+    static constexpr bool persistent = false;
+    static cudaError_t persist(const PHead*, const PItem*, const Inst<T>*, int*, PState*, int, int, int, cudaStream_t) {
+        return cudaErrorNotSupported;
+    }
 };
 
 // A list of shapes for one dimension, indexed by tile id.
@@ -361,6 +402,12 @@ struct ShapeList<> {
     static TileShape shape(int) { return {{0, 0, 0}}; }
     static size_t smem(int) { return 0; }
     static int mode(int) { return 0; }
+    static bool persistent(int) { return false; }
+    template <typename T>
+    static cudaError_t persist(int, const PHead*, const PItem*, const Inst<T>*, int*, PState*, int, int, int,
+                               cudaStream_t) {
+        return cudaErrorInvalidValue;
+    }
 };
 template <typename H, typename... R>
 struct ShapeList<H, R...> {
@@ -380,6 +427,13 @@ struct ShapeList<H, R...> {
     static TileShape shape(int id) { return id == 0 ? H::shape() : Rest::shape(id - 1); }
     static size_t smem(int id) { return id == 0 ? H::smem_bytes() : Rest::smem(id - 1); }
     static int mode(int id) { return id == 0 ? H::mode : Rest::mode(id - 1); }
+    static bool persistent(int id) { return id == 0 ? H::persistent : Rest::persistent(id - 1); }
+    template <typename T>
+    static cudaError_t persist(int id, const PHead* h, const PItem* it, const Inst<T>* in, int* cur, PState* st, int n,
+                               int w, int th, cudaStream_t s) {
+        return id == 0 ? H::persist(h, it, in, cur, st, n, w, th, s)
+                       : Rest::template persist<T>(id - 1, h, it, in, cur, st, n, w, th, s);
+    }
 };
 
 // The shapes of one precision for D = 1, 2, 3.
@@ -400,6 +454,15 @@ struct ShapeTable {
         if (D == 1) return L1::template sweep_batch<T>(id, B, it, n, in, cur, s);
         if (D == 2) return L2::template sweep_batch<T>(id, B, it, n, in, cur, s);
         return L3::template sweep_batch<T>(id, B, it, n, in, cur, s);
+    }
+    static bool persistent(int D, int id) {
+        return D == 1 ? L1::persistent(id) : (D == 2 ? L2::persistent(id) : L3::persistent(id));
+    }
+    static cudaError_t persist(int D, int id, const PHead* h, const PItem* it, const Inst<T>* in, int* cur, PState* st,
+                               int n, int w, int th, cudaStream_t s) {
+        if (D == 1) return L1::template persist<T>(id, h, it, in, cur, st, n, w, th, s);
+        if (D == 2) return L2::template persist<T>(id, h, it, in, cur, st, n, w, th, s);
+        return L3::template persist<T>(id, h, it, in, cur, st, n, w, th, s);
     }
 };
 

@@ -195,8 +195,9 @@ def _time(cfg, precision, tile, groups, context, steps, device):
     return e0.elapsed_time(e1) / steps / (copies * wl.ncells(cfg) * wl.nvel(cfg))
 
 
-def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, refresh=False):
-    """Best (tile_id, velocity_groups) for this instance size; cached."""
+def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, refresh=False, tiles=None):
+    """Best (tile_id, velocity_groups) for this instance size; cached.  tiles:
+    consider only these tile ids (default: every candidate shape)."""
     path = cache or cache_path()
     d = _load_cache(path)
     key = size_key(cfg, precision, context)
@@ -215,7 +216,8 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
         torch.cuda.empty_cache()
 
     for tile, groups in candidates(cfg, precision, context):
-        trial(tile, groups)
+        if tiles is None or tile in tiles:
+            trial(tile, groups)
     if not results:
         raise RuntimeError(f"no tile shape fits on {device} for {key}")
     # refine the group count of the best shape between the powers of two (the
@@ -237,21 +239,28 @@ def tune(cfg, precision, context="alone", steps=5, device="cuda:0", cache=None, 
 
 
 def bench_sizes():
-    """(cfg, precision, context) of every instance size the benchmark runs."""
-    out = [(wl.workload_c3(kn=1e-4)[0], cdugks.FP32, "alone"), (wl.workload_c3(kn=1e-4, scale=2, nv=12)[0],
-                                                              cdugks.FP32, "alone"),
-           (wl.workload_c2()[0], cdugks.FP32, "alone"), (wl.workload_c1()[0], cdugks.FP64, "alone")]
+    """(cfg, precision, context, tile ids or None) of every instance size the
+    benchmark runs.  The full 3D workload is tuned over its face-store shapes
+    only (each trial binds up to ~260 GB)."""
+    c3 = wl.workload_c3(kn=1e-4)[0]
+    nt3 = cdugks.load().cdugks_tile_count(cdugks.FP32, 3)
+    c3_tiles = [t for t in range(nt3) if cdugks.tile_shape(cdugks.FP32, 3, t)[1] & 4
+                and not cdugks.tile_shape(cdugks.FP32, 3, t)[1] & (16 | 32)]
+    out = [(c3, cdugks.FP32, "alone", c3_tiles),
+           (wl.workload_c3(kn=1e-4, scale=2, nv=12)[0], cdugks.FP32, "alone", None),
+           (wl.workload_c2()[0], cdugks.FP32, "alone", None), (wl.workload_c2()[0], cdugks.FP64, "alone", None),
+           (wl.workload_c1()[0], cdugks.FP64, "alone", None)]
     seen = set()
     for cfg, _ in wl.workload_c4():
         k = size_key(cfg, cdugks.FP32, "batch")
         if k not in seen:
             seen.add(k)
-            out.append((cfg, cdugks.FP32, "batch"))
+            out.append((cfg, cdugks.FP32, "batch", None))
     return out
 
 
 if __name__ == "__main__":
     import sys
     dev = sys.argv[1] if len(sys.argv) > 1 else "cuda:0"
-    for cfg, prec, ctx in bench_sizes():
-        print(size_key(cfg, prec, ctx), tune(cfg, prec, context=ctx, device=dev, refresh=True), flush=True)
+    for cfg, prec, ctx, tl in bench_sizes():
+        print(size_key(cfg, prec, ctx), tune(cfg, prec, context=ctx, device=dev, refresh=True, tiles=tl), flush=True)

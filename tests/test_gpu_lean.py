@@ -71,6 +71,28 @@ def test_lean_shapes_match_oracle(oracle_mod, name, cfg, f, steps, Pr):
         assert np.abs(b - bo).max() <= TOL * np.abs(bo).max(), (name, t)
 
 
+@pytest.mark.parametrize("name,cfg,f,steps", [c for c in lean_cases() if c[1]["dim"] == 2],
+                         ids=[c[0] for c in lean_cases() if c[1]["dim"] == 2])
+def test_lean_fp64_shapes_match_oracle(oracle_mod, name, cfg, f, steps):
+    """The FP64 lean shapes (2D): the same scheme to 1e-12, every value."""
+    o = oracle_mod.Oracle(cfg)
+    o.init(f)
+    o.step(steps)
+    ref = o.moments()
+    go, bo = o.distributions()
+    tiles = lean_tiles(cdugks.FP64, 2)
+    assert tiles
+    for t in tiles:
+        s = cdugks.Solver(cfg, precision=cdugks.FP64, tile_id=t, velocity_groups=3)
+        s.init(f)
+        s.step(steps)
+        assert s.sync_status() == 0
+        assert np.all(rel_linf(s.moments(), ref) <= 1e-12), (name, t)
+        g, b = s.distributions()
+        assert np.abs(g - go).max() <= 1e-12 * np.abs(go).max(), (name, t)
+        assert np.abs(b - bo).max() <= 1e-12 * np.abs(bo).max(), (name, t)
+
+
 @pytest.mark.parametrize("D", [2, 3])
 def test_lean_uniform_maxwellian_is_a_fixed_point(D):
     """Every cell computes the same values from the same factors: a uniform
