@@ -9,9 +9,11 @@ Default workload: the 3D shear-wave problem with FP32 storage, 64^3 periodic
 cells x 24^3 velocities on [-6,6]^3, Kn = 1e-4, Pr = 2/3 (synthetic initial
 fields; 3.6e9 phase-space points, 29 GB per state buffer).  One bench step =
 one full time step of the scheme.  The same line carries, as sub-objects, the
-plain FP64 path on the same workload and the batched form (256 uneven 1D
+plain FP64 path on the same workload, the batched form (256 uneven 1D
 thermoacoustic instances in FP32) with its FP64 one-instance-at-a-time
-comparison.
+comparison, and the served stream (the first 8 requests of the Poisson stream
+of 2D solves to t = 1, capped at 60 s of wall time) with modelled one-at-a-time
+FP32 and FP64 servers of the same requests.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c1|c2|c3|c3s|c4|c5|einfeldt] [--tune]
@@ -405,48 +407,140 @@ def run_batched(args, ws, rank, local, sub=False):
     }
 
 
-def run_served(args, ws, rank, local):
-    """The served stream: Poisson arrivals of 2D Gresho / Kelvin-Helmholtz
-    solves admitted by device-memory footprint and stepped together."""
+def solo_step_ms(req, prec, dev, steps=3):
+    """Milliseconds per step of one served request stepped alone (its untuned
+    default shape for the precision): a warm-up step, then `steps` timed."""
     import torch
 
-    from paper_2208_09132_gb300 import serving
+    from paper_2208_09132_gb300 import cdugks, tune
+
+    tile, groups = tune.choose(req.cfg, prec, context="alone", device=dev)
+    s = cdugks.Solver(req.cfg, precision=prec, device=dev, tile_id=tile, velocity_groups=groups)
+    s.init(req.fields)
+    s.step(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    e1.synchronize()
+    ok = s.sync_status() == 0
+    ms = e0.elapsed_time(e1) / steps
+    del s
+    return ms, ok
+
+
+def one_at_a_time(reqs, step_ms, cap_s, order="fifo"):
+    """A server that solves the same requests one at a time, each taking
+    nsteps x its measured step time, in arrival order ("fifo") or, whenever it
+    is free, the shortest waiting solve first ("sjf", non-preemptive): the
+    time-to-solution statistics of the requests it finishes within cap_s and
+    the point-updates per second it delivers within the cap."""
+    jobs = sorted(zip(reqs, step_ms), key=lambda j: j[0].arrival)
+    t, tts, pu_done, busy = 0.0, [], 0.0, 0.0
+    waiting = []
+    while (jobs or waiting) and t < cap_s:
+        while jobs and jobs[0][0].arrival <= t:
+            waiting.append(jobs.pop(0))
+        if not waiting:
+            t = jobs[0][0].arrival
+            continue
+        k = 0 if order == "fifo" else min(range(len(waiting)), key=lambda i: waiting[i][0].nsteps * waiting[i][1])
+        q, ms = waiting.pop(k)
+        dur = q.nsteps * ms * 1e-3
+        run = min(dur, cap_s - t)
+        pu_done += q.points * q.nsteps * run / dur
+        busy += run
+        t += dur
+        if t <= cap_s:
+            tts.append(t - q.arrival)
+    wall = min(cap_s, t)
+    return {"finished": len(tts),
+            "p50_time_to_solution_s": float(np.percentile(tts, 50)) if tts else None,
+            "p99_time_to_solution_s": float(np.percentile(tts, 99)) if tts else None,
+            "aggregate_point_updates_per_s": pu_done / wall if wall > 0 else None,
+            "device_point_updates_per_s": pu_done / busy if busy > 0 else None}
+
+
+def run_served(args, ws, rank, local, sub=False):
+    """The served stream: Poisson arrivals (50/s) of 2D Gresho-vortex and
+    Kelvin-Helmholtz solves, grids 64^2-512^2, velocity grids 16^2-48^2, Kn
+    1e-4..1, each run to t = 1, admitted by device-memory footprint and stepped
+    together (persistent batched step, one launch per round), for at most
+    args.serve_cap seconds of wall time.  Then each request is timed alone in
+    FP32 and in FP64, and a one-at-a-time server of the same requests is modelled
+    from those step times under the same cap.  sub=True: the "served" part of
+    the default line (args.requests requests)."""
+    import torch
+
+    from paper_2208_09132_gb300 import cdugks, serving
 
     dev = f"cuda:{local}"
     torch.cuda.set_device(local)
-    from paper_2208_09132_gb300 import cdugks
-
-    tile = cdugks.find_tile(cdugks.FP32, 2, (32, 8), 4)     # fused sweep A + face store, batchable
-    reqs = serving.stream_c5(count=args.requests, t_end=args.t_end, tile_id=tile)
+    reqs = serving.stream_c5(count=args.requests, t_end=args.t_end)
     free, _ = torch.cuda.mem_get_info()
-    srv = serving.Server(budget_bytes=int(0.6 * free), max_slots=64, max_round=32, device=dev)
-    # warm-up: one tiny request compiles/loads everything
-    warm = serving.stream_c5(count=1, t_end=0.002, tile_id=tile)
-    serving.Server(budget_bytes=int(0.6 * free), device=dev).run(warm)
+    budget = int(0.6 * free)
+    # warm-up: two short solves load and initialise everything
+    serving.Server(budget_bytes=budget, device=dev).run(serving.stream_c5(count=2, t_end=0.002))
+    torch.cuda.synchronize()
+    srv = serving.Server(budget_bytes=budget, max_slots=64, max_round=64, device=dev, policy=args.policy)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    srv.run(reqs)
+    srv.run(reqs, time_limit=args.serve_cap)
     torch.cuda.synchronize()
     wall = max_over_ranks(time.perf_counter() - t0, ws)
     clk = clocks.stop()
     rep = srv.report(wall)
+    del srv
+    torch.cuda.empty_cache()
+    # every request alone, FP32 and FP64 (same requests, full nsteps modelled)
+    ms32, ms64, ok = [], [], True
+    for q in sorted(reqs, key=lambda q: q.arrival):
+        a, oa = solo_step_ms(q, cdugks.FP32, dev)
+        b, ob = solo_step_ms(q, cdugks.FP64, dev)
+        torch.cuda.empty_cache()
+        ms32.append(a)
+        ms64.append(b)
+        ok = ok and oa and ob
+    cap = args.serve_cap
+    alone32 = {o: one_at_a_time(reqs, ms32, cap, o) for o in ("fifo", "sjf")}
+    alone64 = {o: one_at_a_time(reqs, ms64, cap, o) for o in ("fifo", "sjf")}
+    value = ws * rep["point_updates"] / wall
+    total_pu = sum(q.points * q.nsteps for q in reqs)
+    cfgd = {"workload": f"served_stream_{len(reqs)}_requests", "arrivals": "Poisson 50/s, seed 1",
+            "requests": len(reqs), "t_end": args.t_end, "wall_cap_s": cap,
+            "sizes": "cells 64^2-512^2, velocities 16^2-48^2 (log-uniform sides), Gresho or Kelvin-Helmholtz, "
+                     "Kn 1e-4..1 (log-uniform), FP32",
+            "total_point_updates_requested": total_pu,
+            "admission": "device-memory footprint within 60% of free memory, <= 64 slots",
+            "tile_id": serving.persistent_tile(cdugks.FP32, 2), "tile": [32, 8],
+            "sweep_mode": "fused, face store"}
+    served = {"value": value, "unit": UNIT, **rep,
+              "fp32_one_at_a_time": alone32, "fp64_one_at_a_time": alone64,
+              "vs_fp64_one_at_a_time": value / alone64["fifo"]["aggregate_point_updates_per_s"]
+              if alone64["fifo"]["aggregate_point_updates_per_s"] else None,
+              "one_at_a_time_what": "each request timed alone (3 steps after a warm-up, its default shape), "
+                                    "then a one-at-a-time server of the same arrivals modelled from those step "
+                                    "times under the same cap: first come first served (fifo) and shortest "
+                                    "solve first, non-preemptive (sjf)",
+              "status_ok": ok}
     if rank != 0:
         return None
+    if sub:
+        return {"workload": cfgd["workload"], **{k: cfgd[k] for k in ("requests", "t_end", "wall_cap_s", "sizes",
+                                                                      "total_point_updates_requested")},
+                **served}
     return {
-        "metric": METRIC, "value": ws * rep["point_updates"] / wall, "unit": UNIT, "n_gpus": ws,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": rep["rounds"], "warmup": 1, "ms_per_step": wall * 1e3 / max(rep["rounds"], 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"served_stream_{len(reqs)}_requests", "arrivals": "Poisson 50/s, seed 1",
-                   "requests": len(reqs), "t_end": args.t_end,
-                   "sizes": "cells 32^2-128^2, velocities 8^2-24^2, Gresho or Kelvin-Helmholtz, Kn 1e-4..1",
-                   "admission": "device-memory footprint within 60% of free memory, <= 64 slots",
-                   "tile_id": tile, "sweep_mode": MODE_NAMES[cdugks.tile_shape(cdugks.FP32, 2, tile)[1]]},
-        "latency_ms": {"p50": rep["p50_time_to_solution_s"] * 1e3, "p99": rep["p99_time_to_solution_s"] * 1e3,
-                       "what": "time to solution from arrival"},
-        "served": rep, "cpu_baseline": None, "e2e": None, "roofline": None,
+        "config": cfgd,
+        "latency_ms": {"p50": (rep["p50_time_to_solution_s"] or math.nan) * 1e3,
+                       "p99": (rep["p99_time_to_solution_s"] or math.nan) * 1e3,
+                       "what": "time to solution from arrival, finished requests"},
+        "served": served, "cpu_baseline": None, "e2e": None, "roofline": None,
         "gpu_launches": rep["kernel_launches"], "clocks": clk,
     }
 
@@ -633,6 +727,11 @@ def run_ours(args, ws, rank, local):
     if args.workload == "c3" and not args.skip_batched:
         batched = run_batched(args, ws, rank, local, sub=True)
 
+    # ---- the served stream (C5) under its wall-clock cap
+    served = None
+    if args.workload == "c3" and not args.skip_served:
+        served = run_served(args, ws, rank, local, sub=True)
+
     # ---- the plain FP64 path on the same workload (the one-instance comparison)
     fp64 = None
     if prec == cdugks.FP32 and not args.skip_fp64:
@@ -666,6 +765,7 @@ def run_ours(args, ws, rank, local):
             "e2e": e2e,
             "fp64_plain": fp64,
             "batched": batched,
+            "served": served,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "status_ok": status == 0,
@@ -733,14 +833,24 @@ def main():
     ap.add_argument("--collision", type=int, default=0, help="1: the Shakhov collision model")
     ap.add_argument("--accel", default="", help="uniform external acceleration, e.g. 0,-0.5")
     ap.add_argument("--groups", type=int, default=None, help="with --tile: velocity groups")
-    ap.add_argument("--requests", type=int, default=64, help="served stream: number of requests")
-    ap.add_argument("--t-end", type=float, default=0.05, help="served stream: end time of each solve")
+    ap.add_argument("--requests", type=int, default=None,
+                    help="served stream: number of requests (default 64; 8 in the default line)")
+    ap.add_argument("--t-end", type=float, default=1.0, help="served stream: end time of each solve")
+    ap.add_argument("--serve-cap", type=float, default=None,
+                    help="served stream: wall-clock cap in seconds (default 120; 60 in the default line)")
+    ap.add_argument("--policy", choices=["srpt", "share"], default="srpt",
+                    help="served stream: shortest remaining work first, or every request every round")
+    ap.add_argument("--skip-served", action="store_true", help="omit the served sub-object of the 3D workload")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.steps is None:   # the einfeldt workload runs its whole solve; the 3D workload 20 steps, others 1000
         args.steps = (pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt"
                       else (20 if args.workload in ("c3", "c3s") else 1000))
+    if args.requests is None:
+        args.requests = 64 if args.workload == "c5" else 8
+    if args.serve_cap is None:
+        args.serve_cap = 120.0 if args.workload == "c5" else 60.0
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, ws, rank)

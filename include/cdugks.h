@@ -384,6 +384,12 @@ CDUGKS_API void cdugks_batch_destroy(cdugks_batch_t *b);
 CDUGKS_API int cdugks_batch_set_persistent(cdugks_batch_t *b, int on, int max_members, long long max_items);
 /* 1 if the batch is bound (after admit / retire: whether to bind again). */
 CDUGKS_API int cdugks_batch_bound(const cdugks_batch_t *b);
+/* Persistent batches only: one launch in which member i (in the order of
+ * creation and admission, retired members removed) advances steps[i] >= 0
+ * steps (n = the number of members); a member that stops early just waits for
+ * the launch to end.  Asynchronous on the batch stream.  Errors: UNBOUND,
+ * INVALID (not persistent, wrong n, negative count), CUDA. */
+CDUGKS_API int cdugks_batch_step_members(cdugks_batch_t *b, const int *steps, int n);
 /* Testing hook for the persistent step's bounded waits (on = 1; 0 restores):
  * the first face item waits for one item more than exists and every wait gives
  * up after 2^12 polls, so a step stops early and cdugks_batch_sync reports

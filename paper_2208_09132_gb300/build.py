@@ -20,7 +20,6 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libcdugks.so")
 SOURCES = ["api.cu", "sweeps_f32.cu", "sweeps_f64.cu"]
-HEADERS = ["kernels.cuh", "launch.cuh", "sweeps_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +31,8 @@ def _nvcc() -> str:
 
 
 def _deps():
-    files = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
+    headers = sorted(f for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    files = [os.path.join(CSRC, s) for s in SOURCES + headers]
     files.append(os.path.join(ROOT, "include", "cdugks.h"))
     files.append(os.path.abspath(__file__))
     return files

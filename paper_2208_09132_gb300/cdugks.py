@@ -30,6 +30,7 @@ EXPORTS = [
     "cdugks_batch_create", "cdugks_batch_workspace_bytes", "cdugks_batch_bind", "cdugks_batch_capture",
     "cdugks_batch_step", "cdugks_batch_sync", "cdugks_batch_destroy", "cdugks_batch_admit", "cdugks_batch_retire",
     "cdugks_batch_set_persistent", "cdugks_batch_bound", "cdugks_batch_test_wait_timeout",
+    "cdugks_batch_step_members",
 ]
 
 
@@ -124,6 +125,7 @@ def load(build_if_needed: bool = True):
         "cdugks_batch_set_persistent": (i, [vp, i, i, ctypes.c_longlong]),
         "cdugks_batch_bound": (i, [vp]),
         "cdugks_batch_test_wait_timeout": (i, [vp, i]),
+        "cdugks_batch_step_members": (i, [vp, P(i), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -361,6 +363,11 @@ class Batch:
 
     def step(self, nsteps: int = 1):
         _check(self._lib.cdugks_batch_step(self._h, int(nsteps)))
+
+    def step_members(self, steps):
+        """Persistent batches: member i (in self.members order) advances steps[i] steps, in one launch."""
+        arr = (ctypes.c_int * len(steps))(*[int(v) for v in steps])
+        _check(self._lib.cdugks_batch_step_members(self._h, arr, len(steps)))
 
     def sync(self) -> int:
         return int(self._lib.cdugks_batch_sync(self._h))

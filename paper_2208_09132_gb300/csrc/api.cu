@@ -1470,6 +1470,34 @@ int cdugks_batch_set_persistent(cdugks_batch_t* b, int on, int max_members, long
 
 int cdugks_batch_bound(const cdugks_batch_t* b) { return b && b->bound ? 1 : 0; }
 
+int cdugks_batch_step_members(cdugks_batch_t* b, const int* steps, int n) {
+    if (!b || !b->bound) return fail(CDUGKS_ERR_UNBOUND, "batch not bound");
+    if (!b->pers) return fail(CDUGKS_ERR_INVALID, "per-member step counts need the persistent step");
+    if (!steps || n != (int)b->mem.size()) return fail(CDUGKS_ERR_INVALID, "one step count per member");
+    int mx = 0;
+    for (int i = 0; i < n; ++i) {
+        if (steps[i] < 0) return fail(CDUGKS_ERR_INVALID, "negative step count");
+        mx = std::max(mx, steps[i]);
+    }
+    if (mx == 0) return CDUGKS_OK;
+    // the limits, then the launch, then limits off again (all stream-ordered; the
+    // host copies are pageable, so they are staged before each call returns)
+    PHead* h = reinterpret_cast<PHead*>(b->base + b->off_phead);
+    const int on = 1, off = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->lim, steps, sizeof(int) * n, cudaMemcpyHostToDevice, b->stream)) ||
+        (e = cudaMemcpyAsync(&h->use_lim, &on, sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
+        (e = batch_persist_launch(b, mx)) ||
+        (e = cudaMemcpyAsync(&h->use_lim, &off, sizeof(int), cudaMemcpyHostToDevice, b->stream)))
+        return cuda_fail(e, "per-member batch step");
+    for (int i = 0; i < n; ++i) {
+        b->mem[i]->cur ^= (steps[i] & 1);
+        b->mem[i]->steps += steps[i];
+    }
+    b->steps += mx;
+    return CDUGKS_OK;
+}
+
 int cdugks_batch_test_wait_timeout(cdugks_batch_t* b, int on) {
     if (!b) return fail(CDUGKS_ERR_INVALID, "null batch");
     batch_drop_graph(b);

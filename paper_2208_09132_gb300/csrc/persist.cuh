@@ -38,8 +38,9 @@ struct PItem {
 // The plan in device memory: items per step and, per member, the items of each
 // kind per step.
 struct PHead {
-    int nmem, nitems, pad[2];
+    int nmem, nitems, use_lim, pad;
     int per[kPMaxMembers][4];
+    int lim[kPMaxMembers];        // with use_lim: member m runs min(lim[m], nsteps) steps of the launch
 };
 // Per launch (cleared before it): the next item to take, the abort flag and
 // the completed items of each kind per member.
@@ -90,6 +91,13 @@ __global__ void __launch_bounds__(Tile<D, TX, TY, TZ>::NT, (PersistSmem<T, D, TX
         const int s = (int)(gi / (unsigned)nitems);
         const PItem it = items[gi % (unsigned)nitems];
         const int m = it.inst;
+        // this member's steps in this launch (members may stop early: their later
+        // items are no work, and nothing waits for them)
+        const int nm = head->use_lim ? min(head->lim[m], nsteps) : nsteps;
+        if (s >= nm) {
+            __syncthreads();      // every thread has read s_item before thread 0 takes the next
+            continue;
+        }
         // the kind this item waits for, and how many of it its step needs
         int dk;
         unsigned need;
@@ -140,8 +148,7 @@ __global__ void __launch_bounds__(Tile<D, TX, TY, TZ>::NT, (PersistSmem<T, D, TX
             const unsigned done = atomicAdd(&st->cnt[m][it.kind], 1u) + 1u;
             // the member's last W item of the launch: the state buffers trade places
             // nsteps times (no item of this member reads cur afterwards)
-            if (it.kind == PK_W && done == (unsigned)nsteps * (unsigned)head->per[m][PK_W] && (nsteps & 1))
-                cur[m] ^= 1;
+            if (it.kind == PK_W && done == (unsigned)nm * (unsigned)head->per[m][PK_W] && (nm & 1)) cur[m] ^= 1;
         }
     }
 }

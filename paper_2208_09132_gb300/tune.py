@@ -55,9 +55,12 @@ def source_tag() -> str:
 
 
 def default_choice(cfg, precision):
-    """Launch shape without tuning: the face-store shape of the default scheme
+    """Launch shape without tuning: a face-store shape of the default scheme
     with the most cells per tile that fits the problem, velocity groups chosen
-    by the library (enough CTAs for a few waves)."""
+    by the library (enough CTAs for a few waves).  Among them, as measured on
+    the benchmark sizes: in FP64 the lean shapes (the FP64 exponentials of the
+    equilibria become per-axis tables); in 3D FP32 the lean sweep A with the
+    plain sweep B, then the full lean shape; in 1D / 2D FP32 the fused shapes."""
     D = cfg["dim"]
     best = None
     for t, _ in candidates(cfg, precision, "alone"):
@@ -65,7 +68,15 @@ def default_choice(cfg, precision):
         if not mode & 4:
             continue
         cells = int(np.prod(dims[:D]))
-        pref = (bool(mode & 128), mode & 3 == 0, cells if cells <= wl.ncells(cfg) else -cells)
+        if not mode & 128:
+            lean = 0
+        elif precision == cdugks.FP64:
+            lean = 2
+        elif D == 3:
+            lean = 1 if mode & 256 else 2
+        else:
+            lean = -1
+        pref = (lean, mode & 3 == 0, cells if cells <= wl.ncells(cfg) else -cells)
         if best is None or pref > best[0]:
             best = (pref, t)
     return (best[1] if best else 0), 0

@@ -129,3 +129,48 @@ def test_persistent_wait_timeout_is_reported_and_recovers():
     assert b.sync() == 0
     for (cfg, f), s in zip(probs, solvers):
         assert np.array_equal(s.moments(), _solo(cfg, f, prec, 3, tile).moments())
+
+
+def test_persistent_step_members_own_counts():
+    """One launch in which each member advances its own number of steps
+    (zero included), then a captured graph of the whole batch: every member
+    equals stepping it alone by its total."""
+    prec = cdugks.FP32
+    tile = cdugks.find_tile(prec, 1, (128,), 4)
+    probs = _members_1d(seed=21, count=5)
+    solvers = []
+    for cfg, f in probs:
+        s = cdugks.Solver(cfg, precision=prec, tile_id=tile, velocity_groups=2)
+        s.init(f)
+        solvers.append(s)
+    b = cdugks.Batch(solvers, persistent=True)
+    b.capture(2)
+    own = [3, 0, 5, 1, 4]
+    b.step_members(own)
+    b.step(2)                                   # one graph replay after the per-member launch
+    b.step_members([1, 2, 0, 2, 1])
+    assert b.sync() == 0
+    for (cfg, f), s, n in zip(probs, solvers, [3 + 2 + 1, 0 + 2 + 2, 5 + 2, 1 + 2 + 2, 4 + 2 + 1]):
+        assert s.info().steps == n
+        assert np.array_equal(s.moments(), _solo(cfg, f, prec, n, tile, 2).moments())
+
+
+def test_step_members_rejects_bad_calls():
+    prec = cdugks.FP32
+    tile = cdugks.find_tile(prec, 1, (128,), 4)
+    probs = _members_1d(seed=23, count=2)
+    solvers = []
+    for cfg, f in probs:
+        s = cdugks.Solver(cfg, precision=prec, tile_id=tile)
+        s.init(f)
+        solvers.append(s)
+    plain = cdugks.Batch(solvers)
+    with pytest.raises(cdugks.CdugksError):
+        plain.step_members([1, 1])             # needs the persistent step
+    del plain
+    b = cdugks.Batch(solvers, persistent=True)
+    with pytest.raises(cdugks.CdugksError):
+        b.step_members([1])                    # one count per member
+    with pytest.raises(cdugks.CdugksError):
+        b.step_members([1, -1])
+    assert b.sync() == 0

@@ -163,3 +163,26 @@ def test_issue_roofline_of_a_sweep():
     assert r["peak"] == pytest.approx(40.27, abs=0.01)
     assert r["achieved"] == pytest.approx(21.30, abs=0.01)
     assert r["frac"] == pytest.approx(0.529, abs=0.001)
+
+
+def test_one_at_a_time_server_model():
+    """The modelled one-at-a-time servers of the served-stream bench: a long
+    solve at t = 0, then a medium and a short one; FIFO keeps arrival order,
+    shortest-first takes the short one first when the server frees up, and the
+    cap counts only what finishes by then."""
+    import types
+
+    import bench
+
+    R = lambda a, n, p: types.SimpleNamespace(arrival=a, nsteps=n, points=p)
+    reqs = [R(0.0, 100, 10), R(0.1, 10, 10), R(0.2, 1, 10)]
+    fifo = bench.one_at_a_time(reqs, [10.0] * 3, 100.0, "fifo")
+    sjf = bench.one_at_a_time(reqs, [10.0] * 3, 100.0, "sjf")
+    # fifo: 0 -> 1.0, 1.0 -> 1.1, 1.1 -> 1.11 (times to solution 1.0, 1.0, 0.91);
+    # sjf: 0 -> 1.0, 1.0 -> 1.01 (the short one), 1.01 -> 1.11 (1.0, 0.81, 1.01)
+    assert fifo["finished"] == sjf["finished"] == 3
+    assert fifo["p99_time_to_solution_s"] == pytest.approx(1.0, abs=1e-9)
+    assert sjf["p99_time_to_solution_s"] == pytest.approx(float(np.percentile([1.0, 0.81, 1.01], 99)), abs=1e-9)
+    assert fifo["aggregate_point_updates_per_s"] == pytest.approx(1110 / 1.11)
+    capped = bench.one_at_a_time(reqs, [10.0] * 3, 0.5, "fifo")
+    assert capped["finished"] == 0 and capped["aggregate_point_updates_per_s"] == pytest.approx(1000.0)
