@@ -16,7 +16,7 @@ of 2D solves to t = 1, capped at 60 s of wall time) with modelled one-at-a-time
 FP32 and FP64 servers of the same requests.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c3|c3s|c4|c5|einfeldt] [--tune]
+                  [--workload c1|c2|c3|c3s|c3m|c4|c5|einfeldt] [--tune]
 
 N > 1 runs independent replicas (the path does not shard across GPUs on this
 build), one per rank under torch.distributed.run; value = all points / max time.
@@ -81,6 +81,8 @@ def pick_workload(name):
         return wl.workload_c3(kn=1e-4)
     if name == "c3s":        # 3D shear at half resolution in space and velocity
         return wl.workload_c3(kn=1e-4, scale=2, nv=12)
+    if name == "c3m":        # 3D shear on the full velocity grid at half resolution in space (profiling size)
+        return wl.workload_c3(kn=1e-4, scale=2, nv=24)
     if name == "einfeldt":   # the paper's high-resolution Einfeldt run (Sec. 3.2), FP64, to t = 0.125
         cfg, f = wl.einfeldt(nx=8192, nv=129)
         cfg["precision"] = "fp64"
@@ -159,14 +161,15 @@ def measured_peak_hbm():
 
 def kernel_source_sha():
     """Hash of the sweep kernels' source (the section of kernels.cuh that holds
-    them, and their launch helpers): profile counters taken on other source
-    are not reported."""
+    them, the lean sweeps and their launch helpers): profile counters taken on
+    other source are not reported."""
     csrc = os.path.join(ROOT, "paper_2208_09132_gb300", "csrc")
     txt = open(os.path.join(csrc, "kernels.cuh")).read()
     a = txt.index("// --------------------------------------------------------------- the sweep")
     b = txt.index("// Face constants from the group-summed face W")
     h = hashlib.sha256(txt[a:b].encode())
-    h.update(open(os.path.join(csrc, "sweeps_impl.cuh"), "rb").read())
+    for f in ("lean.cuh", "sweeps_impl.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -482,7 +485,8 @@ def run_served(args, ws, rank, local, sub=False):
     # warm-up: two short solves load and initialise everything
     serving.Server(budget_bytes=budget, device=dev).run(serving.stream_c5(count=2, t_end=0.002))
     torch.cuda.synchronize()
-    srv = serving.Server(budget_bytes=budget, max_slots=64, max_round=64, device=dev, policy=args.policy)
+    srv = serving.Server(budget_bytes=budget, max_slots=64, max_round=64, device=dev, policy=args.policy,
+                         fill_points=args.fill_points)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
@@ -497,7 +501,7 @@ def run_served(args, ws, rank, local, sub=False):
     torch.cuda.empty_cache()
     # every request alone, FP32 and FP64 (same requests, full nsteps modelled)
     ms32, ms64, ok = [], [], True
-    for q in sorted(reqs, key=lambda q: q.arrival):
+    for q in sorted(reqs, key=lambda q: q.arrival) if not args.skip_alone else []:
         a, oa = solo_step_ms(q, cdugks.FP32, dev)
         b, ob = solo_step_ms(q, cdugks.FP64, dev)
         torch.cuda.empty_cache()
@@ -505,8 +509,8 @@ def run_served(args, ws, rank, local, sub=False):
         ms64.append(b)
         ok = ok and oa and ob
     cap = args.serve_cap
-    alone32 = {o: one_at_a_time(reqs, ms32, cap, o) for o in ("fifo", "sjf")}
-    alone64 = {o: one_at_a_time(reqs, ms64, cap, o) for o in ("fifo", "sjf")}
+    alone32 = {o: one_at_a_time(reqs, ms32, cap, o) for o in ("fifo", "sjf")} if ms32 else None
+    alone64 = {o: one_at_a_time(reqs, ms64, cap, o) for o in ("fifo", "sjf")} if ms64 else None
     value = ws * rep["point_updates"] / wall
     total_pu = sum(q.points * q.nsteps for q in reqs)
     cfgd = {"workload": f"served_stream_{len(reqs)}_requests", "arrivals": "Poisson 50/s, seed 1",
@@ -520,7 +524,7 @@ def run_served(args, ws, rank, local, sub=False):
     served = {"value": value, "unit": UNIT, **rep,
               "fp32_one_at_a_time": alone32, "fp64_one_at_a_time": alone64,
               "vs_fp64_one_at_a_time": value / alone64["fifo"]["aggregate_point_updates_per_s"]
-              if alone64["fifo"]["aggregate_point_updates_per_s"] else None,
+              if alone64 and alone64["fifo"]["aggregate_point_updates_per_s"] else None,
               "one_at_a_time_what": "each request timed alone (3 steps after a warm-up, its default shape), "
                                     "then a one-at-a-time server of the same arrivals modelled from those step "
                                     "times under the same cap: first come first served (fifo) and shortest "
@@ -597,6 +601,8 @@ def run_ours(args, ws, rank, local):
         cfg["collision"] = args.collision
     if args.accel:
         cfg["accel"] = ([float(v) for v in args.accel.split(",")] + [0.0, 0.0])[:3]
+    if args.precision:
+        cfg["precision"] = args.precision
     prec = cdugks.FP64 if cfg["precision"] == "fp64" else cdugks.FP32
     pname = "fp64" if prec == cdugks.FP64 else "fp32"
     P = points(cfg)
@@ -840,13 +846,19 @@ def main():
                     help="served stream: wall-clock cap in seconds (default 120; 60 in the default line)")
     ap.add_argument("--policy", choices=["srpt", "share"], default="srpt",
                     help="served stream: shortest remaining work first, or every request every round")
+    ap.add_argument("--fill-points", type=float, default=1e8,
+                    help="served stream, srpt: points per step the shortest requests of a round fill")
+    ap.add_argument("--skip-alone", action="store_true",
+                    help="served stream: omit timing each request alone (the one-at-a-time models)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,
+                    help="override the workload's storage precision")
     ap.add_argument("--skip-served", action="store_true", help="omit the served sub-object of the 3D workload")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.steps is None:   # the einfeldt workload runs its whole solve; the 3D workload 20 steps, others 1000
         args.steps = (pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt"
-                      else (20 if args.workload in ("c3", "c3s") else 1000))
+                      else (20 if args.workload in ("c3", "c3s", "c3m") else 1000))
     if args.requests is None:
         args.requests = 64 if args.workload == "c5" else 8
     if args.serve_cap is None:
