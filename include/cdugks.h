@@ -338,8 +338,12 @@ CDUGKS_API int cdugks_test_wait_timeout(cdugks_t *h, int on);
  * bound and initialised, of one precision and dim; each keeps its own
  * workspace.  The batch needs a small caller-owned workspace for its tables
  * and runs on its own stream; do not touch the members on other streams
- * between cdugks_batch_bind and cdugks_batch_sync.  Results of a member are
- * the same as stepping it alone with the same tile shape and groups. */
+ * between cdugks_batch_bind and cdugks_batch_sync.  Members may use different
+ * tile shapes (up to 8) and physics: every fused shape (two-time or Shakhov
+ * collision model, either reconstruction) and the acceleration shapes batch;
+ * the prepared and stored shapes without acceleration do not.  Results of a
+ * member are the same as stepping it alone with the same tile shape and
+ * groups. */
 typedef struct cdugks_batch cdugks_batch_t;
 CDUGKS_API int cdugks_batch_create(cdugks_t *const *members, int n, cdugks_batch_t **out);
 CDUGKS_API int cdugks_batch_workspace_bytes(const cdugks_batch_t *b, size_t *bytes);

@@ -27,6 +27,7 @@ using cdg::Item;
 using cdg::PHead;
 using cdg::PItem;
 using cdg::PState;
+using cdg::QItem;
 using cdg::RItem;
 using cdg::VC;
 
@@ -1040,9 +1041,12 @@ struct cdugks_batch {
     std::vector<int> tile_ids;                 // distinct tile shapes, in plan order
     std::vector<std::vector<Item>> sweep_items;
     std::vector<RItem> face_items, cell_items;
+    std::vector<RItem> prep_items;             // acceleration members: the pre-pass
+    std::vector<QItem> faceq_items, cellq_items;   // Shakhov members: raw moments
     std::vector<unsigned char> insts;          // host image of the Inst<T> table
     std::vector<int> cur;
     size_t off_insts, off_cur, off_sweep[cdg::kMaxBatchShapes], off_face, off_cell, total;
+    size_t off_prep, off_faceq, off_cellq;
     unsigned char* base;
     cudaStream_t stream;
     bool bound;
@@ -1087,6 +1091,12 @@ BatchPlan plan_of(const cdugks_batch* b) {
     p.n_face = (int)b->face_items.size();
     p.cell_items = reinterpret_cast<const RItem*>(b->base + b->off_cell);
     p.n_cell = (int)b->cell_items.size();
+    p.prep_items = reinterpret_cast<const RItem*>(b->base + b->off_prep);
+    p.n_prep = (int)b->prep_items.size();
+    p.faceq_items = reinterpret_cast<const QItem*>(b->base + b->off_faceq);
+    p.n_faceq = (int)b->faceq_items.size();
+    p.cellq_items = reinterpret_cast<const QItem*>(b->base + b->off_cellq);
+    p.n_cellq = (int)b->cellq_items.size();
     return p;
 }
 
@@ -1135,9 +1145,9 @@ void batch_drop_graph(cdugks_batch* b) {
 int batch_member_ok(const cdugks* m, int prec, int D) {
     if (!m || !m->bound || !m->initialised) return fail(CDUGKS_ERR_UNBOUND, "every member must be bound and initialised");
     if (m->prec != prec || m->g.D != D) return fail(CDUGKS_ERR_INVALID, "members must share precision and dim");
-    if (cdg::mode_source(tile_mode(m->prec, m->g.D, m->g.tile_id)) != cdg::MODE_FUSED)
+    const int mode = tile_mode(m->prec, m->g.D, m->g.tile_id);
+    if (cdg::mode_source(mode) != cdg::MODE_FUSED && !cdg::mode_acc(mode))
         return fail(CDUGKS_ERR_INVALID, "prepared and stored tile shapes are not batched; choose another shape");
-    if (m->collision != CDUGKS_COLLISION_TEDDF) return fail(CDUGKS_ERR_INVALID, "Shakhov instances are not batched");
     return CDUGKS_OK;
 }
 
@@ -1191,6 +1201,29 @@ int batch_plan(cdugks_batch* b) {
             for (long long s0 = 0; s0 < g.nf[a]; s0 += R) b->face_items.push_back(RItem{i, a, s0, std::min(R, g.nf[a] - s0)});
         for (long long s0 = 0; s0 < g.Nc; s0 += R) b->cell_items.push_back(RItem{i, 0, s0, std::min(R, g.Nc - s0)});
     }
+    // the pre-pass of acceleration members (cells x runs of chunks) and the raw
+    // moments of Shakhov members (ranges x velocity groups), by member
+    b->prep_items.clear();
+    b->faceq_items.clear();
+    b->cellq_items.clear();
+    const long long RP = cdg::kPrepCells, RQ = 512;
+    for (int i = 0; i < n; ++i) {
+        const Geo& g = b->mem[i]->g;
+        if (g.accel) {
+            const int runs = (g.NVT + cdg::kPrepChunks - 1) / cdg::kPrepChunks;
+            for (int r = 0; r < runs; ++r)
+                for (long long s0 = 0; s0 < g.Nc; s0 += RP) b->prep_items.push_back(RItem{i, r, s0, std::min(RP, g.Nc - s0)});
+        }
+        if (g.shakhov) {
+            for (int gr = 0; gr < g.G; ++gr) {
+                for (int a = 0; a < D; ++a)
+                    for (long long s0 = 0; s0 < g.nf[a]; s0 += RQ)
+                        b->faceq_items.push_back(QItem{i, a, gr, 0, s0, std::min(RQ, g.nf[a] - s0)});
+                for (long long s0 = 0; s0 < g.Nc; s0 += RQ)
+                    b->cellq_items.push_back(QItem{i, -1, gr, 0, s0, std::min(RQ, g.Nc - s0)});
+            }
+        }
+    }
     if (b->prec == CDUGKS_FP32) fill_insts<float>(b);
     else fill_insts<double>(b);
     b->cur.assign(n, 0);
@@ -1241,6 +1274,9 @@ int batch_plan(cdugks_batch* b) {
     for (size_t k = 0; k < b->sweep_items.size(); ++k) b->off_sweep[k] = take(sizeof(Item) * b->sweep_items[k].size());
     b->off_face = take(sizeof(RItem) * b->face_items.size());
     b->off_cell = take(sizeof(RItem) * b->cell_items.size());
+    b->off_prep = take(sizeof(RItem) * b->prep_items.size());
+    b->off_faceq = take(sizeof(QItem) * b->faceq_items.size());
+    b->off_cellq = take(sizeof(QItem) * b->cellq_items.size());
     b->total = off;
     return CDUGKS_OK;
 }
@@ -1380,7 +1416,16 @@ int cdugks_batch_bind(cdugks_batch_t* b, void* device_ptr, size_t bytes, void* c
         ((e = cudaMemcpyAsync(b->base + b->off_face, b->face_items.data(), sizeof(RItem) * b->face_items.size(),
                               cudaMemcpyHostToDevice, b->stream)) ||
          (e = cudaMemcpyAsync(b->base + b->off_cell, b->cell_items.data(), sizeof(RItem) * b->cell_items.size(),
-                              cudaMemcpyHostToDevice, b->stream))))
+                              cudaMemcpyHostToDevice, b->stream)) ||
+         (!b->prep_items.empty() &&
+          (e = cudaMemcpyAsync(b->base + b->off_prep, b->prep_items.data(), sizeof(RItem) * b->prep_items.size(),
+                               cudaMemcpyHostToDevice, b->stream))) ||
+         (!b->faceq_items.empty() &&
+          (e = cudaMemcpyAsync(b->base + b->off_faceq, b->faceq_items.data(), sizeof(QItem) * b->faceq_items.size(),
+                               cudaMemcpyHostToDevice, b->stream))) ||
+         (!b->cellq_items.empty() &&
+          (e = cudaMemcpyAsync(b->base + b->off_cellq, b->cellq_items.data(), sizeof(QItem) * b->cellq_items.size(),
+                               cudaMemcpyHostToDevice, b->stream)))))
         return cuda_fail(e, "upload range items");
     if (b->pers && (e = batch_upload_persist(b))) return cuda_fail(e, "upload persistent plan");
     // members' own streams may still be working on their state

@@ -145,6 +145,12 @@ struct RItem {
     int inst, axis;
     long long start, count;
 };
+// Batched raw-moment work (Shakhov heat flux): faces [start, start + count) of
+// one axis (axis >= 0) or cells (axis = -1) of one instance, one velocity group.
+struct QItem {
+    int inst, axis, grp, pad;
+    long long start, count;
+};
 
 // ------------------------------------------------------------------ numerics
 
@@ -997,15 +1003,9 @@ __device__ __forceinline__ void force_gradient_chunk(const Geo& g, const double*
 // With the acceleration (ACC) it also forms the force terms F^n of the
 // sources from phi^n (= fa phi* + fb phi_eq) at the neighbouring velocities,
 // adds h/2 of them to phibar+ and stores them for the update.
-template <typename T, int D, bool ACC = false>
-__global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_thread) {
-    pdl_wait();
-    const Geo g = in->g;
-    const Bufs<T> bf = in->b[cur];
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.Nc) return;
+template <typename T, int D, bool ACC>
+__device__ __forceinline__ void prep_body(const Geo& g, const Bufs<T>& bf, long long c, int vt0, int vt1) {
     const CellC<T> cs = bf.cellc[c];
-    const int vt0 = blockIdx.y * chunks_per_thread, vt1 = min(g.NVT, vt0 + chunks_per_thread);
     // phi^n of this cell at velocity j (the deferred end of eq. phiupdate)
     auto phin = [&](int j, T& gv, T& bv) {
         const T* rec = bf.vel + (size_t)j * 8;
@@ -1089,6 +1089,34 @@ __global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_t
             Chunk<T>::store(bf.force + ad + VC, fb);
         }
     }
+}
+
+template <typename T, int D, bool ACC = false>
+__global__ void k_prep(const Inst<T>* __restrict__ in, int cur, int chunks_per_thread) {
+    pdl_wait();
+    const Geo g = in->g;
+    const Bufs<T> bf = in->b[cur];
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.Nc) return;
+    const int vt0 = blockIdx.y * chunks_per_thread;
+    prep_body<T, D, ACC>(g, bf, c, vt0, min(g.NVT, vt0 + chunks_per_thread));
+}
+
+// Batched: one CTA per item = cells [start, start + count) of one instance and
+// the run of kPrepChunks velocity chunks numbered axis (count <= blockDim).
+// Both pre-pass launches use blocks of kPrepCells cells, one thread per cell.
+constexpr int kPrepChunks = 8;
+constexpr int kPrepCells = 128;
+template <typename T, int D, bool ACC>
+__global__ void k_prep_batch(const RItem* __restrict__ items, const Inst<T>* __restrict__ insts,
+                             const int* __restrict__ cur) {
+    pdl_wait();
+    const RItem it = items[blockIdx.x];
+    if (threadIdx.x >= it.count) return;
+    const Geo g = insts[it.inst].g;
+    const Bufs<T> bf = insts[it.inst].b[cur[it.inst] & 1];
+    const int vt0 = it.axis * kPrepChunks;
+    prep_body<T, D, ACC>(g, bf, it.start + threadIdx.x, vt0, min(g.NVT, vt0 + kPrepChunks));
 }
 
 // phibar+ and its van Leer slopes for every point, for the stored shapes: one
@@ -2353,14 +2381,14 @@ __global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (Occ<T, D, T0_, T1
     sweep_body<T, D, T0_, T1_, T2_, SWEEP_B, MODE>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
-template <typename T, int D, int T0_, int T1_, int T2_>
-__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_>::value))
+template <typename T, int D, int T0_, int T1_, int T2_, bool SK = false, bool ACC = false>
+__global__ void __launch_bounds__(Tile<D, T0_, T1_, T2_>::NT, (FluxOcc<T, D, T0_, T1_, T2_, SK>::value))
     k_flux_batch(const Item* __restrict__ items, const Inst<T>* __restrict__ insts, const int* __restrict__ cur) {
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_wait();
     const Item it = items[blockIdx.x];
     const Inst<T>& in = insts[it.inst];
-    flux_body<T, D, T0_, T1_, T2_>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
+    flux_body<T, D, T0_, T1_, T2_, SK, ACC>(in.g, in.b[cur[it.inst] & 1], it.tile, it.grp, smem);
 }
 
 // ---- Shakhov model: raw velocity moments for the heat flux
@@ -2436,6 +2464,23 @@ __global__ void k_cellq(const Inst<T>* __restrict__ in, int cur) {
     const Bufs<T> bf = in->b[cur];
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < g.Nc) raw_moments<T, D>(g, bf.vel, bf.phi_out, g.Nc, c, blockIdx.y, bf.qs);
+}
+
+// Batched raw moments: one CTA per item (faces of one axis, or cells, of one
+// instance and one velocity group); faces read the stored face values, cells
+// the phi* that sweep B has just written.
+template <typename T, int D>
+__global__ void k_rawq_batch(const QItem* __restrict__ items, const Inst<T>* __restrict__ insts,
+                             const int* __restrict__ cur) {
+    pdl_wait();
+    const QItem it = items[blockIdx.x];
+    const Geo g = insts[it.inst].g;
+    const Bufs<T> bf = insts[it.inst].b[cur[it.inst] & 1];
+    const T* src = it.axis >= 0 ? bf.face[it.axis] : bf.phi_out;
+    double* dst = it.axis >= 0 ? bf.qf[it.axis] : bf.qs;
+    const long long n = it.axis >= 0 ? g.nf[it.axis] : g.Nc;
+    for (long long k = threadIdx.x; k < it.count; k += blockDim.x)
+        raw_moments<T, D>(g, bf.vel, src, n, it.start + k, it.grp, dst);
 }
 
 // Sums over the velocity groups of M per-group partial sums of one item

@@ -24,6 +24,12 @@ struct BatchPlan {
     int n_face;
     const RItem* cell_items;
     int n_cell;
+    const RItem* prep_items;     // acceleration members: cells x runs of kPrepChunks chunks
+    int n_prep;
+    const QItem* faceq_items;    // Shakhov members: raw face moments
+    int n_faceq;
+    const QItem* cellq_items;    // Shakhov members: raw cell moments
+    int n_cellq;
 };
 
 // Instantiated tile shapes of the sweeps per precision (f32 = FP32 storage) and dimension.

@@ -126,6 +126,9 @@ struct Shape {
     // no b-source (Pr = 1), chosen per launch; the Shakhov shapes have none.
     static constexpr bool NS = FACES && !SK;
     static constexpr int MODE_NS = MODE | MODE_NOSRC;
+    // batched steps: the fused shapes (incl. Shakhov) and the acceleration
+    // shapes (their pre-pass is batched too)
+    static constexpr bool BATCH = SRC == MODE_FUSED || ACC;
 
     // dynamic shared memory of the larger of the two sweeps
     static size_t smem_bytes() {
@@ -162,12 +165,12 @@ struct Shape {
                                           (int)shslope_smem_bytes<T, D, TX, TY, TZ, SK>())))
                 return e;
         }
-        if constexpr (SRC == MODE_FUSED && !SK) {
+        if constexpr (BATCH) {
             if ((e = cudaFuncSetAttribute(k_sweep_batch<T, D, TX, TY, TZ, false, MODE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes(false))))
                 return e;
             if constexpr (FACES) {
-                if ((e = cudaFuncSetAttribute(k_flux_batch<T, D, TX, TY, TZ>,
+                if ((e = cudaFuncSetAttribute(k_flux_batch<T, D, TX, TY, TZ, SK, ACC>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::bytes)))
                     return e;
             } else {
@@ -187,9 +190,9 @@ struct Shape {
         const dim3 grid(g.tiles[0] * g.tiles[1] * g.tiles[2], g.G);
         if (ev) cudaEventRecord(ev[0], s);
         if constexpr (SRC == MODE_PREP) {
-            constexpr int kChunks = 8;
-            const dim3 pg((unsigned)((g.Nc + 127) / 128), (unsigned)((g.NVT + kChunks - 1) / kChunks));
-            if ((e = launch_pdl(k_prep<T, D, ACC>, pg, dim3(128), 0, s, in, cur, kChunks))) return e;
+            const dim3 pg((unsigned)((g.Nc + kPrepCells - 1) / kPrepCells),
+                          (unsigned)((g.NVT + kPrepChunks - 1) / kPrepChunks));
+            if ((e = launch_pdl(k_prep<T, D, ACC>, pg, dim3(kPrepCells), 0, s, in, cur, kPrepChunks))) return e;
         } else if constexpr (SRC == MODE_STORED) {
             if ((e = launch_pdl(k_shslope<T, D, TX, TY, TZ, SK>, grid, dim3(TL::NT),
                                 shslope_smem_bytes<T, D, TX, TY, TZ, SK>(), s, in, cur)))
@@ -240,7 +243,7 @@ struct Shape {
 
     static cudaError_t sweep_batch(bool B, const Item* items, int n, const Inst<T>* insts, const int* cur,
                                    cudaStream_t s) {
-        if constexpr (SRC != MODE_FUSED || SK) {
+        if constexpr (!BATCH) {
             return cudaErrorNotSupported;
         } else {
             cudaError_t e = configure();
@@ -250,7 +253,8 @@ struct Shape {
                 return launch_pdl(k_sweep_batch<T, D, TX, TY, TZ, false, MODE>, dim3(n), dim3(TL::NT), SM::bytes(false),
                                   s, items, insts, cur);
             if constexpr (FACES)
-                return launch_pdl(k_flux_batch<T, D, TX, TY, TZ>, dim3(n), dim3(TL::NT), FS::bytes, s, items, insts, cur);
+                return launch_pdl(k_flux_batch<T, D, TX, TY, TZ, SK, ACC>, dim3(n), dim3(TL::NT), FS::bytes, s, items,
+                                  insts, cur);
             else
                 return launch_pdl(k_sweep_batch<T, D, TX, TY, TZ, true, MODE>, dim3(n), dim3(TL::NT), SM::bytes(true), s,
                                   items, insts, cur);
@@ -466,12 +470,35 @@ struct ShapeTable {
     }
 };
 
+template <typename T>
+cudaError_t launch_rawq_batch(int D, const QItem* items, int n, const Inst<T>* insts, const int* cur, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    switch (D) {
+        case 1: return launch_pdl(k_rawq_batch<T, 1>, dim3(n), dim3(kMomBlock), 0, s, items, insts, cur);
+        case 2: return launch_pdl(k_rawq_batch<T, 2>, dim3(n), dim3(kMomBlock), 0, s, items, insts, cur);
+        default: return launch_pdl(k_rawq_batch<T, 3>, dim3(n), dim3(kMomBlock), 0, s, items, insts, cur);
+    }
+}
+
+// Per batched step: the pre-pass of the acceleration members, sweep A per
+// tile shape, the raw face moments of the Shakhov members, the face
+// constants, sweep B per tile shape, the raw cell moments of the Shakhov
+// members, the W update.
 template <typename Table, typename T>
 cudaError_t run_batch_step(const BatchPlan& p, const Inst<T>* insts, int* cur, cudaStream_t s) {
     cudaError_t e;
+    if (p.n_prep > 0) {
+        switch (p.D) {
+            case 1: e = launch_pdl(k_prep_batch<T, 1, true>, dim3(p.n_prep), dim3(kPrepCells), 0, s, p.prep_items, insts, cur); break;
+            case 2: e = launch_pdl(k_prep_batch<T, 2, true>, dim3(p.n_prep), dim3(kPrepCells), 0, s, p.prep_items, insts, cur); break;
+            default: e = launch_pdl(k_prep_batch<T, 3, true>, dim3(p.n_prep), dim3(kPrepCells), 0, s, p.prep_items, insts, cur); break;
+        }
+        if (e) return e;
+    }
     for (int k = 0; k < p.ntile; ++k)
         if ((e = Table::sweep_batch(p.D, p.tile_id[k], false, p.sweep_items[k], p.n_sweep[k], insts, cur, s)))
             return e;
+    if ((e = launch_rawq_batch<T>(p.D, p.faceq_items, p.n_faceq, insts, cur, s))) return e;
     if (p.n_face > 0) {
         switch (p.D) {
             case 1: e = launch_pdl(k_facec_batch<T, 1>, dim3(p.n_face), dim3(kSmallBlock), 0, s, p.face_items, insts, cur); break;
@@ -483,6 +510,7 @@ cudaError_t run_batch_step(const BatchPlan& p, const Inst<T>* insts, int* cur, c
     for (int k = 0; k < p.ntile; ++k)
         if ((e = Table::sweep_batch(p.D, p.tile_id[k], true, p.sweep_items[k], p.n_sweep[k], insts, cur, s)))
             return e;
+    if ((e = launch_rawq_batch<T>(p.D, p.cellq_items, p.n_cellq, insts, cur, s))) return e;
     if (p.n_cell > 0) {
         switch (p.D) {
             case 1: e = launch_pdl(k_wupdate_batch<T, 1>, dim3(p.n_cell), dim3(kSmallBlock), 0, s, p.cell_items, insts, cur); break;

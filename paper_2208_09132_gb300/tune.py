@@ -148,10 +148,8 @@ def candidates(cfg, precision, context="alone"):
             continue                      # lean shapes need a velocity grid without a node at 0
         if bool(mode & 8) != r2 or bool(mode & 16) != sk or bool(mode & 32) != ac:
             continue                      # shapes of another reconstruction, collision or force compute another scheme
-        if context != "alone" and sk:
-            continue                      # Shakhov instances are not batched
-        if context != "alone" and mode & 3 != 0:
-            continue                      # only shapes that form phibar+ themselves are batched
+        if context != "alone" and mode & 3 != 0 and not mode & 32:
+            continue                      # batched: the fused shapes and the acceleration shapes
         if mode & 3 == 2 and dirichlet:
             continue                      # stored slopes: periodic / specular only
         tiles.append(t)

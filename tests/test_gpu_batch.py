@@ -23,6 +23,25 @@ def _members_1d(seed=0, count=6):
     return out
 
 
+def _batchable(prec, D):
+    """Tile shapes with a batched step: the fused shapes (either collision
+    model and reconstruction) and the acceleration shapes."""
+    out = []
+    for t in range(cdugks.load().cdugks_tile_count(prec, D)):
+        mode = cdugks.tile_shape(prec, D, t)[1]
+        if mode & 3 == 0 or mode & 32:
+            out.append(t)
+    return out
+
+
+def _physics(cfg, prec, D, t):
+    """The problem with the physics the tile shape implements."""
+    mode = cdugks.tile_shape(prec, D, t)[1]
+    acc = [0.4, -0.25, 0.15][:D] + [0.0] * (3 - D)
+    return dict(cfg, recon=1 if mode & 8 else 0, collision=1 if mode & 16 else 0,
+                accel=acc if mode & 32 else [0.0, 0.0, 0.0])
+
+
 def _solo(cfg, f, prec, steps, tile=0, groups=0):
     s = cdugks.Solver(cfg, precision=prec, tile_id=tile, velocity_groups=groups)
     s.init(f)
@@ -34,12 +53,11 @@ def _solo(cfg, f, prec, steps, tile=0, groups=0):
 @pytest.mark.parametrize("graph", [0, 3])
 def test_batch_equals_members_alone(prec, graph):
     steps = 7
-    batched = [t for t in range(cdugks.load().cdugks_tile_count(prec, 1))
-               if not cdugks.tile_shape(prec, 1, t)[1] & 19]          # prepared, stored and Shakhov shapes are not
-    tiles = [batched[k % len(batched)] for k in range(len(_members_1d()))]
-    # every shape, a member of a face-gradient shape with that reconstruction
-    probs = [(dict(cfg, recon=1 if cdugks.tile_shape(prec, 1, t)[1] & 8 else 0), f)
-             for (cfg, f), t in zip(_members_1d(), tiles)]
+    batched = _batchable(prec, 1)[:8]
+    members = _members_1d(count=max(6, len(batched)))
+    tiles = [batched[k % len(batched)] for k in range(len(members))]
+    # every batchable shape, each member with the physics of its shape
+    probs = [(_physics(cfg, prec, 1, t), f) for (cfg, f), t in zip(members, tiles)]
     solvers = []
     for (cfg, f), t in zip(probs, tiles):
         s = cdugks.Solver(cfg, precision=prec, tile_id=t)
@@ -54,6 +72,41 @@ def test_batch_equals_members_alone(prec, graph):
         ref = _solo(cfg, f, prec, steps, tile=t)
         assert np.array_equal(s.moments(), ref)
         assert s.info().steps == steps
+
+
+@pytest.mark.parametrize("prec", [cdugks.FP32, cdugks.FP64])
+@pytest.mark.parametrize("D", [2, 3])
+def test_batch_mixes_collision_models_and_acceleration(prec, D):
+    """One member per batchable shape of the dimension (two-time and Shakhov
+    collision models, the face-gradient reconstruction, the acceleration, the
+    lean shapes), stepped together in one batch and replayed from a graph:
+    each equals stepping it alone."""
+    tiles = _batchable(prec, D)[:8]
+    probs = []
+    for k, t in enumerate(tiles):
+        if D == 2:
+            cfg, f = wl.random_smooth(dim=2, n=(21 + 3 * k, 13 + k), nv=(10, 8), seed=40 + k, amp=0.3, kn=4e-3,
+                                      Pr=2.0 / 3.0)
+        else:
+            cfg, f = wl.random_smooth(dim=3, n=(9 + k, 7, 6), nv=(6, 6, 6), seed=60 + k, amp=0.3, kn=4e-3,
+                                      Pr=2.0 / 3.0)
+        probs.append((_physics(cfg, prec, D, t), f))
+    solvers = []
+    for (cfg, f), t in zip(probs, tiles):
+        s = cdugks.Solver(cfg, precision=prec, tile_id=t)
+        s.init(f)
+        solvers.append(s)
+    b = cdugks.Batch(solvers)
+    b.capture(2)
+    b.step(5)
+    assert b.sync() == 0
+    modes = set()
+    for (cfg, f), t, s in zip(probs, tiles, solvers):
+        modes.add(cdugks.tile_shape(prec, D, t)[1])
+        assert np.array_equal(s.moments(), _solo(cfg, f, prec, 5, tile=t)), (t, cfg.get("collision"), cfg["accel"])
+    assert any(m & 32 for m in modes)                  # an acceleration member took part
+    if D == 2:
+        assert any(m & 16 for m in modes)              # and a Shakhov member
 
 
 def test_batch_2d_members_and_uneven_steps():

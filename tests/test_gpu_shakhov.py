@@ -131,9 +131,26 @@ def test_shakhov_checkpoint_and_graph_replay_are_bitwise(precision):
         c.set_state(blob)                 # an image of the other collision model
 
 
-def test_shakhov_instances_are_not_batched():
+def test_shakhov_batches_in_fused_shapes_only():
+    """A fused Shakhov shape batches (and equals stepping alone); the stored
+    Shakhov shape of 3D, which needs its pre-pass, is refused."""
     (cfg, f), _ = case("1d_periodic_ragged_padded")
-    s = cdugks.Solver(_pr(cfg), precision=cdugks.FP32)
+    cfg = _pr(cfg)
+    s = cdugks.Solver(cfg, precision=cdugks.FP32)
     s.init(f)
+    b = cdugks.Batch([s])
+    b.step(4)
+    assert b.sync() == 0
+    alone = cdugks.Solver(cfg, precision=cdugks.FP32)
+    alone.init(f)
+    alone.step(4)
+    assert np.array_equal(s.moments(), alone.moments())
+    c3, f3 = wl.random_smooth(dim=3, n=(8, 6, 5), nv=(6, 6, 6), seed=2, amp=0.2, kn=1e-2)
+    c3["collision"] = wl.COLLISION_SHAKHOV
+    stored = [t for t in range(cdugks.load().cdugks_tile_count(cdugks.FP32, 3))
+              if cdugks.tile_shape(cdugks.FP32, 3, t)[1] & 16 and cdugks.tile_shape(cdugks.FP32, 3, t)[1] & 3 == 2]
+    assert stored
+    s3 = cdugks.Solver(c3, precision=cdugks.FP32, tile_id=stored[0])
+    s3.init(f3)
     with pytest.raises(cdugks.CdugksError):
-        cdugks.Batch([s])
+        cdugks.Batch([s3])

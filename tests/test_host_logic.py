@@ -38,16 +38,19 @@ def test_tuner_candidates_respect_batching_and_boundaries():
     alone = tune.candidates(cfg, cdugks.FP32, "alone")
     batch = tune.candidates(cfg, cdugks.FP32, "batch")
     modes = _modes(cdugks.FP32, 2)
-    # periodic: every shape of the default reconstruction and collision; batched: those that form phibar+ themselves
+    # periodic: every shape of the default reconstruction and collision; batched: the fused ones
     assert {t for t, _ in alone} == {t for t, m in enumerate(modes) if not m & 56}
     assert {t for t, _ in batch} == {t for t, m in enumerate(modes) if m & 3 == 0 and not m & 56}
     r2 = tune.candidates(dict(cfg, recon=1), cdugks.FP32, "alone")
     assert r2 and all(modes[t] & 8 for t, _ in r2)                      # the face-gradient shapes only
     sk = tune.candidates(dict(cfg, collision=wl.COLLISION_SHAKHOV), cdugks.FP32, "alone")
     assert sk and all(modes[t] & 16 for t, _ in sk)                     # the Shakhov shapes only
-    assert not tune.candidates(dict(cfg, collision=wl.COLLISION_SHAKHOV), cdugks.FP32, "batch")
+    skb = tune.candidates(dict(cfg, collision=wl.COLLISION_SHAKHOV), cdugks.FP32, "batch")
+    assert skb and all(modes[t] & 16 and modes[t] & 3 == 0 for t, _ in skb)   # batched: the fused Shakhov shapes
     ac = tune.candidates(dict(cfg, accel=[0.5, 0.0, 0.0]), cdugks.FP32, "alone")
     assert ac and all(modes[t] & 32 for t, _ in ac)                     # the acceleration shapes only
+    acb = tune.candidates(dict(cfg, accel=[0.5, 0.0, 0.0]), cdugks.FP32, "batch")
+    assert {t for t, _ in acb} == {t for t, _ in ac}                     # which batch too (with their pre-pass)
     assert all(g <= (wl.nvel(cfg) + 3) // 4 for _, g in alone)
     dcfg, _ = wl.random_smooth(dim=2, n=(8, 8), nv=(4, 4), seed=1, amp=0.1, kn=1e-2)
     dcfg = dict(dcfg, bc=[[wl.BC_DIRICHLET] * 2, [wl.BC_PERIODIC] * 2, [wl.BC_PERIODIC] * 2])

@@ -274,3 +274,23 @@ def test_admission_respects_the_memory_budget():
     assert len(done) == 5
     assert peak["used"] == 2 * one
     assert srv.used == 0
+
+
+@pytest.mark.gpu
+def test_server_mixes_collision_models_and_forces():
+    """Two-time, Shakhov and accelerated requests served together (one
+    launch per kernel: the batch holds several tile shapes), each equal to its
+    solve alone."""
+    base = [_req(0, 24, 12, "kh", 0.0, t_end=0.005), _req(1, 20, 12, "gresho", 0.0, t_end=0.004),
+            _req(2, 28, 10, "kh", 0.005, t_end=0.004), _req(3, 18, 12, "gresho", 0.01, t_end=0.003)]
+    base[1].cfg["collision"] = wl.COLLISION_SHAKHOV
+    base[2].cfg["accel"] = [0.0, -0.5, 0.0]
+    base[3].cfg["collision"] = wl.COLLISION_SHAKHOV
+    srv = serving.Server(budget_bytes=8 << 30, max_round=2, persistent=False)
+    done = srv.run(base)
+    assert len(done) == 4
+    for q in done:
+        s = cdugks.Solver(q.cfg, precision=q.precision, tile_id=q.tile_id, velocity_groups=q.velocity_groups)
+        s.init(q.fields)
+        s.step(q.nsteps)
+        assert np.array_equal(s.moments(), q.result), q.rid
