@@ -79,18 +79,19 @@ def _check(oracle_mod, cfg, f, steps_before, nsamples, tile, groups, tol_W, tol_
 
 
 def test_kelvin_helmholtz_full_size(oracle_mod):
-    """256^2 cells x 32^2 velocities, FP32, the tuned launch shape."""
+    """256^2 cells x 32^2 velocities, FP32, the launch shape the bench times."""
     cfg, f = wl.workload_c2()
-    tile, groups = tune.tune(cfg, cdugks.FP32, context="alone")
+    tile, groups = tune.choose(cfg, cdugks.FP32, context="alone")      # the shape bench.py times
     _check(oracle_mod, cfg, f, steps_before=5, nsamples=4, tile=tile, groups=groups, tol_W=1e-5, tol_phi=1e-5)
 
 
 def test_shear_3d_full_size(oracle_mod):
-    """64^3 cells x 24^3 velocities, FP32 (about 29 GB per state buffer), the tuned shape."""
+    """64^3 cells x 24^3 velocities, FP32 (about 29 GB per state buffer), the launch shape the bench
+    times (the lean sweep A with the plain sweep B)."""
     import torch
     free, _ = torch.cuda.mem_get_info()
     cfg, f = wl.workload_c3(kn=1e-2)
     if free < 120e9:
         pytest.skip("needs about 120 GB of free device memory")
-    tile, groups = tune.tune(cfg, cdugks.FP32, context="alone", steps=2)
+    tile, groups = tune.choose(cfg, cdugks.FP32, context="alone")      # the shape bench.py times
     _check(oracle_mod, cfg, f, steps_before=2, nsamples=2, tile=tile, groups=groups, tol_W=1e-5, tol_phi=1e-5)
