@@ -16,7 +16,7 @@ of 2D solves to t = 1, capped at 60 s of wall time) with modelled one-at-a-time
 FP32 and FP64 servers of the same requests.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c3|c3s|c3m|c4|c5|einfeldt] [--tune]
+                  [--workload c1|c2|c3|c3s|c3m|c3p|c4|c5|einfeldt] [--tune]
 
 N > 1 runs independent replicas (the path does not shard across GPUs on this
 build), one per rank under torch.distributed.run; value = all points / max time.
@@ -81,8 +81,10 @@ def pick_workload(name):
         return wl.workload_c3(kn=1e-4)
     if name == "c3s":        # 3D shear at half resolution in space and velocity
         return wl.workload_c3(kn=1e-4, scale=2, nv=12)
-    if name == "c3m":        # 3D shear on the full velocity grid at half resolution in space (profiling size)
+    if name == "c3m":        # 3D shear on the full velocity grid at half resolution in space
         return wl.workload_c3(kn=1e-4, scale=2, nv=24)
+    if name == "c3p":        # the same at quarter resolution in space (a few GB: the counter-capture size)
+        return wl.workload_c3(kn=1e-4, scale=4, nv=24)
     if name == "einfeldt":   # the paper's high-resolution Einfeldt run (Sec. 3.2), FP64, to t = 0.125
         cfg, f = wl.einfeldt(nx=8192, nv=129)
         cfg["precision"] = "fp64"
@@ -858,7 +860,7 @@ def main():
         args.warmup = 3
     if args.steps is None:   # the einfeldt workload runs its whole solve; the 3D workload 20 steps, others 1000
         args.steps = (pick_workload("einfeldt")[0]["steps"] if args.workload == "einfeldt"
-                      else (20 if args.workload in ("c3", "c3s", "c3m") else 1000))
+                      else (20 if args.workload in ("c3", "c3s", "c3m", "c3p") else 1000))
     if args.requests is None:
         args.requests = 64 if args.workload == "c5" else 8
     if args.serve_cap is None:
