@@ -1248,8 +1248,13 @@ int batch_plan(cdugks_batch* b) {
             b->pitems.push_back(PItem{x.inst, cdg::PK_W, 0, 0, x.start, x.count});
             ++b->pper[(size_t)x.inst * 4 + cdg::PK_W];
         }
-        if (n > b->pcap_mem || (long long)b->pitems.size() > b->pcap_items)
-            return fail(CDUGKS_ERR_INVALID, "the persistent batch holds more members or items than reserved");
+        if (n > cdg::kPMaxMembers) return fail(CDUGKS_ERR_INVALID, "too many members for a persistent batch");
+        if (n > b->pcap_mem || (long long)b->pitems.size() > b->pcap_items) {
+            // bound (an in-place rewrite): no room; unbound: grow the reservation
+            if (b->bound) return fail(CDUGKS_ERR_INVALID, "the persistent batch holds more members or items than reserved");
+            b->pcap_mem = std::max(b->pcap_mem, n);
+            b->pcap_items = std::max(b->pcap_items, (long long)b->pitems.size());
+        }
     }
     size_t off = 0;
     auto take = [&](size_t bytes) {
