@@ -848,7 +848,7 @@ def main():
                     help="served stream: wall-clock cap in seconds (default 120; 60 in the default line)")
     ap.add_argument("--policy", choices=["srpt", "share"], default="srpt",
                     help="served stream: shortest remaining work first, or every request every round")
-    ap.add_argument("--fill-points", type=float, default=1e8,
+    ap.add_argument("--fill-points", type=float, default=3e7,
                     help="served stream, srpt: points per step the shortest requests of a round fill")
     ap.add_argument("--skip-alone", action="store_true",
                     help="served stream: omit timing each request alone (the one-at-a-time models)")

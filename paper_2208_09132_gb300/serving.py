@@ -135,7 +135,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_slots: int = 64, max_round: int = 64, device: str = "cuda:0",
                  clock=time.perf_counter, persistent: bool = True, round_target_s: float = 0.025,
-                 max_items: int = 1 << 18, policy: str = "srpt", fill_points: float = 1e8):
+                 max_items: int = 1 << 18, policy: str = "srpt", fill_points: float = 3e7):
         if policy not in ("srpt", "share"):
             raise ValueError(f"unknown policy {policy}")
         self.budget = int(budget_bytes)
