@@ -470,7 +470,7 @@ def run_served(args, ws, rank, local, sub=False):
     """The served stream: Poisson arrivals (50/s) of 2D Gresho-vortex and
     Kelvin-Helmholtz solves, grids 64^2-512^2, velocity grids 16^2-48^2, Kn
     1e-4..1, each run to t = 1, admitted by device-memory footprint and stepped
-    together (persistent batched step, one launch per round), for at most
+    together (one launch per kernel and step), for at most
     args.serve_cap seconds of wall time.  Then each request is timed alone in
     FP32 and in FP64, and a one-at-a-time server of the same requests is modelled
     from those step times under the same cap.  sub=True: the "served" part of
@@ -488,7 +488,7 @@ def run_served(args, ws, rank, local, sub=False):
     serving.Server(budget_bytes=budget, device=dev).run(serving.stream_c5(count=2, t_end=0.002))
     torch.cuda.synchronize()
     srv = serving.Server(budget_bytes=budget, max_slots=64, max_round=64, device=dev, policy=args.policy,
-                         fill_points=args.fill_points)
+                         fill_points=args.fill_points, persistent=args.serve_launch == "persistent")
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
@@ -522,7 +522,7 @@ def run_served(args, ws, rank, local, sub=False):
             "total_point_updates_requested": total_pu,
             "admission": "device-memory footprint within 60% of free memory, <= 64 slots",
             "tile_id": serving.persistent_tile(cdugks.FP32, 2), "tile": [32, 8],
-            "sweep_mode": "fused, face store"}
+            "sweep_mode": "fused, face store", "launch": rep["launch"], "policy": rep["policy"]}
     served = {"value": value, "unit": UNIT, **rep,
               "fp32_one_at_a_time": alone32, "fp64_one_at_a_time": alone64,
               "vs_fp64_one_at_a_time": value / alone64["fifo"]["aggregate_point_updates_per_s"]
@@ -850,6 +850,8 @@ def main():
                     help="served stream: shortest remaining work first, or every request every round")
     ap.add_argument("--fill-points", type=float, default=3e7,
                     help="served stream, srpt: points per step the shortest requests of a round fill")
+    ap.add_argument("--serve-launch", choices=["persistent", "per-kernel"], default="per-kernel",
+                    help="served stream: the persistent batched step (per-member step counts) or one launch per kernel")
     ap.add_argument("--skip-alone", action="store_true",
                     help="served stream: omit timing each request alone (the one-at-a-time models)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,

@@ -1192,14 +1192,34 @@ int batch_plan(cdugks_batch* b) {
             const int wx = std::min(gx.ntpg, gx.NVT - x.grp * gx.ntpg), wy = std::min(gy.ntpg, gy.NVT - y.grp * gy.ntpg);
             return wx > wy;
         });
-    const long long R = 1024;
+    // face and cell ranges: whole blocks of the kernel that runs them (64 threads,
+    // or the persistent shape's threads), sized so that the batch has about 2048
+    // of each (a few ranges of a lone member would leave most SMs idle while
+    // each thread loops over FP64 work; many members need no smaller ones)
+    long long unit = 64;
+    if (b->pers) {
+        const cdg::TileShape ts = tile_of(b->prec, D, b->tile_ids[0]);
+        unit = (long long)ts.t[0] * ts.t[1] * ts.t[2];
+    }
+    long long tot_f = 0, tot_c = 0;
+    for (int i = 0; i < n; ++i) {
+        const Geo& g = b->mem[i]->g;
+        for (int a = 0; a < D; ++a) tot_f += g.nf[a];
+        tot_c += g.Nc;
+    }
+    auto range_size = [&](long long tot) {
+        const long long r = (tot / 2048 + unit - 1) / unit * unit;
+        return std::max(unit, std::min(r, std::max(unit, 1024 / unit * unit)));
+    };
+    const long long RF = range_size(tot_f), RC = range_size(tot_c);
     b->face_items.clear();
     b->cell_items.clear();
     for (int i = 0; i < n; ++i) {
         const Geo& g = b->mem[i]->g;
         for (int a = 0; a < D; ++a)
-            for (long long s0 = 0; s0 < g.nf[a]; s0 += R) b->face_items.push_back(RItem{i, a, s0, std::min(R, g.nf[a] - s0)});
-        for (long long s0 = 0; s0 < g.Nc; s0 += R) b->cell_items.push_back(RItem{i, 0, s0, std::min(R, g.Nc - s0)});
+            for (long long s0 = 0; s0 < g.nf[a]; s0 += RF)
+                b->face_items.push_back(RItem{i, a, s0, std::min(RF, g.nf[a] - s0)});
+        for (long long s0 = 0; s0 < g.Nc; s0 += RC) b->cell_items.push_back(RItem{i, 0, s0, std::min(RC, g.Nc - s0)});
     }
     // the pre-pass of acceleration members (cells x runs of chunks) and the raw
     // moments of Shakhov members (ranges x velocity groups), by member

@@ -7,11 +7,11 @@ The server
   free (admission by HBM footprint: the request's workspace bytes from
   ``cdugks_workspace_bytes``, against a byte budget), allocating its
   workspace and initialising its state on the device while the batch runs;
-* steps every active request together as one batch, in rounds: with the
-  persistent batched step (the default) one launch per round in which each
-  member advances its own number of steps (``cdugks_batch_step_members``),
-  never past its own step count, so a request computes exactly what it would
-  alone;
+* steps the selected requests together as one batch, in rounds of one
+  launch per kernel and step (or, with the persistent batched step, one
+  launch per round in which each member advances its own number of steps,
+  ``cdugks_batch_step_members``), never past a request's own step count, so
+  a request computes exactly what it would alone;
 * retires a request when it reaches its end time: reads its macroscopic
   fields back, frees its workspace, and records its time to solution;
 * changes the batch's membership in place between rounds
@@ -116,12 +116,15 @@ class Server:
     * ``"share"``: every resident request advances every round (processor
       sharing).
 
-    persistent=True (the default) steps the batch with the persistent batched
-    step: a round is one launch in which every member advances
-    min(round steps, its remaining steps), so a member near its end neither
-    shortens the round for the others nor runs past its own step count
-    (otherwise a round is min over members of the remaining steps, one launch
-    per kernel and step).  The round length adapts so that a round takes about
+    By default a round steps the batch with one launch per kernel and step,
+    for min over its members of their remaining steps (a member never runs
+    past its own step count).  persistent=True uses the persistent batched
+    step instead: a round is one launch in which every member advances
+    min(round steps, its remaining steps), so a member near its end does not
+    shorten the round for the others; with the few large members the
+    shortest-first policy selects it is slower than the launch chain (its
+    loads are coherent and its phases wait per member), so it is not the
+    default.  The round length adapts so that a round takes about
     ``round_target_s`` of device time (from the measured point-update rate),
     which bounds how long a new request waits to be scheduled.
 
@@ -134,7 +137,7 @@ class Server:
     """
 
     def __init__(self, budget_bytes: int, max_slots: int = 64, max_round: int = 64, device: str = "cuda:0",
-                 clock=time.perf_counter, persistent: bool = True, round_target_s: float = 0.025,
+                 clock=time.perf_counter, persistent: bool = False, round_target_s: float = 0.025,
                  max_items: int = 1 << 18, policy: str = "srpt", fill_points: float = 3e7):
         if policy not in ("srpt", "share"):
             raise ValueError(f"unknown policy {policy}")
@@ -171,9 +174,23 @@ class Server:
         return q.points * (q.nsteps - q.done_steps)
 
     # -- admission --------------------------------------------------------
+    def _default_tile(self, req: Request) -> int:
+        """The face-store shape with the persistent step for requests of the
+        default physics (the shape the persistent batch needs, and the tuned one
+        for the 2D workloads); the library's default shape for the request's
+        physics otherwise (collision model, force, reconstruction)."""
+        plain = not (req.cfg.get("collision", 0) or req.cfg.get("recon", 0) or any(req.cfg.get("accel", (0.0,))))
+        if self.persistent or plain:
+            try:
+                return persistent_tile(req.precision, int(req.cfg["dim"]))
+            except ValueError:
+                if self.persistent:
+                    raise
+        return 0
+
     def submit(self, req: Request):
-        if self.persistent and not req.tile_id:
-            req.tile_id = persistent_tile(req.precision, int(req.cfg["dim"]))
+        if not req.tile_id:
+            req.tile_id = self._default_tile(req)
         req.footprint = footprint_bytes(req)
         if req.footprint > self.budget:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the budget {self.budget}")
