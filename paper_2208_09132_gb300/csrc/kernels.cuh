@@ -1458,7 +1458,11 @@ __device__ __forceinline__ void sweep_body(const Geo g, const Bufs<T> bf, int ti
     constexpr int NCCV = SM::NCCV, NFCV = SM::NFCV;
     static_assert(VC == 4, "the shared-memory layout packs one chunk in a V4");
     static_assert(TL::NT % 32 == 0, "whole warps");
-    constexpr bool STAGE = SM::stage(SWEEP_B) && !PERS;    // (the persistent step loads directly, coherently)
+    // The persistent step stages too, with cp.async only (no tensor maps): its
+    // copies are issued after the item's acquire of the counts it waits for, and
+    // read through the generic proxy (L2, or L1 after the acquire) -- coherent
+    // like its direct loads, which take no read-only path.
+    constexpr bool STAGE = SM::stage(SWEEP_B);
     constexpr bool NC = !PERS;
     Q* const P = reinterpret_cast<Q*>(smem);      // [2][PN] phibar+ chunk per cell
     Q* const S = P + SM::nP;                      // [D][2][SB] half van Leer slopes times dx
