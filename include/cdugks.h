@@ -381,7 +381,8 @@ CDUGKS_API void cdugks_batch_destroy(cdugks_batch_t *b);
  * the batch workspace (at least the current sizes; items are the batch's work
  * items per step): while later cdugks_batch_admit / cdugks_batch_retire calls
  * of members of that shape fit, they rewrite the device tables in place and
- * keep the binding and any captured graph; otherwise they unbind as usual.
+ * keep the binding and any captured graph; otherwise they unbind as usual and
+ * the plan reserves room for the new sizes (bind again).
  * Results equal the per-kernel launches bit for bit.  Unbinds the batch (query
  * the workspace size and bind again).  Errors: INVALID (several shapes, a shape
  * without it, more than 1024 members). */
@@ -390,9 +391,10 @@ CDUGKS_API int cdugks_batch_set_persistent(cdugks_batch_t *b, int on, int max_me
 CDUGKS_API int cdugks_batch_bound(const cdugks_batch_t *b);
 /* Persistent batches only: one launch in which member i (in the order of
  * creation and admission, retired members removed) advances steps[i] >= 0
- * steps (n = the number of members); a member that stops early just waits for
- * the launch to end.  Asynchronous on the batch stream.  Errors: UNBOUND,
- * INVALID (not persistent, wrong n, negative count), CUDA. */
+ * steps (n = the number of members); the items of a member past its count are
+ * skipped.  Asynchronous on the batch stream (the counts are copied before the
+ * call returns).  Errors: UNBOUND, INVALID (not persistent, wrong n, negative
+ * count), CUDA. */
 CDUGKS_API int cdugks_batch_step_members(cdugks_batch_t *b, const int *steps, int n);
 /* Testing hook for the persistent step's bounded waits (on = 1; 0 restores):
  * the first face item waits for one item more than exists and every wait gives
