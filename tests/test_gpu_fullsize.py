@@ -95,3 +95,37 @@ def test_shear_3d_full_size(oracle_mod):
         pytest.skip("needs about 120 GB of free device memory")
     tile, groups = tune.choose(cfg, cdugks.FP32, context="alone")      # the shape bench.py times
     _check(oracle_mod, cfg, f, steps_before=2, nsamples=2, tile=tile, groups=groups, tol_W=1e-5, tol_phi=1e-5)
+
+
+def test_batched_thermoacoustic_full_size(oracle_mod):
+    """All 256 members of the batched workload in the launch configuration the
+    bench times (the persistent batched step, 1D face-store tiles of 128 cells,
+    one velocity group, a CUDA graph of 10 steps), 20 steps, every member
+    against the oracle: relative L-infinity <= 1e-5 on rho and T, and on u
+    relative to the thermal speed (the gas is at rest up to a conduction-driven
+    flow ~1e-6 of it)."""
+    import math
+
+    probs = wl.workload_c4()
+    tile = cdugks.find_tile(cdugks.FP32, 1, (128,), 4)
+    members = []
+    for cfg, f in probs:
+        s = cdugks.Solver(cfg, precision=cdugks.FP32, tile_id=tile, velocity_groups=1)
+        s.init(f)
+        members.append(s)
+    b = cdugks.Batch(members, persistent=True)
+    b.capture(10)
+    b.step(20)
+    assert b.sync() == 0
+    worst = np.zeros(3)
+    for (cfg, f), s in zip(probs, members):
+        o = oracle_mod.Oracle(cfg)
+        o.init(f)
+        o.step(20)
+        got, ref = s.moments(), o.moments()
+        err = np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)
+        err[1] = np.abs(got[:, 1] - ref[:, 1]).max() / math.sqrt(cfg["R"] * cfg["T_ref"])
+        worst = np.maximum(worst, err)
+        assert np.all(err <= 1e-5), (cfg["name"], err)
+    print(f"\n[fullsize] batched thermoacoustic, 256 members, 20 steps: worst rel Linf rho,u,T = "
+          f"{', '.join(f'{e:.1e}' for e in worst)}")
