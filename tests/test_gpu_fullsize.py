@@ -129,3 +129,31 @@ def test_batched_thermoacoustic_full_size(oracle_mod):
         assert np.all(err <= 1e-5), (cfg["name"], err)
     print(f"\n[fullsize] batched thermoacoustic, 256 members, 20 steps: worst rel Linf rho,u,T = "
           f"{', '.join(f'{e:.1e}' for e in worst)}")
+
+
+def test_served_requests_full_size(oracle_mod):
+    """The first three requests of the served stream at their stated sizes (86^2 x
+    45^2, 150^2 x 29^2, 127^2 x 38^2, Gresho / Kelvin-Helmholtz, Kn from the
+    stream), served together in the server's launch configuration, each to five
+    of its steps, against the oracle (relative L-infinity <= 1e-5)."""
+    from paper_2208_09132_gb300 import serving
+
+    reqs = serving.stream_c5(count=3)
+    for q in reqs:
+        s = cdugks.Solver(q.cfg, precision=q.precision)     # its time step, through the library
+        q.t_end = 5 * s.dt                                  # five steps
+        q.arrival = 0.0
+        del s
+    srv = serving.Server(budget_bytes=32 << 30, max_round=2)
+    done = srv.run(reqs)
+    assert len(done) == 3
+    for q in done:
+        assert q.nsteps == 5 and q.done_steps == 5
+        o = oracle_mod.Oracle(q.cfg)
+        o.init(q.fields)
+        o.step(5)
+        ref = o.moments()
+        den = np.abs(ref).max(axis=0)
+        den[1:-1] = den[1:-1].max()
+        err = np.abs(q.result - ref).max(axis=0) / den
+        assert np.all(err <= 1e-5), (q.cfg["name"], err)
