@@ -163,14 +163,14 @@ def measured_peak_hbm():
 
 def kernel_source_sha():
     """Hash of the sweep kernels' source (the section of kernels.cuh that holds
-    them, the lean sweeps and their launch helpers): profile counters taken on
-    other source are not reported."""
+    them, the lean sweeps, the persistent batched step and their launch
+    helpers): profile counters taken on other source are not reported."""
     csrc = os.path.join(ROOT, "paper_2208_09132_gb300", "csrc")
     txt = open(os.path.join(csrc, "kernels.cuh")).read()
     a = txt.index("// --------------------------------------------------------------- the sweep")
     b = txt.index("// Face constants from the group-summed face W")
     h = hashlib.sha256(txt[a:b].encode())
-    for f in ("lean.cuh", "sweeps_impl.cuh"):
+    for f in ("lean.cuh", "persist.cuh", "sweeps_impl.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -344,6 +344,9 @@ def run_batched(args, ws, rank, local, sub=False):
     value = ws * P * K / (total_ms / 1e3)
     peak, peak_kind = measured_peak_hbm()
     achieved = 24 * P / (total_ms / K / 1e3) / 1e9
+    # DRAM bytes of one launch (gsteps steps of every member) from the committed capture
+    tpp = ncu_traffic("c4", "persistent", "fp32", tile, 1)
+    traffic = None if tpp is None else tpp * P * gsteps
     # step latency: single-step graph replays (one launch each), each between two events
     stream = batch.stream
     batch.capture(1)
@@ -395,7 +398,12 @@ def run_batched(args, ws, rank, local, sub=False):
                 "launch": launch, "tile": [128], "velocity_groups": 1, "latency_ms": lat,
                 "per_kernel_launches": per_kernel, "fp64_plain": fp64,
                 "vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
-                "step_hbm_frac": round(achieved / peak, 4), "status_ok": status == 0}
+                "step_hbm_frac": round(achieved / peak, 4),
+                "roofline": {"bound": "hbm", "kernel": "persistent batched step", "achieved": round(achieved, 1),
+                             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                             "algorithmic_bytes_per_point": 24, "traffic": traffic,
+                             "traffic_per": f"launch ({gsteps} steps of every member)"},
+                "status_ok": status == 0}
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -406,7 +414,7 @@ def run_batched(args, ws, rank, local, sub=False):
         "latency_ms": lat,
         "roofline": {"bound": "hbm", "kernel": "persistent batched step", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "algorithmic_bytes_per_point": 24, "traffic": None},
+                     "algorithmic_bytes_per_point": 24, "traffic": traffic},
         "cpu_baseline": None, "e2e": None, "fp64_plain": fp64, "per_kernel_launches": per_kernel,
         "gpu_launches": K // gsteps, "clocks": clk, "status_ok": status == 0,
     }
