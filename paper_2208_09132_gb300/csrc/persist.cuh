@@ -127,20 +127,21 @@ __global__ void __launch_bounds__(Tile<D, TX, TY, TZ>::NT, (PersistSmem<T, D, TX
         }
         __syncthreads();
         if (!s_ok) break;
-        // the member's record as register / local copies (the bodies read its fields
-        // often; through a reference every store could alias them)
+        // Every body takes the member's record from the table directly: a copy
+        // of the whole record on every thread's stack, made again for every
+        // item, cost more than the items' own state traffic (each item's
+        // acquire also evicts the stack lines from L1, so they go out to L2).
         const int c = (cur[m] + s) & 1;
-        const Geo g = insts[m].g;
-        const Bufs<T> bf = insts[m].b[c];
+        const Inst<T>& in = insts[m];
         if (it.kind == PK_A) {
-            sweep_body<T, D, TX, TY, TZ, false, MODE, true>(g, bf, it.a, it.b, smem);
+            sweep_body<T, D, TX, TY, TZ, false, MODE, true>(in.g, in.b[c], it.a, it.b, smem);
         } else if (it.kind == PK_F) {
-            for (long long k = t; k < it.count; k += NT) facec_body<T, D>(g, bf, it.a, it.start + k);
+            for (long long k = t; k < it.count; k += NT) facec_body<T, D>(in.g, in.b[c], it.a, it.start + k);
         } else if (it.kind == PK_B) {
-            if constexpr (FACES) flux_body<T, D, TX, TY, TZ, false, false, false, true>(g, bf, it.a, it.b, smem);
-            else sweep_body<T, D, TX, TY, TZ, true, MODE, true>(g, bf, it.a, it.b, smem);
+            if constexpr (FACES) flux_body<T, D, TX, TY, TZ, false, false, false, true>(in.g, in.b[c], it.a, it.b, smem);
+            else sweep_body<T, D, TX, TY, TZ, true, MODE, true>(in.g, in.b[c], it.a, it.b, smem);
         } else {
-            for (long long k = t; k < it.count; k += NT) wupdate_body<T, D>(g, bf, it.start + k);
+            for (long long k = t; k < it.count; k += NT) wupdate_body<T, D>(in.g, in.b[c], it.start + k);
         }
         __syncthreads();
         if (t == 0) {
