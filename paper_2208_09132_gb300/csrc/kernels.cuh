@@ -1113,10 +1113,9 @@ __global__ void k_prep_batch(const RItem* __restrict__ items, const Inst<T>* __r
     pdl_wait();
     const RItem it = items[blockIdx.x];
     if (threadIdx.x >= it.count) return;
-    const Geo g = insts[it.inst].g;
-    const Bufs<T> bf = insts[it.inst].b[cur[it.inst] & 1];
+    const Inst<T>& in = insts[it.inst];
     const int vt0 = it.axis * kPrepChunks;
-    prep_body<T, D, ACC>(g, bf, it.start + threadIdx.x, vt0, min(g.NVT, vt0 + kPrepChunks));
+    prep_body<T, D, ACC>(in.g, in.b[cur[it.inst] & 1], it.start + threadIdx.x, vt0, min(in.g.NVT, vt0 + kPrepChunks));
 }
 
 // phibar+ and its van Leer slopes for every point, for the stored shapes: one
@@ -2478,8 +2477,8 @@ __global__ void k_rawq_batch(const QItem* __restrict__ items, const Inst<T>* __r
                              const int* __restrict__ cur) {
     pdl_wait();
     const QItem it = items[blockIdx.x];
-    const Geo g = insts[it.inst].g;
-    const Bufs<T> bf = insts[it.inst].b[cur[it.inst] & 1];
+    const Geo& g = insts[it.inst].g;
+    const Bufs<T>& bf = insts[it.inst].b[cur[it.inst] & 1];
     const T* src = it.axis >= 0 ? bf.face[it.axis] : bf.phi_out;
     double* dst = it.axis >= 0 ? bf.qf[it.axis] : bf.qs;
     const long long n = it.axis >= 0 ? g.nf[it.axis] : g.Nc;
@@ -2569,12 +2568,12 @@ __global__ void k_facec_batch(const RItem* __restrict__ items, const Inst<T>* __
                               const int* __restrict__ cur) {
     pdl_wait();
     const RItem it = items[blockIdx.x];
-    // the member's record as register / local copies: its fields are read per
-    // face, and through a reference into global memory every store of the body
-    // could alias them (measured 1.5x slower on small batched members)
-    const Geo g = insts[it.inst].g;
-    const Bufs<T> bf = insts[it.inst].b[cur[it.inst] & 1];
-    for (long long k = threadIdx.x; k < it.count; k += blockDim.x) facec_body<T, D>(g, bf, it.axis, it.start + k);
+    // the member's record read from the table (the ranges are whole blocks of
+    // about one face per thread: a copy of the record per thread costs more
+    // than the aliasing reloads it avoids)
+    const Inst<T>& in = insts[it.inst];
+    const int c = cur[it.inst] & 1;
+    for (long long k = threadIdx.x; k < it.count; k += blockDim.x) facec_body<T, D>(in.g, in.b[c], it.axis, it.start + k);
 }
 
 // W^{n+1} = W^n - dt sum_a (M_a(right face) - M_a(left face)) / dx_a (outward
@@ -2643,9 +2642,8 @@ __global__ void k_wupdate_batch(const RItem* __restrict__ items, const Inst<T>* 
     // block of the same member may read either value: the two records differ
     // only in the phi buffers, which the W update does not touch.
     const int c0 = cur[it.inst] & 1;
-    const Geo g = insts[it.inst].g;
-    const Bufs<T> bf = insts[it.inst].b[c0];
-    for (long long k = threadIdx.x; k < it.count; k += blockDim.x) wupdate_body<T, D>(g, bf, it.start + k);
+    const Inst<T>& in = insts[it.inst];
+    for (long long k = threadIdx.x; k < it.count; k += blockDim.x) wupdate_body<T, D>(in.g, in.b[c0], it.start + k);
     if (it.start == 0) {
         __syncthreads();
         if (threadIdx.x == 0) cur[it.inst] = c0 ^ 1;
