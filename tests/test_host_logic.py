@@ -189,3 +189,25 @@ def test_one_at_a_time_server_model():
     assert fifo["aggregate_point_updates_per_s"] == pytest.approx(1110 / 1.11)
     capped = bench.one_at_a_time(reqs, [10.0] * 3, 0.5, "fifo")
     assert capped["finished"] == 0 and capped["aggregate_point_updates_per_s"] == pytest.approx(1000.0)
+
+
+def test_default_choice_follows_the_measured_preferences():
+    """Without a cached tuning the launch shape is a face-store shape: in 3D FP32
+    the lean sweep A with the plain sweep B, in 1D / 2D FP32 a fused shape (no
+    lean), in FP64 2D the lean pair; grids with a node at xi = 0 take no lean
+    shape."""
+    modes3 = _modes(cdugks.FP32, 3)
+    modes2 = _modes(cdugks.FP32, 2)
+    modes2d = _modes(cdugks.FP64, 2)
+    cfg3, _ = wl.shear3d(n=16, nv=12, kn=1e-2)
+    t, g = tune.default_choice(cfg3, cdugks.FP32)
+    assert modes3[t] & 128 and not modes3[t] & 256 and g == 0
+    cfg2, _ = wl.kelvin_helmholtz(n=128, nv=16, kn=1e-3)
+    t2, _ = tune.default_choice(cfg2, cdugks.FP32)
+    assert modes2[t2] & 4 and not modes2[t2] & 128 and modes2[t2] & 3 == 0
+    t64, _ = tune.default_choice(cfg2, cdugks.FP64)
+    assert modes2d[t64] & 128
+    odd, _ = wl.kelvin_helmholtz(n=64, nv=15, kn=1e-3)       # 15 nodes on [-6, 6]: a node at 0
+    assert tune.has_zero_node(odd)
+    t0, _ = tune.default_choice(odd, cdugks.FP64)
+    assert not modes2d[t0] & 128
