@@ -496,7 +496,8 @@ def run_served(args, ws, rank, local, sub=False):
     serving.Server(budget_bytes=budget, device=dev).run(serving.stream_c5(count=2, t_end=0.002))
     torch.cuda.synchronize()
     srv = serving.Server(budget_bytes=budget, max_slots=64, max_round=64, device=dev, policy=args.policy,
-                         fill_points=args.fill_points, persistent=args.serve_launch == "persistent")
+                         fill_points=args.fill_points, persistent=args.serve_launch == "persistent",
+                         velocity_groups=args.serve_groups)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
@@ -860,6 +861,8 @@ def main():
                     help="served stream, srpt: points per step the shortest requests of a round fill")
     ap.add_argument("--serve-launch", choices=["persistent", "per-kernel"], default="per-kernel",
                     help="served stream: the persistent batched step (per-member step counts) or one launch per kernel")
+    ap.add_argument("--serve-groups", type=int, default=0,
+                    help="served stream: velocity groups of every request (0: the library's choice per request)")
     ap.add_argument("--skip-alone", action="store_true",
                     help="served stream: omit timing each request alone (the one-at-a-time models)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,

@@ -138,7 +138,8 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_slots: int = 64, max_round: int = 64, device: str = "cuda:0",
                  clock=time.perf_counter, persistent: bool = False, round_target_s: float = 0.025,
-                 max_items: int = 1 << 18, policy: str = "srpt", fill_points: float = 3e7):
+                 max_items: int = 1 << 18, policy: str = "srpt", fill_points: float = 3e7,
+                 velocity_groups: int = 0):
         if policy not in ("srpt", "share"):
             raise ValueError(f"unknown policy {policy}")
         self.budget = int(budget_bytes)
@@ -151,6 +152,7 @@ class Server:
         self.max_items = int(max_items)
         self.policy = policy
         self.fill_points = float(fill_points)
+        self.velocity_groups = int(velocity_groups)     # for requests that name none (0: the library's choice)
         self.waiting: list[Request] = []           # submitted, not yet prepared
         self.resident: list[Request] = []          # prepared (state on the device), not finished
         self.active: list[Request] = []            # batch members, in the batch's member order
@@ -191,6 +193,8 @@ class Server:
     def submit(self, req: Request):
         if not req.tile_id:
             req.tile_id = self._default_tile(req)
+        if not req.velocity_groups:
+            req.velocity_groups = self.velocity_groups
         req.footprint = footprint_bytes(req)
         if req.footprint > self.budget:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the budget {self.budget}")
